@@ -1,0 +1,119 @@
+"""Planted mistakes in the oracle (on the CPU) must each fail a pin.
+
+Each case monkeypatches one oracle function with a plausible error (a sign,
+a dropped term, a transposed operand, a wrong frame) and checks that the
+pin written for that part of the paper catches it."""
+import numpy as np
+import pytest
+
+import oracle.coarsening as CO
+import oracle.criteria as C
+import oracle.prolongation as PR
+import oracle.solve as S
+import oracle.topology as T
+from tests import test_oracle_criteria as tc
+from tests import test_oracle_prolongation as tp
+from tests import test_oracle_solve as ts
+from tests import test_oracle_topology as tt
+
+
+def _fails(fn, *a, **kw):
+    with pytest.raises((AssertionError, np.linalg.LinAlgError)):
+        fn(*a, **kw)
+
+
+def test_wrong_sign_in_half_transfer(monkeypatch):
+    monkeypatch.setattr(T, "Q_half", lambda xi, xj: T.Q(-0.5 * (np.asarray(xj) - np.asarray(xi))))
+    _fails(tt.test_aux_matrix_annihilates_rigid_modes, (5, 5))
+
+
+def test_transposed_skew(monkeypatch):
+    orig = T.skew
+    monkeypatch.setattr(T, "skew", lambda t: orig(t).T if len(t) == 3 else orig(t))
+    _fails(tt.test_skew_is_cross_product, 3)
+
+
+def test_dirichlet_edges_not_folded(monkeypatch):
+    orig = T.coarse_topology
+    monkeypatch.setattr(T, "coarse_topology",
+                        lambda topo, agg, n_c, xc, use_dirichlet=True: orig(topo, agg, n_c, xc, False))
+    monkeypatch.setattr(CO, "coarse_topology", T.coarse_topology)
+    _fails(tt.test_galerkin_of_aux_matrix_is_coarse_aux_matrix, (7, 6), True)
+
+
+def test_missing_l1_term(monkeypatch):
+    def no_l1(A):
+        n, k = A.n_rows, A.br
+        rows = np.repeat(np.arange(n), np.diff(A.rowptr))
+        diag = A.colidx == rows
+        Mv = np.zeros((n, k, k))
+        Mv[rows[diag]] = A.vals[diag]
+        return S.batched_pinv(Mv, S.KERNEL_RTOL)
+    monkeypatch.setattr(S, "block_l1_inverse", no_l1)
+    p = tt.make_problem((11, 10), seed=21)
+    H = ts.hierarchy.setup(p, ts.hierarchy.SetupParams(coarse_max=6, passes_first=2, passes_later=2))
+    _fails(_l1_check, H)
+
+
+def _l1_check(H):
+    class Req:
+        def getfixturevalue(self, name):
+            return (None, H)
+    ts.test_block_l1_smoother_dominates_A("h", Req())
+
+
+def test_transposed_galerkin_operand(monkeypatch):
+    orig = S.galerkin
+
+    def bad(P, A):
+        # P A P^T-style slip: each coarse block transposed
+        C = orig(P, A)
+        C.vals = np.ascontiguousarray(np.transpose(C.vals, (0, 2, 1)))
+        return C
+    p = tt.make_problem((11, 10), seed=21)
+    H = ts.hierarchy.setup(p, ts.hierarchy.SetupParams(coarse_max=6, passes_first=2, passes_later=2))
+    H.A = [H.A[0]] + [bad(P, A) for P, A in zip(H.P, H.A[:-1])]
+
+    class Req:
+        def getfixturevalue(self, name):
+            return (p, H)
+    _fails(ts.test_galerkin_pattern_and_values_brute_force, "h", Req())
+
+
+def test_skipped_post_smoother(monkeypatch):
+    def vc(H, b, level=0):
+        if level == H.n_levels - 1:
+            return S.coarse_solve(H, b)
+        x = S.smooth(H.A[level], H.Minv[level], b)
+        r = b - S.spmv(H.A[level], x)
+        ec = vc(H, S.spmv(H.R[level], r), level + 1)
+        return x + S.spmv(H.P[level], ec)
+    monkeypatch.setattr(S, "vcycle", vc)
+    p = tt.make_problem((11, 10), seed=21)
+    H = ts.hierarchy.setup(p, ts.hierarchy.SetupParams(coarse_max=6, passes_first=2, passes_later=2))
+
+    class Req:
+        def getfixturevalue(self, name):
+            return (p, H)
+    _fails(ts.test_vcycle_is_spd, "h", Req())
+
+
+def test_auxiliary_row_in_wrong_frame(monkeypatch):
+    orig_half = T.Q_half
+
+    def smoothed_wrong(A_rows, P_rows, topo, agg, D, rowmap, bad, first_level, pp=PR.ProlongParams()):
+        # diagonal of an auxiliary row transported with Q^{li} instead of Q^{il}
+        monkeypatch.setattr(PR, "Q_half", lambda xi, xj: orig_half(xj, xi))
+        try:
+            return orig_smoothed(A_rows, P_rows, topo, agg, D, rowmap, bad, first_level, pp)
+        finally:
+            monkeypatch.setattr(PR, "Q_half", orig_half)
+    orig_smoothed = PR.smoothed
+    monkeypatch.setattr(PR, "smoothed", smoothed_wrong)
+    _fails(tp.test_prolongations_reproduce_rigid_modes, (10, 9), False)
+
+
+def test_dropped_delta_term(monkeypatch):
+    orig = C.mu_p
+    monkeypatch.setattr(C, "mu_p", lambda topo, Dhat, nbrs, i, j, delta=1: orig(topo, Dhat, nbrs, i, j, 0))
+    _fails(tc.test_mu_p_equals_mu_g_on_coarse_neumann_level)

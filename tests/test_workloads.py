@@ -1,0 +1,77 @@
+"""Pins of the seeded input generator: P1 elasticity matrices are symmetric,
+annihilate the rigid-body modes (Neumann), are SPD after clamping, and the
+load vector integrates the body force."""
+import numpy as np
+import pytest
+import scipy.sparse as sp
+
+from workloads import configs, make_problem
+
+
+def _csr(B):
+    return sp.bsr_matrix((B.vals, B.colidx, B.rowptr),
+                         shape=(B.n_rows * B.br, B.n_cols * B.bc)).tocsr()
+
+
+def _rigid(x):
+    n, d = x.shape
+    if d == 2:
+        W = np.zeros((n, 2, 3))
+        W[:, 0, 0] = W[:, 1, 1] = 1
+        W[:, 0, 2], W[:, 1, 2] = -x[:, 1], x[:, 0]
+        return W.reshape(2 * n, 3)
+    W = np.zeros((n, 3, 6))
+    for a in range(3):
+        W[:, a, a] = 1
+        for b in range(3):
+            pass
+    for r in range(3):
+        e = np.zeros(3)
+        e[r] = 1
+        W[:, :, 3 + r] = np.cross(e, x)
+    return W.reshape(3 * n, 6)
+
+
+@pytest.mark.parametrize("shape", [(6, 5), (4, 5, 3)])
+def test_matrix_symmetric_rigid_spd(shape):
+    p = make_problem(shape, seed=3, nu_range=(0.25, 0.45), jump_boxes=3)
+    AN = _csr(p.A_full)
+    assert abs(AN - AN.T).max() == 0.0
+    W = _rigid(p.coords)
+    assert np.abs(AN @ W).max() <= 1e-13 * np.abs(AN).max()
+    A = _csr(p.A).toarray()
+    assert np.linalg.eigvalsh(A).min() > 0
+    assert np.all(np.diff(p.A.colidx[p.A.rowptr[0]:p.A.rowptr[1]]) > 0)
+
+
+def test_structured_sizes():
+    p = configs.square32()
+    assert (p.n_all, p.n_free, p.ndof) == (1089, 1056, 2112)
+    assert np.diff(p.A_full.rowptr).max() == 7
+    q = make_problem((6, 6, 6), seed=1)
+    assert np.diff(q.A_full.rowptr).max() == 15
+    assert q.n_free == 6 * 6 * 5
+
+
+def test_load_vector_integrates_force():
+    p = make_problem((7, 7), seed=4, forces=[[0.0, -1.0]], clamp=False)
+    # sum of f |T|/(d+1) over vertices = f * area of the unit square
+    assert abs(p.b[0].reshape(-1, 2)[:, 1].sum() + 1.0) < 1e-13
+
+
+def test_boundary_stays_on_box():
+    p = make_problem((5, 6, 4), seed=9)
+    idx = np.stack(np.meshgrid(*[np.arange(s) for s in (5, 6, 4)], indexing="ij"), -1)
+    idx = idx.reshape(-1, 3, order="F")
+    for a, s in enumerate((5, 6, 4)):
+        on = idx[:, a] == 0
+        assert np.all(p.coords[on, a] == 0.0)
+    X = p.coords[p.elements]
+    J = np.transpose(X[:, 1:, :] - X[:, :1, :], (0, 2, 1))
+    assert np.linalg.det(J).min() > 0
+
+
+def test_seeded_reproducible():
+    a = make_problem((5, 5), seed=12)
+    b = make_problem((5, 5), seed=12)
+    assert np.array_equal(a.A.vals, b.A.vals) and np.array_equal(a.coords, b.coords)
