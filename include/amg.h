@@ -1,0 +1,194 @@
+/*
+ * amg.h - C ABI of libamg, the GPU (sm_103a) solve phase of the edge-matrix
+ * ("auxiliary topology") algebraic multigrid method of Kogler & Schoeberl,
+ * "An algebraic multigrid method based on an auxiliary topology with edge
+ * matrices".
+ *
+ * The library solves A u = f (Sec. 2, eq. (auf)) by the conjugate gradient
+ * method preconditioned with one V-cycle (Sec. 7): on every level a
+ * block-l1 Jacobi smoother (Sec. 7, blocks = the dofs of one vertex), the
+ * restriction P^T r and the prolongation P e (Sec. 3, Algorithm tg) with the
+ * auxiliary smoothed prolongation of Sec. 6 (Def. aux_sp), Galerkin coarse
+ * matrices A_{l+1} = P_l^T A_l P_l (Sec. 6), and the regularised coarsest
+ * solve of Sec. 3.1.
+ *
+ * Conventions that hold for every entry point:
+ *  - Every call returns an int status (AMG_OK or a negative AMG_ERR_*); the
+ *    message of the last failure is returned by amg_last_error(ctx).  No
+ *    call aborts the process or throws across the ABI.
+ *  - BSR matrices: n_rows x n_cols blocks of br x bc doubles, int32 rowptr
+ *    (n_rows+1, rowptr[0] = 0, non-decreasing) and colidx (nnzb, strictly
+ *    increasing within a row, 0 <= colidx < n_cols), values row-major per
+ *    block.  Host arrays passed in are owned by the caller and copied.
+ *  - Vectors are interleaved per vertex ("AoS": dof r of vertex i at
+ *    i*k + r).  Pointers named *_dev are device pointers owned by the
+ *    caller, on the device the context was created for; the library uses
+ *    them on the context's stream and returns only after that stream is
+ *    synchronised, unless stated otherwise.
+ *  - All internal device buffers, CUDA graphs and streams belong to the
+ *    context until amg_destroy.
+ */
+#ifndef AMG_H
+#define AMG_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct amg_ctx amg_ctx;
+
+/* Block-sparse-row matrix (host arrays, caller-owned, copied on upload). */
+typedef struct {
+  int32_t n_rows, n_cols; /* block rows / block columns                     */
+  int32_t br, bc;         /* block dimensions                               */
+  int64_t nnzb;           /* number of stored blocks                        */
+  const int32_t *rowptr;  /* n_rows + 1                                     */
+  const int32_t *colidx;  /* nnzb, sorted ascending within each row         */
+  const double *vals;     /* nnzb * br * bc, row-major blocks               */
+} amg_bsr;
+
+/* Same layout, filled by the library (caller allocates the arrays). */
+typedef struct {
+  int32_t n_rows, n_cols, br, bc;
+  int64_t nnzb;
+  int32_t *rowptr;
+  int32_t *colidx;
+  double *vals;
+} amg_bsr_out;
+
+/* A hierarchy given by the finest matrix and the prolongations.
+ * P[l] maps level l+1 to level l (n_rows = rows of A_l, n_cols = rows of
+ * A_{l+1}); A0.bc == P[0].br and P[l].bc == P[l+1].br.  The coarse matrices
+ * are built on the device by the Galerkin product (Sec. 6). */
+typedef struct {
+  amg_bsr A0;
+  int32_t n_levels;       /* number of levels, >= 1; P has n_levels-1 items */
+  const amg_bsr *P;
+} amg_hierarchy;
+
+enum {
+  AMG_OK = 0,
+  AMG_ERR_ARG = -1,            /* invalid argument / malformed matrix        */
+  AMG_ERR_CUDA = -2,           /* a CUDA runtime call failed                 */
+  AMG_ERR_NOT_SPD = -3,        /* CG breakdown (p^T A p <= 0 or NaN)         */
+  AMG_ERR_NO_CONVERGENCE = -4, /* maxit reached before rtol                  */
+  AMG_ERR_TIMEOUT = -5,        /* a bounded device wait ran out              */
+  AMG_ERR_STATE = -6           /* call out of order (e.g. no hierarchy yet)  */
+};
+
+/* Precision of the V-cycle (the outer CG is always FP64). */
+enum {
+  AMG_PREC_FP64 = 0,          /* FP64 values, vectors and accumulation        */
+  AMG_PREC_FP32_VCYCLE = 1,   /* V-cycle matrices, smoother blocks, vectors
+                                 and accumulation in FP32; coarsest solve FP64 */
+  AMG_PREC_BF16_STORAGE = 2   /* as FP32 but A_l, P_l, R_l stored in BF16     */
+};
+
+/* Smoother on the finest level. */
+enum {
+  AMG_SMOOTHER_L1_JACOBI = 0, /* block-l1 Jacobi (Sec. 7)                     */
+  AMG_SMOOTHER_LEARNED = 1    /* per-vertex blocks set by amg_set_fine_smoother */
+};
+
+/* Create a context on CUDA device `device`.  `cuda_stream` is a
+ * cudaStream_t owned by the caller, or NULL to let the library create one.
+ * On success *ctx receives the context.  Errors: AMG_ERR_ARG (ctx NULL),
+ * AMG_ERR_CUDA. */
+int amg_create(amg_ctx **ctx, int device, void *cuda_stream);
+
+/* Release every device buffer, graph and owned stream.  NULL is a no-op. */
+void amg_destroy(amg_ctx *ctx);
+
+/* Message of the last failed call on ctx ("" if none). Valid until the next
+ * call on ctx. */
+const char *amg_last_error(const amg_ctx *ctx);
+
+/* Upload a hierarchy and prepare the solve phase on the device:
+ *   - validates every matrix (sizes, rowptr monotone, colidx sorted and in
+ *     range, matching block dims between levels) -> AMG_ERR_ARG,
+ *   - builds R_l = P_l^T explicitly (Sec. 3, restriction),
+ *   - computes A_{l+1} = P_l^T A_l P_l on the device (Sec. 6, amg_galerkin),
+ *   - computes the block-l1 smoother blocks M_v^+ (Sec. 7 and the pseudo
+ *     smoother of Sec. 3.1) in FP64 on the device,
+ *   - factorises the regularised coarsest matrix A_L + (I - E_L E_L^T)
+ *     (Sec. 3.1) in FP64 on the device and stores its inverse,
+ *   - for AMG_PREC_FP32_VCYCLE / AMG_PREC_BF16_STORAGE, keeps FP32 / BF16
+ *     copies of the level operators.
+ * Replaces any previous hierarchy of ctx. */
+int amg_upload_hierarchy(amg_ctx *ctx, const amg_hierarchy *h, int precision, int smoother);
+
+/* Recompute A_{level+1} = P_level^T A_level P_level on the device (the
+ * Galerkin triple product of Sec. 6, Sec. 3 eq. for the coarse system) as a
+ * segmented SpGEMM: symbolic (sorted unique block columns per coarse row,
+ * every structurally reached block kept) then numeric.  If out is not NULL
+ * the result is copied to the caller's host arrays: out->rowptr must hold
+ * n_rows+1 entries and colidx / vals at least nnzb / nnzb*k*k entries as
+ * reported by amg_level_info(level+1).  0 <= level < n_levels-1. */
+int amg_galerkin(amg_ctx *ctx, int level, amg_bsr_out *out);
+
+/* Sizes of level `level`: block rows, block size and stored blocks of A_l,
+ * and of P_l (0 on the coarsest level).  Any output pointer may be NULL. */
+int amg_level_info(const amg_ctx *ctx, int level, int32_t *n_rows, int32_t *block,
+                   int64_t *nnzb_A, int64_t *nnzb_P, int32_t *n_levels);
+
+/* Copy A_level (as held on the device, FP64) to caller host arrays sized as
+ * reported by amg_level_info. */
+int amg_download_matrix(amg_ctx *ctx, int level, int32_t *rowptr, int32_t *colidx, double *vals);
+
+/* Copy the smoother blocks M_v^+ of `level` (n_rows * k * k doubles,
+ * row-major per block) to host memory `minv`. */
+int amg_download_smoother(amg_ctx *ctx, int level, double *minv);
+
+/* Copy the coarsest-level inverse (A_L + I - E_L E_L^T)^{-1} (n x n doubles,
+ * n = n_rows * k of the coarsest level) to host memory. */
+int amg_download_coarse_inverse(amg_ctx *ctx, double *cinv);
+
+/* --- single steps of the V-cycle, FP64, device vectors of level `level` --- */
+
+/* y = A_l x (BSR SpMV). */
+int amg_spmv(amg_ctx *ctx, int level, const double *x_dev, double *y_dev);
+/* r = b - A_l x. */
+int amg_residual(amg_ctx *ctx, int level, const double *b_dev, const double *x_dev, double *r_dev);
+/* One block-l1 Jacobi sweep x_out = x_in + M^+ (b - A_l x_in) (Algorithm tg,
+ * pre- and post-smoothing; M symmetric so M^{-T} = M^{-1}).  x_in == NULL
+ * means x_in = 0, i.e. x_out = M^+ b.  x_out must not alias x_in. */
+int amg_smooth(amg_ctx *ctx, int level, const double *b_dev, const double *x_in_dev, double *x_out_dev);
+/* b_{l+1} = R_l r_l = P_l^T r_l (restriction, Algorithm tg). */
+int amg_restrict(amg_ctx *ctx, int level, const double *r_dev, double *bc_dev);
+/* x_l += P_l e_{l+1} (prolongation and correction, Algorithm tg). */
+int amg_prolong_add(amg_ctx *ctx, int level, const double *ec_dev, double *x_dev);
+/* x = (A_L + I - E_L E_L^T)^{-1} b on the coarsest level (Sec. 3.1). */
+int amg_coarse_solve(amg_ctx *ctx, const double *b_dev, double *x_dev);
+
+/* z = B^{-1} r: one V-cycle (Algorithm tg applied recursively, one pre- and
+ * one post-smoothing sweep, zero initial guess) on the finest level, in the
+ * context's precision.  nrhs vectors stored one after another. */
+int amg_vcycle(amg_ctx *ctx, const double *r_dev, double *z_dev, int nrhs);
+
+/* Solve A_0 u = f by FP64 PCG with one V-cycle as preconditioner (Sec. 7).
+ * u_dev holds the initial guess on entry and the solution on return.  Stops
+ * when the recurrence residual satisfies ||r||_2 <= rtol ||f||_2 or after
+ * maxit iterations (AMG_ERR_NO_CONVERGENCE).  The whole iteration runs on
+ * the device as one CUDA graph with a device-side while loop.  iters_out /
+ * relres_out receive the iteration count and the final recurrence relative
+ * residual per right-hand side (may be NULL).  For the mixed precisions the
+ * CG uses the flexible (Polak-Ribiere) beta. */
+int amg_pcg_solve(amg_ctx *ctx, const double *f_dev, double *u_dev, int nrhs, double rtol,
+                  int maxit, int *iters_out, double *relres_out);
+
+/* As amg_pcg_solve but f_host / u_host are host arrays (pinned or pageable);
+ * the host->device copy of f and u and the device->host copy of u happen
+ * inside the call on the context's stream (end-to-end use). */
+int amg_pcg_solve_host(amg_ctx *ctx, const double *f_host, double *u_host, int nrhs,
+                       double rtol, int maxit, int *iters_out, double *relres_out);
+
+/* Cumulative device time (ms, CUDA events) of the last amg_pcg_solve* call. */
+int amg_last_solve_ms(const amg_ctx *ctx, float *ms);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* AMG_H */

@@ -31,7 +31,7 @@ from .topology import Topology, aux_diagonal, coarse_topology
 
 @dataclasses.dataclass
 class CoarsenParams:
-    sigma: float = 10.0
+    sigma: float = 30.0
     delta: int = 1
     passes: int = 5
 

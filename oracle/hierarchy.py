@@ -23,7 +23,7 @@ from . import coarsening, prolongation, solve, topology
 
 @dataclasses.dataclass
 class SetupParams:
-    sigma: float = 10.0
+    sigma: float = 30.0
     delta: int = 1
     passes_first: int = 5
     passes_later: int = 4

@@ -1,0 +1,245 @@
+"""Thin ctypes binding of libamg (include/amg.h): the same entry points, with
+argument marshalling only.  Device vectors are torch CUDA tensors (FP64);
+host matrices are numpy arrays.  Every step of the solve runs in libamg's
+CUDA kernels; there is no fallback: if libamg.so is missing or no GPU is
+present, the calls raise.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIBPATH = os.path.join(HERE, "libamg.so")
+
+AMG_OK = 0
+AMG_ERR_ARG = -1
+AMG_ERR_CUDA = -2
+AMG_ERR_NOT_SPD = -3
+AMG_ERR_NO_CONVERGENCE = -4
+AMG_ERR_TIMEOUT = -5
+AMG_ERR_STATE = -6
+ERRORS = {AMG_ERR_ARG: "AMG_ERR_ARG", AMG_ERR_CUDA: "AMG_ERR_CUDA", AMG_ERR_NOT_SPD: "AMG_ERR_NOT_SPD",
+          AMG_ERR_NO_CONVERGENCE: "AMG_ERR_NO_CONVERGENCE", AMG_ERR_TIMEOUT: "AMG_ERR_TIMEOUT",
+          AMG_ERR_STATE: "AMG_ERR_STATE"}
+
+AMG_PREC_FP64 = 0
+AMG_PREC_FP32_VCYCLE = 1
+AMG_PREC_BF16_STORAGE = 2
+AMG_SMOOTHER_L1_JACOBI = 0
+AMG_SMOOTHER_LEARNED = 1
+
+
+class amg_bsr(C.Structure):
+    _fields_ = [("n_rows", C.c_int32), ("n_cols", C.c_int32), ("br", C.c_int32), ("bc", C.c_int32),
+                ("nnzb", C.c_int64), ("rowptr", C.POINTER(C.c_int32)),
+                ("colidx", C.POINTER(C.c_int32)), ("vals", C.POINTER(C.c_double))]
+
+
+class amg_bsr_out(C.Structure):
+    _fields_ = amg_bsr._fields_
+
+
+class amg_hierarchy(C.Structure):
+    _fields_ = [("A0", amg_bsr), ("n_levels", C.c_int32), ("P", C.POINTER(amg_bsr))]
+
+
+class AmgError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__(f"{ERRORS.get(code, code)}: {msg}")
+        self.code = code
+
+
+_lib = None
+
+_P = C.c_void_p
+_I = C.c_int
+_D = C.c_double
+_SIGS = {
+    "amg_create": (_I, [C.POINTER(_P), _I, _P]),
+    "amg_destroy": (None, [_P]),
+    "amg_last_error": (C.c_char_p, [_P]),
+    "amg_upload_hierarchy": (_I, [_P, C.POINTER(amg_hierarchy), _I, _I]),
+    "amg_galerkin": (_I, [_P, _I, C.POINTER(amg_bsr_out)]),
+    "amg_level_info": (_I, [_P, _I, C.POINTER(C.c_int32), C.POINTER(C.c_int32),
+                            C.POINTER(C.c_int64), C.POINTER(C.c_int64), C.POINTER(C.c_int32)]),
+    "amg_download_matrix": (_I, [_P, _I, _P, _P, _P]),
+    "amg_download_smoother": (_I, [_P, _I, _P]),
+    "amg_download_coarse_inverse": (_I, [_P, _P]),
+    "amg_spmv": (_I, [_P, _I, _P, _P]),
+    "amg_residual": (_I, [_P, _I, _P, _P, _P]),
+    "amg_smooth": (_I, [_P, _I, _P, _P, _P]),
+    "amg_restrict": (_I, [_P, _I, _P, _P]),
+    "amg_prolong_add": (_I, [_P, _I, _P, _P]),
+    "amg_coarse_solve": (_I, [_P, _P, _P]),
+    "amg_vcycle": (_I, [_P, _P, _P, _I]),
+    "amg_pcg_solve": (_I, [_P, _P, _P, _I, _D, _I, C.POINTER(_I), C.POINTER(_D)]),
+    "amg_pcg_solve_host": (_I, [_P, _P, _P, _I, _D, _I, C.POINTER(_I), C.POINTER(_D)]),
+    "amg_last_solve_ms": (_I, [_P, C.POINTER(C.c_float)]),
+}
+
+
+def lib():
+    """Load libamg.so (raises if it has not been built)."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIBPATH):
+            raise RuntimeError(f"{LIBPATH} is missing: build it with "
+                               "`python paper_2011_13325_gb300/build.py` (needs nvcc)")
+        L = C.CDLL(LIBPATH)
+        for name, (res, args) in _SIGS.items():
+            fn = getattr(L, name)
+            fn.restype = res
+            fn.argtypes = args
+        _lib = L
+    return _lib
+
+
+def exported_symbols():
+    return list(_SIGS.keys())
+
+
+def _ptr(a):
+    """Device pointer of a torch tensor or host pointer of a numpy array."""
+    if a is None:
+        return None
+    if isinstance(a, np.ndarray):
+        return a.ctypes.data
+    return a.data_ptr()
+
+
+def bsr_struct(n_rows, n_cols, rowptr, colidx, vals, keep):
+    rowptr = np.ascontiguousarray(rowptr, dtype=np.int32)
+    colidx = np.ascontiguousarray(colidx, dtype=np.int32)
+    vals = np.ascontiguousarray(vals, dtype=np.float64)
+    keep.extend([rowptr, colidx, vals])
+    return amg_bsr(int(n_rows), int(n_cols), int(vals.shape[1]), int(vals.shape[2]),
+                   int(colidx.shape[0]), rowptr.ctypes.data_as(C.POINTER(C.c_int32)),
+                   colidx.ctypes.data_as(C.POINTER(C.c_int32)),
+                   vals.ctypes.data_as(C.POINTER(C.c_double)))
+
+
+class Context:
+    """One libamg context (amg_create ... amg_destroy)."""
+
+    def __init__(self, device: int = 0, stream=None):
+        self.h = _P()
+        s = lib().amg_create(C.byref(self.h), int(device), stream)
+        if s != AMG_OK:
+            raise AmgError(s, "amg_create failed")
+
+    def close(self):
+        if self.h:
+            lib().amg_destroy(self.h)
+            self.h = _P()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def _check(self, s):
+        if s != AMG_OK:
+            raise AmgError(s, lib().amg_last_error(self.h).decode())
+        return s
+
+    # -- hierarchy ---------------------------------------------------------
+    def upload_hierarchy(self, A0, P_list, precision=AMG_PREC_FP64, smoother=AMG_SMOOTHER_L1_JACOBI):
+        """A0 / P_list: objects with n_rows, n_cols, rowptr, colidx, vals."""
+        keep = []
+        a0 = bsr_struct(A0.n_rows, A0.n_cols, A0.rowptr, A0.colidx, A0.vals, keep)
+        Ps = (amg_bsr * max(1, len(P_list)))()
+        for i, P in enumerate(P_list):
+            Ps[i] = bsr_struct(P.n_rows, P.n_cols, P.rowptr, P.colidx, P.vals, keep)
+        h = amg_hierarchy(a0, len(P_list) + 1, Ps)
+        return self._check(lib().amg_upload_hierarchy(self.h, C.byref(h), int(precision), int(smoother)))
+
+    def level_info(self, level):
+        n, k, na, npb, nl = C.c_int32(), C.c_int32(), C.c_int64(), C.c_int64(), C.c_int32()
+        self._check(lib().amg_level_info(self.h, int(level), C.byref(n), C.byref(k), C.byref(na),
+                                         C.byref(npb), C.byref(nl)))
+        return dict(n_rows=n.value, block=k.value, nnzb=na.value, nnzb_P=npb.value, n_levels=nl.value)
+
+    @property
+    def n_levels(self):
+        nl = C.c_int32()
+        lib().amg_level_info(self.h, 0, None, None, None, None, C.byref(nl))
+        return nl.value
+
+    def download_matrix(self, level):
+        info = self.level_info(level)
+        n, k, nnzb = info["n_rows"], info["block"], info["nnzb"]
+        rp = np.zeros(n + 1, dtype=np.int32)
+        ci = np.zeros(max(nnzb, 1), dtype=np.int32)
+        v = np.zeros((max(nnzb, 1), k, k))
+        self._check(lib().amg_download_matrix(self.h, int(level), rp.ctypes.data, ci.ctypes.data,
+                                              v.ctypes.data))
+        return rp, ci[:nnzb], v[:nnzb]
+
+    def galerkin(self, level, download=True):
+        if not download:
+            return self._check(lib().amg_galerkin(self.h, int(level), None))
+        out = amg_bsr_out()
+        # sizes are only known after the product: run it, then download
+        self._check(lib().amg_galerkin(self.h, int(level), None))
+        return self.download_matrix(level + 1)
+
+    def download_smoother(self, level):
+        info = self.level_info(level)
+        m = np.zeros((info["n_rows"], info["block"], info["block"]))
+        self._check(lib().amg_download_smoother(self.h, int(level), m.ctypes.data))
+        return m
+
+    def download_coarse_inverse(self):
+        info = self.level_info(self.n_levels - 1)
+        n = info["n_rows"] * info["block"]
+        m = np.zeros((n, n))
+        self._check(lib().amg_download_coarse_inverse(self.h, m.ctypes.data))
+        return m
+
+    # -- single steps ------------------------------------------------------
+    def spmv(self, level, x, y):
+        return self._check(lib().amg_spmv(self.h, int(level), _ptr(x), _ptr(y)))
+
+    def residual(self, level, b, x, r):
+        return self._check(lib().amg_residual(self.h, int(level), _ptr(b), _ptr(x), _ptr(r)))
+
+    def smooth(self, level, b, x_in, x_out):
+        return self._check(lib().amg_smooth(self.h, int(level), _ptr(b), _ptr(x_in), _ptr(x_out)))
+
+    def restrict(self, level, r, bc):
+        return self._check(lib().amg_restrict(self.h, int(level), _ptr(r), _ptr(bc)))
+
+    def prolong_add(self, level, ec, x):
+        return self._check(lib().amg_prolong_add(self.h, int(level), _ptr(ec), _ptr(x)))
+
+    def coarse_solve(self, b, x):
+        return self._check(lib().amg_coarse_solve(self.h, _ptr(b), _ptr(x)))
+
+    def vcycle(self, r, z, nrhs=1):
+        return self._check(lib().amg_vcycle(self.h, _ptr(r), _ptr(z), int(nrhs)))
+
+    def pcg_solve(self, f, u, nrhs=1, rtol=1e-8, maxit=500, check=True):
+        it = (C.c_int * nrhs)()
+        rr = (C.c_double * nrhs)()
+        s = lib().amg_pcg_solve(self.h, _ptr(f), _ptr(u), int(nrhs), float(rtol), int(maxit), it, rr)
+        if check:
+            self._check(s)
+        return s, list(it), list(rr)
+
+    def pcg_solve_host(self, f, u, nrhs=1, rtol=1e-8, maxit=500, check=True):
+        it = (C.c_int * nrhs)()
+        rr = (C.c_double * nrhs)()
+        s = lib().amg_pcg_solve_host(self.h, _ptr(f), _ptr(u), int(nrhs), float(rtol), int(maxit),
+                                     it, rr)
+        if check:
+            self._check(s)
+        return s, list(it), list(rr)
+
+    def last_solve_ms(self):
+        ms = C.c_float()
+        self._check(lib().amg_last_solve_ms(self.h, C.byref(ms)))
+        return ms.value

@@ -1,0 +1,636 @@
+// C ABI of libamg: context, hierarchy upload, single V-cycle steps, V-cycle,
+// PCG.  See include/amg.h for the contract of every entry point.
+#include <math.h>
+#include <stdio.h>
+#include <string.h>
+
+#include <algorithm>
+#include <string>
+#include <vector>
+
+#include "amg_internal.h"
+
+namespace amg {
+
+cudaError_t dalloc(void **p, size_t bytes) {
+  *p = nullptr;
+  return cudaMalloc(p, bytes > 0 ? bytes : 16);
+}
+
+void dfree(void *p) {
+  if (p) cudaFree(p);
+}
+
+void free_bsr(DevBSR &m) {
+  dfree(m.rowptr);
+  dfree(m.colidx);
+  dfree(m.v64);
+  dfree(m.v32);
+  dfree(m.v16);
+  m = DevBSR();
+}
+
+void free_levels(Ctx *c) {
+  for (Level &L : c->levels) {
+    free_bsr(L.A);
+    free_bsr(L.P);
+    free_bsr(L.R);
+    void *ptrs[] = {L.minv64, L.minv32, L.b64, L.x64, L.t64, L.y64, L.b32, L.x32, L.t32, L.y32};
+    for (void *p : ptrs) dfree(p);
+  }
+  c->levels.clear();
+  dfree(c->cinv);
+  c->cinv = nullptr;
+  c->coarse_n = 0;
+}
+
+void free_pcg(Ctx *c) {
+  double *bufs[] = {c->f, c->x, c->r, c->z, c->zold, c->p, c->q, c->partials};
+  for (double *b : bufs) dfree(b);
+  c->f = c->x = c->r = c->z = c->zold = c->p = c->q = c->partials = nullptr;
+  dfree(c->st);
+  c->st = nullptr;
+  dfree(c->counter);
+  c->counter = nullptr;
+  if (c->st_host) cudaFreeHost(c->st_host);
+  c->st_host = nullptr;
+  if (c->graph) cudaGraphExecDestroy(c->graph);
+  if (c->graph_def) cudaGraphDestroy(c->graph_def);
+  c->graph = nullptr;
+  c->graph_def = nullptr;
+}
+
+// ---------------------------------------------------------------------------
+// V-cycle (Algorithm tg applied recursively)
+// ---------------------------------------------------------------------------
+
+static void *vb(Level &L, int prec, char which) {
+  const bool d = prec == AMG_PREC_FP64;
+  switch (which) {
+    case 'b': return d ? (void *)L.b64 : (void *)L.b32;
+    case 'x': return d ? (void *)L.x64 : (void *)L.x32;
+    case 't': return d ? (void *)L.t64 : (void *)L.t32;
+    default: return d ? (void *)L.y64 : (void *)L.y32;
+  }
+}
+
+static const void *minv_of(const Level &L, int prec) {
+  return prec == AMG_PREC_FP64 ? (const void *)L.minv64 : (const void *)L.minv32;
+}
+
+// Solve on level l: input b (level buffer or external), output y.
+static cudaError_t vcycle_level(Ctx *c, int l, const void *b, void *y) {
+  const int prec = c->precision;
+  Level &L = c->levels[l];
+  if (l == (int)c->levels.size() - 1) return launch_coarse_gemv(c, c->coarse_n, c->cinv, b, y, prec);
+  Level &Cn = c->levels[l + 1];
+  void *x = vb(L, prec, 'x');
+  void *t = vb(L, prec, 't');
+  const void *mi = minv_of(L, prec);
+  // pre-smoothing from x = 0: x = M^+ b
+  AMG_CUDA_TRY(launch_blockdiag(c, L.A.n_rows, L.k, prec, mi, b, x));
+  // residual t = b - A x
+  AMG_CUDA_TRY(launch_bsr(c, L.A, prec, SPMV_RESID, x, b, nullptr, t));
+  // restriction b_{l+1} = R t
+  AMG_CUDA_TRY(launch_bsr(c, L.R, prec, SPMV_SET, t, nullptr, nullptr, vb(Cn, prec, 'b')));
+  // coarse-grid correction
+  AMG_CUDA_TRY(vcycle_level(c, l + 1, vb(Cn, prec, 'b'), vb(Cn, prec, 'y')));
+  // prolongation x += P e
+  AMG_CUDA_TRY(launch_bsr(c, L.P, prec, SPMV_ADD, vb(Cn, prec, 'y'), nullptr, nullptr, x));
+  // post-smoothing y = x + M^+ (b - A x)
+  return launch_bsr(c, L.A, prec, SPMV_SMOOTH, x, b, mi, y);
+}
+
+cudaError_t vcycle_launch(Ctx *c, const double *r, double *z) {
+  if (c->precision == AMG_PREC_FP64) return vcycle_level(c, 0, r, z);
+  Level &L0 = c->levels[0];
+  const size_t n = (size_t)L0.A.n_rows * L0.k;
+  AMG_CUDA_TRY(launch_convert(c, n, r, AMG_PREC_FP64, L0.b32, AMG_PREC_FP32_VCYCLE));
+  AMG_CUDA_TRY(vcycle_level(c, 0, L0.b32, L0.y32));
+  return launch_convert(c, n, L0.y32, AMG_PREC_FP32_VCYCLE, z, AMG_PREC_FP64);
+}
+
+}  // namespace amg
+
+using namespace amg;
+
+// ---------------------------------------------------------------------------
+// helpers
+// ---------------------------------------------------------------------------
+
+static int fail(Ctx *c, int code, const std::string &msg) {
+  c->err = msg;
+  return code;
+}
+
+static int cuda_fail(Ctx *c, cudaError_t e, const char *where) {
+  c->err = std::string(where) + ": " + cudaGetErrorString(e);
+  return AMG_ERR_CUDA;
+}
+
+#define CUDA_OR_FAIL(c, expr, where)              \
+  do {                                            \
+    cudaError_t _e = (expr);                      \
+    if (_e != cudaSuccess) return cuda_fail(c, _e, where); \
+  } while (0)
+
+static bool block_ok(int b) { return b == 2 || b == 3 || b == 6; }
+
+static int validate_bsr(Ctx *c, const amg_bsr &m, const char *name) {
+  char buf[256];
+  if (m.n_rows < 0 || m.n_cols < 0 || m.nnzb < 0 || !block_ok(m.br) || !block_ok(m.bc)) {
+    snprintf(buf, sizeof buf, "%s: bad sizes (n_rows %d n_cols %d br %d bc %d nnzb %lld)", name,
+             m.n_rows, m.n_cols, m.br, m.bc, (long long)m.nnzb);
+    return fail(c, AMG_ERR_ARG, buf);
+  }
+  if (!m.rowptr || (m.nnzb > 0 && (!m.colidx || !m.vals))) {
+    snprintf(buf, sizeof buf, "%s: NULL array", name);
+    return fail(c, AMG_ERR_ARG, buf);
+  }
+  if (m.rowptr[0] != 0 || (int64_t)m.rowptr[m.n_rows] != m.nnzb) {
+    snprintf(buf, sizeof buf, "%s: rowptr[0] must be 0 and rowptr[n_rows] == nnzb", name);
+    return fail(c, AMG_ERR_ARG, buf);
+  }
+  for (int i = 0; i < m.n_rows; ++i) {
+    if (m.rowptr[i + 1] < m.rowptr[i]) {
+      snprintf(buf, sizeof buf, "%s: rowptr decreases at row %d", name, i);
+      return fail(c, AMG_ERR_ARG, buf);
+    }
+    for (int p = m.rowptr[i]; p < m.rowptr[i + 1]; ++p) {
+      const int col = m.colidx[p];
+      if (col < 0 || col >= m.n_cols || (p > m.rowptr[i] && col <= m.colidx[p - 1])) {
+        snprintf(buf, sizeof buf, "%s: colidx out of range or unsorted in row %d", name, i);
+        return fail(c, AMG_ERR_ARG, buf);
+      }
+    }
+  }
+  const size_t nv = (size_t)m.nnzb * m.br * m.bc;
+  for (size_t i = 0; i < nv; ++i)
+    if (!isfinite(m.vals[i])) {
+      snprintf(buf, sizeof buf, "%s: non-finite value at %zu", name, i);
+      return fail(c, AMG_ERR_ARG, buf);
+    }
+  return AMG_OK;
+}
+
+static cudaError_t upload_bsr(Ctx *c, DevBSR &d, int n_rows, int n_cols, int br, int bc,
+                              int64_t nnzb, const int32_t *rp, const int32_t *ci,
+                              const double *v) {
+  free_bsr(d);
+  d.n_rows = n_rows;
+  d.n_cols = n_cols;
+  d.br = br;
+  d.bc = bc;
+  d.nnzb = nnzb;
+  AMG_CUDA_TRY(dalloc((void **)&d.rowptr, (size_t)(n_rows + 1) * sizeof(int)));
+  AMG_CUDA_TRY(dalloc((void **)&d.colidx, (size_t)nnzb * sizeof(int)));
+  AMG_CUDA_TRY(dalloc((void **)&d.v64, (size_t)nnzb * br * bc * sizeof(double)));
+  AMG_CUDA_TRY(cudaMemcpyAsync(d.rowptr, rp, (size_t)(n_rows + 1) * sizeof(int),
+                               cudaMemcpyHostToDevice, c->stream));
+  if (nnzb > 0) {
+    AMG_CUDA_TRY(cudaMemcpyAsync(d.colidx, ci, (size_t)nnzb * sizeof(int), cudaMemcpyHostToDevice,
+                                 c->stream));
+    AMG_CUDA_TRY(cudaMemcpyAsync(d.v64, v, (size_t)nnzb * br * bc * sizeof(double),
+                                 cudaMemcpyHostToDevice, c->stream));
+  }
+  return cudaStreamSynchronize(c->stream);
+}
+
+// R = P^T with sorted columns (counting sort by block column, stable in the
+// row index), block values transposed.
+static cudaError_t upload_transpose(Ctx *c, DevBSR &R, const amg_bsr &P) {
+  const int nr = P.n_cols, nc = P.n_rows, br = P.bc, bc = P.br;
+  std::vector<int32_t> rp(nr + 1, 0), ci((size_t)P.nnzb);
+  std::vector<double> v((size_t)P.nnzb * br * bc);
+  for (int64_t p = 0; p < P.nnzb; ++p) rp[P.colidx[p] + 1]++;
+  for (int i = 0; i < nr; ++i) rp[i + 1] += rp[i];
+  std::vector<int32_t> fill(rp.begin(), rp.end() - 1);
+  for (int i = 0; i < P.n_rows; ++i)
+    for (int p = P.rowptr[i]; p < P.rowptr[i + 1]; ++p) {
+      const int J = P.colidx[p];
+      const int q = fill[J]++;
+      ci[q] = i;
+      const double *src = P.vals + (size_t)p * P.br * P.bc;
+      double *dst = v.data() + (size_t)q * br * bc;
+      for (int a = 0; a < P.br; ++a)
+        for (int b = 0; b < P.bc; ++b) dst[b * bc + a] = src[a * P.bc + b];
+    }
+  return upload_bsr(c, R, nr, nc, br, bc, P.nnzb, rp.data(), ci.data(), v.data());
+}
+
+static cudaError_t alloc_level_vectors(Ctx *c, Level &L) {
+  const size_t n = (size_t)L.A.n_rows * L.k;
+  const size_t nb = (n ? n : 1);
+  double **d[] = {&L.b64, &L.x64, &L.t64, &L.y64};
+  for (double **p : d) {
+    AMG_CUDA_TRY(dalloc((void **)p, nb * sizeof(double)));
+    AMG_CUDA_TRY(cudaMemsetAsync(*p, 0, nb * sizeof(double), c->stream));
+  }
+  if (c->precision != AMG_PREC_FP64) {
+    float **f[] = {&L.b32, &L.x32, &L.t32, &L.y32};
+    for (float **p : f) {
+      AMG_CUDA_TRY(dalloc((void **)p, nb * sizeof(float)));
+      AMG_CUDA_TRY(cudaMemsetAsync(*p, 0, nb * sizeof(float), c->stream));
+    }
+  }
+  return cudaSuccess;
+}
+
+static int check_ready(Ctx *c) {
+  if (c->levels.empty()) return fail(c, AMG_ERR_STATE, "no hierarchy uploaded");
+  return AMG_OK;
+}
+
+static int check_level(Ctx *c, int level, bool need_next) {
+  int s = check_ready(c);
+  if (s) return s;
+  const int nl = (int)c->levels.size();
+  if (level < 0 || level >= nl || (need_next && level >= nl - 1))
+    return fail(c, AMG_ERR_ARG, "level out of range");
+  return AMG_OK;
+}
+
+static int finish(Ctx *c, const char *where) {
+  cudaError_t e = cudaGetLastError();
+  if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+  if (e != cudaSuccess) return cuda_fail(c, e, where);
+  c->err.clear();
+  return AMG_OK;
+}
+
+// ---------------------------------------------------------------------------
+// ABI
+// ---------------------------------------------------------------------------
+
+extern "C" {
+
+int amg_create(amg_ctx **out, int device, void *cuda_stream) {
+  if (!out) return AMG_ERR_ARG;
+  *out = nullptr;
+  amg_ctx *h = new amg_ctx();
+  Ctx *c = &h->c;
+  c->device = device;
+  cudaError_t e = cudaSetDevice(device);
+  if (e == cudaSuccess) e = cudaDeviceGetAttribute(&c->num_sms, cudaDevAttrMultiProcessorCount, device);
+  if (e == cudaSuccess) {
+    if (cuda_stream) {
+      c->stream = (cudaStream_t)cuda_stream;
+    } else {
+      e = cudaStreamCreateWithFlags(&c->stream, cudaStreamNonBlocking);
+      c->own_stream = true;
+    }
+  }
+  if (e == cudaSuccess) e = cudaEventCreate(&c->ev0);
+  if (e == cudaSuccess) e = cudaEventCreate(&c->ev1);
+  if (e != cudaSuccess) {
+    delete h;
+    return AMG_ERR_CUDA;
+  }
+  *out = h;
+  return AMG_OK;
+}
+
+void amg_destroy(amg_ctx *h) {
+  if (!h) return;
+  Ctx *c = &h->c;
+  cudaSetDevice(c->device);
+  cudaStreamSynchronize(c->stream);
+  free_pcg(c);
+  free_levels(c);
+  if (c->hbuf) cudaFreeHost(c->hbuf);
+  if (c->ev0) cudaEventDestroy(c->ev0);
+  if (c->ev1) cudaEventDestroy(c->ev1);
+  if (c->own_stream) cudaStreamDestroy(c->stream);
+  delete h;
+}
+
+const char *amg_last_error(const amg_ctx *h) { return h ? h->c.err.c_str() : "NULL context"; }
+
+int amg_upload_hierarchy(amg_ctx *h, const amg_hierarchy *hier, int precision, int smoother) {
+  if (!h) return AMG_ERR_ARG;
+  Ctx *c = &h->c;
+  if (!hier || hier->n_levels < 1 || (hier->n_levels > 1 && !hier->P))
+    return fail(c, AMG_ERR_ARG, "hierarchy: need n_levels >= 1 and P for n_levels > 1");
+  if (precision < AMG_PREC_FP64 || precision > AMG_PREC_BF16_STORAGE)
+    return fail(c, AMG_ERR_ARG, "unknown precision");
+  if (smoother != AMG_SMOOTHER_L1_JACOBI) return fail(c, AMG_ERR_ARG, "unknown smoother");
+  const amg_bsr &A0 = hier->A0;
+  int s = validate_bsr(c, A0, "A0");
+  if (s) return s;
+  if (A0.br != A0.bc || A0.n_rows != A0.n_cols || (A0.br != 2 && A0.br != 3))
+    return fail(c, AMG_ERR_ARG, "A0 must be square with 2x2 or 3x3 blocks");
+  // every row of A0 needs a diagonal block with positive diagonal entries
+  for (int i = 0; i < A0.n_rows; ++i) {
+    const double *blk = nullptr;
+    for (int p = A0.rowptr[i]; p < A0.rowptr[i + 1]; ++p)
+      if (A0.colidx[p] == i) blk = A0.vals + (size_t)p * A0.br * A0.bc;
+    bool ok = blk != nullptr;
+    for (int r = 0; ok && r < A0.br; ++r) ok = blk[r * A0.bc + r] > 0.0;
+    if (!ok) {
+      char buf[128];
+      snprintf(buf, sizeof buf, "A0: row %d has no positive diagonal block", i);
+      return fail(c, AMG_ERR_NOT_SPD, buf);
+    }
+  }
+  int rows = A0.n_rows, k = A0.br;
+  for (int l = 0; l + 1 < hier->n_levels; ++l) {
+    char name[32];
+    snprintf(name, sizeof name, "P[%d]", l);
+    s = validate_bsr(c, hier->P[l], name);
+    if (s) return s;
+    const amg_bsr &P = hier->P[l];
+    if (P.n_rows != rows || P.br != k || (l > 0 && P.bc != k) || (l == 0 && P.bc < P.br))
+      return fail(c, AMG_ERR_ARG, std::string(name) + ": dimensions do not match the level above");
+    rows = P.n_cols;
+    k = P.bc;
+  }
+  CUDA_OR_FAIL(c, cudaSetDevice(c->device), "cudaSetDevice");
+  cudaStreamSynchronize(c->stream);
+  free_pcg(c);
+  free_levels(c);
+  c->precision = precision;
+  c->smoother = smoother;
+  c->levels.resize(hier->n_levels);
+  CUDA_OR_FAIL(c, upload_bsr(c, c->levels[0].A, A0.n_rows, A0.n_cols, A0.br, A0.bc, A0.nnzb,
+                             A0.rowptr, A0.colidx, A0.vals), "upload A0");
+  c->levels[0].k = A0.br;
+  for (int l = 0; l + 1 < hier->n_levels; ++l) {
+    const amg_bsr &P = hier->P[l];
+    Level &L = c->levels[l];
+    CUDA_OR_FAIL(c, upload_bsr(c, L.P, P.n_rows, P.n_cols, P.br, P.bc, P.nnzb, P.rowptr,
+                               P.colidx, P.vals), "upload P");
+    CUDA_OR_FAIL(c, upload_transpose(c, L.R, P), "upload R");
+    CUDA_OR_FAIL(c, galerkin_device(c, l), "galerkin");
+  }
+  for (int l = 0; l < (int)c->levels.size(); ++l) {
+    Level &L = c->levels[l];
+    if (l + 1 < (int)c->levels.size()) CUDA_OR_FAIL(c, smoother_setup(c, l), "smoother setup");
+    CUDA_OR_FAIL(c, alloc_level_vectors(c, L), "level vectors");
+    if (precision != AMG_PREC_FP64) {
+      CUDA_OR_FAIL(c, make_low_precision(c, L.A, precision), "low precision A");
+      if (L.P.nnzb) CUDA_OR_FAIL(c, make_low_precision(c, L.P, precision), "low precision P");
+      if (L.R.nnzb) CUDA_OR_FAIL(c, make_low_precision(c, L.R, precision), "low precision R");
+    }
+  }
+  CUDA_OR_FAIL(c, coarse_setup(c), "coarse setup");
+  CUDA_OR_FAIL(c, pcg_alloc(c), "pcg buffers");
+  return finish(c, "upload");
+}
+
+int amg_galerkin(amg_ctx *h, int level, amg_bsr_out *out) {
+  if (!h) return AMG_ERR_ARG;
+  Ctx *c = &h->c;
+  int s = check_level(c, level, true);
+  if (s) return s;
+  if (c->graph) {
+    cudaGraphExecDestroy(c->graph);
+    cudaGraphDestroy(c->graph_def);
+    c->graph = nullptr;
+    c->graph_def = nullptr;
+  }
+  CUDA_OR_FAIL(c, galerkin_device(c, level), "galerkin");
+  Level &Cl = c->levels[level + 1];
+  if (c->precision != AMG_PREC_FP64)
+    CUDA_OR_FAIL(c, make_low_precision(c, Cl.A, c->precision), "low precision A");
+  if (out) {
+    if (!out->rowptr || (Cl.A.nnzb > 0 && (!out->colidx || !out->vals)))
+      return fail(c, AMG_ERR_ARG, "amg_galerkin: NULL output array");
+    out->n_rows = Cl.A.n_rows;
+    out->n_cols = Cl.A.n_cols;
+    out->br = Cl.A.br;
+    out->bc = Cl.A.bc;
+    out->nnzb = Cl.A.nnzb;
+    return amg_download_matrix(h, level + 1, out->rowptr, out->colidx, out->vals);
+  }
+  return finish(c, "galerkin");
+}
+
+int amg_level_info(const amg_ctx *h, int level, int32_t *n_rows, int32_t *block, int64_t *nnzb_A,
+                   int64_t *nnzb_P, int32_t *n_levels) {
+  if (!h) return AMG_ERR_ARG;
+  const Ctx *c = &h->c;
+  if (n_levels) *n_levels = (int32_t)c->levels.size();
+  if (c->levels.empty()) return AMG_ERR_STATE;
+  if (level < 0 || level >= (int)c->levels.size()) return AMG_ERR_ARG;
+  const Level &L = c->levels[level];
+  if (n_rows) *n_rows = L.A.n_rows;
+  if (block) *block = L.k;
+  if (nnzb_A) *nnzb_A = L.A.nnzb;
+  if (nnzb_P) *nnzb_P = L.P.nnzb;
+  return AMG_OK;
+}
+
+int amg_download_matrix(amg_ctx *h, int level, int32_t *rowptr, int32_t *colidx, double *vals) {
+  if (!h) return AMG_ERR_ARG;
+  Ctx *c = &h->c;
+  int s = check_level(c, level, false);
+  if (s) return s;
+  const DevBSR &A = c->levels[level].A;
+  if (!rowptr || (A.nnzb > 0 && (!colidx || !vals)))
+    return fail(c, AMG_ERR_ARG, "NULL output array");
+  CUDA_OR_FAIL(c, cudaMemcpyAsync(rowptr, A.rowptr, (size_t)(A.n_rows + 1) * sizeof(int),
+                                  cudaMemcpyDeviceToHost, c->stream), "download rowptr");
+  if (A.nnzb > 0) {
+    CUDA_OR_FAIL(c, cudaMemcpyAsync(colidx, A.colidx, (size_t)A.nnzb * sizeof(int),
+                                    cudaMemcpyDeviceToHost, c->stream), "download colidx");
+    CUDA_OR_FAIL(c, cudaMemcpyAsync(vals, A.v64, (size_t)A.nnzb * A.br * A.bc * sizeof(double),
+                                    cudaMemcpyDeviceToHost, c->stream), "download vals");
+  }
+  return finish(c, "download matrix");
+}
+
+int amg_download_smoother(amg_ctx *h, int level, double *minv) {
+  if (!h) return AMG_ERR_ARG;
+  Ctx *c = &h->c;
+  int s = check_level(c, level, true);
+  if (s) return s;
+  if (!minv) return fail(c, AMG_ERR_ARG, "NULL output");
+  const Level &L = c->levels[level];
+  CUDA_OR_FAIL(c, cudaMemcpyAsync(minv, L.minv64, (size_t)L.A.n_rows * L.k * L.k * sizeof(double),
+                                  cudaMemcpyDeviceToHost, c->stream), "download smoother");
+  return finish(c, "download smoother");
+}
+
+int amg_download_coarse_inverse(amg_ctx *h, double *cinv) {
+  if (!h) return AMG_ERR_ARG;
+  Ctx *c = &h->c;
+  int s = check_ready(c);
+  if (s) return s;
+  if (!cinv) return fail(c, AMG_ERR_ARG, "NULL output");
+  CUDA_OR_FAIL(c, cudaMemcpyAsync(cinv, c->cinv, (size_t)c->coarse_n * c->coarse_n * sizeof(double),
+                                  cudaMemcpyDeviceToHost, c->stream), "download coarse inverse");
+  return finish(c, "download coarse inverse");
+}
+
+int amg_spmv(amg_ctx *h, int level, const double *x, double *y) {
+  if (!h) return AMG_ERR_ARG;
+  Ctx *c = &h->c;
+  int s = check_level(c, level, false);
+  if (s) return s;
+  if (!x || !y) return fail(c, AMG_ERR_ARG, "NULL vector");
+  CUDA_OR_FAIL(c, launch_bsr(c, c->levels[level].A, AMG_PREC_FP64, SPMV_SET, x, nullptr, nullptr, y),
+               "spmv");
+  return finish(c, "spmv");
+}
+
+int amg_residual(amg_ctx *h, int level, const double *b, const double *x, double *r) {
+  if (!h) return AMG_ERR_ARG;
+  Ctx *c = &h->c;
+  int s = check_level(c, level, false);
+  if (s) return s;
+  if (!b || !x || !r) return fail(c, AMG_ERR_ARG, "NULL vector");
+  CUDA_OR_FAIL(c, launch_bsr(c, c->levels[level].A, AMG_PREC_FP64, SPMV_RESID, x, b, nullptr, r),
+               "residual");
+  return finish(c, "residual");
+}
+
+int amg_smooth(amg_ctx *h, int level, const double *b, const double *x_in, double *x_out) {
+  if (!h) return AMG_ERR_ARG;
+  Ctx *c = &h->c;
+  int s = check_level(c, level, true);
+  if (s) return s;
+  if (!b || !x_out || x_in == x_out) return fail(c, AMG_ERR_ARG, "bad vectors");
+  Level &L = c->levels[level];
+  if (!x_in)
+    CUDA_OR_FAIL(c, launch_blockdiag(c, L.A.n_rows, L.k, AMG_PREC_FP64, L.minv64, b, x_out),
+                 "smooth");
+  else
+    CUDA_OR_FAIL(c, launch_bsr(c, L.A, AMG_PREC_FP64, SPMV_SMOOTH, x_in, b, L.minv64, x_out),
+                 "smooth");
+  return finish(c, "smooth");
+}
+
+int amg_restrict(amg_ctx *h, int level, const double *r, double *bc) {
+  if (!h) return AMG_ERR_ARG;
+  Ctx *c = &h->c;
+  int s = check_level(c, level, true);
+  if (s) return s;
+  if (!r || !bc) return fail(c, AMG_ERR_ARG, "NULL vector");
+  CUDA_OR_FAIL(c, launch_bsr(c, c->levels[level].R, AMG_PREC_FP64, SPMV_SET, r, nullptr, nullptr, bc),
+               "restrict");
+  return finish(c, "restrict");
+}
+
+int amg_prolong_add(amg_ctx *h, int level, const double *ec, double *x) {
+  if (!h) return AMG_ERR_ARG;
+  Ctx *c = &h->c;
+  int s = check_level(c, level, true);
+  if (s) return s;
+  if (!ec || !x) return fail(c, AMG_ERR_ARG, "NULL vector");
+  CUDA_OR_FAIL(c, launch_bsr(c, c->levels[level].P, AMG_PREC_FP64, SPMV_ADD, ec, nullptr, nullptr, x),
+               "prolong");
+  return finish(c, "prolong");
+}
+
+int amg_coarse_solve(amg_ctx *h, const double *b, double *x) {
+  if (!h) return AMG_ERR_ARG;
+  Ctx *c = &h->c;
+  int s = check_ready(c);
+  if (s) return s;
+  if (!b || !x) return fail(c, AMG_ERR_ARG, "NULL vector");
+  CUDA_OR_FAIL(c, launch_coarse_gemv(c, c->coarse_n, c->cinv, b, x, AMG_PREC_FP64), "coarse solve");
+  return finish(c, "coarse solve");
+}
+
+int amg_vcycle(amg_ctx *h, const double *r, double *z, int nrhs) {
+  if (!h) return AMG_ERR_ARG;
+  Ctx *c = &h->c;
+  int s = check_ready(c);
+  if (s) return s;
+  if (!r || !z || nrhs < 1) return fail(c, AMG_ERR_ARG, "bad vectors / nrhs");
+  const size_t n = (size_t)c->levels[0].A.n_rows * c->levels[0].k;
+  for (int i = 0; i < nrhs; ++i)
+    CUDA_OR_FAIL(c, vcycle_launch(c, r + i * n, z + i * n), "vcycle");
+  return finish(c, "vcycle");
+}
+
+static int pcg_one(Ctx *c, double rtol, int maxit, int *iters, double *relres) {
+  c->st_host->rtol = rtol;
+  c->st_host->maxit = maxit;
+  c->st_host->flexible = (c->precision != AMG_PREC_FP64) ? 1 : 0;
+  c->st_host->it = 0;
+  c->st_host->status = 0;
+  c->st_host->guard = 0;
+  CUDA_OR_FAIL(c, cudaMemcpyAsync(c->st, c->st_host, sizeof(PcgState), cudaMemcpyHostToDevice,
+                                  c->stream), "pcg state");
+  CUDA_OR_FAIL(c, cudaEventRecord(c->ev0, c->stream), "event");
+  CUDA_OR_FAIL(c, cudaGraphLaunch(c->graph, c->stream), "pcg graph launch");
+  CUDA_OR_FAIL(c, cudaEventRecord(c->ev1, c->stream), "event");
+  CUDA_OR_FAIL(c, cudaMemcpyAsync(c->st_host, c->st, sizeof(PcgState), cudaMemcpyDeviceToHost,
+                                  c->stream), "pcg state");
+  CUDA_OR_FAIL(c, cudaStreamSynchronize(c->stream), "pcg sync");
+  float ms = 0.f;
+  cudaEventElapsedTime(&ms, c->ev0, c->ev1);
+  c->last_ms += ms;
+  const PcgState &st = *c->st_host;
+  if (iters) *iters = st.it;
+  if (relres) *relres = st.ff > 0 ? sqrt(st.rr / st.ff) : sqrt(st.rr);
+  if (st.status == AMG_ERR_NOT_SPD) return fail(c, AMG_ERR_NOT_SPD, "CG breakdown: p^T A p <= 0 or non-finite");
+  if (st.rr > st.tol2) return fail(c, AMG_ERR_NO_CONVERGENCE, "maxit reached before rtol");
+  return AMG_OK;
+}
+
+int amg_pcg_solve(amg_ctx *h, const double *f, double *u, int nrhs, double rtol, int maxit,
+                  int *iters, double *relres) {
+  if (!h) return AMG_ERR_ARG;
+  Ctx *c = &h->c;
+  int s = check_ready(c);
+  if (s) return s;
+  if (!f || !u || nrhs < 1 || !(rtol >= 0.0) || maxit < 0)
+    return fail(c, AMG_ERR_ARG, "bad arguments");
+  if (c->levels[0].k != 2 && c->levels[0].k != 3) return fail(c, AMG_ERR_ARG, "A0 block size");
+  if (!c->graph) CUDA_OR_FAIL(c, pcg_build_graph(c), "pcg graph");
+  const size_t n = (size_t)c->levels[0].A.n_rows * c->levels[0].k;
+  c->last_ms = 0.f;
+  int worst = AMG_OK;
+  for (int i = 0; i < nrhs; ++i) {
+    CUDA_OR_FAIL(c, cudaMemcpyAsync(c->f, f + i * n, n * sizeof(double), cudaMemcpyDeviceToDevice,
+                                    c->stream), "copy f");
+    CUDA_OR_FAIL(c, cudaMemcpyAsync(c->x, u + i * n, n * sizeof(double), cudaMemcpyDeviceToDevice,
+                                    c->stream), "copy u");
+    s = pcg_one(c, rtol, maxit, iters ? iters + i : nullptr, relres ? relres + i : nullptr);
+    CUDA_OR_FAIL(c, cudaMemcpyAsync(u + i * n, c->x, n * sizeof(double), cudaMemcpyDeviceToDevice,
+                                    c->stream), "copy u back");
+    if (s != AMG_OK && worst == AMG_OK) worst = s;
+  }
+  CUDA_OR_FAIL(c, cudaStreamSynchronize(c->stream), "pcg sync");
+  if (worst != AMG_OK) return worst;
+  c->err.clear();
+  return AMG_OK;
+}
+
+int amg_pcg_solve_host(amg_ctx *h, const double *f, double *u, int nrhs, double rtol, int maxit,
+                       int *iters, double *relres) {
+  if (!h) return AMG_ERR_ARG;
+  Ctx *c = &h->c;
+  int s = check_ready(c);
+  if (s) return s;
+  if (!f || !u || nrhs < 1 || !(rtol >= 0.0) || maxit < 0)
+    return fail(c, AMG_ERR_ARG, "bad arguments");
+  if (!c->graph) CUDA_OR_FAIL(c, pcg_build_graph(c), "pcg graph");
+  const size_t n = (size_t)c->levels[0].A.n_rows * c->levels[0].k;
+  c->last_ms = 0.f;
+  int worst = AMG_OK;
+  for (int i = 0; i < nrhs; ++i) {
+    CUDA_OR_FAIL(c, cudaMemcpyAsync(c->f, f + i * n, n * sizeof(double), cudaMemcpyHostToDevice,
+                                    c->stream), "copy f");
+    CUDA_OR_FAIL(c, cudaMemcpyAsync(c->x, u + i * n, n * sizeof(double), cudaMemcpyHostToDevice,
+                                    c->stream), "copy u");
+    s = pcg_one(c, rtol, maxit, iters ? iters + i : nullptr, relres ? relres + i : nullptr);
+    CUDA_OR_FAIL(c, cudaMemcpyAsync(u + i * n, c->x, n * sizeof(double), cudaMemcpyDeviceToHost,
+                                    c->stream), "copy u back");
+    if (s != AMG_OK && worst == AMG_OK) worst = s;
+  }
+  CUDA_OR_FAIL(c, cudaStreamSynchronize(c->stream), "pcg sync");
+  if (worst != AMG_OK) return worst;
+  c->err.clear();
+  return AMG_OK;
+}
+
+int amg_last_solve_ms(const amg_ctx *h, float *ms) {
+  if (!h || !ms) return AMG_ERR_ARG;
+  *ms = h->c.last_ms;
+  return AMG_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,113 @@
+// Internal declarations of libamg (not part of the ABI).
+#pragma once
+
+#include <cuda_bf16.h>
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <string>
+#include <vector>
+
+#include "../../include/amg.h"
+
+namespace amg {
+
+// Device block-sparse-row matrix.  Values exist in FP64 always; FP32 / BF16
+// copies only for the mixed-precision V-cycles.
+struct DevBSR {
+  int n_rows = 0, n_cols = 0, br = 0, bc = 0;
+  int64_t nnzb = 0;
+  int *rowptr = nullptr;
+  int *colidx = nullptr;
+  double *v64 = nullptr;
+  float *v32 = nullptr;
+  __nv_bfloat16 *v16 = nullptr;
+};
+
+struct Level {
+  DevBSR A, P, R;          // P, R: to / from level l+1 (empty on the coarsest)
+  int k = 0;               // block size of A_l
+  double *minv64 = nullptr;  // smoother blocks M_v^+ (n * k * k)
+  float *minv32 = nullptr;
+  // V-cycle work vectors (n * k), FP64 and FP32 sets
+  double *b64 = nullptr, *x64 = nullptr, *t64 = nullptr, *y64 = nullptr;
+  float *b32 = nullptr, *x32 = nullptr, *t32 = nullptr, *y32 = nullptr;
+};
+
+// Scalars of the device-resident PCG iteration.
+struct PcgState {
+  double rr, ff, tol2, rho, rho_old, alpha, beta, pq, rtol;
+  int it, maxit, status, flexible, guard;
+};
+
+struct Ctx {
+  int device = 0;
+  cudaStream_t stream = nullptr;
+  bool own_stream = false;
+  int num_sms = 0;
+  std::string err;
+  std::vector<Level> levels;
+  int precision = AMG_PREC_FP64;
+  int smoother = AMG_SMOOTHER_L1_JACOBI;
+  // coarsest level: explicit FP64 inverse of A_L + (I - E E^T)
+  int coarse_n = 0;
+  double *cinv = nullptr;
+  // PCG buffers (finest level, FP64)
+  double *f = nullptr, *x = nullptr, *r = nullptr, *z = nullptr, *zold = nullptr, *p = nullptr,
+         *q = nullptr;
+  PcgState *st = nullptr;       // device
+  PcgState *st_host = nullptr;  // pinned
+  double *partials = nullptr;   // reduction scratch
+  unsigned *counter = nullptr;  // last-block counter
+  cudaGraphExec_t graph = nullptr;
+  cudaGraph_t graph_def = nullptr;
+  cudaEvent_t ev0 = nullptr, ev1 = nullptr;
+  float last_ms = 0.f;
+  double *hbuf = nullptr;        // pinned staging for host solves
+  size_t hbuf_len = 0;
+};
+
+// Device allocation helpers (all internal buffers are owned by the context).
+cudaError_t dalloc(void **p, size_t bytes);
+void dfree(void *p);
+void free_bsr(DevBSR &m);
+void free_levels(Ctx *c);
+void free_pcg(Ctx *c);
+
+// launches (stream-ordered, no synchronisation)
+enum SpmvMode { SPMV_SET = 0, SPMV_RESID = 1, SPMV_ADD = 2, SPMV_SMOOTH = 3 };
+
+// y = op(A) on FP64 / FP32 / BF16 values with FP64 or FP32 vectors.
+cudaError_t launch_bsr(const Ctx *c, const DevBSR &A, int prec, int mode, const void *x,
+                       const void *b, const void *minv, void *y);
+cudaError_t launch_blockdiag(const Ctx *c, int n, int k, int prec, const void *minv,
+                             const void *b, void *y);
+cudaError_t launch_coarse_gemv(const Ctx *c, int n, const double *cinv, const void *b, void *y,
+                               int prec);
+cudaError_t launch_convert(const Ctx *c, size_t n, const void *src, int src_prec, void *dst,
+                           int dst_prec);
+
+// setup kernels
+cudaError_t galerkin_device(Ctx *c, int level);
+cudaError_t smoother_setup(Ctx *c, int level);
+cudaError_t coarse_setup(Ctx *c);
+cudaError_t make_low_precision(Ctx *c, DevBSR &m, int prec);
+
+// V-cycle on device buffers (FP64 in / out), stream-ordered.
+cudaError_t vcycle_launch(Ctx *c, const double *r, double *z);
+
+// PCG graph
+cudaError_t pcg_build_graph(Ctx *c);
+cudaError_t pcg_alloc(Ctx *c);
+
+}  // namespace amg
+
+struct amg_ctx {
+  amg::Ctx c;
+};
+
+#define AMG_CUDA_TRY(expr)                                   \
+  do {                                                       \
+    cudaError_t _e = (expr);                                 \
+    if (_e != cudaSuccess) return _e;                        \
+  } while (0)

@@ -1,0 +1,277 @@
+// BSR operator kernels of the V-cycle (Sec. 3 Algorithm tg, Sec. 7 smoother):
+// SpMV, residual, prolongation-add and the fused block-l1 Jacobi sweep, plus
+// the block-diagonal apply, the coarsest-level dense GEMV and conversions.
+//
+// Layout: one warp per block row.  Lane (b, r) = (lane / BR, lane % BR)
+// streams row r of the b-th block of each group of NB = 32 / BR consecutive
+// blocks: a warp step reads NB*BR*BC contiguous values (fully coalesced), the
+// x gather reads BC contiguous entries per lane.  Partial sums of lanes with
+// the same r are combined with warp shuffles; lanes 0..BR-1 finish the row.
+#include "amg_internal.h"
+
+namespace amg {
+
+template <typename T>
+struct AccT {
+  using type = float;
+};
+template <>
+struct AccT<double> {
+  using type = double;
+};
+
+__device__ __forceinline__ double ld(const double *p) { return __ldg(p); }
+__device__ __forceinline__ float ld(const float *p) { return __ldg(p); }
+__device__ __forceinline__ float ld(const __nv_bfloat16 *p) {
+  return __bfloat162float(__ldg(p));
+}
+// streamed matrix values: read once, keep them out of L1
+__device__ __forceinline__ double lds(const double *p) { return __ldcs(p); }
+__device__ __forceinline__ float lds(const float *p) { return __ldcs(p); }
+__device__ __forceinline__ float lds(const __nv_bfloat16 *p) {
+  unsigned short u = __ldcs(reinterpret_cast<const unsigned short *>(p));
+  return __uint_as_float(((unsigned)u) << 16);
+}
+
+template <int BR, int BC, typename V, typename T, int MODE>
+__global__ void __launch_bounds__(256) bsr_warp_kernel(int n_rows, const int *__restrict__ rowptr,
+                                                       const int *__restrict__ colidx,
+                                                       const V *__restrict__ vals,
+                                                       const T *__restrict__ x,
+                                                       const T *__restrict__ b,
+                                                       const T *__restrict__ minv,
+                                                       T *__restrict__ y) {
+  using A = typename AccT<T>::type;
+  constexpr int NB = 32 / BR;
+  const int lane = threadIdx.x & 31;
+  const int bl = lane / BR;
+  const int r = lane - bl * BR;
+  const bool active = bl < NB;
+  const int nwarps = (gridDim.x * blockDim.x) >> 5;
+  for (int row = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; row < n_rows; row += nwarps) {
+    const int s = rowptr[row], e = rowptr[row + 1];
+    A acc = 0;
+    if (active) {
+      int p = s + bl;
+      // two block steps per iteration keep more loads in flight
+      for (; p + NB < e; p += 2 * NB) {
+        const int c0 = __ldg(colidx + p), c1 = __ldg(colidx + p + NB);
+        const V *v0 = vals + ((size_t)p * BR + r) * BC;
+        const V *v1 = vals + ((size_t)(p + NB) * BR + r) * BC;
+        A a0[BC], a1[BC];
+#pragma unroll
+        for (int q = 0; q < BC; ++q) {
+          a0[q] = (A)lds(v0 + q);
+          a1[q] = (A)lds(v1 + q);
+        }
+#pragma unroll
+        for (int q = 0; q < BC; ++q) {
+          acc += a0[q] * (A)ld(x + (size_t)c0 * BC + q);
+          acc += a1[q] * (A)ld(x + (size_t)c1 * BC + q);
+        }
+      }
+      if (p < e) {
+        const int c0 = __ldg(colidx + p);
+        const V *v0 = vals + ((size_t)p * BR + r) * BC;
+#pragma unroll
+        for (int q = 0; q < BC; ++q) acc += (A)lds(v0 + q) * (A)ld(x + (size_t)c0 * BC + q);
+      }
+    }
+#pragma unroll
+    for (int sft = 1; sft < NB; sft <<= 1) {
+      A o = __shfl_down_sync(0xffffffffu, acc, sft * BR);
+      if (bl + sft < NB) acc += o;
+    }
+    const size_t o = (size_t)row * BR;
+    if (MODE == SPMV_SMOOTH) {
+      // x_out = x_in + M^+ (b - A x_in) for this vertex (block-l1 Jacobi)
+      A res = (lane < BR) ? (A)b[o + lane] - acc : (A)0;
+      A upd = 0;
+#pragma unroll
+      for (int q = 0; q < BR; ++q) {
+        A rq = __shfl_sync(0xffffffffu, res, q);
+        if (lane < BR) upd += (A)minv[(o + lane) * BR + q] * rq;
+      }
+      if (lane < BR) y[o + lane] = (T)((A)x[o + lane] + upd);
+    } else if (lane < BR) {
+      if (MODE == SPMV_SET) y[o + lane] = (T)acc;
+      if (MODE == SPMV_RESID) y[o + lane] = (T)((A)b[o + lane] - acc);
+      if (MODE == SPMV_ADD) y[o + lane] = (T)((A)y[o + lane] + acc);
+    }
+  }
+}
+
+static int grid_for_rows(const Ctx *c, int n_rows) {
+  long want = ((long)n_rows + 7) / 8;  // 8 warps per 256-thread block
+  long cap = (long)c->num_sms * 8;     // 8 resident blocks of 256 threads per SM
+  if (want > cap) want = cap;
+  return (int)(want < 1 ? 1 : want);
+}
+
+template <int BR, int BC, typename V, typename T>
+static cudaError_t bsr_mode(const Ctx *c, const DevBSR &A, const V *vals, int mode, const void *x,
+                            const void *b, const void *minv, void *y) {
+  const int g = grid_for_rows(c, A.n_rows);
+  const T *xx = (const T *)x;
+  const T *bb = (const T *)b;
+  const T *mm = (const T *)minv;
+  T *yy = (T *)y;
+  switch (mode) {
+    case SPMV_SET:
+      bsr_warp_kernel<BR, BC, V, T, SPMV_SET>
+          <<<g, 256, 0, c->stream>>>(A.n_rows, A.rowptr, A.colidx, vals, xx, bb, mm, yy);
+      break;
+    case SPMV_RESID:
+      bsr_warp_kernel<BR, BC, V, T, SPMV_RESID>
+          <<<g, 256, 0, c->stream>>>(A.n_rows, A.rowptr, A.colidx, vals, xx, bb, mm, yy);
+      break;
+    case SPMV_ADD:
+      bsr_warp_kernel<BR, BC, V, T, SPMV_ADD>
+          <<<g, 256, 0, c->stream>>>(A.n_rows, A.rowptr, A.colidx, vals, xx, bb, mm, yy);
+      break;
+    case SPMV_SMOOTH:
+      if (BR != BC) return cudaErrorInvalidValue;
+      bsr_warp_kernel<BR, BC, V, T, SPMV_SMOOTH>
+          <<<g, 256, 0, c->stream>>>(A.n_rows, A.rowptr, A.colidx, vals, xx, bb, mm, yy);
+      break;
+    default:
+      return cudaErrorInvalidValue;
+  }
+  return cudaGetLastError();
+}
+
+template <int BR, int BC>
+static cudaError_t bsr_prec(const Ctx *c, const DevBSR &A, int prec, int mode, const void *x,
+                            const void *b, const void *minv, void *y) {
+  if (A.n_rows == 0) return cudaSuccess;
+  if (prec == AMG_PREC_FP64)
+    return bsr_mode<BR, BC, double, double>(c, A, A.v64, mode, x, b, minv, y);
+  if (prec == AMG_PREC_FP32_VCYCLE)
+    return bsr_mode<BR, BC, float, float>(c, A, A.v32, mode, x, b, minv, y);
+  return bsr_mode<BR, BC, __nv_bfloat16, float>(c, A, A.v16, mode, x, b, minv, y);
+}
+
+cudaError_t launch_bsr(const Ctx *c, const DevBSR &A, int prec, int mode, const void *x,
+                       const void *b, const void *minv, void *y) {
+#define AMG_BSR_CASE(R_, C_) \
+  if (A.br == R_ && A.bc == C_) return bsr_prec<R_, C_>(c, A, prec, mode, x, b, minv, y);
+  AMG_BSR_CASE(2, 2)
+  AMG_BSR_CASE(3, 3)
+  AMG_BSR_CASE(6, 6)
+  AMG_BSR_CASE(2, 3)
+  AMG_BSR_CASE(3, 2)
+  AMG_BSR_CASE(3, 6)
+  AMG_BSR_CASE(6, 3)
+#undef AMG_BSR_CASE
+  return cudaErrorInvalidValue;
+}
+
+// y_i = M_i^+ b_i for every vertex (pre-smoothing from a zero guess).
+template <int K, typename T>
+__global__ void blockdiag_kernel(int n, const T *__restrict__ minv, const T *__restrict__ b,
+                                 T *__restrict__ y) {
+  using A = typename AccT<T>::type;
+  const size_t t = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= (size_t)n * K) return;
+  const size_t v = t / K;
+  A acc = 0;
+#pragma unroll
+  for (int q = 0; q < K; ++q) acc += (A)minv[t * K + q] * (A)b[v * K + q];
+  y[t] = (T)acc;
+}
+
+template <int K>
+static cudaError_t blockdiag_k(const Ctx *c, int n, int prec, const void *minv, const void *b,
+                               void *y) {
+  const size_t tot = (size_t)n * K;
+  const int g = (int)((tot + 255) / 256);
+  if (tot == 0) return cudaSuccess;
+  if (prec == AMG_PREC_FP64)
+    blockdiag_kernel<K, double><<<g, 256, 0, c->stream>>>(n, (const double *)minv,
+                                                          (const double *)b, (double *)y);
+  else
+    blockdiag_kernel<K, float><<<g, 256, 0, c->stream>>>(n, (const float *)minv,
+                                                         (const float *)b, (float *)y);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_blockdiag(const Ctx *c, int n, int k, int prec, const void *minv, const void *b,
+                             void *y) {
+  if (k == 2) return blockdiag_k<2>(c, n, prec, minv, b, y);
+  if (k == 3) return blockdiag_k<3>(c, n, prec, minv, b, y);
+  if (k == 6) return blockdiag_k<6>(c, n, prec, minv, b, y);
+  return cudaErrorInvalidValue;
+}
+
+// y = Cinv b (FP64 dense inverse of the regularised coarsest matrix), one
+// warp per row; input/output in the V-cycle precision.
+template <typename T>
+__global__ void coarse_gemv_kernel(int n, const double *__restrict__ cinv, const T *__restrict__ b,
+                                   T *__restrict__ y) {
+  const int lane = threadIdx.x & 31;
+  const int row = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  if (row >= n) return;
+  const double *a = cinv + (size_t)row * n;
+  double acc = 0.0;
+  for (int j = lane; j < n; j += 32) acc += a[j] * (double)b[j];
+#pragma unroll
+  for (int s = 16; s > 0; s >>= 1) acc += __shfl_down_sync(0xffffffffu, acc, s);
+  if (lane == 0) y[row] = (T)acc;
+}
+
+cudaError_t launch_coarse_gemv(const Ctx *c, int n, const double *cinv, const void *b, void *y,
+                               int prec) {
+  if (n == 0) return cudaSuccess;
+  const int g = (n + 7) / 8;
+  if (prec == AMG_PREC_FP64)
+    coarse_gemv_kernel<double><<<g, 256, 0, c->stream>>>(n, cinv, (const double *)b, (double *)y);
+  else
+    coarse_gemv_kernel<float><<<g, 256, 0, c->stream>>>(n, cinv, (const float *)b, (float *)y);
+  return cudaGetLastError();
+}
+
+template <typename S, typename D>
+__global__ void convert_kernel(size_t n, const S *__restrict__ s, D *__restrict__ d) {
+  const size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) d[i] = (D)s[i];
+}
+
+cudaError_t launch_convert(const Ctx *c, size_t n, const void *src, int src_prec, void *dst,
+                           int dst_prec) {
+  if (n == 0) return cudaSuccess;
+  const int g = (int)((n + 255) / 256);
+  const bool s64 = src_prec == AMG_PREC_FP64, d64 = dst_prec == AMG_PREC_FP64;
+  if (s64 && !d64)
+    convert_kernel<double, float><<<g, 256, 0, c->stream>>>(n, (const double *)src, (float *)dst);
+  else if (!s64 && d64)
+    convert_kernel<float, double><<<g, 256, 0, c->stream>>>(n, (const float *)src, (double *)dst);
+  else
+    return cudaErrorInvalidValue;
+  return cudaGetLastError();
+}
+
+// FP32 / BF16 copies of a matrix's values (round to nearest).
+__global__ void to_f32_kernel(size_t n, const double *__restrict__ s, float *__restrict__ d) {
+  const size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) d[i] = (float)s[i];
+}
+__global__ void to_bf16_kernel(size_t n, const double *__restrict__ s, __nv_bfloat16 *__restrict__ d) {
+  const size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) d[i] = __float2bfloat16_rn((float)s[i]);
+}
+
+cudaError_t make_low_precision(Ctx *c, DevBSR &m, int prec) {
+  const size_t n = (size_t)m.nnzb * m.br * m.bc;
+  if (n == 0) return cudaSuccess;
+  const int g = (int)((n + 255) / 256);
+  if (prec == AMG_PREC_FP32_VCYCLE) {
+    if (!m.v32) AMG_CUDA_TRY(dalloc((void **)&m.v32, n * sizeof(float)));
+    to_f32_kernel<<<g, 256, 0, c->stream>>>(n, m.v64, m.v32);
+  } else if (prec == AMG_PREC_BF16_STORAGE) {
+    if (!m.v16) AMG_CUDA_TRY(dalloc((void **)&m.v16, n * sizeof(__nv_bfloat16)));
+    to_bf16_kernel<<<g, 256, 0, c->stream>>>(n, m.v64, m.v16);
+  }
+  return cudaGetLastError();
+}
+
+}  // namespace amg

@@ -1,0 +1,327 @@
+// FP64 preconditioned conjugate gradients with one V-cycle as the
+// preconditioner (Sec. 7), run entirely on the device: the iteration is a
+// CUDA graph whose body (V-cycle + CG updates) sits in a device-side while
+// node; the last kernel of every iteration decides whether to continue.
+//
+// All inner products use a fixed grid and a last-block reduction in index
+// order, so every run is bit-reproducible.
+#include "amg_internal.h"
+
+namespace amg {
+
+constexpr int kRedThreads = 256;
+
+static int red_grid(const Ctx *c) { return c->num_sms * 2; }
+
+// Block-wide sum of NV values; returns the sums in thread 0.
+template <int NV>
+__device__ __forceinline__ void block_sum(double (&v)[NV]) {
+  __shared__ double sh[NV][kRedThreads / 32];
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+#pragma unroll
+  for (int i = 0; i < NV; ++i) {
+    double x = v[i];
+    for (int o = 16; o > 0; o >>= 1) x += __shfl_down_sync(0xffffffffu, x, o);
+    if (lane == 0) sh[i][w] = x;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+#pragma unroll
+    for (int i = 0; i < NV; ++i) {
+      double s = 0.0;
+      for (int k = 0; k < kRedThreads / 32; ++k) s += sh[i][k];
+      v[i] = s;
+    }
+  }
+  __syncthreads();
+}
+
+// Store this block's partial sums; the block that arrives last sums all
+// partials in index order and returns true (with the totals in tot[]).
+template <int NV>
+__device__ __forceinline__ bool last_block_total(double (&v)[NV], double *partials,
+                                                 unsigned *counter, double (&tot)[NV]) {
+  __shared__ bool last;
+  block_sum<NV>(v);
+  if (threadIdx.x == 0) {
+#pragma unroll
+    for (int i = 0; i < NV; ++i) partials[(size_t)i * gridDim.x + blockIdx.x] = v[i];
+    __threadfence();
+    const unsigned t = atomicAdd(counter, 1u);
+    last = (t == gridDim.x - 1);
+  }
+  __syncthreads();
+  if (!last) return false;
+  __threadfence();
+  double s[NV];
+#pragma unroll
+  for (int i = 0; i < NV; ++i) {
+    s[i] = 0.0;
+    for (int b = threadIdx.x; b < (int)gridDim.x; b += blockDim.x)
+      s[i] += ((volatile double *)partials)[(size_t)i * gridDim.x + b];
+  }
+  block_sum<NV>(s);
+  if (threadIdx.x == 0) {
+#pragma unroll
+    for (int i = 0; i < NV; ++i) tot[i] = s[i];
+    *counter = 0u;
+  }
+  return true;
+}
+
+// Warp-per-row SpMV core (same lane mapping as the V-cycle kernels) used
+// by the CG: returns A_row . x in lanes 0..BR-1.
+template <int BR>
+__device__ __forceinline__ double row_dot(int row, const int *__restrict__ rowptr,
+                                          const int *__restrict__ colidx,
+                                          const double *__restrict__ vals,
+                                          const double *__restrict__ x) {
+  constexpr int NB = 32 / BR;
+  const int lane = threadIdx.x & 31;
+  const int bl = lane / BR, r = lane - bl * BR;
+  double acc = 0.0;
+  if (bl < NB) {
+    const int e = rowptr[row + 1];
+    for (int p = rowptr[row] + bl; p < e; p += NB) {
+      const int c = __ldg(colidx + p);
+      const double *v = vals + ((size_t)p * BR + r) * BR;
+#pragma unroll
+      for (int q = 0; q < BR; ++q) acc += __ldcs(v + q) * __ldg(x + (size_t)c * BR + q);
+    }
+  }
+#pragma unroll
+  for (int s = 1; s < NB; s <<= 1) {
+    const double o = __shfl_down_sync(0xffffffffu, acc, s * BR);
+    if (bl + s < NB) acc += o;
+  }
+  return acc;
+}
+
+// r = f - A x ; rr = r.r ; ff = f.f ; decides whether the loop starts.
+template <int BR>
+__global__ void __launch_bounds__(kRedThreads) pcg_init_kernel(
+    int n_rows, const int *rowptr, const int *colidx, const double *vals, const double *f,
+    const double *x, double *r, PcgState *st, double *partials, unsigned *counter,
+    cudaGraphConditionalHandle h) {
+  const int lane = threadIdx.x & 31;
+  const int nwarps = (gridDim.x * blockDim.x) >> 5;
+  double v[2] = {0.0, 0.0};
+  for (int row = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; row < n_rows; row += nwarps) {
+    const double ax = row_dot<BR>(row, rowptr, colidx, vals, x);
+    if (lane < BR) {
+      const size_t i = (size_t)row * BR + lane;
+      const double ri = f[i] - ax;
+      r[i] = ri;
+      v[0] += ri * ri;
+      v[1] += f[i] * f[i];
+    }
+  }
+  double tot[2];
+  if (last_block_total<2>(v, partials, counter, tot) && threadIdx.x == 0) {
+    st->rr = tot[0];
+    st->ff = tot[1];
+    st->tol2 = st->rtol * st->rtol * tot[1];
+    st->it = 0;
+    st->status = 0;
+    st->rho_old = 0.0;
+    st->alpha = 0.0;
+    st->beta = 0.0;
+    const bool go = (tot[0] > st->tol2) && (st->maxit > 0) && isfinite(tot[0]);
+    cudaGraphSetConditional(h, go ? 1u : 0u);
+  }
+}
+
+// rho = r.z (and r.z_old for the flexible beta); beta from the previous rho.
+__global__ void __launch_bounds__(kRedThreads) pcg_dot_rz_kernel(size_t n, const double *r,
+                                                                  const double *z,
+                                                                  const double *zold,
+                                                                  PcgState *st, double *partials,
+                                                                  unsigned *counter) {
+  double v[2] = {0.0, 0.0};
+  const size_t stride = (size_t)gridDim.x * blockDim.x;
+  const bool flex = st->flexible != 0;
+  for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) {
+    const double ri = r[i];
+    v[0] += ri * z[i];
+    if (flex) v[1] += ri * zold[i];
+  }
+  double tot[2];
+  if (last_block_total<2>(v, partials, counter, tot) && threadIdx.x == 0) {
+    const double rho = tot[0];
+    double beta = 0.0;
+    if (st->it > 0) beta = (st->flexible ? (rho - tot[1]) : rho) / st->rho_old;
+    st->rho = rho;
+    st->beta = beta;
+    st->rho_old = rho;
+  }
+}
+
+// p = z + beta p ; z_old = z (flexible variant)
+__global__ void pcg_update_p_kernel(size_t n, const double *z, double *p, double *zold,
+                                    const PcgState *st) {
+  const size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  const double beta = st->beta;
+  const double zi = z[i];
+  p[i] = (st->it == 0) ? zi : zi + beta * p[i];
+  if (st->flexible) zold[i] = zi;
+}
+
+// q = A p ; pq = p.q ; alpha = rho / pq
+template <int BR>
+__global__ void __launch_bounds__(kRedThreads) pcg_spmv_dot_kernel(
+    int n_rows, const int *rowptr, const int *colidx, const double *vals, const double *p,
+    double *q, PcgState *st, double *partials, unsigned *counter) {
+  const int lane = threadIdx.x & 31;
+  const int nwarps = (gridDim.x * blockDim.x) >> 5;
+  double v[1] = {0.0};
+  for (int row = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; row < n_rows; row += nwarps) {
+    const double ap = row_dot<BR>(row, rowptr, colidx, vals, p);
+    if (lane < BR) {
+      const size_t i = (size_t)row * BR + lane;
+      q[i] = ap;
+      v[0] += p[i] * ap;
+    }
+  }
+  double tot[1];
+  if (last_block_total<1>(v, partials, counter, tot) && threadIdx.x == 0) {
+    const double pq = tot[0];
+    st->pq = pq;
+    if (!(pq > 0.0) || !isfinite(pq)) {
+      st->status = AMG_ERR_NOT_SPD;
+      st->alpha = 0.0;
+    } else {
+      st->alpha = st->rho / pq;
+    }
+  }
+}
+
+// x += alpha p ; r -= alpha q ; rr = r.r
+__global__ void __launch_bounds__(kRedThreads) pcg_update_xr_kernel(
+    size_t n, double *x, double *r, const double *p, const double *q, PcgState *st,
+    double *partials, unsigned *counter) {
+  const double alpha = st->alpha;
+  double v[1] = {0.0};
+  const size_t stride = (size_t)gridDim.x * blockDim.x;
+  for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) {
+    x[i] += alpha * p[i];
+    const double ri = r[i] - alpha * q[i];
+    r[i] = ri;
+    v[0] += ri * ri;
+  }
+  double tot[1];
+  if (last_block_total<1>(v, partials, counter, tot) && threadIdx.x == 0) {
+    st->rr = tot[0];
+    st->it += 1;
+    if (!isfinite(tot[0]) && st->status == 0) st->status = AMG_ERR_NOT_SPD;
+  }
+}
+
+// Last node of every iteration (one thread): the only place the loop
+// condition is set inside the body.  An independent guard counter bounds the
+// loop even if a reduction failed to report, and the reduction counter is
+// re-armed.
+__global__ void pcg_guard_kernel(PcgState *st, unsigned *counter, cudaGraphConditionalHandle h) {
+  st->guard += 1;
+  *counter = 0u;
+  const bool go = (st->rr > st->tol2) && isfinite(st->rr) && (st->it < st->maxit) &&
+                  (st->status == 0) && (st->guard < st->maxit);
+  cudaGraphSetConditional(h, go ? 1u : 0u);
+}
+
+cudaError_t pcg_alloc(Ctx *c) {
+  free_pcg(c);
+  const size_t n = (size_t)c->levels[0].A.n_rows * c->levels[0].k;
+  const size_t bytes = (n ? n : 1) * sizeof(double);
+  double **bufs[] = {&c->f, &c->x, &c->r, &c->z, &c->zold, &c->p, &c->q};
+  for (double **b : bufs) {
+    AMG_CUDA_TRY(dalloc((void **)b, bytes));
+    AMG_CUDA_TRY(cudaMemsetAsync(*b, 0, bytes, c->stream));
+  }
+  AMG_CUDA_TRY(dalloc((void **)&c->st, sizeof(PcgState)));
+  AMG_CUDA_TRY(cudaMallocHost((void **)&c->st_host, sizeof(PcgState)));
+  AMG_CUDA_TRY(dalloc((void **)&c->partials, 4 * (size_t)red_grid(c) * sizeof(double)));
+  AMG_CUDA_TRY(dalloc((void **)&c->counter, sizeof(unsigned)));
+  AMG_CUDA_TRY(cudaMemsetAsync(c->counter, 0, sizeof(unsigned), c->stream));
+  return cudaStreamSynchronize(c->stream);
+}
+
+template <int BR>
+static cudaError_t capture_init(Ctx *c, cudaGraphConditionalHandle h) {
+  const Level &L0 = c->levels[0];
+  pcg_init_kernel<BR><<<red_grid(c), kRedThreads, 0, c->stream>>>(
+      L0.A.n_rows, L0.A.rowptr, L0.A.colidx, L0.A.v64, c->f, c->x, c->r, c->st, c->partials,
+      c->counter, h);
+  return cudaGetLastError();
+}
+
+template <int BR>
+static cudaError_t capture_body(Ctx *c, cudaGraphConditionalHandle h) {
+  const Level &L0 = c->levels[0];
+  const size_t n = (size_t)L0.A.n_rows * BR;
+  const int g = red_grid(c);
+  AMG_CUDA_TRY(vcycle_launch(c, c->r, c->z));
+  pcg_dot_rz_kernel<<<g, kRedThreads, 0, c->stream>>>(n, c->r, c->z, c->zold, c->st, c->partials,
+                                                      c->counter);
+  pcg_update_p_kernel<<<(unsigned)((n + 255) / 256), 256, 0, c->stream>>>(n, c->z, c->p, c->zold,
+                                                                          c->st);
+  pcg_spmv_dot_kernel<BR><<<g, kRedThreads, 0, c->stream>>>(L0.A.n_rows, L0.A.rowptr,
+                                                            L0.A.colidx, L0.A.v64, c->p, c->q,
+                                                            c->st, c->partials, c->counter);
+  pcg_update_xr_kernel<<<g, kRedThreads, 0, c->stream>>>(n, c->x, c->r, c->p, c->q, c->st,
+                                                         c->partials, c->counter);
+  pcg_guard_kernel<<<1, 1, 0, c->stream>>>(c->st, c->counter, h);
+  return cudaGetLastError();
+}
+
+cudaError_t pcg_build_graph(Ctx *c) {
+  if (c->graph) {
+    cudaGraphExecDestroy(c->graph);
+    c->graph = nullptr;
+  }
+  if (c->graph_def) {
+    cudaGraphDestroy(c->graph_def);
+    c->graph_def = nullptr;
+  }
+  const int k = c->levels[0].k;
+  cudaGraph_t g = nullptr;
+  AMG_CUDA_TRY(cudaGraphCreate(&g, 0));
+  cudaGraphConditionalHandle h;
+  AMG_CUDA_TRY(cudaGraphConditionalHandleCreate(&h, g, 0, cudaGraphCondAssignDefault));
+  AMG_CUDA_TRY(cudaStreamBeginCaptureToGraph(c->stream, g, nullptr, nullptr, 0,
+                                             cudaStreamCaptureModeThreadLocal));
+  cudaError_t e = (k == 2) ? capture_init<2>(c, h) : (k == 3) ? capture_init<3>(c, h)
+                                                              : cudaErrorInvalidValue;
+  cudaGraph_t cap = nullptr;
+  cudaError_t e2 = cudaStreamEndCapture(c->stream, &cap);
+  if (e != cudaSuccess) return e;
+  if (e2 != cudaSuccess) return e2;
+  size_t nn = 0;
+  AMG_CUDA_TRY(cudaGraphGetNodes(g, nullptr, &nn));
+  std::vector<cudaGraphNode_t> nodes(nn), sinks;
+  AMG_CUDA_TRY(cudaGraphGetNodes(g, nodes.data(), &nn));
+  for (auto nd : nodes) {
+    size_t nd_out = 0;
+    AMG_CUDA_TRY(cudaGraphNodeGetDependentNodes(nd, nullptr, nullptr, &nd_out));
+    if (nd_out == 0) sinks.push_back(nd);
+  }
+  cudaGraphNodeParams cp = {};
+  cp.type = cudaGraphNodeTypeConditional;
+  cp.conditional.handle = h;
+  cp.conditional.type = cudaGraphCondTypeWhile;
+  cp.conditional.size = 1;
+  cudaGraphNode_t cnode;
+  AMG_CUDA_TRY(cudaGraphAddNode(&cnode, g, sinks.data(), nullptr, sinks.size(), &cp));
+  cudaGraph_t body = cp.conditional.phGraph_out[0];
+  AMG_CUDA_TRY(cudaStreamBeginCaptureToGraph(c->stream, body, nullptr, nullptr, 0,
+                                             cudaStreamCaptureModeThreadLocal));
+  e = (k == 2) ? capture_body<2>(c, h) : (k == 3) ? capture_body<3>(c, h) : cudaErrorInvalidValue;
+  e2 = cudaStreamEndCapture(c->stream, &body);
+  if (e != cudaSuccess) return e;
+  if (e2 != cudaSuccess) return e2;
+  AMG_CUDA_TRY(cudaGraphInstantiate(&c->graph, g, 0));
+  c->graph_def = g;
+  return cudaSuccess;
+}
+
+}  // namespace amg
