@@ -1,0 +1,436 @@
+"""Benchmark of the AMG-PCG solve phase (time to FP64 relative residual 1e-8).
+
+One step = one complete PCG solve, preconditioned by one V-cycle, of the
+seeded synthetic 3D P1 elasticity system on 64^3 vertices (774,144 dofs,
+3x3 blocks) from a zero initial guess to ||r|| <= 1e-8 ||f||: every row of
+the solve phase (BSR SpMV, block-l1 smoother, restriction, prolongation,
+coarsest solve, V-cycle, PCG) runs inside the timed region; the hierarchy
+(setup + device Galerkin products) is built before it.  Inputs live in HBM
+when the timed region starts; A_0 alone (280 MB) is larger than L2.
+
+Prints one JSON line.  ``--impl reference`` times the CPU oracle instead.
+Multi-GPU (torchrun): independent replicas, one per GPU (the solve phase of
+one system does not shard without a halo exchange, which is not built).
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import subprocess
+import sys
+import time
+
+for _v in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS"):
+    os.environ.setdefault(_v, "1")
+
+import numpy as np  # noqa: E402
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+PEAKS_FALLBACK = {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0}
+WORKLOADS = {
+    "cube64": ("3D P1 elasticity, unit cube, 64^3 vertices (Kuhn tetrahedra, +-20% h "
+               "perturbation, seed 2), E=1, nu=0.3, clamped x=0, body force (0,0,-1); "
+               "774,144 dofs, 3x3 BSR"),
+    "square32": ("2D P1 elasticity, unit square, 33x33 vertices (seed 1), E=1, nu=0.3, "
+                 "clamped x=0, body force (0,-1); 2,112 dofs, 2x2 BSR"),
+    "cube128jump": ("3D P1 elasticity, 128^3 vertices, 200 inclusion boxes E=10^U(-3,3), "
+                    "nu U[0.25,0.45] (seed 3); 6.24M dofs"),
+}
+PREC_NAMES = {0: "fp64", 1: "fp32_vcycle", 2: "bf16_storage"}
+
+
+def make_workload(name):
+    from workloads import configs
+    if name == "cube64":
+        return configs.cube64()
+    if name == "square32":
+        return configs.square32()
+    if name == "cube128jump":
+        return configs.cube128jump()
+    raise SystemExit(f"unknown workload {name}")
+
+
+def peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        with open(p) as f:
+            d = json.load(f)
+        return d, "measured"
+    return PEAKS_FALLBACK, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi sampling of SM clocks and throttle reasons during a region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "50"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except OSError:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            out, _ = self.proc.communicate(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+            out, _ = self.proc.communicate()
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in out.strip().splitlines():
+            parts = [x.strip() for x in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax.append(float(parts[2]))
+            except ValueError:
+                continue
+            for nm, val in zip(names, parts[5:9]):
+                if val.lower().startswith("active"):
+                    reasons.add(nm)
+        if not sm:
+            return None
+        return {"sm_mhz": float(np.median(sm)), "sm_max_mhz": float(max(smax)),
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def vcycle_launches(levels, prec):
+    """Kernels of one V-cycle: 5 per non-coarsest level, 1 coarsest, +2 casts."""
+    return 5 * (len(levels) - 1) + 1 + (2 if prec else 0)
+
+
+def algorithmic_bytes_per_iteration(levels, prec):
+    """Bytes one PCG iteration must move at least once (matrices, smoother
+    blocks, vectors), from the actual level sizes."""
+    w = {0: 8, 1: 4, 2: 2}[prec]          # matrix value bytes
+    wv = 8 if prec == 0 else 4            # V-cycle vector / smoother bytes
+    n0, k0 = levels[0]["n_rows"], levels[0]["block"]
+    N0 = n0 * k0
+    A0 = levels[0]["nnzb"] * (k0 * k0 * 8 + 4) + 4 * (n0 + 1)
+    total = A0 + N0 * 8 * 2                            # q = A p (p read, q written)
+    total += N0 * 8 * 2 + N0 * 8 * 3 + N0 * 8 * 6      # dots and updates
+    for l, L in enumerate(levels):
+        n, k = L["n_rows"], L["block"]
+        N = n * k
+        if l == len(levels) - 1:
+            total += (N * N) * 8 + 2 * N * wv
+            continue
+        Ab = L["nnzb"] * (k * k * w + 4) + 4 * (n + 1)
+        kc = levels[l + 1]["block"]
+        Pb = L["nnzb_P"] * (k * kc * w + 4) + 4 * (n + 1)
+        Rb = L["nnzb_P"] * (k * kc * w + 4) + 4 * (levels[l + 1]["n_rows"] + 1)
+        Mb = n * k * k * wv
+        total += Mb + 2 * N * wv                    # x = M b
+        total += Ab + 3 * N * wv                    # t = b - A x
+        total += Rb + N * wv + levels[l + 1]["n_rows"] * kc * wv
+        total += Pb + levels[l + 1]["n_rows"] * kc * wv + 2 * N * wv
+        total += Ab + Mb + 3 * N * wv               # y = x + M(b - A x)
+    if prec:
+        total += N0 * (8 + 4) * 2
+    return total
+
+
+def spmv_bytes(L):
+    n, k = L["n_rows"], L["block"]
+    return L["nnzb"] * (k * k * 8 + 4) + 4 * (n + 1) + 2 * n * k * 8
+
+
+def traffic_record():
+    """dram bytes per launch of the dominant kernel from the committed ncu
+    summary, if the kernel source has not changed since."""
+    import hashlib
+    p = os.path.join(ROOT, "profiles", "ncu_traffic.json")
+    src = os.path.join(ROOT, "paper_2011_13325_gb300", "csrc", "bsr_kernels.cu")
+    if not (os.path.exists(p) and os.path.exists(src)):
+        return None
+    with open(p) as f:
+        rec = json.load(f)
+    sha = hashlib.sha1(open(src, "rb").read()).hexdigest()
+    if rec.get("source_sha1") != sha:
+        return None
+    return rec
+
+
+# ---------------------------------------------------------------------------
+# CPU oracle timing (cpu_baseline and the reference arm)
+# ---------------------------------------------------------------------------
+
+def oracle_hierarchy(problem, P_list):
+    from oracle import solve
+    A0 = solve.mat_from(problem.A)
+    Ps = [solve.Mat(n, m, rp.astype(np.int64), ci.astype(np.int64), v) for (n, m, rp, ci, v) in P_list]
+    return solve.prepare(A0, Ps)
+
+
+def time_oracle(H, f, gpu_iters, budget_s=15.0):
+    """Times oracle PCG iterations on the same hierarchy until ~budget_s of
+    CPU work; returns ms per full solve (scaled by the iteration count)."""
+    from oracle import solve
+    t0 = time.perf_counter()
+    solve.pcg(H, f, rtol=0.0, maxit=1)
+    t1 = time.perf_counter() - t0
+    m = int(max(1, min(gpu_iters, budget_s / max(t1, 1e-6))))
+    t0 = time.perf_counter()
+    solve.pcg(H, f, rtol=0.0, maxit=m)
+    dt = time.perf_counter() - t0
+    per_it = dt / m
+    return per_it * gpu_iters * 1e3, m, dt
+
+
+# ---------------------------------------------------------------------------
+
+
+def dist_env():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
+    ap.add_argument("--workload", default="cube64", choices=sorted(WORKLOADS))
+    ap.add_argument("--variants", default="1,2", help="extra V-cycle precisions (1 fp32, 2 bf16)")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--rtol", type=float, default=1e-8)
+    args = ap.parse_args()
+    if args.warmup < 3:
+        raise SystemExit("--warmup must be >= 3")
+
+    import torch
+    ws, rank, local = dist_env()
+    if ws > 1:
+        import torch.distributed as dist
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    if args.impl == "reference":
+        return run_reference(args, ws, rank, local)
+
+    from paper_2011_13325_gb300 import amg
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    # one non-default stream for the library and for torch's own ops (graph
+    # capture is not allowed on the legacy default stream)
+    stream = torch.cuda.Stream(dev)
+    torch.cuda.set_stream(stream)
+
+    t0 = time.perf_counter()
+    problem = make_workload(args.workload)
+    gen_s = time.perf_counter() - t0
+
+    ctx = amg.Context(local, stream.cuda_stream)
+    t0 = time.perf_counter()
+    ctx.setup(problem, amg.AMG_PREC_FP64)
+    torch.cuda.synchronize()
+    setup_s = time.perf_counter() - t0
+    levels = []
+    for l in range(ctx.n_levels):
+        levels.append(ctx.level_info(l))
+    f = torch.from_numpy(np.ascontiguousarray(problem.b[0])).to(dev)
+    u = torch.zeros_like(f)
+
+    def run_steps(c, k, record):
+        times, its = [], []
+        for _ in range(k):
+            u.zero_()
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            _, it, rr = c.pcg_solve(f, u, rtol=args.rtol, maxit=1000)
+            e1.record(stream)
+            if record:
+                e1.synchronize()
+                times.append(e0.elapsed_time(e1))
+                its.append(it[0])
+        return times, its
+
+    run_steps(ctx, args.warmup, False)
+    if ws > 1:
+        torch.distributed.barrier()
+    torch.cuda.synchronize()
+    sampler = ClockSampler(local)
+    sampler.start()
+    time.sleep(0.15)
+    t_wall = time.perf_counter()
+    times, its = run_steps(ctx, args.steps, True)
+    torch.cuda.synchronize()
+    wall = time.perf_counter() - t_wall
+    clocks = sampler.stop()
+    if ws > 1:
+        torch.distributed.barrier()
+    ms = float(np.mean(times))
+    if ws > 1:
+        t = torch.tensor([ms], device=dev)
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        ms = float(t.item())
+
+    # final FP64 true residual (computed on the device by the library)
+    res = torch.zeros_like(f)
+    ctx.residual(0, f, u, res)
+    true_rel = float(torch.linalg.norm(res) / torch.linalg.norm(f))
+
+    # dominant kernel: A_0 BSR SpMV (warp per block row), events per launch
+    x = torch.randn_like(f)
+    y = torch.empty_like(f)
+    for _ in range(3):
+        ctx.spmv(0, x, y)
+    kt = []
+    for _ in range(20):
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        ctx.spmv(0, x, y)
+        e1.record(stream)
+        e1.synchronize()
+        kt.append(e0.elapsed_time(e1))
+    k_ms = float(np.mean(kt))
+    pk, pk_kind = peaks()
+    k_bytes = spmv_bytes(levels[0])
+    achieved = k_bytes / (k_ms * 1e-3) / 1e9
+    tr = traffic_record()
+    roofline = {"bound": "hbm", "achieved": round(achieved, 1), "peak": pk["hbm_gbs"], "unit": "GB/s",
+                "frac": round(achieved / pk["hbm_gbs"], 3), "traffic": tr["bytes_per_launch"] if tr else None,
+                "kernel": "bsr_warp_kernel<3,3,f64> y = A_0 x", "bytes_per_launch": int(k_bytes),
+                "us_per_launch": round(k_ms * 1e3, 2), "peak_kind": f"{pk_kind} copy bandwidth"}
+
+    it_mean = float(np.mean(its))
+    per_it_bytes = algorithmic_bytes_per_iteration(levels, 0)
+    solve_gbs = per_it_bytes * it_mean / (ms * 1e-3) / 1e9
+    launches = 1 + int(round(it_mean)) * (vcycle_launches(levels, 0) + 6)
+
+    # precision variants (same prolongations, re-uploaded)
+    variants = {}
+    P_list = [ctx.download_prolongation(l) for l in range(ctx.n_levels - 1)]
+    for prec in [int(v) for v in args.variants.split(",") if v.strip()]:
+        c2 = amg.Context(local, stream.cuda_stream)
+        Ps = [type("P", (), dict(n_rows=n, n_cols=m, rowptr=rp, colidx=ci, vals=v))
+              for (n, m, rp, ci, v) in P_list]
+        c2.upload_hierarchy(problem.A, Ps, prec)
+        run_steps(c2, args.warmup, False)
+        tv, iv = run_steps(c2, args.steps, True)
+        c2.residual(0, f, u, res)
+        variants[PREC_NAMES[prec]] = {
+            "ms": round(float(np.mean(tv)), 3), "iters": float(np.mean(iv)),
+            "true_relres": float(torch.linalg.norm(res) / torch.linalg.norm(f)),
+            "speedup_vs_fp64": round(ms / float(np.mean(tv)), 3),
+            "solve_gbs": round(algorithmic_bytes_per_iteration(levels, prec) * float(np.mean(iv)) /
+                               (float(np.mean(tv)) * 1e-3) / 1e9, 1)}
+        c2.close()
+
+    # end-to-end through the host entry point (H2D f, u0; D2H u inside)
+    fh = torch.from_numpy(np.ascontiguousarray(problem.b[0])).pin_memory()
+    uh = torch.zeros_like(fh).pin_memory()
+    for _ in range(2):
+        uh.zero_()
+        ctx.pcg_solve_host(fh, uh, rtol=args.rtol, maxit=1000)
+    et = []
+    for _ in range(args.steps):
+        uh.zero_()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        ctx.pcg_solve_host(fh, uh, rtol=args.rtol, maxit=1000)
+        e1.record(stream)
+        e1.synchronize()
+        et.append(e0.elapsed_time(e1))
+    n_dof = int(f.numel())
+
+    cpu = None
+    if rank == 0 and ws == 1 and not args.no_cpu_baseline:
+        H = oracle_hierarchy(problem, P_list)
+        cms, m, dt = time_oracle(H, problem.b[0], int(round(it_mean)))
+        cpu = {"value": round(cms, 1), "unit": "ms", "cores": 1, "kind": "oracle",
+               "sample": f"{m} oracle PCG iterations ({dt:.1f} s) on the same hierarchy, "
+                         f"scaled to {int(round(it_mean))} iterations"}
+
+    line = {
+        "metric": "AMG-PCG time-to-1e-8 (FP64 residual), 3D elasticity",
+        "value": round(ms, 3), "unit": "ms", "n_gpus": ws, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": round(ms, 3), "higher_is_better": False,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": args.workload, "description": WORKLOADS[args.workload],
+                   "precision": "fp64 V-cycle, fp64 CG", "rtol": args.rtol,
+                   "levels": [L["n_rows"] for L in levels],
+                   "nnzb": [L["nnzb"] for L in levels],
+                   "l2": "inputs larger than L2 (A_0 values 280 MB)",
+                   "parallelism": f"replicas x{ws}"},
+        "iters": it_mean, "true_relres": true_rel, "setup_s": round(setup_s, 2),
+        "generate_s": round(gen_s, 2), "solve_gbs": round(solve_gbs, 1),
+        "bytes_per_iteration": int(per_it_bytes), "solves_per_s": round(ws * 1e3 / ms, 2),
+        "wall_s_timed": round(wall, 3),
+        "roofline": roofline, "clocks": clocks, "variants": variants,
+        "e2e": {"value": round(float(np.mean(et)), 3), "unit": "ms",
+                "h2d_bytes_per_step": 2 * n_dof * 8, "d2h_bytes_per_step": n_dof * 8},
+        "gpu_launches": launches * args.steps, "gpu_launches_per_step": launches,
+        "cpu_baseline": cpu,
+    }
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    ctx.close()
+    if ws > 1:
+        torch.distributed.destroy_process_group()
+
+
+def run_reference(args, ws, rank, local):
+    """The CPU oracle on the machine's host cores, on the same workload and
+    hierarchy, each step a bounded sample of oracle PCG iterations."""
+    import torch
+    if rank != 0:
+        if ws > 1:
+            torch.distributed.destroy_process_group()
+        return
+    from paper_2011_13325_gb300 import amg
+    problem = make_workload(args.workload)
+    ctx = amg.Context(local)
+    ctx.setup(problem, amg.AMG_PREC_FP64)
+    f = torch.from_numpy(np.ascontiguousarray(problem.b[0])).cuda(local)
+    u = torch.zeros_like(f)
+    _, its, _ = ctx.pcg_solve(f, u, rtol=args.rtol, maxit=1000)
+    P_list = [ctx.download_prolongation(l) for l in range(ctx.n_levels - 1)]
+    ctx.close()
+    H = oracle_hierarchy(problem, P_list)
+    per_step = []
+    budget = max(2.0, 60.0 / max(1, args.steps + args.warmup))
+    for s in range(args.warmup + args.steps):
+        cms, m, dt = time_oracle(H, problem.b[0], its[0], budget_s=budget)
+        if s >= args.warmup:
+            per_step.append(cms)
+    v = float(np.mean(per_step))
+    line = {"impl": "reference", "metric": "AMG-PCG time-to-1e-8 (FP64 residual), 3D elasticity",
+            "value": round(v, 1), "unit": "ms", "n_gpus": ws, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": round(v, 1), "higher_is_better": False,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": args.workload, "description": WORKLOADS[args.workload]},
+            "cpu_baseline": {"value": round(v, 1), "unit": "ms", "cores": 1, "kind": "oracle",
+                             "sample": f"each step: oracle PCG iterations for ~{budget:.0f} s, "
+                                       f"scaled to {its[0]} iterations"},
+            "e2e": {"value": round(v, 1), "unit": "ms", "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    if ws > 1:
+        torch.distributed.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

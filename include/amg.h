@@ -93,7 +93,9 @@ enum {
 };
 
 /* Create a context on CUDA device `device`.  `cuda_stream` is a
- * cudaStream_t owned by the caller, or NULL to let the library create one.
+ * cudaStream_t owned by the caller (not the legacy default stream: the CG is
+ * captured into a CUDA graph), or NULL to let the library create a blocking
+ * stream, ordered with the legacy default stream.
  * On success *ctx receives the context.  Errors: AMG_ERR_ARG (ctx NULL),
  * AMG_ERR_CUDA. */
 int amg_create(amg_ctx **ctx, int device, void *cuda_stream);
@@ -186,6 +188,73 @@ int amg_pcg_solve_host(amg_ctx *ctx, const double *f_host, double *u_host, int n
 
 /* Cumulative device time (ms, CUDA events) of the last amg_pcg_solve* call. */
 int amg_last_solve_ms(const amg_ctx *ctx, float *ms);
+
+
+/* ------------------------------------------------------------------------
+ * Setup: build the hierarchy from the finite element problem (host setup of
+ * the paper's method + device Galerkin products), then prepare the solve
+ * phase exactly as amg_upload_hierarchy does.
+ * ---------------------------------------------------------------------- */
+
+/* The problem of Sec. 2 before the Dirichlet elimination. */
+typedef struct {
+  int32_t dim;              /* 2 or 3 (elasticity, dim x dim blocks)             */
+  int32_t n_vertices;       /* all mesh vertices, Dirichlet ones included         */
+  const double *coords;     /* n_vertices * dim vertex positions (host)           */
+  const uint8_t *dirichlet; /* n_vertices flags, 1 = clamped vertex (may be NULL) */
+  amg_bsr A_full;           /* stiffness matrix over all vertices (Neumann)       */
+} amg_problem;
+
+/* Parameters of the setup and the readings taken where the paper is silent:
+ *  sigma        threshold of Algorithm 1 for mu_s, mu_p, mu_g and mu_D
+ *               (not given; 30, chosen so the operator complexity lands in
+ *               the paper's range 1.2-1.5 on 3D elasticity)
+ *  delta        stabilisation of mu_p / mu_g (Sec. 5, delta = 1)
+ *  passes_*     matching passes on the first / later levels (Sec. 7: 5 / 4)
+ *  omega        damping of Def. aux_sp (not given; 2/3)
+ *  cap_*        row caps of the smoothed prolongation (Sec. 7: 8 first
+ *               level / 6 later for real-matrix rows, 4 for auxiliary rows)
+ *  coarse_max   stop when a level has at most this many vertices
+ *               (0: min(1000, max(64, ceil(n_0 / 10^4))))
+ *  min_ratio    stop when a level shrinks by less than this factor
+ *  max_levels   upper bound on the number of levels
+ * A vertex is "standard" (real matrix row in P_s) when its row touches at
+ * most cap agglomerates, does not couple to D and is kernel-exact; the
+ * auxiliary rows use the own agglomerate and the 3 others with the largest
+ * sum of tr E^{il}. */
+typedef struct {
+  double sigma;
+  int32_t delta;
+  int32_t passes_first, passes_later;
+  double omega;
+  int32_t cap_S_first, cap_S_later, cap_A;
+  int32_t coarse_max;
+  double min_ratio;
+  int32_t max_levels;
+} amg_setup_params;
+
+/* Fill *p with the defaults listed above. */
+void amg_default_setup_params(amg_setup_params *p);
+
+/* Build the hierarchy of `prob` on ctx: A_0 = A_full restricted to the free
+ * vertices (Sec. 2, eq. (auf)); per level: edge/vertex matrices (Thm.
+ * deng_elast, Thm. cemats), Algorithm 1, tentative P (Def. pwp / pwp_el),
+ * auxiliary smoothed P_s (Def. aux_sp) on the host, A_{l+1} = P_s^T A_l P_s
+ * on the device; then smoothers and the coarsest inverse as in
+ * amg_upload_hierarchy.  params may be NULL (defaults).  Replaces any
+ * previous hierarchy.  Errors: AMG_ERR_ARG (malformed problem),
+ * AMG_ERR_CUDA. */
+int amg_setup(amg_ctx *ctx, const amg_problem *prob, const amg_setup_params *params, int precision,
+              int smoother);
+
+/* Size of P_level (0 <= level < n_levels-1): rows, columns, block dims and
+ * stored blocks.  Any pointer may be NULL. */
+int amg_prolongation_info(const amg_ctx *ctx, int level, int32_t *n_rows, int32_t *n_cols,
+                          int32_t *br, int32_t *bc, int64_t *nnzb);
+
+/* Copy P_level (FP64) to caller host arrays sized by amg_prolongation_info. */
+int amg_download_prolongation(amg_ctx *ctx, int level, int32_t *rowptr, int32_t *colidx,
+                              double *vals);
 
 #ifdef __cplusplus
 }

@@ -46,6 +46,18 @@ class amg_hierarchy(C.Structure):
     _fields_ = [("A0", amg_bsr), ("n_levels", C.c_int32), ("P", C.POINTER(amg_bsr))]
 
 
+class amg_problem(C.Structure):
+    _fields_ = [("dim", C.c_int32), ("n_vertices", C.c_int32), ("coords", C.POINTER(C.c_double)),
+                ("dirichlet", C.POINTER(C.c_uint8)), ("A_full", amg_bsr)]
+
+
+class amg_setup_params(C.Structure):
+    _fields_ = [("sigma", C.c_double), ("delta", C.c_int32), ("passes_first", C.c_int32),
+                ("passes_later", C.c_int32), ("omega", C.c_double), ("cap_S_first", C.c_int32),
+                ("cap_S_later", C.c_int32), ("cap_A", C.c_int32), ("coarse_max", C.c_int32),
+                ("min_ratio", C.c_double), ("max_levels", C.c_int32)]
+
+
 class AmgError(RuntimeError):
     def __init__(self, code, msg):
         super().__init__(f"{ERRORS.get(code, code)}: {msg}")
@@ -78,6 +90,11 @@ _SIGS = {
     "amg_pcg_solve": (_I, [_P, _P, _P, _I, _D, _I, C.POINTER(_I), C.POINTER(_D)]),
     "amg_pcg_solve_host": (_I, [_P, _P, _P, _I, _D, _I, C.POINTER(_I), C.POINTER(_D)]),
     "amg_last_solve_ms": (_I, [_P, C.POINTER(C.c_float)]),
+    "amg_default_setup_params": (None, [C.POINTER(amg_setup_params)]),
+    "amg_setup": (_I, [_P, C.POINTER(amg_problem), C.POINTER(amg_setup_params), _I, _I]),
+    "amg_prolongation_info": (_I, [_P, _I, C.POINTER(C.c_int32), C.POINTER(C.c_int32),
+                                   C.POINTER(C.c_int32), C.POINTER(C.c_int32), C.POINTER(C.c_int64)]),
+    "amg_download_prolongation": (_I, [_P, _I, _P, _P, _P]),
 }
 
 
@@ -156,6 +173,36 @@ class Context:
             Ps[i] = bsr_struct(P.n_rows, P.n_cols, P.rowptr, P.colidx, P.vals, keep)
         h = amg_hierarchy(a0, len(P_list) + 1, Ps)
         return self._check(lib().amg_upload_hierarchy(self.h, C.byref(h), int(precision), int(smoother)))
+
+    def setup(self, problem, precision=AMG_PREC_FP64, smoother=AMG_SMOOTHER_L1_JACOBI, **params):
+        """amg_setup on a ``workloads.Problem`` (full matrix, coordinates,
+        Dirichlet flags); keyword arguments override amg_setup_params."""
+        keep = []
+        prm = amg_setup_params()
+        lib().amg_default_setup_params(C.byref(prm))
+        for k, v in params.items():
+            setattr(prm, k, v)
+        coords = np.ascontiguousarray(problem.coords, dtype=np.float64)
+        dmask = np.ascontiguousarray(problem.dirichlet, dtype=np.uint8)
+        keep.extend([coords, dmask])
+        Af = problem.A_full
+        pr = amg_problem(int(problem.dim), int(coords.shape[0]),
+                         coords.ctypes.data_as(C.POINTER(C.c_double)),
+                         dmask.ctypes.data_as(C.POINTER(C.c_uint8)),
+                         bsr_struct(Af.n_rows, Af.n_cols, Af.rowptr, Af.colidx, Af.vals, keep))
+        return self._check(lib().amg_setup(self.h, C.byref(pr), C.byref(prm), int(precision),
+                                           int(smoother)))
+
+    def download_prolongation(self, level):
+        n, m, br, bc, nnzb = C.c_int32(), C.c_int32(), C.c_int32(), C.c_int32(), C.c_int64()
+        self._check(lib().amg_prolongation_info(self.h, int(level), C.byref(n), C.byref(m),
+                                                C.byref(br), C.byref(bc), C.byref(nnzb)))
+        rp = np.zeros(n.value + 1, dtype=np.int32)
+        ci = np.zeros(max(nnzb.value, 1), dtype=np.int32)
+        v = np.zeros((max(nnzb.value, 1), br.value, bc.value))
+        self._check(lib().amg_download_prolongation(self.h, int(level), rp.ctypes.data,
+                                                    ci.ctypes.data, v.ctypes.data))
+        return n.value, m.value, rp, ci[:nnzb.value], v[:nnzb.value]
 
     def level_info(self, level):
         n, k, na, npb, nl = C.c_int32(), C.c_int32(), C.c_int64(), C.c_int64(), C.c_int32()

@@ -9,6 +9,7 @@
 #include <vector>
 
 #include "amg_internal.h"
+#include "setup_host.h"
 
 namespace amg {
 
@@ -258,6 +259,67 @@ static int finish(Ctx *c, const char *where) {
   return AMG_OK;
 }
 
+// Smoothers, level vectors, low-precision copies, coarsest inverse, CG buffers.
+static int finalize_hierarchy(Ctx *c) {
+  const int precision = c->precision;
+  for (int l = 0; l < (int)c->levels.size(); ++l) {
+    Level &L = c->levels[l];
+    if (l + 1 < (int)c->levels.size()) CUDA_OR_FAIL(c, smoother_setup(c, l), "smoother setup");
+    CUDA_OR_FAIL(c, alloc_level_vectors(c, L), "level vectors");
+    if (precision != AMG_PREC_FP64) {
+      CUDA_OR_FAIL(c, make_low_precision(c, L.A, precision), "low precision A");
+      if (L.P.nnzb) CUDA_OR_FAIL(c, make_low_precision(c, L.P, precision), "low precision P");
+      if (L.R.nnzb) CUDA_OR_FAIL(c, make_low_precision(c, L.R, precision), "low precision R");
+    }
+  }
+  CUDA_OR_FAIL(c, coarse_setup(c), "coarse setup");
+  CUDA_OR_FAIL(c, pcg_alloc(c), "pcg buffers");
+  return finish(c, "upload");
+}
+
+// Level sink of the host setup: uploads A_0, then per level P_l, R_l and the
+// device Galerkin product, handing A_{l+1} back to the host.
+struct DeviceSink : amgsetup::LevelSink {
+  Ctx *c;
+  explicit DeviceSink(Ctx *cc) : c(cc) {}
+  int first(const amgsetup::HostBSR &A) override {
+    c->levels.clear();
+    c->levels.resize(1);
+    if (upload_bsr(c, c->levels[0].A, A.n_rows, A.n_cols, A.br, A.bc, (int64_t)A.colidx.size(),
+                   A.rowptr.data(), A.colidx.data(), A.vals.data()) != cudaSuccess)
+      return -1;
+    c->levels[0].k = A.br;
+    return 0;
+  }
+  int next(int level, const amgsetup::HostBSR &P, amgsetup::HostBSR &An) override {
+    c->levels.resize(level + 2);
+    Level &L = c->levels[level];
+    amg_bsr pv = {P.n_rows, P.n_cols, P.br, P.bc, (int64_t)P.colidx.size(), P.rowptr.data(),
+                  P.colidx.data(), P.vals.data()};
+    if (upload_bsr(c, L.P, P.n_rows, P.n_cols, P.br, P.bc, pv.nnzb, P.rowptr.data(),
+                   P.colidx.data(), P.vals.data()) != cudaSuccess)
+      return -1;
+    if (upload_transpose(c, L.R, pv) != cudaSuccess) return -1;
+    if (galerkin_device(c, level) != cudaSuccess) return -1;
+    const DevBSR &A = c->levels[level + 1].A;
+    An.n_rows = A.n_rows;
+    An.n_cols = A.n_cols;
+    An.br = A.br;
+    An.bc = A.bc;
+    An.rowptr.resize(A.n_rows + 1);
+    An.colidx.resize(A.nnzb);
+    An.vals.resize((size_t)A.nnzb * A.br * A.bc);
+    if (cudaMemcpy(An.rowptr.data(), A.rowptr, (A.n_rows + 1) * sizeof(int),
+                   cudaMemcpyDeviceToHost) != cudaSuccess ||
+        cudaMemcpy(An.colidx.data(), A.colidx, A.nnzb * sizeof(int), cudaMemcpyDeviceToHost) !=
+            cudaSuccess ||
+        cudaMemcpy(An.vals.data(), A.v64, An.vals.size() * sizeof(double),
+                   cudaMemcpyDeviceToHost) != cudaSuccess)
+      return -1;
+    return 0;
+  }
+};
+
 // ---------------------------------------------------------------------------
 // ABI
 // ---------------------------------------------------------------------------
@@ -276,7 +338,7 @@ int amg_create(amg_ctx **out, int device, void *cuda_stream) {
     if (cuda_stream) {
       c->stream = (cudaStream_t)cuda_stream;
     } else {
-      e = cudaStreamCreateWithFlags(&c->stream, cudaStreamNonBlocking);
+      e = cudaStreamCreate(&c->stream);  // blocking: ordered with the legacy default stream
       c->own_stream = true;
     }
   }
@@ -362,19 +424,7 @@ int amg_upload_hierarchy(amg_ctx *h, const amg_hierarchy *hier, int precision, i
     CUDA_OR_FAIL(c, upload_transpose(c, L.R, P), "upload R");
     CUDA_OR_FAIL(c, galerkin_device(c, l), "galerkin");
   }
-  for (int l = 0; l < (int)c->levels.size(); ++l) {
-    Level &L = c->levels[l];
-    if (l + 1 < (int)c->levels.size()) CUDA_OR_FAIL(c, smoother_setup(c, l), "smoother setup");
-    CUDA_OR_FAIL(c, alloc_level_vectors(c, L), "level vectors");
-    if (precision != AMG_PREC_FP64) {
-      CUDA_OR_FAIL(c, make_low_precision(c, L.A, precision), "low precision A");
-      if (L.P.nnzb) CUDA_OR_FAIL(c, make_low_precision(c, L.P, precision), "low precision P");
-      if (L.R.nnzb) CUDA_OR_FAIL(c, make_low_precision(c, L.R, precision), "low precision R");
-    }
-  }
-  CUDA_OR_FAIL(c, coarse_setup(c), "coarse setup");
-  CUDA_OR_FAIL(c, pcg_alloc(c), "pcg buffers");
-  return finish(c, "upload");
+  return finalize_hierarchy(c);
 }
 
 int amg_galerkin(amg_ctx *h, int level, amg_bsr_out *out) {
@@ -631,6 +681,109 @@ int amg_last_solve_ms(const amg_ctx *h, float *ms) {
   if (!h || !ms) return AMG_ERR_ARG;
   *ms = h->c.last_ms;
   return AMG_OK;
+}
+
+void amg_default_setup_params(amg_setup_params *p) {
+  if (!p) return;
+  const amgsetup::SetupParams d;
+  p->sigma = d.sigma;
+  p->delta = d.delta;
+  p->passes_first = d.passes_first;
+  p->passes_later = d.passes_later;
+  p->omega = d.omega;
+  p->cap_S_first = d.cap_S_first;
+  p->cap_S_later = d.cap_S_later;
+  p->cap_A = d.cap_A;
+  p->coarse_max = d.coarse_max;
+  p->min_ratio = d.min_ratio;
+  p->max_levels = d.max_levels;
+}
+
+int amg_setup(amg_ctx *h, const amg_problem *prob, const amg_setup_params *params, int precision,
+              int smoother) {
+  if (!h) return AMG_ERR_ARG;
+  Ctx *c = &h->c;
+  if (!prob || (prob->dim != 2 && prob->dim != 3) || prob->n_vertices < 1 || !prob->coords)
+    return fail(c, AMG_ERR_ARG, "amg_setup: bad problem");
+  if (precision < AMG_PREC_FP64 || precision > AMG_PREC_BF16_STORAGE)
+    return fail(c, AMG_ERR_ARG, "unknown precision");
+  if (smoother != AMG_SMOOTHER_L1_JACOBI) return fail(c, AMG_ERR_ARG, "unknown smoother");
+  const amg_bsr &A = prob->A_full;
+  int s = validate_bsr(c, A, "A_full");
+  if (s) return s;
+  if (A.n_rows != prob->n_vertices || A.n_cols != A.n_rows || A.br != prob->dim || A.bc != prob->dim)
+    return fail(c, AMG_ERR_ARG, "A_full must be n_vertices x n_vertices with dim x dim blocks");
+  amgsetup::SetupParams prm;
+  if (params) {
+    prm.sigma = params->sigma;
+    prm.delta = params->delta;
+    prm.passes_first = params->passes_first;
+    prm.passes_later = params->passes_later;
+    prm.omega = params->omega;
+    prm.cap_S_first = params->cap_S_first;
+    prm.cap_S_later = params->cap_S_later;
+    prm.cap_A = params->cap_A;
+    prm.coarse_max = params->coarse_max;
+    prm.min_ratio = params->min_ratio;
+    prm.max_levels = params->max_levels;
+  }
+  if (!(prm.sigma > 0) || prm.passes_first < 1 || prm.passes_later < 1 || prm.cap_A < 1 ||
+      prm.max_levels < 1)
+    return fail(c, AMG_ERR_ARG, "amg_setup: bad parameters");
+  CUDA_OR_FAIL(c, cudaSetDevice(c->device), "cudaSetDevice");
+  cudaStreamSynchronize(c->stream);
+  free_pcg(c);
+  free_levels(c);
+  c->precision = precision;
+  c->smoother = smoother;
+  amgsetup::Problem pb;
+  pb.dim = prob->dim;
+  pb.n_vertices = prob->n_vertices;
+  pb.coords = prob->coords;
+  pb.dirichlet = prob->dirichlet;
+  pb.rowptr = A.rowptr;
+  pb.colidx = A.colidx;
+  pb.vals = A.vals;
+  DeviceSink sink(c);
+  std::string err;
+  if (amgsetup::build_levels(pb, prm, sink, err) != 0) {
+    free_levels(c);
+    return fail(c, AMG_ERR_CUDA, "amg_setup: " + err);
+  }
+  return finalize_hierarchy(c);
+}
+
+int amg_prolongation_info(const amg_ctx *h, int level, int32_t *n_rows, int32_t *n_cols,
+                          int32_t *br, int32_t *bc, int64_t *nnzb) {
+  if (!h) return AMG_ERR_ARG;
+  const Ctx *c = &h->c;
+  if (level < 0 || level + 1 >= (int)c->levels.size()) return AMG_ERR_ARG;
+  const DevBSR &P = c->levels[level].P;
+  if (n_rows) *n_rows = P.n_rows;
+  if (n_cols) *n_cols = P.n_cols;
+  if (br) *br = P.br;
+  if (bc) *bc = P.bc;
+  if (nnzb) *nnzb = P.nnzb;
+  return AMG_OK;
+}
+
+int amg_download_prolongation(amg_ctx *h, int level, int32_t *rowptr, int32_t *colidx,
+                              double *vals) {
+  if (!h) return AMG_ERR_ARG;
+  Ctx *c = &h->c;
+  int s = check_level(c, level, true);
+  if (s) return s;
+  const DevBSR &P = c->levels[level].P;
+  if (!rowptr || (P.nnzb > 0 && (!colidx || !vals))) return fail(c, AMG_ERR_ARG, "NULL output array");
+  CUDA_OR_FAIL(c, cudaMemcpyAsync(rowptr, P.rowptr, (size_t)(P.n_rows + 1) * sizeof(int),
+                                  cudaMemcpyDeviceToHost, c->stream), "download P");
+  if (P.nnzb > 0) {
+    CUDA_OR_FAIL(c, cudaMemcpyAsync(colidx, P.colidx, (size_t)P.nnzb * sizeof(int),
+                                    cudaMemcpyDeviceToHost, c->stream), "download P");
+    CUDA_OR_FAIL(c, cudaMemcpyAsync(vals, P.v64, (size_t)P.nnzb * P.br * P.bc * sizeof(double),
+                                    cudaMemcpyDeviceToHost, c->stream), "download P");
+  }
+  return finish(c, "download P");
 }
 
 }  // extern "C"

@@ -1,0 +1,980 @@
+// Host setup of the hierarchy (the part of the method that precedes the
+// solve phase): finest edge matrices (Thm. deng_elast and its Remark),
+// Algorithm 1 "successive matching" with the measures mu_D, mu_s, mu_p and
+// mu_g (Sec. 5), coarse edge/vertex matrices (Thm. cemats), tentative
+// prolongation (Def. pwp / pwp_el) and the auxiliary smoothed prolongation
+// (Def. aux_sp, Sec. 6).  The Galerkin products between levels run on the
+// device (galerkin.cu).  The readings where the paper is silent (sigma,
+// omega, the S / A split, the filtered neighbours, the coarse size) are the
+// ones documented with amg_setup_params in include/amg.h.
+//
+// mu_g is checked, as the paper suggests after Thm. mu1, by a semidefinite
+// Cholesky factorisation of sigma * R - L instead of an eigen-solve.
+#include <math.h>
+#include <stdint.h>
+#include <string.h>
+
+#include <algorithm>
+#include <array>
+#include <unordered_map>
+#include <vector>
+
+#include "setup_host.h"
+
+namespace amgsetup {
+
+// ------------------------------------------------------------------ small dense algebra
+
+using Mat = std::vector<double>;  // row-major, size n*n (n <= 6 here unless noted)
+
+static inline int kdim(int d) { return d + d * (d - 1) / 2; }
+
+// Q(t) = [[I, Skew(t)], [0, I]] (Sec. 3, eq. qij_epseps)
+static void qmat(int d, const double *t, double *q) {
+  const int k = kdim(d);
+  for (int i = 0; i < k * k; ++i) q[i] = 0.0;
+  for (int i = 0; i < k; ++i) q[i * k + i] = 1.0;
+  if (d == 2) {
+    q[0 * k + 2] = -t[1];
+    q[1 * k + 2] = t[0];
+  } else {
+    // Skew(t) r = t x r
+    q[0 * k + 4] = -t[2];
+    q[0 * k + 5] = t[1];
+    q[1 * k + 3] = t[2];
+    q[1 * k + 5] = -t[0];
+    q[2 * k + 3] = -t[1];
+    q[2 * k + 4] = t[0];
+  }
+}
+
+// C = A B (n x m)(m x p)
+static void mm(const double *A, const double *B, double *C, int n, int m, int p) {
+  for (int i = 0; i < n; ++i)
+    for (int j = 0; j < p; ++j) {
+      double s = 0.0;
+      for (int l = 0; l < m; ++l) s += A[i * m + l] * B[l * p + j];
+      C[i * p + j] = s;
+    }
+}
+
+// C = A^T B (A: m x n, B: m x p) -> n x p
+static void mtm(const double *A, const double *B, double *C, int m, int n, int p) {
+  for (int i = 0; i < n; ++i)
+    for (int j = 0; j < p; ++j) {
+      double s = 0.0;
+      for (int l = 0; l < m; ++l) s += A[l * n + i] * B[l * p + j];
+      C[i * p + j] = s;
+    }
+}
+
+// Q^T X Q for the shift t (k x k)
+static void transport(int d, const double *t, const double *X, double *out) {
+  const int k = kdim(d);
+  double q[36], tmp[36];
+  qmat(d, t, q);
+  mm(X, q, tmp, k, k, k);
+  mtm(q, tmp, out, k, k, k);
+}
+
+// Cyclic Jacobi eigen-decomposition of a symmetric n x n matrix (Golub & Van
+// Loan, Sec. 8.5); w eigenvalues, V eigenvectors in columns.
+static void sym_eig(int n, const double *A, double *w, double *V) {
+  double a[36];
+  for (int i = 0; i < n * n; ++i) a[i] = A[i];
+  for (int i = 0; i < n; ++i)
+    for (int j = i + 1; j < n; ++j) {
+      const double m = 0.5 * (a[i * n + j] + a[j * n + i]);
+      a[i * n + j] = a[j * n + i] = m;
+    }
+  for (int i = 0; i < n; ++i)
+    for (int j = 0; j < n; ++j) V[i * n + j] = (i == j) ? 1.0 : 0.0;
+  double fro = 0.0;
+  for (int i = 0; i < n * n; ++i) fro += a[i] * a[i];
+  for (int sweep = 0; sweep < 60 && fro > 0.0; ++sweep) {
+    double off = 0.0;
+    for (int p = 0; p < n; ++p)
+      for (int q = p + 1; q < n; ++q) off += a[p * n + q] * a[p * n + q];
+    if (off <= 1e-34 * fro) break;
+    for (int p = 0; p < n; ++p)
+      for (int q = p + 1; q < n; ++q) {
+        const double apq = a[p * n + q];
+        if (fabs(apq) <= 1e-300) continue;
+        const double th = (a[q * n + q] - a[p * n + p]) / (2.0 * apq);
+        const double t = (th >= 0.0 ? 1.0 : -1.0) / (fabs(th) + sqrt(1.0 + th * th));
+        const double c = 1.0 / sqrt(1.0 + t * t), s = t * c;
+        for (int r = 0; r < n; ++r) {
+          const double x = a[r * n + p], y = a[r * n + q];
+          a[r * n + p] = c * x - s * y;
+          a[r * n + q] = s * x + c * y;
+        }
+        for (int r = 0; r < n; ++r) {
+          const double x = a[p * n + r], y = a[q * n + r];
+          a[p * n + r] = c * x - s * y;
+          a[q * n + r] = s * x + c * y;
+        }
+        for (int r = 0; r < n; ++r) {
+          const double x = V[r * n + p], y = V[r * n + q];
+          V[r * n + p] = c * x - s * y;
+          V[r * n + q] = s * x + c * y;
+        }
+      }
+  }
+  for (int i = 0; i < n; ++i) w[i] = a[i * n + i];
+}
+
+static void pinv_sym(int n, const double *A, double *out, double rtol = 1e-12) {
+  double w[6], V[36];
+  sym_eig(n, A, w, V);
+  double wmax = 0.0;
+  for (int i = 0; i < n; ++i) wmax = std::max(wmax, fabs(w[i]));
+  for (int i = 0; i < n * n; ++i) out[i] = 0.0;
+  if (wmax <= 0.0) return;
+  for (int m = 0; m < n; ++m) {
+    if (!(w[m] > rtol * wmax)) continue;
+    const double inv = 1.0 / w[m];
+    for (int i = 0; i < n; ++i)
+      for (int j = 0; j < n; ++j) out[i * n + j] += V[i * n + m] * inv * V[j * n + m];
+  }
+}
+
+// H(A, B) = A (A + B)^+ B (Lemma mu2), symmetrised
+static void harmonic(int n, const double *A, const double *B, double *H) {
+  double S[36], P[36], T[36];
+  for (int i = 0; i < n * n; ++i) S[i] = A[i] + B[i];
+  pinv_sym(n, S, P);
+  mm(P, B, T, n, n, n);
+  mm(A, T, S, n, n, n);
+  for (int i = 0; i < n; ++i)
+    for (int j = 0; j < n; ++j) H[i * n + j] = 0.5 * (S[i * n + j] + S[j * n + i]);
+}
+
+// smallest mu with L <= mu R (range of R; +inf if L has energy on ker R)
+static double gen_lambda_max(int n, const double *L, const double *R) {
+  double wl[6], Vl[36], wr[6], Vr[36];
+  sym_eig(n, L, wl, Vl);
+  double lmax = 0.0;
+  for (int i = 0; i < n; ++i) lmax = std::max(lmax, wl[i]);
+  if (lmax <= 0.0) return 0.0;
+  sym_eig(n, R, wr, Vr);
+  double rmax = 0.0;
+  for (int i = 0; i < n; ++i) rmax = std::max(rmax, wr[i]);
+  if (rmax <= 0.0) return INFINITY;
+  int nr = 0, nk = 0;
+  double Sr[36], K[36];
+  for (int m = 0; m < n; ++m) {
+    if (wr[m] > 1e-10 * rmax) {
+      const double s = 1.0 / sqrt(wr[m]);
+      for (int i = 0; i < n; ++i) Sr[i * n + nr] = Vr[i * n + m] * s;
+      ++nr;
+    } else {
+      for (int i = 0; i < n; ++i) K[i * n + nk] = Vr[i * n + m];
+      ++nk;
+    }
+  }
+  double LS[36], C[36], w[6], V[36];
+  if (nk > 0) {
+    // K^T L K (n x nk columns stored with stride n)
+    double Kc[36], LK[36];
+    for (int i = 0; i < n; ++i)
+      for (int j = 0; j < nk; ++j) Kc[i * nk + j] = K[i * n + j];
+    mm(L, Kc, LK, n, n, nk);
+    mtm(Kc, LK, C, n, nk, nk);
+    sym_eig(nk, C, w, V);
+    double leak = -INFINITY;
+    for (int i = 0; i < nk; ++i) leak = std::max(leak, w[i]);
+    if (leak > 1e-8 * lmax) return INFINITY;
+  }
+  double Sc[36];
+  for (int i = 0; i < n; ++i)
+    for (int j = 0; j < nr; ++j) Sc[i * nr + j] = Sr[i * n + j];
+  mm(L, Sc, LS, n, n, nr);
+  mtm(Sc, LS, C, n, nr, nr);
+  sym_eig(nr, C, w, V);
+  double mu = 0.0;
+  for (int i = 0; i < nr; ++i) mu = std::max(mu, w[i]);
+  return mu;
+}
+
+// semidefinite Cholesky test of a symmetric N x N matrix (any N)
+static bool psd_cholesky(int N, std::vector<double> &M, double tol) {
+  for (int j = 0; j < N; ++j) {
+    double dj = M[(size_t)j * N + j];
+    for (int l = 0; l < j; ++l) dj -= M[(size_t)j * N + l] * M[(size_t)j * N + l];
+    if (dj < -tol) return false;
+    if (dj <= tol) {
+      for (int i = j + 1; i < N; ++i) {
+        double v = M[(size_t)i * N + j];
+        for (int l = 0; l < j; ++l) v -= M[(size_t)i * N + l] * M[(size_t)j * N + l];
+        if (fabs(v) > sqrt(tol) * sqrt(std::max(tol, fabs(M[(size_t)i * N + i])))) return false;
+        M[(size_t)i * N + j] = 0.0;
+      }
+      M[(size_t)j * N + j] = 0.0;
+      continue;
+    }
+    const double ljj = sqrt(dj);
+    M[(size_t)j * N + j] = ljj;
+    for (int i = j + 1; i < N; ++i) {
+      double v = M[(size_t)i * N + j];
+      for (int l = 0; l < j; ++l) v -= M[(size_t)i * N + l] * M[(size_t)j * N + l];
+      M[(size_t)i * N + j] = v / ljj;
+    }
+  }
+  return true;
+}
+
+// ------------------------------------------------------------------ topology
+
+void Topo::build_adj() {
+  adj_ptr.assign(n + 1, 0);
+  const int m = (int)ei.size();
+  for (int e = 0; e < m; ++e) {
+    adj_ptr[ei[e] + 1]++;
+    adj_ptr[ej[e] + 1]++;
+  }
+  for (int i = 0; i < n; ++i) adj_ptr[i + 1] += adj_ptr[i];
+  adj_nbr.assign(adj_ptr[n], 0);
+  adj_edge.assign(adj_ptr[n], 0);
+  std::vector<int> fill(adj_ptr.begin(), adj_ptr.end() - 1);
+  for (int e = 0; e < m; ++e) {
+    adj_nbr[fill[ei[e]]] = ej[e];
+    adj_edge[fill[ei[e]]++] = e;
+    adj_nbr[fill[ej[e]]] = ei[e];
+    adj_edge[fill[ej[e]]++] = e;
+  }
+  // neighbours sorted by id within each vertex (edge ids follow)
+  for (int v = 0; v < n; ++v) {
+    std::vector<std::pair<int, int>> t;
+    for (int p = adj_ptr[v]; p < adj_ptr[v + 1]; ++p) t.push_back({adj_nbr[p], adj_edge[p]});
+    std::sort(t.begin(), t.end());
+    for (int p = adj_ptr[v], q = 0; p < adj_ptr[v + 1]; ++p, ++q) {
+      adj_nbr[p] = t[q].first;
+      adj_edge[p] = t[q].second;
+    }
+  }
+}
+
+int Topo::edge(int a, int b) const {
+  const int *s = adj_nbr.data() + adj_ptr[a], *e = adj_nbr.data() + adj_ptr[a + 1];
+  const int *it = std::lower_bound(s, e, b);
+  if (it == e || *it != b) return -1;
+  return adj_edge[adj_ptr[a] + (int)(it - s)];
+}
+
+// Thm. deng_elast: E^{ij} = c [[t t^T, 0], [0, 0]], c = mean |(A_ij)_lm|, M = 0
+Topo finest_topology(int d, int n, const double *coords, const uint8_t *dirichlet,
+                     const int32_t *rp, const int32_t *ci, const double *vals) {
+  Topo T;
+  T.n = n;
+  T.d = d;
+  T.k = kdim(d);
+  const int k = T.k;
+  T.pos.assign(coords, coords + (size_t)n * d);
+  T.dir.assign(n, 0);
+  for (int i = 0; i < n; ++i) T.dir[i] = dirichlet ? (dirichlet[i] != 0) : 0;
+  for (int i = 0; i < n; ++i)
+    for (int p = rp[i]; p < rp[i + 1]; ++p)
+      if (ci[p] > i) {
+        T.ei.push_back(i);
+        T.ej.push_back(ci[p]);
+      }
+  const size_t m = T.ei.size();
+  T.E.assign(m * k * k, 0.0);
+  T.M.assign((size_t)n * k * k, 0.0);
+  size_t e = 0;
+  for (int i = 0; i < n; ++i)
+    for (int p = rp[i]; p < rp[i + 1]; ++p)
+      if (ci[p] > i) {
+        const double *blk = vals + (size_t)p * d * d;
+        double c = 0.0;
+        for (int q = 0; q < d * d; ++q) c += fabs(blk[q]);
+        c /= (double)(d * d);
+        double t[3];
+        for (int a = 0; a < d; ++a) t[a] = coords[(size_t)ci[p] * d + a] - coords[(size_t)i * d + a];
+        double *E = T.E.data() + e * k * k;
+        for (int a = 0; a < d; ++a)
+          for (int b = 0; b < d; ++b) E[a * k + b] = c * t[a] * t[b];
+        ++e;
+      }
+  T.build_adj();
+  return T;
+}
+
+static void half_shift(const Topo &T, int i, int j, double *t) {  // (x_j - x_i)/2
+  for (int a = 0; a < T.d; ++a) t[a] = 0.5 * (T.pos[(size_t)j * T.d + a] - T.pos[(size_t)i * T.d + a]);
+}
+
+// D-hat_ii = M^i + sum_j Q^{ij,T} E^{ij} Q^{ij}
+static std::vector<double> aux_diagonal(const Topo &T) {
+  const int k = T.k;
+  std::vector<double> D(T.M);
+  double t[3], X[36];
+  for (size_t e = 0; e < T.ei.size(); ++e) {
+    const int i = T.ei[e], j = T.ej[e];
+    const double *E = T.E.data() + e * k * k;
+    half_shift(T, i, j, t);
+    transport(T.d, t, E, X);
+    for (int q = 0; q < k * k; ++q) D[(size_t)i * k * k + q] += X[q];
+    half_shift(T, j, i, t);
+    transport(T.d, t, E, X);
+    for (int q = 0; q < k * k; ++q) D[(size_t)j * k * k + q] += X[q];
+  }
+  return D;
+}
+
+// Thm. cemats for an agglomeration map (agg = -1 for D)
+static Topo coarse_topology(const Topo &T, const std::vector<int> &agg, int nc,
+                            const std::vector<double> &xc, bool use_dir) {
+  const int k = T.k, d = T.d;
+  Topo C;
+  C.n = nc;
+  C.d = d;
+  C.k = k;
+  C.pos = xc;
+  C.dir.assign(nc, 0);
+  C.M.assign((size_t)nc * k * k, 0.0);
+  double t[3], X[36], Y[36];
+  for (int i = 0; i < T.n; ++i) {
+    const int I = agg[i];
+    if (I < 0) continue;
+    for (int a = 0; a < d; ++a) t[a] = T.pos[(size_t)i * d + a] - xc[(size_t)I * d + a];
+    transport(d, t, T.M.data() + (size_t)i * k * k, X);
+    for (int q = 0; q < k * k; ++q) C.M[(size_t)I * k * k + q] += X[q];
+  }
+  std::unordered_map<long long, int> idx;
+  std::vector<std::array<double, 36>> acc;
+  std::vector<std::pair<int, int>> keys;
+  for (size_t e = 0; e < T.ei.size(); ++e) {
+    const int i = T.ei[e], j = T.ej[e];
+    const int I = agg[i], J = agg[j];
+    const double *E = T.E.data() + e * k * k;
+    if (I >= 0 && J >= 0) {
+      if (I == J) continue;
+      const int a = std::min(I, J), b = std::max(I, J);
+      // Q^{IJ->ij} = Q((x_i + x_j)/2 - (x_I + x_J)/2)
+      for (int q = 0; q < d; ++q)
+        t[q] = 0.5 * (T.pos[(size_t)i * d + q] + T.pos[(size_t)j * d + q]) -
+               0.5 * (xc[(size_t)a * d + q] + xc[(size_t)b * d + q]);
+      transport(d, t, E, X);
+      const long long key = (long long)a * nc + b;
+      auto it = idx.find(key);
+      if (it == idx.end()) {
+        idx[key] = (int)acc.size();
+        std::array<double, 36> z;
+        z.fill(0.0);
+        for (int q = 0; q < k * k; ++q) z[q] = X[q];
+        acc.push_back(z);
+        keys.push_back({a, b});
+      } else {
+        for (int q = 0; q < k * k; ++q) acc[it->second][q] += X[q];
+      }
+    } else if (use_dir && ((I >= 0) != (J >= 0))) {
+      const int v = (I >= 0) ? i : j, w = (I >= 0) ? j : i, V = (I >= 0) ? I : J;
+      // Q^{v_I -> v_i, T} Q^{ij,T} E Q^{ij} Q^{v_I -> v_i}: one shift (x_i+x_j)/2 - x_I
+      for (int q = 0; q < d; ++q)
+        t[q] = 0.5 * (T.pos[(size_t)v * d + q] + T.pos[(size_t)w * d + q]) - xc[(size_t)V * d + q];
+      transport(d, t, E, Y);
+      for (int q = 0; q < k * k; ++q) C.M[(size_t)V * k * k + q] += Y[q];
+    }
+  }
+  std::vector<int> order(keys.size());
+  for (size_t q = 0; q < order.size(); ++q) order[q] = (int)q;
+  std::sort(order.begin(), order.end(), [&](int a, int b) { return keys[a] < keys[b]; });
+  C.ei.resize(order.size());
+  C.ej.resize(order.size());
+  C.E.assign(order.size() * k * k, 0.0);
+  for (size_t q = 0; q < order.size(); ++q) {
+    C.ei[q] = keys[order[q]].first;
+    C.ej[q] = keys[order[q]].second;
+    for (int r = 0; r < k * k; ++r) C.E[q * k * k + r] = acc[order[q]][r];
+  }
+  C.build_adj();
+  return C;
+}
+
+// ------------------------------------------------------------------ measures
+
+static double trace(int k, const double *A) {
+  double s = 0.0;
+  for (int i = 0; i < k; ++i) s += A[i * k + i];
+  return s;
+}
+
+// Lemma mu2 (delta-stabilised pair measure)
+static double mu_p(const Topo &T, const std::vector<double> &Dh, int i, int j, int delta) {
+  const int k = T.k, d = T.d;
+  double t[3], A[36], B[36], L[36], R[36], X[36], Y[36], H[36];
+  half_shift(T, j, i, t);  // Q^{ji} = Q((x_i - x_j)/2)
+  transport(d, t, Dh.data() + (size_t)i * k * k, A);
+  half_shift(T, i, j, t);  // Q^{ij}
+  transport(d, t, Dh.data() + (size_t)j * k * k, B);
+  harmonic(k, A, B, L);
+  const int eij = T.edge(i, j);
+  for (int q = 0; q < k * k; ++q) R[q] = T.E[(size_t)eij * k * k + q];
+  if (delta) {
+    int p = T.adj_ptr[i], q = T.adj_ptr[j];
+    const int pe = T.adj_ptr[i + 1], qe = T.adj_ptr[j + 1];
+    while (p < pe && q < qe) {
+      const int a = T.adj_nbr[p], b = T.adj_nbr[q];
+      if (a < b) {
+        ++p;
+      } else if (b < a) {
+        ++q;
+      } else {
+        const int l = a;
+        half_shift(T, l, i, t);  // Q^{li}
+        transport(d, t, T.E.data() + (size_t)T.adj_edge[p] * k * k, X);
+        half_shift(T, l, j, t);  // Q^{lj}
+        transport(d, t, T.E.data() + (size_t)T.adj_edge[q] * k * k, Y);
+        harmonic(k, X, Y, H);
+        // pull back with Q^{v_i -> v_l} Q^{ji}: a single shift x_l - (x_i + x_j)/2
+        for (int s = 0; s < d; ++s)
+          t[s] = T.pos[(size_t)l * d + s] - 0.5 * (T.pos[(size_t)i * d + s] + T.pos[(size_t)j * d + s]);
+        transport(d, t, H, X);
+        for (int s = 0; s < k * k; ++s) R[s] += 0.5 * delta * X[s];
+        ++p;
+        ++q;
+      }
+    }
+  }
+  return gen_lambda_max(k, L, R);
+}
+
+// Thm. mu1: checks mu_g^delta(C) < sigma by a semidefinite Cholesky of
+// sigma * Right - Left.
+static bool mu_g_below(const Topo &T, const std::vector<double> &Dh, std::vector<int> C, int delta,
+                       double sigma) {
+  std::sort(C.begin(), C.end());
+  const int k = T.k, d = T.d, nC = (int)C.size(), N = nC * k;
+  double xH[3] = {0, 0, 0};
+  for (int v : C)
+    for (int a = 0; a < d; ++a) xH[a] += T.pos[(size_t)v * d + a];
+  for (int a = 0; a < d; ++a) xH[a] /= nC;
+  // D_C P_C blocks and S = P^T D P
+  std::vector<double> DP((size_t)N * k);
+  double S[36] = {0}, q[36], tmp[36], t[3];
+  for (int a = 0; a < nC; ++a) {
+    const int v = C[a];
+    for (int s = 0; s < d; ++s) t[s] = T.pos[(size_t)v * d + s] - xH[s];
+    qmat(d, t, q);
+    mm(Dh.data() + (size_t)v * k * k, q, tmp, k, k, k);
+    for (int i = 0; i < k * k; ++i) DP[(size_t)a * k * k + i] = tmp[i];
+    double qt[36];
+    mtm(q, tmp, qt, k, k, k);
+    for (int i = 0; i < k * k; ++i) S[i] += qt[i];
+  }
+  double Sp[36];
+  pinv_sym(k, S, Sp);
+  // M = sigma * Right - Left, Left = D_C - DP S^+ DP^T
+  std::vector<double> M((size_t)N * N, 0.0);
+  std::vector<double> DPS((size_t)N * k);
+  mm(DP.data(), Sp, DPS.data(), N, k, k);
+  for (int i = 0; i < N; ++i)
+    for (int j = 0; j < N; ++j) {
+      double s = 0.0;
+      for (int l = 0; l < k; ++l) s += DPS[(size_t)i * k + l] * DP[(size_t)j * k + l];
+      M[(size_t)i * N + j] = s;  // + DP S^+ DP^T
+    }
+  for (int a = 0; a < nC; ++a) {
+    const double *Da = Dh.data() + (size_t)C[a] * k * k;
+    for (int i = 0; i < k; ++i)
+      for (int j = 0; j < k; ++j) M[((size_t)a * k + i) * N + a * k + j] -= Da[i * k + j];
+  }
+  auto local = [&](int v) -> int {
+    auto it = std::lower_bound(C.begin(), C.end(), v);
+    return (it != C.end() && *it == v) ? (int)(it - C.begin()) : -1;
+  };
+  auto add_block = [&](int a, int b, const double *X, double f) {
+    for (int i = 0; i < k; ++i)
+      for (int j = 0; j < k; ++j) M[((size_t)a * k + i) * N + b * k + j] += f * X[i * k + j];
+  };
+  // Right: M^i, edges inside C (each once), delta/2 Schur complements of outside neighbours
+  std::vector<int> outs;
+  std::vector<std::array<int, 3>> olist;  // (l, a, edge)
+  for (int a = 0; a < nC; ++a) {
+    const int v = C[a];
+    add_block(a, a, T.M.data() + (size_t)v * k * k, sigma);
+    for (int p = T.adj_ptr[v]; p < T.adj_ptr[v + 1]; ++p) {
+      const int l = T.adj_nbr[p], e = T.adj_edge[p];
+      const int b = local(l);
+      const double *E = T.E.data() + (size_t)e * k * k;
+      if (b >= 0) {
+        if (l > v) {
+          double tv[3], tl[3], qv[36], ql[36], X[36], Y[36];
+          half_shift(T, v, l, tv);  // Q^{vl}
+          half_shift(T, l, v, tl);  // Q^{lv}
+          qmat(d, tv, qv);
+          qmat(d, tl, ql);
+          transport(d, tv, E, X);
+          add_block(a, a, X, sigma);
+          transport(d, tl, E, X);
+          add_block(b, b, X, sigma);
+          mm(E, ql, Y, k, k, k);
+          mtm(qv, Y, X, k, k, k);  // Q^{vl,T} E Q^{lv}
+          add_block(a, b, X, -sigma);
+          double XT[36];
+          for (int i = 0; i < k; ++i)
+            for (int j = 0; j < k; ++j) XT[i * k + j] = X[j * k + i];
+          add_block(b, a, XT, -sigma);
+        }
+      } else if (delta) {
+        olist.push_back({l, a, e});
+      }
+    }
+  }
+  if (delta) {
+    std::sort(olist.begin(), olist.end());
+    size_t s0 = 0;
+    while (s0 < olist.size()) {
+      size_t s1 = s0;
+      while (s1 < olist.size() && olist[s1][0] == olist[s0][0]) ++s1;
+      const int l = olist[s0][0];
+      const int m = (int)(s1 - s0);
+      double Kll[36] = {0};
+      std::vector<double> KCl((size_t)m * k * k);
+      std::vector<int> av(m);
+      for (int u = 0; u < m; ++u) {
+        const int a = olist[s0 + u][1], e = olist[s0 + u][2], v = C[a];
+        const double *E = T.E.data() + (size_t)e * k * k;
+        double tv[3], tl[3], qv[36], ql[36], X[36], Y[36];
+        half_shift(T, v, l, tv);
+        half_shift(T, l, v, tl);
+        qmat(d, tv, qv);
+        qmat(d, tl, ql);
+        transport(d, tv, E, X);  // K_CC diagonal block of v
+        add_block(a, a, X, 0.5 * delta * sigma);
+        mm(E, ql, Y, k, k, k);
+        mtm(qv, Y, X, k, k, k);  // Q^{vl,T} E Q^{lv}  (K_Cl = -this)
+        for (int i = 0; i < k * k; ++i) KCl[(size_t)u * k * k + i] = -X[i];
+        transport(d, tl, E, X);
+        for (int i = 0; i < k * k; ++i) Kll[i] += X[i];
+        av[u] = a;
+      }
+      double Kp[36];
+      pinv_sym(k, Kll, Kp);
+      for (int u = 0; u < m; ++u)
+        for (int w = 0; w < m; ++w) {
+          double T1[36], T2[36];
+          mm(KCl.data() + (size_t)u * k * k, Kp, T1, k, k, k);
+          // T2 = T1 * KCl_w^T
+          for (int i = 0; i < k; ++i)
+            for (int j = 0; j < k; ++j) {
+              double s = 0.0;
+              for (int q2 = 0; q2 < k; ++q2) s += T1[i * k + q2] * KCl[(size_t)w * k * k + j * k + q2];
+              T2[i * k + j] = s;
+            }
+          add_block(av[u], av[w], T2, -0.5 * delta * sigma);
+        }
+      s0 = s1;
+    }
+  }
+  double scale = 0.0;
+  for (int i = 0; i < N; ++i) scale = std::max(scale, fabs(M[(size_t)i * N + i]));
+  for (int a = 0; a < nC; ++a) scale = std::max(scale, trace(k, Dh.data() + (size_t)C[a] * k * k));
+  for (int i = 0; i < N; ++i)
+    for (int j = i + 1; j < N; ++j) {
+      const double m = 0.5 * (M[(size_t)i * N + j] + M[(size_t)j * N + i]);
+      M[(size_t)i * N + j] = M[(size_t)j * N + i] = m;
+    }
+  return psd_cholesky(N, M, 1e-10 * scale);
+}
+
+// ------------------------------------------------------------------ Algorithm 1
+
+static std::vector<int> cuthill_mckee(const Topo &T, const std::vector<char> &active) {
+  std::vector<int> deg(T.n, 0);
+  for (int v = 0; v < T.n; ++v)
+    if (active[v])
+      for (int p = T.adj_ptr[v]; p < T.adj_ptr[v + 1]; ++p) deg[v] += active[T.adj_nbr[p]] ? 1 : 0;
+  std::vector<char> seen(T.n, 0);
+  for (int v = 0; v < T.n; ++v) seen[v] = !active[v];
+  std::vector<int> order;
+  order.reserve(T.n);
+  // candidates for a new start, by (degree, id)
+  std::vector<int> starts;
+  for (int v = 0; v < T.n; ++v)
+    if (active[v]) starts.push_back(v);
+  std::stable_sort(starts.begin(), starts.end(), [&](int a, int b) { return deg[a] < deg[b]; });
+  size_t sp = 0;
+  std::vector<int> nb;
+  while (true) {
+    while (sp < starts.size() && seen[starts[sp]]) ++sp;
+    if (sp == starts.size()) break;
+    const int s = starts[sp];
+    seen[s] = 1;
+    size_t head = order.size();
+    order.push_back(s);
+    while (head < order.size()) {
+      const int v = order[head++];
+      nb.clear();
+      for (int p = T.adj_ptr[v]; p < T.adj_ptr[v + 1]; ++p) {
+        const int w = T.adj_nbr[p];
+        if (active[w] && !seen[w]) nb.push_back(w);
+      }
+      std::sort(nb.begin(), nb.end(), [&](int a, int b) {
+        return deg[a] != deg[b] ? deg[a] < deg[b] : a < b;
+      });
+      for (int w : nb) {
+        seen[w] = 1;
+        order.push_back(w);
+      }
+    }
+  }
+  return order;
+}
+
+struct Coarsening {
+  std::vector<int> agg;
+  int nc = 0;
+  std::vector<double> xc;
+  Topo coarse;
+  std::vector<char> D;
+};
+
+static Coarsening successive_matching(const Topo &T0, const SetupParams &prm, int passes) {
+  const int n = T0.n, k = T0.k, d = T0.d;
+  const double sigma = prm.sigma;
+  std::vector<double> Dh0 = aux_diagonal(T0);
+  Coarsening out;
+  out.D = T0.dir;
+  for (int v = 0; v < n; ++v)
+    if (!out.D[v]) {
+      // mu_D(v) = lambda_max(D-hat_vv, M^v) (eq. mu_d)
+      const double m = gen_lambda_max(k, Dh0.data() + (size_t)v * k * k, T0.M.data() + (size_t)v * k * k);
+      if (m < sigma) out.D[v] = 1;
+    }
+  std::vector<char> active(n);
+  for (int v = 0; v < n; ++v) active[v] = !out.D[v];
+  std::vector<int> order = cuthill_mckee(T0, active);
+  std::vector<std::vector<int>> members(n);
+  for (int v = 0; v < n; ++v) members[v] = {v};
+  Topo cur;  // intermediate topology of passes >= 2
+  const Topo *Tc = &T0;
+  for (int pass = 1; pass <= passes; ++pass) {
+    std::vector<double> Dh = (pass == 1) ? Dh0 : aux_diagonal(*Tc);
+    const int m = Tc->n;
+    std::vector<double> tmax(m, 0.0);
+    for (int v = 0; v < m; ++v) {
+      tmax[v] = trace(k, Tc->M.data() + (size_t)v * k * k);
+      for (int p = Tc->adj_ptr[v]; p < Tc->adj_ptr[v + 1]; ++p)
+        tmax[v] = std::max(tmax[v], trace(k, Tc->E.data() + (size_t)Tc->adj_edge[p] * k * k));
+    }
+    std::vector<int> rank(m, 0);
+    std::vector<char> inT(m, 0);
+    for (size_t r = 0; r < order.size(); ++r) {
+      rank[order[r]] = (int)r;
+      inT[order[r]] = 1;
+    }
+    std::vector<std::vector<int>> groups;
+    std::vector<int> singles;
+    struct Cand {
+      double mu;
+      int rank, cj;
+    };
+    std::vector<Cand> cands;
+    for (int ci : order) {
+      if (!inT[ci]) continue;
+      inT[ci] = 0;
+      cands.clear();
+      for (int p = Tc->adj_ptr[ci]; p < Tc->adj_ptr[ci + 1]; ++p) {
+        const int cj = Tc->adj_nbr[p];
+        if (!inT[cj]) continue;
+        const double tr = trace(k, Tc->E.data() + (size_t)Tc->adj_edge[p] * k * k);
+        if (!(tr > 0.0)) continue;
+        const double ms = sqrt(tmax[ci] * tmax[cj]) / tr;  // Def. muc
+        if (ms < sigma) cands.push_back({ms, rank[cj], cj});
+      }
+      std::sort(cands.begin(), cands.end(), [](const Cand &a, const Cand &b) {
+        return a.mu != b.mu ? a.mu < b.mu : a.rank < b.rank;
+      });
+      bool matched = false;
+      for (const Cand &cd : cands) {
+        const int cj = cd.cj;
+        const double mu = mu_p(*Tc, Dh, ci, cj, prm.delta);
+        if (!(mu < sigma)) continue;
+        bool ok = true;
+        if (members[ci].size() + members[cj].size() > 2) {
+          std::vector<int> uni(members[ci]);
+          uni.insert(uni.end(), members[cj].begin(), members[cj].end());
+          ok = mu_g_below(T0, Dh0, uni, prm.delta, sigma);
+        }
+        if (ok) {
+          groups.push_back({ci, cj});
+          inT[cj] = 0;
+          matched = true;
+          break;
+        }
+      }
+      if (!matched) singles.push_back(ci);
+    }
+    for (int s : singles) groups.push_back({s});
+    const int mc = (int)groups.size();
+    std::vector<std::vector<int>> nm(mc);
+    std::vector<int> cagg(m, -1);
+    std::vector<double> xc((size_t)mc * d, 0.0);
+    for (int g = 0; g < mc; ++g) {
+      for (int c : groups[g]) {
+        cagg[c] = g;
+        nm[g].insert(nm[g].end(), members[c].begin(), members[c].end());
+      }
+      for (int v : nm[g])
+        for (int a = 0; a < d; ++a) xc[(size_t)g * d + a] += T0.pos[(size_t)v * d + a];
+      for (int a = 0; a < d; ++a) xc[(size_t)g * d + a] /= (double)nm[g].size();
+    }
+    Topo next = coarse_topology(*Tc, cagg, mc, xc, pass == 1);
+    cur = std::move(next);
+    Tc = &cur;
+    members = std::move(nm);
+    order.resize(mc);
+    for (int g = 0; g < mc; ++g) order[g] = mc - 1 - g;
+  }
+  out.nc = (int)members.size();
+  out.agg.assign(n, -1);
+  for (int g = 0; g < out.nc; ++g)
+    for (int v : members[g]) out.agg[v] = g;
+  out.xc = cur.pos;
+  out.coarse = std::move(cur);
+  return out;
+}
+
+// ------------------------------------------------------------------ prolongation
+
+struct RowBlocks {  // one prolongation row: sorted columns, kr x k blocks
+  std::vector<int> col;
+  std::vector<double> val;
+};
+
+static void add_to_row(std::vector<std::pair<int, std::array<double, 36>>> &acc, int J, const double *X,
+                       int sz) {
+  for (auto &pr : acc)
+    if (pr.first == J) {
+      for (int i = 0; i < sz; ++i) pr.second[i] += X[i];
+      return;
+    }
+  std::array<double, 36> z;
+  z.fill(0.0);
+  for (int i = 0; i < sz; ++i) z[i] = X[i];
+  acc.push_back({J, z});
+}
+
+// Def. aux_sp with the S / A split; returns BSR rows and next-level "bad" flags.
+static void smoothed_prolongation(const HostBSR &A, const Topo &T, const Coarsening &cs,
+                                  const std::vector<int> &rowmap, const std::vector<char> &bad,
+                                  bool first, const SetupParams &prm, HostBSR &P,
+                                  std::vector<char> &next_bad) {
+  const int d = T.d, k = T.k, kr = first ? d : k;
+  const int nrows = A.n_rows;
+  const int capS = first ? prm.cap_S_first : prm.cap_S_later;
+  std::vector<int> row_of(T.n, -1);
+  for (int r = 0; r < nrows; ++r) row_of[rowmap[r]] = r;
+  // tentative rows (one block each)
+  std::vector<std::array<double, 36>> Pt(nrows);
+  std::vector<int> Pcol(nrows, -1);
+  for (int r = 0; r < nrows; ++r) {
+    const int v = rowmap[r], J = cs.agg[v];
+    if (J < 0) continue;
+    double t[3], q[36];
+    for (int a = 0; a < d; ++a) t[a] = T.pos[(size_t)v * d + a] - cs.xc[(size_t)J * d + a];
+    qmat(d, t, q);
+    Pcol[r] = J;
+    for (int i = 0; i < kr; ++i)
+      for (int j = 0; j < k; ++j) Pt[r][i * k + j] = q[i * k + j];
+  }
+  P.n_rows = nrows;
+  P.n_cols = cs.nc;
+  P.br = kr;
+  P.bc = k;
+  P.rowptr.assign(nrows + 1, 0);
+  P.colidx.clear();
+  P.vals.clear();
+  std::vector<std::pair<int, std::array<double, 36>>> acc;
+  const double om = prm.omega;
+  for (int r = 0; r < nrows; ++r) {
+    const int v = rowmap[r];
+    acc.clear();
+    double Dinv[36];
+    if (!cs.D[v]) {
+      std::vector<int> touched;
+      for (int p = A.rowptr[r]; p < A.rowptr[r + 1]; ++p) {
+        const int c = A.colidx[p];
+        const int w = rowmap[c];
+        if (cs.D[w]) continue;
+        const int J = cs.agg[w];
+        if (std::find(touched.begin(), touched.end(), J) == touched.end()) touched.push_back(J);
+      }
+      const bool standard = (int)touched.size() <= capS && !bad[r];
+      if (standard) {
+        double Arr[36] = {0};
+        for (int p = A.rowptr[r]; p < A.rowptr[r + 1]; ++p) {
+          const int c = A.colidx[p];
+          const double *Ab = A.vals.data() + (size_t)p * kr * kr;
+          if (c == r)
+            for (int i = 0; i < kr * kr; ++i) Arr[i] = Ab[i];
+          if (Pcol[c] < 0) continue;
+          double X[36];
+          mm(Ab, Pt[c].data(), X, kr, kr, k);
+          add_to_row(acc, Pcol[c], X, kr * k);
+        }
+        pinv_sym(kr, Arr, Dinv);
+      } else {
+        // filtered neighbours F^i: own agglomerate + top (cap_A - 1) by sum tr E
+        std::vector<std::pair<int, double>> wsum;
+        for (int p = T.adj_ptr[v]; p < T.adj_ptr[v + 1]; ++p) {
+          const int l = T.adj_nbr[p];
+          if (cs.D[l]) continue;
+          const int J = cs.agg[l];
+          const double tr = trace(k, T.E.data() + (size_t)T.adj_edge[p] * k * k);
+          bool found = false;
+          for (auto &pr : wsum)
+            if (pr.first == J) {
+              pr.second += tr;
+              found = true;
+            }
+          if (!found) wsum.push_back({J, tr});
+        }
+        const int own = cs.agg[v];
+        std::vector<std::pair<int, double>> others;
+        for (auto &pr : wsum)
+          if (pr.first != own) others.push_back(pr);
+        std::sort(others.begin(), others.end(), [](const std::pair<int, double> &a,
+                                                   const std::pair<int, double> &b) {
+          return a.second != b.second ? a.second > b.second : a.first < b.first;
+        });
+        std::vector<int> keep = {own};
+        for (int q = 0; q < (int)others.size() && q < prm.cap_A - 1; ++q) keep.push_back(others[q].first);
+        double Aii[36] = {0};
+        std::vector<std::pair<int, std::array<double, 36>>> offd;
+        for (int p = T.adj_ptr[v]; p < T.adj_ptr[v + 1]; ++p) {
+          const int l = T.adj_nbr[p];
+          if (cs.D[l] || std::find(keep.begin(), keep.end(), cs.agg[l]) == keep.end()) continue;
+          const double *E = T.E.data() + (size_t)T.adj_edge[p] * k * k;
+          std::array<double, 36> X;
+          X.fill(0.0);
+          if (first) {
+            for (int i = 0; i < d; ++i)
+              for (int j = 0; j < d; ++j) {
+                Aii[i * d + j] += E[i * k + j];
+                X[i * d + j] = -E[i * k + j];
+              }
+          } else {
+            double tv[3], tl[3], qv[36], ql[36], Y[36], Z[36];
+            half_shift(T, v, l, tv);
+            half_shift(T, l, v, tl);
+            transport(d, tv, E, Z);
+            for (int i = 0; i < k * k; ++i) Aii[i] += Z[i];
+            qmat(d, tv, qv);
+            qmat(d, tl, ql);
+            mm(E, ql, Y, k, k, k);
+            mtm(qv, Y, Z, k, k, k);
+            for (int i = 0; i < k * k; ++i) X[i] = -Z[i];
+          }
+          offd.push_back({l, X});
+        }
+        pinv_sym(kr, Aii, Dinv);
+        double X[36];
+        if (Pcol[r] >= 0) {
+          mm(Aii, Pt[r].data(), X, kr, kr, k);
+          add_to_row(acc, Pcol[r], X, kr * k);
+        }
+        for (auto &pr : offd) {
+          const int c = row_of[pr.first];
+          if (c < 0 || Pcol[c] < 0) continue;
+          mm(pr.second.data(), Pt[c].data(), X, kr, kr, k);
+          add_to_row(acc, Pcol[c], X, kr * k);
+        }
+      }
+    }
+    std::sort(acc.begin(), acc.end(), [](const std::pair<int, std::array<double, 36>> &a,
+                                         const std::pair<int, std::array<double, 36>> &b) {
+      return a.first < b.first;
+    });
+    for (auto &pr : acc) {
+      double X[36];
+      mm(Dinv, pr.second.data(), X, kr, kr, k);
+      P.colidx.push_back(pr.first);
+      for (int i = 0; i < kr * k; ++i) {
+        const double base = (pr.first == Pcol[r]) ? Pt[r][i] : 0.0;
+        P.vals.push_back(base - om * X[i]);
+      }
+    }
+    P.rowptr[r + 1] = (int)P.colidx.size();
+  }
+  next_bad.assign(cs.nc, 0);
+  for (int r = 0; r < nrows; ++r)
+    if (bad[r])
+      for (int p = P.rowptr[r]; p < P.rowptr[r + 1]; ++p) next_bad[P.colidx[p]] = 1;
+}
+
+// ------------------------------------------------------------------ level loop
+
+int build_levels(const Problem &prob, const SetupParams &prm, LevelSink &sink, std::string &err) {
+  const int d = prob.dim, n_all = prob.n_vertices;
+  if (d != 2 && d != 3) {
+    err = "dim must be 2 or 3";
+    return -1;
+  }
+  Topo T = finest_topology(d, n_all, prob.coords, prob.dirichlet, prob.rowptr, prob.colidx, prob.vals);
+  // A_0: rows / columns of the free vertices
+  std::vector<int> rowmap, newid(n_all, -1);
+  for (int v = 0; v < n_all; ++v)
+    if (!T.dir[v]) {
+      newid[v] = (int)rowmap.size();
+      rowmap.push_back(v);
+    }
+  HostBSR A;
+  A.n_rows = A.n_cols = (int)rowmap.size();
+  A.br = A.bc = d;
+  A.rowptr.assign(A.n_rows + 1, 0);
+  for (int r = 0; r < A.n_rows; ++r) {
+    const int v = rowmap[r];
+    for (int p = prob.rowptr[v]; p < prob.rowptr[v + 1]; ++p) {
+      const int w = newid[prob.colidx[p]];
+      if (w < 0) continue;
+      A.colidx.push_back(w);
+      A.vals.insert(A.vals.end(), prob.vals + (size_t)p * d * d, prob.vals + (size_t)(p + 1) * d * d);
+    }
+    A.rowptr[r + 1] = (int)A.colidx.size();
+  }
+  if (sink.first(A) != 0) {
+    err = "upload of A_0 failed";
+    return -1;
+  }
+  const int n0 = A.n_rows;
+  const int cmax = prm.coarse_max > 0 ? prm.coarse_max
+                                      : std::min(1000, std::max(64, (int)ceil(n0 / 1e4)));
+  std::vector<char> bad_exact(A.n_rows, 0);
+  int level = 0;
+  while (A.n_rows > cmax && level + 1 < prm.max_levels) {
+    const bool first = level == 0;
+    Coarsening cs = successive_matching(T, prm, first ? prm.passes_first : prm.passes_later);
+    if (cs.nc == 0 || A.n_rows < prm.min_ratio * cs.nc) break;
+    std::vector<char> bad(A.n_rows, 0);
+    for (int r = 0; r < A.n_rows; ++r) {
+      bool couples = false;
+      if (first) {
+        const int v = rowmap[r];
+        for (int p = T.adj_ptr[v]; p < T.adj_ptr[v + 1] && !couples; ++p) couples = cs.D[T.adj_nbr[p]];
+      } else {
+        for (int p = A.rowptr[r]; p < A.rowptr[r + 1] && !couples; ++p) couples = cs.D[rowmap[A.colidx[p]]];
+      }
+      bad[r] = bad_exact[r] || couples;
+    }
+    HostBSR P;
+    std::vector<char> next_bad;
+    smoothed_prolongation(A, T, cs, rowmap, bad, first, prm, P, next_bad);
+    HostBSR Anext;
+    if (sink.next(level, P, Anext) != 0) {
+      err = "device Galerkin product failed";
+      return -1;
+    }
+    A = std::move(Anext);
+    T = std::move(cs.coarse);
+    rowmap.resize(cs.nc);
+    for (int i = 0; i < cs.nc; ++i) rowmap[i] = i;
+    bad_exact = std::move(next_bad);
+    ++level;
+  }
+  return 0;
+}
+
+}  // namespace amgsetup

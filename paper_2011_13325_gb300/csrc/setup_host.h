@@ -1,0 +1,61 @@
+// Host setup of the hierarchy (internal to libamg).
+#pragma once
+
+#include <stdint.h>
+
+#include <string>
+#include <vector>
+
+namespace amgsetup {
+
+struct HostBSR {
+  int n_rows = 0, n_cols = 0, br = 0, bc = 0;
+  std::vector<int> rowptr, colidx;
+  std::vector<double> vals;
+};
+
+// Auxiliary topology of one level: vertices, edges (i < j) with k x k edge
+// matrices E, vertex matrices M, Dirichlet flags, sorted adjacency.
+struct Topo {
+  int n = 0, d = 0, k = 0;
+  std::vector<double> pos, E, M;
+  std::vector<int> ei, ej;
+  std::vector<char> dir;
+  std::vector<int> adj_ptr, adj_nbr, adj_edge;
+  void build_adj();
+  int edge(int a, int b) const;
+};
+
+struct Problem {
+  int dim = 0, n_vertices = 0;
+  const double *coords = nullptr;
+  const uint8_t *dirichlet = nullptr;
+  const int32_t *rowptr = nullptr, *colidx = nullptr;
+  const double *vals = nullptr;
+};
+
+struct SetupParams {
+  double sigma = 30.0;
+  int delta = 1;
+  int passes_first = 5, passes_later = 4;
+  double omega = 2.0 / 3.0;
+  int cap_S_first = 8, cap_S_later = 6, cap_A = 4;
+  int coarse_max = 0;
+  double min_ratio = 1.5;
+  int max_levels = 16;
+};
+
+// Receives the levels as they are built: first(A_0), then for every level
+// the prolongation P_l; it must return A_{l+1} = P_l^T A_l P_l on the host.
+struct LevelSink {
+  virtual ~LevelSink() {}
+  virtual int first(const HostBSR &A0) = 0;
+  virtual int next(int level, const HostBSR &P, HostBSR &A_next) = 0;
+};
+
+Topo finest_topology(int d, int n, const double *coords, const uint8_t *dirichlet,
+                     const int32_t *rp, const int32_t *ci, const double *vals);
+
+int build_levels(const Problem &prob, const SetupParams &prm, LevelSink &sink, std::string &err);
+
+}  // namespace amgsetup
