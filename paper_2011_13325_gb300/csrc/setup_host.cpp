@@ -68,13 +68,62 @@ static void mtm(const double *A, const double *B, double *C, int m, int n, int p
     }
 }
 
+// S = Skew(t) as a d x (k-d) block
+static void skew_block(int d, const double *t, double *S) {
+  if (d == 2) {
+    S[0] = -t[1];
+    S[1] = t[0];
+  } else {
+    S[0] = 0.0;   S[1] = -t[2]; S[2] = t[1];
+    S[3] = t[2];  S[4] = 0.0;   S[5] = -t[0];
+    S[6] = -t[1]; S[7] = t[0];  S[8] = 0.0;
+  }
+}
+
+// Q(t1)^T X Q(t2) in closed form: with X = [[A, B], [B^T, C]] (blocks d x d,
+// d x r, r x r; r = k - d) and S_i = Skew(t_i),
+//   [[A, A S2 + B], [S1^T A + B^T, S1^T A S2 + S1^T B + B^T S2 + C]].
+// (B^T here is X's lower-left block; X need not be symmetric.)
+static void transport2(int d, const double *t1, const double *t2, const double *X, double *out) {
+  const int k = kdim(d), r = k - d;
+  double S1[9], S2[9], AS2[18], BL[18];
+  skew_block(d, t1, S1);
+  skew_block(d, t2, S2);
+  // A S2 (d x r)
+  for (int i = 0; i < d; ++i)
+    for (int j = 0; j < r; ++j) {
+      double s = 0.0;
+      for (int l = 0; l < d; ++l) s += X[i * k + l] * S2[l * r + j];
+      AS2[i * r + j] = s;
+    }
+  // S1^T A (r x d)
+  for (int i = 0; i < r; ++i)
+    for (int j = 0; j < d; ++j) {
+      double s = 0.0;
+      for (int l = 0; l < d; ++l) s += S1[l * r + i] * X[l * k + j];
+      BL[i * d + j] = s;
+    }
+  for (int i = 0; i < d; ++i)
+    for (int j = 0; j < d; ++j) out[i * k + j] = X[i * k + j];
+  for (int i = 0; i < d; ++i)
+    for (int j = 0; j < r; ++j) out[i * k + d + j] = AS2[i * r + j] + X[i * k + d + j];
+  for (int i = 0; i < r; ++i)
+    for (int j = 0; j < d; ++j) out[(d + i) * k + j] = BL[i * d + j] + X[(d + i) * k + j];
+  for (int i = 0; i < r; ++i)
+    for (int j = 0; j < r; ++j) {
+      double s = X[(d + i) * k + d + j];
+      for (int l = 0; l < d; ++l) {
+        s += S1[l * r + i] * AS2[l * r + j];      // S1^T A S2
+        s += S1[l * r + i] * X[l * k + d + j];    // S1^T B
+        s += X[(d + i) * k + l] * S2[l * r + j];  // B^T S2 (lower-left block of X)
+      }
+      out[(d + i) * k + d + j] = s;
+    }
+}
+
 // Q^T X Q for the shift t (k x k)
 static void transport(int d, const double *t, const double *X, double *out) {
-  const int k = kdim(d);
-  double q[36], tmp[36];
-  qmat(d, t, q);
-  mm(X, q, tmp, k, k, k);
-  mtm(q, tmp, out, k, k, k);
+  transport2(d, t, t, X, out);
 }
 
 // Cyclic Jacobi eigen-decomposition of a symmetric n x n matrix (Golub & Van
@@ -196,28 +245,47 @@ static double gen_lambda_max(int n, const double *L, const double *R) {
   return mu;
 }
 
-// semidefinite Cholesky test of a symmetric N x N matrix (any N)
-static bool psd_cholesky(int N, std::vector<double> &M, double tol) {
+// Positive-semidefiniteness test of a symmetric N x N matrix M = sigma R - L
+// (any N) by Cholesky with diagonal pivoting (the largest remaining diagonal
+// first, as for semidefinite matrices in Golub & Van Loan, Sec. 4.2.8): the
+// factorisation runs while the largest remaining pivot exceeds
+// tol = rtol * max|M_ii|; the remaining Schur complement (the common kernel
+// of R and L plus rounding) must then vanish to within tol.  Rows made of
+// rounding noise are never used as pivots, so coefficient jumps of many
+// orders of magnitude do not spoil the test.
+static bool psd_cholesky(int N, std::vector<double> &A, double rtol) {
+  // only the lower triangle (i >= l) of A is read and updated
+  double scale = 0.0;
+  for (int i = 0; i < N; ++i) scale = std::max(scale, fabs(A[(size_t)i * N + i]));
+  const double tol = rtol * scale;
+  auto at = [&](int i, int l) -> double & { return A[(size_t)i * N + l]; };
+  std::vector<double> colj;
   for (int j = 0; j < N; ++j) {
-    double dj = M[(size_t)j * N + j];
-    for (int l = 0; l < j; ++l) dj -= M[(size_t)j * N + l] * M[(size_t)j * N + l];
-    if (dj < -tol) return false;
-    if (dj <= tol) {
-      for (int i = j + 1; i < N; ++i) {
-        double v = M[(size_t)i * N + j];
-        for (int l = 0; l < j; ++l) v -= M[(size_t)i * N + l] * M[(size_t)j * N + l];
-        if (fabs(v) > sqrt(tol) * sqrt(std::max(tol, fabs(M[(size_t)i * N + i])))) return false;
-        M[(size_t)i * N + j] = 0.0;
-      }
-      M[(size_t)j * N + j] = 0.0;
-      continue;
+    int p = j;
+    for (int i = j + 1; i < N; ++i)
+      if (at(i, i) > at(p, p)) p = i;
+    if (at(p, p) <= tol) {
+      for (int l = j; l < N; ++l)
+        for (int i = l; i < N; ++i)
+          if (fabs(at(i, l)) > 10.0 * tol) return false;
+      return true;
     }
-    const double ljj = sqrt(dj);
-    M[(size_t)j * N + j] = ljj;
+    if (p != j) {  // symmetric exchange of rows/columns j and p (lower triangle)
+      std::swap(at(j, j), at(p, p));
+      for (int l = 0; l < j; ++l) std::swap(at(j, l), at(p, l));
+      for (int i = j + 1; i < p; ++i) std::swap(at(i, j), at(p, i));
+      for (int i = p + 1; i < N; ++i) std::swap(at(i, j), at(i, p));
+    }
+    const double ljj = sqrt(at(j, j));
+    at(j, j) = ljj;
+    for (int i = j + 1; i < N; ++i) at(i, j) /= ljj;
+    colj.resize(N);
+    for (int i = j + 1; i < N; ++i) colj[i] = at(i, j);
     for (int i = j + 1; i < N; ++i) {
-      double v = M[(size_t)i * N + j];
-      for (int l = 0; l < j; ++l) v -= M[(size_t)i * N + l] * M[(size_t)j * N + l];
-      M[(size_t)i * N + j] = v / ljj;
+      const double aij = colj[i];
+      if (aij == 0.0) continue;
+      double *row = &A[(size_t)i * N];
+      for (int l = j + 1; l <= i; ++l) row[l] -= aij * colj[l];
     }
   }
   return true;
@@ -297,6 +365,7 @@ Topo finest_topology(int d, int n, const double *coords, const uint8_t *dirichle
         ++e;
       }
   T.build_adj();
+  T.rot_free = true;  // finest elasticity edges: displacement blocks only, M = 0
   return T;
 }
 
@@ -308,16 +377,14 @@ static void half_shift(const Topo &T, int i, int j, double *t) {  // (x_j - x_i)
 static std::vector<double> aux_diagonal(const Topo &T) {
   const int k = T.k;
   std::vector<double> D(T.M);
-  double t[3], X[36];
-  for (size_t e = 0; e < T.ei.size(); ++e) {
-    const int i = T.ei[e], j = T.ej[e];
-    const double *E = T.E.data() + e * k * k;
-    half_shift(T, i, j, t);
-    transport(T.d, t, E, X);
-    for (int q = 0; q < k * k; ++q) D[(size_t)i * k * k + q] += X[q];
-    half_shift(T, j, i, t);
-    transport(T.d, t, E, X);
-    for (int q = 0; q < k * k; ++q) D[(size_t)j * k * k + q] += X[q];
+#pragma omp parallel for schedule(static)
+  for (int i = 0; i < T.n; ++i) {
+    double t[3], X[36];
+    for (int p = T.adj_ptr[i]; p < T.adj_ptr[i + 1]; ++p) {
+      half_shift(T, i, T.adj_nbr[p], t);
+      transport(T.d, t, T.E.data() + (size_t)T.adj_edge[p] * k * k, X);
+      for (int q = 0; q < k * k; ++q) D[(size_t)i * k * k + q] += X[q];
+    }
   }
   return D;
 }
@@ -441,81 +508,100 @@ static double mu_p(const Topo &T, const std::vector<double> &Dh, int i, int j, i
 }
 
 // Thm. mu1: checks mu_g^delta(C) < sigma by a semidefinite Cholesky of
-// sigma * Right - Left.
+// sigma * Right - Left.  On a level whose edge and vertex matrices have no
+// rotation part (the finest elasticity level) both sides vanish on the
+// rotation dofs, so the test runs on the displacement dofs only.
 static bool mu_g_below(const Topo &T, const std::vector<double> &Dh, std::vector<int> C, int delta,
                        double sigma) {
   std::sort(C.begin(), C.end());
-  const int k = T.k, d = T.d, nC = (int)C.size(), N = nC * k;
+  const int k = T.k, d = T.d, nC = (int)C.size();
+  const int b = T.rot_free ? d : k;  // dofs per vertex in the test
+  const int N = nC * b;
   double xH[3] = {0, 0, 0};
   for (int v : C)
     for (int a = 0; a < d; ++a) xH[a] += T.pos[(size_t)v * d + a];
   for (int a = 0; a < d; ++a) xH[a] /= nC;
-  // D_C P_C blocks and S = P^T D P
+  // sub-block (first b rows / columns) of a k x k matrix
+  auto sub = [&](const double *X, double *Y) {
+    for (int i = 0; i < b; ++i)
+      for (int j = 0; j < b; ++j) Y[i * b + j] = X[i * k + j];
+  };
+  // DP = D_C P_C (N x k, P_C rows Q^{v_H -> v}) and S = P_C^T D_C P_C
   std::vector<double> DP((size_t)N * k);
-  double S[36] = {0}, q[36], tmp[36], t[3];
+  double S[36] = {0}, q[36], Db[36], t[3];
   for (int a = 0; a < nC; ++a) {
     const int v = C[a];
-    for (int s = 0; s < d; ++s) t[s] = T.pos[(size_t)v * d + s] - xH[s];
-    qmat(d, t, q);
-    mm(Dh.data() + (size_t)v * k * k, q, tmp, k, k, k);
-    for (int i = 0; i < k * k; ++i) DP[(size_t)a * k * k + i] = tmp[i];
+    for (int s2 = 0; s2 < d; ++s2) t[s2] = T.pos[(size_t)v * d + s2] - xH[s2];
+    qmat(d, t, q);  // rows 0..b-1 are the dofs kept
+    sub(Dh.data() + (size_t)v * k * k, Db);
+    double *dp = DP.data() + (size_t)a * b * k;
+    mm(Db, q, dp, b, b, k);
     double qt[36];
-    mtm(q, tmp, qt, k, k, k);
+    mtm(q, dp, qt, b, k, k);
     for (int i = 0; i < k * k; ++i) S[i] += qt[i];
   }
   double Sp[36];
   pinv_sym(k, S, Sp);
-  // M = sigma * Right - Left, Left = D_C - DP S^+ DP^T
+  // M = DP S^+ DP^T - D_C = -Left
   std::vector<double> M((size_t)N * N, 0.0);
   std::vector<double> DPS((size_t)N * k);
   mm(DP.data(), Sp, DPS.data(), N, k, k);
   for (int i = 0; i < N; ++i)
-    for (int j = 0; j < N; ++j) {
-      double s = 0.0;
-      for (int l = 0; l < k; ++l) s += DPS[(size_t)i * k + l] * DP[(size_t)j * k + l];
-      M[(size_t)i * N + j] = s;  // + DP S^+ DP^T
+    for (int j = 0; j <= i; ++j) {
+      double sm = 0.0;
+      for (int l = 0; l < k; ++l) sm += DPS[(size_t)i * k + l] * DP[(size_t)j * k + l];
+      M[(size_t)i * N + j] = sm;
+      M[(size_t)j * N + i] = sm;
     }
   for (int a = 0; a < nC; ++a) {
-    const double *Da = Dh.data() + (size_t)C[a] * k * k;
-    for (int i = 0; i < k; ++i)
-      for (int j = 0; j < k; ++j) M[((size_t)a * k + i) * N + a * k + j] -= Da[i * k + j];
+    sub(Dh.data() + (size_t)C[a] * k * k, Db);
+    for (int i = 0; i < b; ++i)
+      for (int j = 0; j < b; ++j) M[((size_t)a * b + i) * N + a * b + j] -= Db[i * b + j];
   }
   auto local = [&](int v) -> int {
     auto it = std::lower_bound(C.begin(), C.end(), v);
     return (it != C.end() && *it == v) ? (int)(it - C.begin()) : -1;
   };
-  auto add_block = [&](int a, int b, const double *X, double f) {
-    for (int i = 0; i < k; ++i)
-      for (int j = 0; j < k; ++j) M[((size_t)a * k + i) * N + b * k + j] += f * X[i * k + j];
+  auto add_block = [&](int a, int c, const double *X, double f) {  // X is b x b
+    for (int i = 0; i < b; ++i)
+      for (int j = 0; j < b; ++j) M[((size_t)a * b + i) * N + c * b + j] += f * X[i * b + j];
+  };
+  // edge-form blocks of the edge (v, l) in the frames of v and l:
+  // Evv = Q^{vl,T} E Q^{vl}, Ell = Q^{lv,T} E Q^{lv}, Evl = Q^{vl,T} E Q^{lv}
+  auto edge_blocks = [&](int v, int l, const double *E, double *Evv, double *Ell, double *Evl) {
+    if (T.rot_free) {
+      sub(E, Evv);
+      sub(E, Ell);
+      sub(E, Evl);
+      return;
+    }
+    double tv[3], tl[3];
+    half_shift(T, v, l, tv);
+    half_shift(T, l, v, tl);
+    transport(d, tv, E, Evv);
+    transport(d, tl, E, Ell);
+    transport2(d, tv, tl, E, Evl);
   };
   // Right: M^i, edges inside C (each once), delta/2 Schur complements of outside neighbours
-  std::vector<int> outs;
   std::vector<std::array<int, 3>> olist;  // (l, a, edge)
   for (int a = 0; a < nC; ++a) {
     const int v = C[a];
-    add_block(a, a, T.M.data() + (size_t)v * k * k, sigma);
+    sub(T.M.data() + (size_t)v * k * k, Db);
+    add_block(a, a, Db, sigma);
     for (int p = T.adj_ptr[v]; p < T.adj_ptr[v + 1]; ++p) {
       const int l = T.adj_nbr[p], e = T.adj_edge[p];
-      const int b = local(l);
+      const int c = local(l);
       const double *E = T.E.data() + (size_t)e * k * k;
-      if (b >= 0) {
+      if (c >= 0) {
         if (l > v) {
-          double tv[3], tl[3], qv[36], ql[36], X[36], Y[36];
-          half_shift(T, v, l, tv);  // Q^{vl}
-          half_shift(T, l, v, tl);  // Q^{lv}
-          qmat(d, tv, qv);
-          qmat(d, tl, ql);
-          transport(d, tv, E, X);
-          add_block(a, a, X, sigma);
-          transport(d, tl, E, X);
-          add_block(b, b, X, sigma);
-          mm(E, ql, Y, k, k, k);
-          mtm(qv, Y, X, k, k, k);  // Q^{vl,T} E Q^{lv}
-          add_block(a, b, X, -sigma);
-          double XT[36];
-          for (int i = 0; i < k; ++i)
-            for (int j = 0; j < k; ++j) XT[i * k + j] = X[j * k + i];
-          add_block(b, a, XT, -sigma);
+          double Evv[36], Ell[36], Evl[36], EvlT[36];
+          edge_blocks(v, l, E, Evv, Ell, Evl);
+          add_block(a, a, Evv, sigma);
+          add_block(c, c, Ell, sigma);
+          add_block(a, c, Evl, -sigma);
+          for (int i = 0; i < b; ++i)
+            for (int j = 0; j < b; ++j) EvlT[i * b + j] = Evl[j * b + i];
+          add_block(c, a, EvlT, -sigma);
         }
       } else if (delta) {
         olist.push_back({l, a, e});
@@ -531,52 +617,43 @@ static bool mu_g_below(const Topo &T, const std::vector<double> &Dh, std::vector
       const int l = olist[s0][0];
       const int m = (int)(s1 - s0);
       double Kll[36] = {0};
-      std::vector<double> KCl((size_t)m * k * k);
+      std::vector<double> KCl((size_t)m * b * b);
       std::vector<int> av(m);
       for (int u = 0; u < m; ++u) {
         const int a = olist[s0 + u][1], e = olist[s0 + u][2], v = C[a];
         const double *E = T.E.data() + (size_t)e * k * k;
-        double tv[3], tl[3], qv[36], ql[36], X[36], Y[36];
-        half_shift(T, v, l, tv);
-        half_shift(T, l, v, tl);
-        qmat(d, tv, qv);
-        qmat(d, tl, ql);
-        transport(d, tv, E, X);  // K_CC diagonal block of v
-        add_block(a, a, X, 0.5 * delta * sigma);
-        mm(E, ql, Y, k, k, k);
-        mtm(qv, Y, X, k, k, k);  // Q^{vl,T} E Q^{lv}  (K_Cl = -this)
-        for (int i = 0; i < k * k; ++i) KCl[(size_t)u * k * k + i] = -X[i];
-        transport(d, tl, E, X);
-        for (int i = 0; i < k * k; ++i) Kll[i] += X[i];
+        double Evv[36], Ell[36], Evl[36];
+        edge_blocks(v, l, E, Evv, Ell, Evl);
+        add_block(a, a, Evv, 0.5 * delta * sigma);  // K_CC
+        for (int i = 0; i < b * b; ++i) KCl[(size_t)u * b * b + i] = -Evl[i];
+        for (int i = 0; i < b * b; ++i) Kll[i] += Ell[i];
         av[u] = a;
       }
       double Kp[36];
-      pinv_sym(k, Kll, Kp);
-      for (int u = 0; u < m; ++u)
+      pinv_sym(b, Kll, Kp);
+      for (int u = 0; u < m; ++u) {
+        double T1[36];
+        mm(KCl.data() + (size_t)u * b * b, Kp, T1, b, b, b);
         for (int w = 0; w < m; ++w) {
-          double T1[36], T2[36];
-          mm(KCl.data() + (size_t)u * k * k, Kp, T1, k, k, k);
-          // T2 = T1 * KCl_w^T
-          for (int i = 0; i < k; ++i)
-            for (int j = 0; j < k; ++j) {
-              double s = 0.0;
-              for (int q2 = 0; q2 < k; ++q2) s += T1[i * k + q2] * KCl[(size_t)w * k * k + j * k + q2];
-              T2[i * k + j] = s;
+          double T2[36];
+          for (int i = 0; i < b; ++i)
+            for (int j = 0; j < b; ++j) {
+              double sm = 0.0;
+              for (int q2 = 0; q2 < b; ++q2) sm += T1[i * b + q2] * KCl[(size_t)w * b * b + j * b + q2];
+              T2[i * b + j] = sm;
             }
           add_block(av[u], av[w], T2, -0.5 * delta * sigma);
         }
+      }
       s0 = s1;
     }
   }
-  double scale = 0.0;
-  for (int i = 0; i < N; ++i) scale = std::max(scale, fabs(M[(size_t)i * N + i]));
-  for (int a = 0; a < nC; ++a) scale = std::max(scale, trace(k, Dh.data() + (size_t)C[a] * k * k));
   for (int i = 0; i < N; ++i)
     for (int j = i + 1; j < N; ++j) {
-      const double m = 0.5 * (M[(size_t)i * N + j] + M[(size_t)j * N + i]);
-      M[(size_t)i * N + j] = M[(size_t)j * N + i] = m;
+      const double mm2 = 0.5 * (M[(size_t)i * N + j] + M[(size_t)j * N + i]);
+      M[(size_t)i * N + j] = M[(size_t)j * N + i] = mm2;
     }
-  return psd_cholesky(N, M, 1e-10 * scale);
+  return psd_cholesky(N, M, 1e-10);
 }
 
 // ------------------------------------------------------------------ Algorithm 1
@@ -671,41 +748,77 @@ static Coarsening successive_matching(const Topo &T0, const SetupParams &prm, in
       double mu;
       int rank, cj;
     };
-    std::vector<Cand> cands;
-    for (int ci : order) {
-      if (!inT[ci]) continue;
-      inT[ci] = 0;
+    // candidates of ci among the unmatched neighbours with mu_s < sigma,
+    // ordered by mu_s, ties by the iteration order (Def. muc, Algorithm 1)
+    auto candidates = [&](int ci, std::vector<Cand> &cands) {
       cands.clear();
       for (int p = Tc->adj_ptr[ci]; p < Tc->adj_ptr[ci + 1]; ++p) {
         const int cj = Tc->adj_nbr[p];
         if (!inT[cj]) continue;
         const double tr = trace(k, Tc->E.data() + (size_t)Tc->adj_edge[p] * k * k);
         if (!(tr > 0.0)) continue;
-        const double ms = sqrt(tmax[ci] * tmax[cj]) / tr;  // Def. muc
+        const double ms = sqrt(tmax[ci] * tmax[cj]) / tr;
         if (ms < sigma) cands.push_back({ms, rank[cj], cj});
       }
       std::sort(cands.begin(), cands.end(), [](const Cand &a, const Cand &b) {
         return a.mu != b.mu ? a.mu < b.mu : a.rank < b.rank;
       });
-      bool matched = false;
-      for (const Cand &cd : cands) {
-        const int cj = cd.cj;
-        const double mu = mu_p(*Tc, Dh, ci, cj, prm.delta);
-        if (!(mu < sigma)) continue;
-        bool ok = true;
-        if (members[ci].size() + members[cj].size() > 2) {
-          std::vector<int> uni(members[ci]);
-          uni.insert(uni.end(), members[cj].begin(), members[cj].end());
-          ok = mu_g_below(T0, Dh0, uni, prm.delta, sigma);
-        }
-        if (ok) {
-          groups.push_back({ci, cj});
-          inT[cj] = 0;
-          matched = true;
-          break;
-        }
+    };
+    // mu_p and (when needed) the mu_g test of one pair; pure functions of
+    // the pass's topology, so they can be evaluated ahead of the greedy loop
+    auto evaluate = [&](int ci, int cj, double &mu, int &gok) {
+      mu = mu_p(*Tc, Dh, ci, cj, prm.delta);
+      gok = 1;
+      if (mu < sigma && members[ci].size() + members[cj].size() > 2) {
+        std::vector<int> uni(members[ci]);
+        uni.insert(uni.end(), members[cj].begin(), members[cj].end());
+        gok = mu_g_below(T0, Dh0, uni, prm.delta, sigma) ? 1 : 0;
       }
-      if (!matched) singles.push_back(ci);
+    };
+    const int chunk = 2048;
+    std::vector<Cand> cands;
+    for (size_t c0 = 0; c0 < order.size(); c0 += chunk) {
+      const size_t c1 = std::min(order.size(), c0 + chunk);
+      // speculative parallel evaluation of the first eight live candidates
+      std::vector<std::array<int, 2>> tasks;
+      for (size_t q = c0; q < c1; ++q) {
+        const int ci = order[q];
+        if (!inT[ci]) continue;
+        candidates(ci, cands);
+        for (size_t u = 0; u < cands.size() && u < 8; ++u) tasks.push_back({ci, cands[u].cj});
+      }
+      std::vector<double> tmu(tasks.size());
+      std::vector<int> tg(tasks.size());
+#pragma omp parallel for schedule(dynamic, 8)
+      for (long long q = 0; q < (long long)tasks.size(); ++q) evaluate(tasks[q][0], tasks[q][1], tmu[q], tg[q]);
+      std::unordered_map<long long, size_t> done;
+      for (size_t q = 0; q < tasks.size(); ++q) done[(long long)tasks[q][0] * m + tasks[q][1]] = q;
+      for (size_t q = c0; q < c1; ++q) {
+        const int ci = order[q];
+        if (!inT[ci]) continue;
+        inT[ci] = 0;
+        candidates(ci, cands);
+        bool matched = false;
+        for (const Cand &cd : cands) {
+          const int cj = cd.cj;
+          double mu;
+          int gok;
+          auto it = done.find((long long)ci * m + cj);
+          if (it != done.end()) {
+            mu = tmu[it->second];
+            gok = tg[it->second];
+          } else {
+            evaluate(ci, cj, mu, gok);
+          }
+          if (mu < sigma && gok) {
+            groups.push_back({ci, cj});
+            inT[cj] = 0;
+            matched = true;
+            break;
+          }
+        }
+        if (!matched) singles.push_back(ci);
+      }
     }
     for (int s : singles) groups.push_back({s});
     const int mc = (int)groups.size();
@@ -857,15 +970,12 @@ static void smoothed_prolongation(const HostBSR &A, const Topo &T, const Coarsen
                 X[i * d + j] = -E[i * k + j];
               }
           } else {
-            double tv[3], tl[3], qv[36], ql[36], Y[36], Z[36];
+            double tv[3], tl[3], Z[36];
             half_shift(T, v, l, tv);
             half_shift(T, l, v, tl);
             transport(d, tv, E, Z);
             for (int i = 0; i < k * k; ++i) Aii[i] += Z[i];
-            qmat(d, tv, qv);
-            qmat(d, tl, ql);
-            mm(E, ql, Y, k, k, k);
-            mtm(qv, Y, Z, k, k, k);
+            transport2(d, tv, tl, E, Z);
             for (int i = 0; i < k * k; ++i) X[i] = -Z[i];
           }
           offd.push_back({l, X});

@@ -22,6 +22,9 @@ struct Topo {
   std::vector<int> ei, ej;
   std::vector<char> dir;
   std::vector<int> adj_ptr, adj_nbr, adj_edge;
+  // true when every E and M lives in the displacement block only (finest
+  // elasticity level, Thm. deng_elast with M = 0)
+  bool rot_free = false;
   void build_adj();
   int edge(int a, int b) const;
 };
