@@ -214,6 +214,9 @@ def main():
     ap.add_argument("--variants", default="1,2", help="extra V-cycle precisions (1 fp32, 2 bf16)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--rtol", type=float, default=1e-8)
+    ap.add_argument("--pcg-mode", default="graph", choices=["graph", "host"],
+                    help="graph: whole PCG in one CUDA graph (default); host: the same kernels "
+                         "launched one by one (per-kernel view for profilers)")
     args = ap.parse_args()
     if args.warmup < 3:
         raise SystemExit("--warmup must be >= 3")
@@ -240,6 +243,7 @@ def main():
     gen_s = time.perf_counter() - t0
 
     ctx = amg.Context(local, stream.cuda_stream)
+    ctx.set_pcg_graph(args.pcg_mode == "graph")
     t0 = time.perf_counter()
     ctx.setup(problem, amg.AMG_PREC_FP64)
     torch.cuda.synchronize()
@@ -324,6 +328,7 @@ def main():
     P_list = [ctx.download_prolongation(l) for l in range(ctx.n_levels - 1)]
     for prec in [int(v) for v in args.variants.split(",") if v.strip()]:
         c2 = amg.Context(local, stream.cuda_stream)
+        c2.set_pcg_graph(args.pcg_mode == "graph")
         Ps = [type("P", (), dict(n_rows=n, n_cols=m, rowptr=rp, colidx=ci, vals=v))
               for (n, m, rp, ci, v) in P_list]
         c2.upload_hierarchy(problem.A, Ps, prec)
@@ -371,6 +376,7 @@ def main():
         "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
         "config": {"workload": args.workload, "description": WORKLOADS[args.workload],
                    "precision": "fp64 V-cycle, fp64 CG", "rtol": args.rtol,
+                   "pcg_mode": args.pcg_mode,
                    "levels": [L["n_rows"] for L in levels],
                    "nnzb": [L["nnzb"] for L in levels],
                    "l2": "inputs larger than L2 (A_0 values 280 MB)",

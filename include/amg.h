@@ -186,6 +186,25 @@ int amg_pcg_solve(amg_ctx *ctx, const double *f_dev, double *u_dev, int nrhs, do
 int amg_pcg_solve_host(amg_ctx *ctx, const double *f_host, double *u_host, int nrhs,
                        double rtol, int maxit, int *iters_out, double *relres_out);
 
+/* Execution mode of amg_pcg_solve*: enable != 0 (default) runs the whole
+ * iteration as one CUDA graph with a device-side while loop; enable == 0
+ * launches the same kernels one by one and reads the loop condition back
+ * after every iteration (a kernel-by-kernel view for profilers, which do not
+ * see inside graphs with conditional nodes).  Results are identical. */
+int amg_set_pcg_graph(amg_ctx *ctx, int enable);
+
+/* Storage layout of the level operators, applied by the next
+ * amg_upload_hierarchy / amg_setup:
+ *   AMG_LAYOUT_AUTO             SELL-32 copy (one thread per block row) for
+ *                               operators with >= 16 * 32 rows per SM and at
+ *                               most 32 blocks per row; warp-per-row BSR
+ *                               kernels for the rest (default)
+ *   AMG_LAYOUT_SELL_SHORT_ROWS  SELL-32 for every operator with short rows
+ *   AMG_LAYOUT_WARP_ROWS        warp-per-row BSR kernels only
+ * The result of every operator is the same up to the order of the sums. */
+enum { AMG_LAYOUT_AUTO = 0, AMG_LAYOUT_SELL_SHORT_ROWS = 1, AMG_LAYOUT_WARP_ROWS = 2 };
+int amg_set_layout_policy(amg_ctx *ctx, int policy);
+
 /* Cumulative device time (ms, CUDA events) of the last amg_pcg_solve* call. */
 int amg_last_solve_ms(const amg_ctx *ctx, float *ms);
 

@@ -28,6 +28,9 @@ ERRORS = {AMG_ERR_ARG: "AMG_ERR_ARG", AMG_ERR_CUDA: "AMG_ERR_CUDA", AMG_ERR_NOT_
 AMG_PREC_FP64 = 0
 AMG_PREC_FP32_VCYCLE = 1
 AMG_PREC_BF16_STORAGE = 2
+AMG_LAYOUT_AUTO = 0
+AMG_LAYOUT_SELL_SHORT_ROWS = 1
+AMG_LAYOUT_WARP_ROWS = 2
 AMG_SMOOTHER_L1_JACOBI = 0
 AMG_SMOOTHER_LEARNED = 1
 
@@ -90,6 +93,8 @@ _SIGS = {
     "amg_pcg_solve": (_I, [_P, _P, _P, _I, _D, _I, C.POINTER(_I), C.POINTER(_D)]),
     "amg_pcg_solve_host": (_I, [_P, _P, _P, _I, _D, _I, C.POINTER(_I), C.POINTER(_D)]),
     "amg_last_solve_ms": (_I, [_P, C.POINTER(C.c_float)]),
+    "amg_set_pcg_graph": (_I, [_P, _I]),
+    "amg_set_layout_policy": (_I, [_P, _I]),
     "amg_default_setup_params": (None, [C.POINTER(amg_setup_params)]),
     "amg_setup": (_I, [_P, C.POINTER(amg_problem), C.POINTER(amg_setup_params), _I, _I]),
     "amg_prolongation_info": (_I, [_P, _I, C.POINTER(C.c_int32), C.POINTER(C.c_int32),
@@ -285,6 +290,12 @@ class Context:
         if check:
             self._check(s)
         return s, list(it), list(rr)
+
+    def set_layout_policy(self, policy: int):
+        return self._check(lib().amg_set_layout_policy(self.h, int(policy)))
+
+    def set_pcg_graph(self, enable: bool):
+        return self._check(lib().amg_set_pcg_graph(self.h, int(bool(enable))))
 
     def last_solve_ms(self):
         ms = C.c_float()

@@ -28,6 +28,11 @@ void free_bsr(DevBSR &m) {
   dfree(m.v64);
   dfree(m.v32);
   dfree(m.v16);
+  dfree(m.sell_ptr);
+  dfree(m.sell_col);
+  dfree(m.s64);
+  dfree(m.s32);
+  dfree(m.s16);
   m = DevBSR();
 }
 
@@ -266,6 +271,9 @@ static int finalize_hierarchy(Ctx *c) {
     Level &L = c->levels[l];
     if (l + 1 < (int)c->levels.size()) CUDA_OR_FAIL(c, smoother_setup(c, l), "smoother setup");
     CUDA_OR_FAIL(c, alloc_level_vectors(c, L), "level vectors");
+    DevBSR *ops[] = {&L.A, &L.P, &L.R};
+    for (DevBSR *m : ops)
+      if (m->nnzb && want_sell(c, *m)) CUDA_OR_FAIL(c, build_sell(c, *m), "sell layout");
     if (precision != AMG_PREC_FP64) {
       CUDA_OR_FAIL(c, make_low_precision(c, L.A, precision), "low precision A");
       if (L.P.nnzb) CUDA_OR_FAIL(c, make_low_precision(c, L.P, precision), "low precision P");
@@ -440,6 +448,7 @@ int amg_galerkin(amg_ctx *h, int level, amg_bsr_out *out) {
   }
   CUDA_OR_FAIL(c, galerkin_device(c, level), "galerkin");
   Level &Cl = c->levels[level + 1];
+  if (want_sell(c, Cl.A)) CUDA_OR_FAIL(c, build_sell(c, Cl.A), "sell layout");
   if (c->precision != AMG_PREC_FP64)
     CUDA_OR_FAIL(c, make_low_precision(c, Cl.A, c->precision), "low precision A");
   if (out) {
@@ -604,11 +613,17 @@ static int pcg_one(Ctx *c, double rtol, int maxit, int *iters, double *relres) {
   CUDA_OR_FAIL(c, cudaMemcpyAsync(c->st, c->st_host, sizeof(PcgState), cudaMemcpyHostToDevice,
                                   c->stream), "pcg state");
   CUDA_OR_FAIL(c, cudaEventRecord(c->ev0, c->stream), "event");
-  CUDA_OR_FAIL(c, cudaGraphLaunch(c->graph, c->stream), "pcg graph launch");
-  CUDA_OR_FAIL(c, cudaEventRecord(c->ev1, c->stream), "event");
-  CUDA_OR_FAIL(c, cudaMemcpyAsync(c->st_host, c->st, sizeof(PcgState), cudaMemcpyDeviceToHost,
-                                  c->stream), "pcg state");
-  CUDA_OR_FAIL(c, cudaStreamSynchronize(c->stream), "pcg sync");
+  if (c->pcg_graph) {
+    CUDA_OR_FAIL(c, cudaGraphLaunch(c->graph, c->stream), "pcg graph launch");
+    CUDA_OR_FAIL(c, cudaEventRecord(c->ev1, c->stream), "event");
+    CUDA_OR_FAIL(c, cudaMemcpyAsync(c->st_host, c->st, sizeof(PcgState), cudaMemcpyDeviceToHost,
+                                    c->stream), "pcg state");
+    CUDA_OR_FAIL(c, cudaStreamSynchronize(c->stream), "pcg sync");
+  } else {
+    CUDA_OR_FAIL(c, pcg_host_loop(c), "pcg host loop");
+    CUDA_OR_FAIL(c, cudaEventRecord(c->ev1, c->stream), "event");
+    CUDA_OR_FAIL(c, cudaStreamSynchronize(c->stream), "pcg sync");
+  }
   float ms = 0.f;
   cudaEventElapsedTime(&ms, c->ev0, c->ev1);
   c->last_ms += ms;
@@ -629,7 +644,7 @@ int amg_pcg_solve(amg_ctx *h, const double *f, double *u, int nrhs, double rtol,
   if (!f || !u || nrhs < 1 || !(rtol >= 0.0) || maxit < 0)
     return fail(c, AMG_ERR_ARG, "bad arguments");
   if (c->levels[0].k != 2 && c->levels[0].k != 3) return fail(c, AMG_ERR_ARG, "A0 block size");
-  if (!c->graph) CUDA_OR_FAIL(c, pcg_build_graph(c), "pcg graph");
+  if (c->pcg_graph && !c->graph) CUDA_OR_FAIL(c, pcg_build_graph(c), "pcg graph");
   const size_t n = (size_t)c->levels[0].A.n_rows * c->levels[0].k;
   c->last_ms = 0.f;
   int worst = AMG_OK;
@@ -657,7 +672,7 @@ int amg_pcg_solve_host(amg_ctx *h, const double *f, double *u, int nrhs, double 
   if (s) return s;
   if (!f || !u || nrhs < 1 || !(rtol >= 0.0) || maxit < 0)
     return fail(c, AMG_ERR_ARG, "bad arguments");
-  if (!c->graph) CUDA_OR_FAIL(c, pcg_build_graph(c), "pcg graph");
+  if (c->pcg_graph && !c->graph) CUDA_OR_FAIL(c, pcg_build_graph(c), "pcg graph");
   const size_t n = (size_t)c->levels[0].A.n_rows * c->levels[0].k;
   c->last_ms = 0.f;
   int worst = AMG_OK;
@@ -674,6 +689,20 @@ int amg_pcg_solve_host(amg_ctx *h, const double *f, double *u, int nrhs, double 
   CUDA_OR_FAIL(c, cudaStreamSynchronize(c->stream), "pcg sync");
   if (worst != AMG_OK) return worst;
   c->err.clear();
+  return AMG_OK;
+}
+
+int amg_set_layout_policy(amg_ctx *h, int policy) {
+  if (!h) return AMG_ERR_ARG;
+  if (policy < AMG_LAYOUT_AUTO || policy > AMG_LAYOUT_WARP_ROWS)
+    return fail(&h->c, AMG_ERR_ARG, "unknown layout policy");
+  h->c.layout_policy = policy;
+  return AMG_OK;
+}
+
+int amg_set_pcg_graph(amg_ctx *h, int enable) {
+  if (!h) return AMG_ERR_ARG;
+  h->c.pcg_graph = enable != 0;
   return AMG_OK;
 }
 

@@ -22,6 +22,18 @@ struct DevBSR {
   double *v64 = nullptr;
   float *v32 = nullptr;
   __nv_bfloat16 *v16 = nullptr;
+  // SELL-32 copy for operators with many short rows (thread per block row):
+  // slice s holds rows 32s..32s+31 in slots sell_ptr[s]..sell_ptr[s+1]-1;
+  // slot j of lane t: column sell_col[j*32 + t], element q of its block at
+  // s??[(j*br*bc + q)*32 + t] (every element of a slot is one coalesced
+  // 32-wide row); padding slots have column 0 and zero values.
+  int n_slices = 0;
+  int64_t sell_slots = 0;
+  int *sell_ptr = nullptr;
+  int *sell_col = nullptr;
+  double *s64 = nullptr;
+  float *s32 = nullptr;
+  __nv_bfloat16 *s16 = nullptr;
 };
 
 struct Level {
@@ -59,6 +71,8 @@ struct Ctx {
   PcgState *st_host = nullptr;  // pinned
   double *partials = nullptr;   // reduction scratch
   unsigned *counter = nullptr;  // last-block counter
+  int layout_policy = 0;        // AMG_LAYOUT_*: which operators get the SELL-32 copy
+  bool pcg_graph = true;        // false: host-driven loop (same kernels, for profiling)
   cudaGraphExec_t graph = nullptr;
   cudaGraph_t graph_def = nullptr;
   cudaEvent_t ev0 = nullptr, ev1 = nullptr;
@@ -92,6 +106,9 @@ cudaError_t galerkin_device(Ctx *c, int level);
 cudaError_t smoother_setup(Ctx *c, int level);
 cudaError_t coarse_setup(Ctx *c);
 cudaError_t make_low_precision(Ctx *c, DevBSR &m, int prec);
+cudaError_t build_sell(Ctx *c, DevBSR &m);
+bool want_sell(const Ctx *c, const DevBSR &m);
+cudaError_t scan_exclusive(Ctx *c, int n, int *a, int *total_dev);
 
 // V-cycle on device buffers (FP64 in / out), stream-ordered.
 cudaError_t vcycle_launch(Ctx *c, const double *r, double *z);
@@ -99,6 +116,8 @@ cudaError_t vcycle_launch(Ctx *c, const double *r, double *z);
 // PCG graph
 cudaError_t pcg_build_graph(Ctx *c);
 cudaError_t pcg_alloc(Ctx *c);
+// host-driven PCG (no graph): returns the device status in *st_host
+cudaError_t pcg_host_loop(Ctx *c);
 
 }  // namespace amg
 

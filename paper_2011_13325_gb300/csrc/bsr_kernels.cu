@@ -140,10 +140,101 @@ static cudaError_t bsr_mode(const Ctx *c, const DevBSR &A, const V *vals, int mo
   return cudaGetLastError();
 }
 
+// SELL-32 variant: one thread per block row, all lanes of a warp on 32
+// consecutive rows.  Every value load of a slot is a coalesced 32-wide row,
+// no cross-lane reduction is needed, and every FP64 lane does useful work
+// (on sm_103a each FP64 warp instruction occupies the SM's FP64 pipe for
+// many cycles, so idle or reducing lanes cost as much as useful ones).
+template <int BR, int BC, typename V, typename T, int MODE>
+__global__ void __launch_bounds__(256) sell_kernel(int n_rows, int n_slices,
+                                                   const int *__restrict__ sell_ptr,
+                                                   const int *__restrict__ sell_col,
+                                                   const V *__restrict__ vals,
+                                                   const T *__restrict__ x,
+                                                   const T *__restrict__ b,
+                                                   const T *__restrict__ minv,
+                                                   T *__restrict__ y) {
+  using A = typename AccT<T>::type;
+  constexpr int E = BR * BC;
+  const int slice = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  if (slice >= n_slices) return;
+  const int t = threadIdx.x & 31;
+  const int row = slice * 32 + t;
+  const int j0 = sell_ptr[slice], j1 = sell_ptr[slice + 1];
+  A acc[BR];
+#pragma unroll
+  for (int r = 0; r < BR; ++r) acc[r] = 0;
+#pragma unroll 2
+  for (int j = j0; j < j1; ++j) {
+    const int c = __ldg(sell_col + (size_t)j * 32 + t);
+    const V *v = vals + (size_t)j * E * 32 + t;
+    A xv[BC];
+#pragma unroll
+    for (int q = 0; q < BC; ++q) xv[q] = (A)ld(x + (size_t)c * BC + q);
+#pragma unroll
+    for (int r = 0; r < BR; ++r)
+#pragma unroll
+      for (int q = 0; q < BC; ++q) acc[r] += (A)lds(v + (r * BC + q) * 32) * xv[q];
+  }
+  if (row >= n_rows) return;
+  const size_t o = (size_t)row * BR;
+  if (MODE == SPMV_SMOOTH) {
+    A res[BR];
+#pragma unroll
+    for (int r = 0; r < BR; ++r) res[r] = (A)b[o + r] - acc[r];
+#pragma unroll
+    for (int r = 0; r < BR; ++r) {
+      A u = 0;
+#pragma unroll
+      for (int q = 0; q < BR; ++q) u += (A)minv[(o + r) * BR + q] * res[q];
+      y[o + r] = (T)((A)x[o + r] + u);
+    }
+  } else {
+#pragma unroll
+    for (int r = 0; r < BR; ++r) {
+      if (MODE == SPMV_SET) y[o + r] = (T)acc[r];
+      if (MODE == SPMV_RESID) y[o + r] = (T)((A)b[o + r] - acc[r]);
+      if (MODE == SPMV_ADD) y[o + r] = (T)((A)y[o + r] + acc[r]);
+    }
+  }
+}
+
+template <int BR, int BC, typename V, typename T>
+static cudaError_t sell_mode(const Ctx *c, const DevBSR &A, const V *vals, int mode, const void *x,
+                             const void *b, const void *minv, void *y) {
+  const int g = (A.n_slices + 7) / 8;
+  const T *xx = (const T *)x;
+  const T *bb = (const T *)b;
+  const T *mm = (const T *)minv;
+  T *yy = (T *)y;
+#define AMG_SELL_LAUNCH(M_)                                                                    \
+  sell_kernel<BR, BC, V, T, M_><<<g, 256, 0, c->stream>>>(A.n_rows, A.n_slices, A.sell_ptr,  \
+                                                          A.sell_col, vals, xx, bb, mm, yy)
+  switch (mode) {
+    case SPMV_SET: AMG_SELL_LAUNCH(SPMV_SET); break;
+    case SPMV_RESID: AMG_SELL_LAUNCH(SPMV_RESID); break;
+    case SPMV_ADD: AMG_SELL_LAUNCH(SPMV_ADD); break;
+    case SPMV_SMOOTH:
+      if (BR != BC) return cudaErrorInvalidValue;
+      AMG_SELL_LAUNCH(SPMV_SMOOTH);
+      break;
+    default: return cudaErrorInvalidValue;
+  }
+#undef AMG_SELL_LAUNCH
+  return cudaGetLastError();
+}
+
 template <int BR, int BC>
 static cudaError_t bsr_prec(const Ctx *c, const DevBSR &A, int prec, int mode, const void *x,
                             const void *b, const void *minv, void *y) {
   if (A.n_rows == 0) return cudaSuccess;
+  if (A.sell_ptr) {
+    if (prec == AMG_PREC_FP64)
+      return sell_mode<BR, BC, double, double>(c, A, A.s64, mode, x, b, minv, y);
+    if (prec == AMG_PREC_FP32_VCYCLE)
+      return sell_mode<BR, BC, float, float>(c, A, A.s32, mode, x, b, minv, y);
+    return sell_mode<BR, BC, __nv_bfloat16, float>(c, A, A.s16, mode, x, b, minv, y);
+  }
   if (prec == AMG_PREC_FP64)
     return bsr_mode<BR, BC, double, double>(c, A, A.v64, mode, x, b, minv, y);
   if (prec == AMG_PREC_FP32_VCYCLE)
@@ -260,6 +351,86 @@ __global__ void to_bf16_kernel(size_t n, const double *__restrict__ s, __nv_bflo
   if (i < n) d[i] = __float2bfloat16_rn((float)s[i]);
 }
 
+// ---------------------------------------------------------------------------
+// SELL-32 construction from the BSR arrays (device)
+// ---------------------------------------------------------------------------
+
+__global__ void sell_width_kernel(int n_rows, int n_slices, const int *__restrict__ rowptr,
+                                  int *__restrict__ w) {
+  const int s = blockIdx.x * blockDim.x + threadIdx.x;
+  if (s > n_slices) return;
+  if (s == n_slices) {
+    w[s] = 0;
+    return;
+  }
+  int m = 0;
+  for (int r = s * 32; r < min(n_rows, s * 32 + 32); ++r) m = max(m, rowptr[r + 1] - rowptr[r]);
+  w[s] = m;
+}
+
+template <int E>
+__global__ void sell_fill_kernel(int n_rows, int n_slices, const int *__restrict__ rowptr,
+                                 const int *__restrict__ colidx, const double *__restrict__ vals,
+                                 const int *__restrict__ sell_ptr, int *__restrict__ sell_col,
+                                 double *__restrict__ s64) {
+  const int g = blockIdx.x * blockDim.x + threadIdx.x;
+  const int slice = g >> 5, t = g & 31;
+  if (slice >= n_slices) return;
+  const int row = slice * 32 + t;
+  const int rs = row < n_rows ? rowptr[row] : 0;
+  const int len = row < n_rows ? rowptr[row + 1] - rs : 0;
+  for (int j = sell_ptr[slice]; j < sell_ptr[slice + 1]; ++j) {
+    const int jj = j - sell_ptr[slice];
+    const bool real = jj < len;
+    sell_col[(size_t)j * 32 + t] = real ? colidx[rs + jj] : 0;
+    for (int q = 0; q < E; ++q)
+      s64[((size_t)j * E + q) * 32 + t] = real ? vals[(size_t)(rs + jj) * E + q] : 0.0;
+  }
+}
+
+bool want_sell(const Ctx *c, const DevBSR &m) {
+  // thread-per-row pays off when there are enough rows to fill the GPU with
+  // warps (>= 16 warps per SM) and the rows are short
+  const double avg = m.n_rows ? (double)m.nnzb / m.n_rows : 0.0;
+  if (c->layout_policy == AMG_LAYOUT_WARP_ROWS) return false;
+  if (c->layout_policy == AMG_LAYOUT_SELL_SHORT_ROWS) return avg <= 32.0;
+  return m.n_rows >= 32 * 16 * c->num_sms && avg <= 32.0;
+}
+
+cudaError_t build_sell(Ctx *c, DevBSR &m) {
+  const int E = m.br * m.bc;
+  dfree(m.sell_ptr);
+  dfree(m.sell_col);
+  dfree(m.s64);
+  m.sell_ptr = nullptr;
+  m.sell_col = nullptr;
+  m.s64 = nullptr;
+  m.n_slices = (m.n_rows + 31) / 32;
+  AMG_CUDA_TRY(dalloc((void **)&m.sell_ptr, (size_t)(m.n_slices + 1) * sizeof(int)));
+  int *total = nullptr;
+  AMG_CUDA_TRY(dalloc((void **)&total, sizeof(int)));
+  sell_width_kernel<<<(m.n_slices + 256) / 256, 256, 0, c->stream>>>(m.n_rows, m.n_slices, m.rowptr,
+                                                                     m.sell_ptr);
+  AMG_CUDA_TRY(cudaGetLastError());
+  AMG_CUDA_TRY(scan_exclusive(c, m.n_slices + 1, m.sell_ptr, total));
+  int slots = 0;
+  AMG_CUDA_TRY(cudaMemcpyAsync(&slots, total, sizeof(int), cudaMemcpyDeviceToHost, c->stream));
+  AMG_CUDA_TRY(cudaStreamSynchronize(c->stream));
+  dfree(total);
+  m.sell_slots = slots;
+  AMG_CUDA_TRY(dalloc((void **)&m.sell_col, (size_t)slots * 32 * sizeof(int)));
+  AMG_CUDA_TRY(dalloc((void **)&m.s64, (size_t)slots * 32 * E * sizeof(double)));
+  const int g = (m.n_slices * 32 + 255) / 256;
+#define AMG_FILL(E_)                                                                     \
+  if (E == E_)                                                                          \
+    sell_fill_kernel<E_><<<g, 256, 0, c->stream>>>(m.n_rows, m.n_slices, m.rowptr,     \
+                                                   m.colidx, m.v64, m.sell_ptr,        \
+                                                   m.sell_col, m.s64);
+  AMG_FILL(4) AMG_FILL(9) AMG_FILL(36) AMG_FILL(6) AMG_FILL(18)
+#undef AMG_FILL
+  return cudaGetLastError();
+}
+
 cudaError_t make_low_precision(Ctx *c, DevBSR &m, int prec) {
   const size_t n = (size_t)m.nnzb * m.br * m.bc;
   if (n == 0) return cudaSuccess;
@@ -270,6 +441,18 @@ cudaError_t make_low_precision(Ctx *c, DevBSR &m, int prec) {
   } else if (prec == AMG_PREC_BF16_STORAGE) {
     if (!m.v16) AMG_CUDA_TRY(dalloc((void **)&m.v16, n * sizeof(__nv_bfloat16)));
     to_bf16_kernel<<<g, 256, 0, c->stream>>>(n, m.v64, m.v16);
+  }
+  AMG_CUDA_TRY(cudaGetLastError());
+  if (m.s64) {
+    const size_t ns = (size_t)m.sell_slots * 32 * m.br * m.bc;
+    const int gs = (int)((ns + 255) / 256);
+    if (prec == AMG_PREC_FP32_VCYCLE) {
+      if (!m.s32) AMG_CUDA_TRY(dalloc((void **)&m.s32, ns * sizeof(float)));
+      to_f32_kernel<<<gs, 256, 0, c->stream>>>(ns, m.s64, m.s32);
+    } else if (prec == AMG_PREC_BF16_STORAGE) {
+      if (!m.s16) AMG_CUDA_TRY(dalloc((void **)&m.s16, ns * sizeof(__nv_bfloat16)));
+      to_bf16_kernel<<<gs, 256, 0, c->stream>>>(ns, m.s64, m.s16);
+    }
   }
   return cudaGetLastError();
 }

@@ -155,6 +155,11 @@ __global__ void __launch_bounds__(32 * kWarpsPerBlock) spgemm_numeric(
   }
 }
 
+cudaError_t scan_exclusive(Ctx *c, int n, int *a, int *total_dev) {
+  scan_exclusive_kernel<<<1, 1024, 0, c->stream>>>(n, a, total_dev);
+  return cudaGetLastError();
+}
+
 template <int BLR, int BLC, int BRC>
 static cudaError_t spgemm(Ctx *c, const DevBSR &L, const DevBSR &R, DevBSR &C) {
   C.n_rows = L.n_rows;

@@ -11,7 +11,7 @@ namespace amg {
 
 constexpr int kRedThreads = 256;
 
-static int red_grid(const Ctx *c) { return c->num_sms * 2; }
+static int red_grid(const Ctx *c) { return c->num_sms * 8; }
 
 // Block-wide sum of NV values; returns the sums in thread 0.
 template <int NV>
@@ -97,12 +97,111 @@ __device__ __forceinline__ double row_dot(int row, const int *__restrict__ rowpt
   return acc;
 }
 
+// SELL-32 row product (thread per block row): y[0..BR) = A_row . x
+template <int BR>
+__device__ __forceinline__ void sell_row(int slice, int t, const int *__restrict__ sptr,
+                                         const int *__restrict__ scol,
+                                         const double *__restrict__ sv,
+                                         const double *__restrict__ x, double (&y)[BR]) {
+  constexpr int E = BR * BR;
+#pragma unroll
+  for (int r = 0; r < BR; ++r) y[r] = 0.0;
+  const int j1 = sptr[slice + 1];
+#pragma unroll 2
+  for (int j = sptr[slice]; j < j1; ++j) {
+    const int c = __ldg(scol + (size_t)j * 32 + t);
+    const double *v = sv + (size_t)j * E * 32 + t;
+    double xv[BR];
+#pragma unroll
+    for (int q = 0; q < BR; ++q) xv[q] = __ldg(x + (size_t)c * BR + q);
+#pragma unroll
+    for (int r = 0; r < BR; ++r)
+#pragma unroll
+      for (int q = 0; q < BR; ++q) y[r] += __ldcs(v + (r * BR + q) * 32) * xv[q];
+  }
+}
+
+struct SellView {
+  int n_rows, n_slices;
+  const int *ptr, *col;
+  const double *v;
+};
+
+template <int BR>
+__global__ void __launch_bounds__(kRedThreads) pcg_init_sell_kernel(
+    SellView A, const double *f, const double *x, double *r, PcgState *st, double *partials,
+    unsigned *counter, cudaGraphConditionalHandle h, int in_graph) {
+  const int t = threadIdx.x & 31;
+  const int nw = (gridDim.x * blockDim.x) >> 5;
+  double v[2] = {0.0, 0.0};
+  for (int s = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; s < A.n_slices; s += nw) {
+    double ax[BR];
+    sell_row<BR>(s, t, A.ptr, A.col, A.v, x, ax);
+    const int row = s * 32 + t;
+    if (row < A.n_rows) {
+#pragma unroll
+      for (int q = 0; q < BR; ++q) {
+        const size_t i = (size_t)row * BR + q;
+        const double ri = f[i] - ax[q];
+        r[i] = ri;
+        v[0] += ri * ri;
+        v[1] += f[i] * f[i];
+      }
+    }
+  }
+  double tot[2];
+  if (last_block_total<2>(v, partials, counter, tot) && threadIdx.x == 0) {
+    st->rr = tot[0];
+    st->ff = tot[1];
+    st->tol2 = st->rtol * st->rtol * tot[1];
+    st->it = 0;
+    st->status = 0;
+    st->rho_old = 0.0;
+    st->alpha = 0.0;
+    st->beta = 0.0;
+    const bool go = (tot[0] > st->tol2) && (st->maxit > 0) && isfinite(tot[0]);
+    if (in_graph) cudaGraphSetConditional(h, go ? 1u : 0u);
+  }
+}
+
+template <int BR>
+__global__ void __launch_bounds__(kRedThreads) pcg_spmv_dot_sell_kernel(
+    SellView A, const double *p, double *q, PcgState *st, double *partials, unsigned *counter) {
+  const int t = threadIdx.x & 31;
+  const int nw = (gridDim.x * blockDim.x) >> 5;
+  double v[1] = {0.0};
+  for (int s = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; s < A.n_slices; s += nw) {
+    double ap[BR];
+    sell_row<BR>(s, t, A.ptr, A.col, A.v, p, ap);
+    const int row = s * 32 + t;
+    if (row < A.n_rows) {
+#pragma unroll
+      for (int c = 0; c < BR; ++c) {
+        const size_t i = (size_t)row * BR + c;
+        q[i] = ap[c];
+        v[0] += p[i] * ap[c];
+      }
+    }
+  }
+  double tot[1];
+  if (last_block_total<1>(v, partials, counter, tot) && threadIdx.x == 0) {
+    const double pq = tot[0];
+    st->pq = pq;
+    if (!(pq > 0.0) || !isfinite(pq)) {
+      st->status = AMG_ERR_NOT_SPD;
+      st->alpha = 0.0;
+    } else {
+      st->alpha = st->rho / pq;
+    }
+  }
+}
+
 // r = f - A x ; rr = r.r ; ff = f.f ; decides whether the loop starts.
 template <int BR>
 __global__ void __launch_bounds__(kRedThreads) pcg_init_kernel(
     int n_rows, const int *rowptr, const int *colidx, const double *vals, const double *f,
     const double *x, double *r, PcgState *st, double *partials, unsigned *counter,
-    cudaGraphConditionalHandle h) {
+    cudaGraphConditionalHandle h, int in_graph) {
   const int lane = threadIdx.x & 31;
   const int nwarps = (gridDim.x * blockDim.x) >> 5;
   double v[2] = {0.0, 0.0};
@@ -127,7 +226,7 @@ __global__ void __launch_bounds__(kRedThreads) pcg_init_kernel(
     st->alpha = 0.0;
     st->beta = 0.0;
     const bool go = (tot[0] > st->tol2) && (st->maxit > 0) && isfinite(tot[0]);
-    cudaGraphSetConditional(h, go ? 1u : 0u);
+    if (in_graph) cudaGraphSetConditional(h, go ? 1u : 0u);
   }
 }
 
@@ -221,12 +320,13 @@ __global__ void __launch_bounds__(kRedThreads) pcg_update_xr_kernel(
 // condition is set inside the body.  An independent guard counter bounds the
 // loop even if a reduction failed to report, and the reduction counter is
 // re-armed.
-__global__ void pcg_guard_kernel(PcgState *st, unsigned *counter, cudaGraphConditionalHandle h) {
+__global__ void pcg_guard_kernel(PcgState *st, unsigned *counter, cudaGraphConditionalHandle h,
+                                 int in_graph) {
   st->guard += 1;
   *counter = 0u;
   const bool go = (st->rr > st->tol2) && isfinite(st->rr) && (st->it < st->maxit) &&
                   (st->status == 0) && (st->guard < st->maxit);
-  cudaGraphSetConditional(h, go ? 1u : 0u);
+  if (in_graph) cudaGraphSetConditional(h, go ? 1u : 0u);
 }
 
 cudaError_t pcg_alloc(Ctx *c) {
@@ -246,17 +346,25 @@ cudaError_t pcg_alloc(Ctx *c) {
   return cudaStreamSynchronize(c->stream);
 }
 
+static SellView sell_view(const DevBSR &A) {
+  return SellView{A.n_rows, A.n_slices, A.sell_ptr, A.sell_col, A.s64};
+}
+
 template <int BR>
-static cudaError_t capture_init(Ctx *c, cudaGraphConditionalHandle h) {
+static cudaError_t launch_init(Ctx *c, cudaGraphConditionalHandle h, int in_graph) {
   const Level &L0 = c->levels[0];
-  pcg_init_kernel<BR><<<red_grid(c), kRedThreads, 0, c->stream>>>(
-      L0.A.n_rows, L0.A.rowptr, L0.A.colidx, L0.A.v64, c->f, c->x, c->r, c->st, c->partials,
-      c->counter, h);
+  if (L0.A.sell_ptr)
+    pcg_init_sell_kernel<BR><<<red_grid(c), kRedThreads, 0, c->stream>>>(
+        sell_view(L0.A), c->f, c->x, c->r, c->st, c->partials, c->counter, h, in_graph);
+  else
+    pcg_init_kernel<BR><<<red_grid(c), kRedThreads, 0, c->stream>>>(
+        L0.A.n_rows, L0.A.rowptr, L0.A.colidx, L0.A.v64, c->f, c->x, c->r, c->st, c->partials,
+        c->counter, h, in_graph);
   return cudaGetLastError();
 }
 
 template <int BR>
-static cudaError_t capture_body(Ctx *c, cudaGraphConditionalHandle h) {
+static cudaError_t launch_body(Ctx *c, cudaGraphConditionalHandle h, int in_graph) {
   const Level &L0 = c->levels[0];
   const size_t n = (size_t)L0.A.n_rows * BR;
   const int g = red_grid(c);
@@ -265,13 +373,49 @@ static cudaError_t capture_body(Ctx *c, cudaGraphConditionalHandle h) {
                                                       c->counter);
   pcg_update_p_kernel<<<(unsigned)((n + 255) / 256), 256, 0, c->stream>>>(n, c->z, c->p, c->zold,
                                                                           c->st);
-  pcg_spmv_dot_kernel<BR><<<g, kRedThreads, 0, c->stream>>>(L0.A.n_rows, L0.A.rowptr,
-                                                            L0.A.colidx, L0.A.v64, c->p, c->q,
-                                                            c->st, c->partials, c->counter);
+  if (L0.A.sell_ptr)
+    pcg_spmv_dot_sell_kernel<BR><<<g, kRedThreads, 0, c->stream>>>(sell_view(L0.A), c->p, c->q,
+                                                                   c->st, c->partials, c->counter);
+  else
+    pcg_spmv_dot_kernel<BR><<<g, kRedThreads, 0, c->stream>>>(L0.A.n_rows, L0.A.rowptr,
+                                                              L0.A.colidx, L0.A.v64, c->p, c->q,
+                                                              c->st, c->partials, c->counter);
   pcg_update_xr_kernel<<<g, kRedThreads, 0, c->stream>>>(n, c->x, c->r, c->p, c->q, c->st,
                                                          c->partials, c->counter);
-  pcg_guard_kernel<<<1, 1, 0, c->stream>>>(c->st, c->counter, h);
+  pcg_guard_kernel<<<1, 1, 0, c->stream>>>(c->st, c->counter, h, in_graph);
   return cudaGetLastError();
+}
+
+static cudaError_t capture_init(Ctx *c, int k, cudaGraphConditionalHandle h) {
+  return k == 2 ? launch_init<2>(c, h, 1) : k == 3 ? launch_init<3>(c, h, 1) : cudaErrorInvalidValue;
+}
+
+static cudaError_t capture_body(Ctx *c, int k, cudaGraphConditionalHandle h) {
+  return k == 2 ? launch_body<2>(c, h, 1) : k == 3 ? launch_body<3>(c, h, 1) : cudaErrorInvalidValue;
+}
+
+static bool host_go(const PcgState &s) {
+  return s.rr > s.tol2 && isfinite(s.rr) && s.it < s.maxit && s.status == 0 && s.guard < s.maxit;
+}
+
+// Host-driven PCG: the same kernels launched one by one, the loop condition
+// read back after every iteration (no graph; used for per-kernel profiling).
+cudaError_t pcg_host_loop(Ctx *c) {
+  const int k = c->levels[0].k;
+  if (k != 2 && k != 3) return cudaErrorInvalidValue;
+  AMG_CUDA_TRY(k == 2 ? launch_init<2>(c, 0, 0) : launch_init<3>(c, 0, 0));
+  AMG_CUDA_TRY(cudaMemcpyAsync(c->st_host, c->st, sizeof(PcgState), cudaMemcpyDeviceToHost,
+                               c->stream));
+  AMG_CUDA_TRY(cudaStreamSynchronize(c->stream));
+  bool go = c->st_host->rr > c->st_host->tol2 && c->st_host->maxit > 0 && isfinite(c->st_host->rr);
+  while (go) {
+    AMG_CUDA_TRY(k == 2 ? launch_body<2>(c, 0, 0) : launch_body<3>(c, 0, 0));
+    AMG_CUDA_TRY(cudaMemcpyAsync(c->st_host, c->st, sizeof(PcgState), cudaMemcpyDeviceToHost,
+                                 c->stream));
+    AMG_CUDA_TRY(cudaStreamSynchronize(c->stream));
+    go = host_go(*c->st_host);
+  }
+  return cudaSuccess;
 }
 
 cudaError_t pcg_build_graph(Ctx *c) {
@@ -290,8 +434,7 @@ cudaError_t pcg_build_graph(Ctx *c) {
   AMG_CUDA_TRY(cudaGraphConditionalHandleCreate(&h, g, 0, cudaGraphCondAssignDefault));
   AMG_CUDA_TRY(cudaStreamBeginCaptureToGraph(c->stream, g, nullptr, nullptr, 0,
                                              cudaStreamCaptureModeThreadLocal));
-  cudaError_t e = (k == 2) ? capture_init<2>(c, h) : (k == 3) ? capture_init<3>(c, h)
-                                                              : cudaErrorInvalidValue;
+  cudaError_t e = capture_init(c, k, h);
   cudaGraph_t cap = nullptr;
   cudaError_t e2 = cudaStreamEndCapture(c->stream, &cap);
   if (e != cudaSuccess) return e;
@@ -315,7 +458,7 @@ cudaError_t pcg_build_graph(Ctx *c) {
   cudaGraph_t body = cp.conditional.phGraph_out[0];
   AMG_CUDA_TRY(cudaStreamBeginCaptureToGraph(c->stream, body, nullptr, nullptr, 0,
                                              cudaStreamCaptureModeThreadLocal));
-  e = (k == 2) ? capture_body<2>(c, h) : (k == 3) ? capture_body<3>(c, h) : cudaErrorInvalidValue;
+  e = capture_body(c, k, h);
   e2 = cudaStreamEndCapture(c->stream, &body);
   if (e != cudaSuccess) return e;
   if (e2 != cudaSuccess) return e2;

@@ -32,14 +32,27 @@ CASES = {
 }
 
 
-@pytest.fixture(scope="module", params=sorted(CASES))
+_HIER = {}
+
+
+def _hier(name):
+    if name not in _HIER:
+        p, params = CASES[name]()
+        _HIER[name] = (p, hierarchy.setup(p, params))
+    return _HIER[name]
+
+
+# every case runs with the warp-per-row kernels and with the SELL-32 layout
+@pytest.fixture(scope="module", params=[(n, lay) for n in sorted(CASES) for lay in ("warp", "sell")],
+                ids=lambda v: f"{v[0]}-{v[1]}")
 def case(request):
     amg = _amg()
-    p, params = CASES[request.param]()
-    H = hierarchy.setup(p, params)
+    name, lay = request.param
+    p, H = _hier(name)
     ctx = amg.Context(0)
+    ctx.set_layout_policy(amg.AMG_LAYOUT_WARP_ROWS if lay == "warp" else amg.AMG_LAYOUT_SELL_SHORT_ROWS)
     ctx.upload_hierarchy(H.A[0], H.P, amg.AMG_PREC_FP64)
-    yield request.param, p, H, ctx
+    yield name, p, H, ctx
     ctx.close()
 
 
@@ -181,6 +194,7 @@ def test_mixed_precision_reaches_fp64_tolerance(case, prec):
     amg = _amg()
     name, p, H, _ = case
     ctx = amg.Context(0)
+    ctx.set_layout_policy(amg.AMG_LAYOUT_SELL_SHORT_ROWS)
     ctx.upload_hierarchy(H.A[0], H.P, prec)
     f = p.b[0]
     u = dev(np.zeros_like(f))
@@ -196,6 +210,23 @@ def test_mixed_precision_reaches_fp64_tolerance(case, prec):
     _, it64, _ = solve.pcg(H, f, rtol=1e-8)
     assert its[0] <= it64 + 10
     ctx.close()
+
+
+def test_host_loop_mode_matches_graph(case):
+    """The host-driven PCG (kernels launched one by one) gives bit-identical
+    results to the CUDA-graph PCG."""
+    name, p, H, ctx = case
+    f = dev(p.b[0])
+    u1 = dev(np.zeros(p.b[0].shape[0]))
+    u2 = dev(np.zeros(p.b[0].shape[0]))
+    _, it1, r1 = ctx.pcg_solve(f, u1, rtol=1e-8)
+    ctx.set_pcg_graph(False)
+    try:
+        _, it2, r2 = ctx.pcg_solve(f, u2, rtol=1e-8)
+    finally:
+        ctx.set_pcg_graph(True)
+    assert it1 == it2 and r1 == r2
+    assert torch.equal(u1, u2)
 
 
 def test_errors_are_reported():
