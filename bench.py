@@ -211,7 +211,12 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
     ap.add_argument("--workload", default="cube64", choices=sorted(WORKLOADS))
-    ap.add_argument("--variants", default="1,2", help="extra V-cycle precisions (1 fp32, 2 bf16)")
+    ap.add_argument("--precision", type=int, default=1, choices=[0, 1, 2],
+                    help="V-cycle precision of the timed path: 0 fp64, 1 fp32 (default), 2 bf16 "
+                         "storage; the CG is FP64 in all three")
+    ap.add_argument("--variants", default="auto",
+                    help="comma list of other precisions timed for comparison ('auto': the two "
+                         "others, '': none)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--rtol", type=float, default=1e-8)
     ap.add_argument("--pcg-mode", default="graph", choices=["graph", "host"],
@@ -245,9 +250,10 @@ def main():
     ctx = amg.Context(local, stream.cuda_stream)
     ctx.set_pcg_graph(args.pcg_mode == "graph")
     t0 = time.perf_counter()
-    ctx.setup(problem, amg.AMG_PREC_FP64)
+    ctx.setup(problem, args.precision)
     torch.cuda.synchronize()
     setup_s = time.perf_counter() - t0
+    setup_parts = {k: round(v, 2) for k, v in ctx.setup_times().items()}
     levels = []
     for l in range(ctx.n_levels):
         levels.append(ctx.level_info(l))
@@ -294,7 +300,8 @@ def main():
     ctx.residual(0, f, u, res)
     true_rel = float(torch.linalg.norm(res) / torch.linalg.norm(f))
 
-    # dominant kernel: A_0 BSR SpMV (warp per block row), events per launch
+    # A_0 SpMV (SELL-32, FP64), events per launch: FP64 on sm_103a is bound by
+    # the FP64 pipe; report flops against the live FMA probe and bytes against HBM
     x = torch.randn_like(f)
     y = torch.empty_like(f)
     for _ in range(3):
@@ -310,23 +317,37 @@ def main():
         kt.append(e0.elapsed_time(e1))
     k_ms = float(np.mean(kt))
     pk, pk_kind = peaks()
+    fp64_gflops, fp32_gflops = ctx.probe_fma_rate()
     k_bytes = spmv_bytes(levels[0])
-    achieved = k_bytes / (k_ms * 1e-3) / 1e9
+    k_flops = 2.0 * levels[0]["nnzb"] * levels[0]["block"] ** 2
+    achieved_bw = k_bytes / (k_ms * 1e-3) / 1e9
+    achieved_fl = k_flops / (k_ms * 1e-3) / 1e12
     tr = traffic_record()
-    roofline = {"bound": "hbm", "achieved": round(achieved, 1), "peak": pk["hbm_gbs"], "unit": "GB/s",
-                "frac": round(achieved / pk["hbm_gbs"], 3), "traffic": tr["bytes_per_launch"] if tr else None,
-                "kernel": "bsr_warp_kernel<3,3,f64> y = A_0 x", "bytes_per_launch": int(k_bytes),
-                "us_per_launch": round(k_ms * 1e3, 2), "peak_kind": f"{pk_kind} copy bandwidth"}
+    roofline = {"bound": "alu", "achieved": round(achieved_fl, 3),
+                "peak": round(fp64_gflops / 1e3, 3), "unit": "TFLOP/s",
+                "frac": round(achieved_fl / (fp64_gflops / 1e3), 3),
+                "traffic": tr["bytes_per_launch"] if tr else None,
+                "kernel": "sell_kernel<3,3,f64> y = A_0 x (CG SpMV operator)",
+                "flops_per_launch": int(k_flops), "bytes_per_launch": int(k_bytes),
+                "us_per_launch": round(k_ms * 1e3, 2),
+                "peak_kind": "FP64 FMA rate measured live (amg_probe_fma_rate)",
+                "hbm": {"achieved": round(achieved_bw, 1), "peak": pk["hbm_gbs"], "unit": "GB/s",
+                        "frac": round(achieved_bw / pk["hbm_gbs"], 3), "peak_kind": f"{pk_kind} copy"},
+                "fp32_peak_tflops": round(fp32_gflops / 1e3, 1)}
 
     it_mean = float(np.mean(its))
-    per_it_bytes = algorithmic_bytes_per_iteration(levels, 0)
+    per_it_bytes = algorithmic_bytes_per_iteration(levels, args.precision)
     solve_gbs = per_it_bytes * it_mean / (ms * 1e-3) / 1e9
-    launches = 1 + int(round(it_mean)) * (vcycle_launches(levels, 0) + 6)
+    launches = 1 + int(round(it_mean)) * (vcycle_launches(levels, args.precision) + 6)
 
     # precision variants (same prolongations, re-uploaded)
     variants = {}
     P_list = [ctx.download_prolongation(l) for l in range(ctx.n_levels - 1)]
-    for prec in [int(v) for v in args.variants.split(",") if v.strip()]:
+    if args.variants == "auto":
+        vlist = [p for p in (0, 1, 2) if p != args.precision]
+    else:
+        vlist = [int(v) for v in args.variants.split(",") if v.strip()]
+    for prec in vlist:
         c2 = amg.Context(local, stream.cuda_stream)
         c2.set_pcg_graph(args.pcg_mode == "graph")
         Ps = [type("P", (), dict(n_rows=n, n_cols=m, rowptr=rp, colidx=ci, vals=v))
@@ -338,7 +359,7 @@ def main():
         variants[PREC_NAMES[prec]] = {
             "ms": round(float(np.mean(tv)), 3), "iters": float(np.mean(iv)),
             "true_relres": float(torch.linalg.norm(res) / torch.linalg.norm(f)),
-            "speedup_vs_fp64": round(ms / float(np.mean(tv)), 3),
+            "ms_ratio_to_main": round(float(np.mean(tv)) / ms, 3),
             "solve_gbs": round(algorithmic_bytes_per_iteration(levels, prec) * float(np.mean(iv)) /
                                (float(np.mean(tv)) * 1e-3) / 1e9, 1)}
         c2.close()
@@ -373,15 +394,18 @@ def main():
         "metric": "AMG-PCG time-to-1e-8 (FP64 residual), 3D elasticity",
         "value": round(ms, 3), "unit": "ms", "n_gpus": ws, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": round(ms, 3), "higher_is_better": False,
-        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "scaling": "weak", "vs_baseline": None,
+        "dtype": {0: "f64", 1: "f64 CG + f32 V-cycle", 2: "f64 CG + f32 V-cycle (bf16 storage)"}[args.precision],
+        "data": "synthetic",
         "config": {"workload": args.workload, "description": WORKLOADS[args.workload],
-                   "precision": "fp64 V-cycle, fp64 CG", "rtol": args.rtol,
+                   "precision": PREC_NAMES[args.precision] + " V-cycle, fp64 CG (FP64 residual 1e-8)",
+                   "rtol": args.rtol,
                    "pcg_mode": args.pcg_mode,
                    "levels": [L["n_rows"] for L in levels],
                    "nnzb": [L["nnzb"] for L in levels],
                    "l2": "inputs larger than L2 (A_0 values 280 MB)",
                    "parallelism": f"replicas x{ws}"},
-        "iters": it_mean, "true_relres": true_rel, "setup_s": round(setup_s, 2),
+        "iters": it_mean, "true_relres": true_rel, "setup_s": round(setup_s, 2), "setup_parts": setup_parts,
         "generate_s": round(gen_s, 2), "solve_gbs": round(solve_gbs, 1),
         "bytes_per_iteration": int(per_it_bytes), "solves_per_s": round(ws * 1e3 / ms, 2),
         "wall_s_timed": round(wall, 3),

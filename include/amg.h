@@ -197,13 +197,33 @@ int amg_set_pcg_graph(amg_ctx *ctx, int enable);
  * amg_upload_hierarchy / amg_setup:
  *   AMG_LAYOUT_AUTO             SELL-32 copy (one thread per block row) for
  *                               operators with >= 16 * 32 rows per SM and at
- *                               most 32 blocks per row; warp-per-row BSR
- *                               kernels for the rest (default)
- *   AMG_LAYOUT_SELL_SHORT_ROWS  SELL-32 for every operator with short rows
- *   AMG_LAYOUT_WARP_ROWS        warp-per-row BSR kernels only
+ *                               most 32 blocks per row; BSR row-lane kernels
+ *                               (one lane per scalar row, no cross-lane
+ *                               reduction) for the rest (default)
+ *   AMG_LAYOUT_SELL_SHORT_ROWS  SELL-32 for every operator with short rows,
+ *                               row-lane kernels for the rest
+ *   AMG_LAYOUT_WARP_ROWS        warp-per-row BSR kernels only (one warp
+ *                               streams a block row, shuffle reduction)
+ *   AMG_LAYOUT_ROW_LANES        row-lane BSR kernels only
  * The result of every operator is the same up to the order of the sums. */
-enum { AMG_LAYOUT_AUTO = 0, AMG_LAYOUT_SELL_SHORT_ROWS = 1, AMG_LAYOUT_WARP_ROWS = 2 };
+enum {
+  AMG_LAYOUT_AUTO = 0,
+  AMG_LAYOUT_SELL_SHORT_ROWS = 1,
+  AMG_LAYOUT_WARP_ROWS = 2,
+  AMG_LAYOUT_ROW_LANES = 3
+};
 int amg_set_layout_policy(amg_ctx *ctx, int policy);
+
+/* Wall-clock seconds of the last amg_setup: [0] host setup (edge matrices,
+ * Algorithm 1, prolongations), [1] device Galerkin products and transfers,
+ * [2] smoothers / coarsest inverse / layouts, [3] total. */
+int amg_setup_times(const amg_ctx *ctx, double *times4);
+
+/* Measure the device's FP64 and FP32 fused-multiply-add throughput (GFLOP/s)
+ * with a short synthetic kernel (no counterpart in the paper: it provides the
+ * arithmetic peak against which the FP64 sparse kernels, bound by the FP64
+ * pipe on sm_103a, are reported).  Takes a few tens of milliseconds. */
+int amg_probe_fma_rate(amg_ctx *ctx, double *fp64_gflops, double *fp32_gflops);
 
 /* Cumulative device time (ms, CUDA events) of the last amg_pcg_solve* call. */
 int amg_last_solve_ms(const amg_ctx *ctx, float *ms);

@@ -31,6 +31,7 @@ AMG_PREC_BF16_STORAGE = 2
 AMG_LAYOUT_AUTO = 0
 AMG_LAYOUT_SELL_SHORT_ROWS = 1
 AMG_LAYOUT_WARP_ROWS = 2
+AMG_LAYOUT_ROW_LANES = 3
 AMG_SMOOTHER_L1_JACOBI = 0
 AMG_SMOOTHER_LEARNED = 1
 
@@ -95,6 +96,8 @@ _SIGS = {
     "amg_last_solve_ms": (_I, [_P, C.POINTER(C.c_float)]),
     "amg_set_pcg_graph": (_I, [_P, _I]),
     "amg_set_layout_policy": (_I, [_P, _I]),
+    "amg_probe_fma_rate": (_I, [_P, C.POINTER(C.c_double), C.POINTER(C.c_double)]),
+    "amg_setup_times": (_I, [_P, C.POINTER(C.c_double)]),
     "amg_default_setup_params": (None, [C.POINTER(amg_setup_params)]),
     "amg_setup": (_I, [_P, C.POINTER(amg_problem), C.POINTER(amg_setup_params), _I, _I]),
     "amg_prolongation_info": (_I, [_P, _I, C.POINTER(C.c_int32), C.POINTER(C.c_int32),
@@ -290,6 +293,16 @@ class Context:
         if check:
             self._check(s)
         return s, list(it), list(rr)
+
+    def setup_times(self):
+        t = (C.c_double * 4)()
+        self._check(lib().amg_setup_times(self.h, t))
+        return dict(host_s=t[0], device_s=t[1], finalize_s=t[2], total_s=t[3])
+
+    def probe_fma_rate(self):
+        a, b = C.c_double(), C.c_double()
+        self._check(lib().amg_probe_fma_rate(self.h, C.byref(a), C.byref(b)))
+        return a.value, b.value
 
     def set_layout_policy(self, policy: int):
         return self._check(lib().amg_set_layout_policy(self.h, int(policy)))

@@ -5,6 +5,7 @@
 #include <string.h>
 
 #include <algorithm>
+#include <chrono>
 #include <string>
 #include <vector>
 
@@ -287,8 +288,13 @@ static int finalize_hierarchy(Ctx *c) {
 
 // Level sink of the host setup: uploads A_0, then per level P_l, R_l and the
 // device Galerkin product, handing A_{l+1} back to the host.
+static double wall_s() {
+  return std::chrono::duration<double>(std::chrono::steady_clock::now().time_since_epoch()).count();
+}
+
 struct DeviceSink : amgsetup::LevelSink {
   Ctx *c;
+  double device_s = 0.0;
   explicit DeviceSink(Ctx *cc) : c(cc) {}
   int first(const amgsetup::HostBSR &A) override {
     c->levels.clear();
@@ -300,6 +306,12 @@ struct DeviceSink : amgsetup::LevelSink {
     return 0;
   }
   int next(int level, const amgsetup::HostBSR &P, amgsetup::HostBSR &An) override {
+    const double t0 = wall_s();
+    const int rc = next_impl(level, P, An);
+    device_s += wall_s() - t0;
+    return rc;
+  }
+  int next_impl(int level, const amgsetup::HostBSR &P, amgsetup::HostBSR &An) {
     c->levels.resize(level + 2);
     Level &L = c->levels[level];
     amg_bsr pv = {P.n_rows, P.n_cols, P.br, P.bc, (int64_t)P.colidx.size(), P.rowptr.data(),
@@ -692,9 +704,22 @@ int amg_pcg_solve_host(amg_ctx *h, const double *f, double *u, int nrhs, double 
   return AMG_OK;
 }
 
+int amg_setup_times(const amg_ctx *h, double *times4) {
+  if (!h || !times4) return AMG_ERR_ARG;
+  for (int i = 0; i < 4; ++i) times4[i] = h->c.setup_times[i];
+  return AMG_OK;
+}
+
+int amg_probe_fma_rate(amg_ctx *h, double *fp64_gflops, double *fp32_gflops) {
+  if (!h || !fp64_gflops || !fp32_gflops) return AMG_ERR_ARG;
+  Ctx *c = &h->c;
+  CUDA_OR_FAIL(c, probe_fma(c, fp64_gflops, fp32_gflops), "fma probe");
+  return finish(c, "fma probe");
+}
+
 int amg_set_layout_policy(amg_ctx *h, int policy) {
   if (!h) return AMG_ERR_ARG;
-  if (policy < AMG_LAYOUT_AUTO || policy > AMG_LAYOUT_WARP_ROWS)
+  if (policy < AMG_LAYOUT_AUTO || policy > AMG_LAYOUT_ROW_LANES)
     return fail(&h->c, AMG_ERR_ARG, "unknown layout policy");
   h->c.layout_policy = policy;
   return AMG_OK;
@@ -775,11 +800,19 @@ int amg_setup(amg_ctx *h, const amg_problem *prob, const amg_setup_params *param
   pb.vals = A.vals;
   DeviceSink sink(c);
   std::string err;
+  const double t0 = wall_s();
   if (amgsetup::build_levels(pb, prm, sink, err) != 0) {
     free_levels(c);
     return fail(c, AMG_ERR_CUDA, "amg_setup: " + err);
   }
-  return finalize_hierarchy(c);
+  const double t1 = wall_s();
+  const int rc = finalize_hierarchy(c);
+  const double t2 = wall_s();
+  c->setup_times[0] = (t1 - t0) - sink.device_s;
+  c->setup_times[1] = sink.device_s;
+  c->setup_times[2] = t2 - t1;
+  c->setup_times[3] = t2 - t0;
+  return rc;
 }
 
 int amg_prolongation_info(const amg_ctx *h, int level, int32_t *n_rows, int32_t *n_cols,

@@ -77,6 +77,7 @@ struct Ctx {
   cudaGraph_t graph_def = nullptr;
   cudaEvent_t ev0 = nullptr, ev1 = nullptr;
   float last_ms = 0.f;
+  double setup_times[4] = {0, 0, 0, 0};  // host setup, device Galerkin + transfers, finalize, total (s)
   double *hbuf = nullptr;        // pinned staging for host solves
   size_t hbuf_len = 0;
 };
@@ -112,6 +113,8 @@ cudaError_t scan_exclusive(Ctx *c, int n, int *a, int *total_dev);
 
 // V-cycle on device buffers (FP64 in / out), stream-ordered.
 cudaError_t vcycle_launch(Ctx *c, const double *r, double *z);
+
+cudaError_t probe_fma(Ctx *c, double *fp64_gflops, double *fp32_gflops);
 
 // PCG graph
 cudaError_t pcg_build_graph(Ctx *c);

@@ -140,6 +140,98 @@ static cudaError_t bsr_mode(const Ctx *c, const DevBSR &A, const V *vals, int mo
   return cudaGetLastError();
 }
 
+// Row-lane variant: BR lanes per block row (lane r owns scalar row r of the
+// block row and streams row r of each of its blocks), 32 / BR block rows per
+// warp.  The BR lanes of a block row read its blocks as contiguous
+// BR * BC-value chunks; no cross-lane reduction; 30 or 32 of 32 lanes busy.
+// Used for operators with long rows and few block rows (coarse levels,
+// restriction), where one thread per block row would leave the GPU idle.
+template <int BR, int BC, typename V, typename T, int MODE>
+__global__ void __launch_bounds__(256) bsr_rowlane_kernel(int n_rows, const int *__restrict__ rowptr,
+                                                          const int *__restrict__ colidx,
+                                                          const V *__restrict__ vals,
+                                                          const T *__restrict__ x,
+                                                          const T *__restrict__ b,
+                                                          const T *__restrict__ minv,
+                                                          T *__restrict__ y) {
+  using A = typename AccT<T>::type;
+  constexpr int G = 32 / BR;
+  const int lane = threadIdx.x & 31;
+  const int g = lane / BR;
+  const int r = lane - g * BR;
+  const int row = ((blockIdx.x * blockDim.x + threadIdx.x) >> 5) * G + g;
+  const bool active = g < G && row < n_rows;
+  A acc = 0;
+  if (active) {
+    const int e = rowptr[row + 1];
+    int p = rowptr[row];
+    for (; p + 1 < e; p += 2) {
+      const int c0 = __ldg(colidx + p), c1 = __ldg(colidx + p + 1);
+      const V *v0 = vals + ((size_t)p * BR + r) * BC;
+      const V *v1 = v0 + BR * BC;
+      A a0[BC], a1[BC];
+#pragma unroll
+      for (int q = 0; q < BC; ++q) {
+        a0[q] = (A)lds(v0 + q);
+        a1[q] = (A)lds(v1 + q);
+      }
+#pragma unroll
+      for (int q = 0; q < BC; ++q) {
+        acc += a0[q] * (A)ld(x + (size_t)c0 * BC + q);
+        acc += a1[q] * (A)ld(x + (size_t)c1 * BC + q);
+      }
+    }
+    if (p < e) {
+      const int c0 = __ldg(colidx + p);
+      const V *v0 = vals + ((size_t)p * BR + r) * BC;
+#pragma unroll
+      for (int q = 0; q < BC; ++q) acc += (A)lds(v0 + q) * (A)ld(x + (size_t)c0 * BC + q);
+    }
+  }
+  const size_t o = (size_t)row * BR;
+  if (MODE == SPMV_SMOOTH) {
+    A res = active ? (A)b[o + r] - acc : (A)0;
+    A upd = 0;
+#pragma unroll
+    for (int q = 0; q < BR; ++q) {
+      const A rq = __shfl_sync(0xffffffffu, res, (g < G ? g : 0) * BR + q);
+      if (active) upd += (A)minv[(o + r) * BR + q] * rq;
+    }
+    if (active) y[o + r] = (T)((A)x[o + r] + upd);
+  } else if (active) {
+    if (MODE == SPMV_SET) y[o + r] = (T)acc;
+    if (MODE == SPMV_RESID) y[o + r] = (T)((A)b[o + r] - acc);
+    if (MODE == SPMV_ADD) y[o + r] = (T)((A)y[o + r] + acc);
+  }
+}
+
+template <int BR, int BC, typename V, typename T>
+static cudaError_t rowlane_mode(const Ctx *c, const DevBSR &A, const V *vals, int mode,
+                                const void *x, const void *b, const void *minv, void *y) {
+  constexpr int G = 32 / BR;
+  const long warps = ((long)A.n_rows + G - 1) / G;
+  const int g = (int)((warps + 7) / 8);
+  const T *xx = (const T *)x;
+  const T *bb = (const T *)b;
+  const T *mm = (const T *)minv;
+  T *yy = (T *)y;
+#define AMG_RL_LAUNCH(M_)                                                                      \
+  bsr_rowlane_kernel<BR, BC, V, T, M_><<<g, 256, 0, c->stream>>>(A.n_rows, A.rowptr, A.colidx, \
+                                                                 vals, xx, bb, mm, yy)
+  switch (mode) {
+    case SPMV_SET: AMG_RL_LAUNCH(SPMV_SET); break;
+    case SPMV_RESID: AMG_RL_LAUNCH(SPMV_RESID); break;
+    case SPMV_ADD: AMG_RL_LAUNCH(SPMV_ADD); break;
+    case SPMV_SMOOTH:
+      if (BR != BC) return cudaErrorInvalidValue;
+      AMG_RL_LAUNCH(SPMV_SMOOTH);
+      break;
+    default: return cudaErrorInvalidValue;
+  }
+#undef AMG_RL_LAUNCH
+  return cudaGetLastError();
+}
+
 // SELL-32 variant: one thread per block row, all lanes of a warp on 32
 // consecutive rows.  Every value load of a slot is a coalesced 32-wide row,
 // no cross-lane reduction is needed, and every FP64 lane does useful work
@@ -235,11 +327,18 @@ static cudaError_t bsr_prec(const Ctx *c, const DevBSR &A, int prec, int mode, c
       return sell_mode<BR, BC, float, float>(c, A, A.s32, mode, x, b, minv, y);
     return sell_mode<BR, BC, __nv_bfloat16, float>(c, A, A.s16, mode, x, b, minv, y);
   }
+  if (c->layout_policy == AMG_LAYOUT_WARP_ROWS) {
+    if (prec == AMG_PREC_FP64)
+      return bsr_mode<BR, BC, double, double>(c, A, A.v64, mode, x, b, minv, y);
+    if (prec == AMG_PREC_FP32_VCYCLE)
+      return bsr_mode<BR, BC, float, float>(c, A, A.v32, mode, x, b, minv, y);
+    return bsr_mode<BR, BC, __nv_bfloat16, float>(c, A, A.v16, mode, x, b, minv, y);
+  }
   if (prec == AMG_PREC_FP64)
-    return bsr_mode<BR, BC, double, double>(c, A, A.v64, mode, x, b, minv, y);
+    return rowlane_mode<BR, BC, double, double>(c, A, A.v64, mode, x, b, minv, y);
   if (prec == AMG_PREC_FP32_VCYCLE)
-    return bsr_mode<BR, BC, float, float>(c, A, A.v32, mode, x, b, minv, y);
-  return bsr_mode<BR, BC, __nv_bfloat16, float>(c, A, A.v16, mode, x, b, minv, y);
+    return rowlane_mode<BR, BC, float, float>(c, A, A.v32, mode, x, b, minv, y);
+  return rowlane_mode<BR, BC, __nv_bfloat16, float>(c, A, A.v16, mode, x, b, minv, y);
 }
 
 cudaError_t launch_bsr(const Ctx *c, const DevBSR &A, int prec, int mode, const void *x,
@@ -392,7 +491,8 @@ bool want_sell(const Ctx *c, const DevBSR &m) {
   // thread-per-row pays off when there are enough rows to fill the GPU with
   // warps (>= 16 warps per SM) and the rows are short
   const double avg = m.n_rows ? (double)m.nnzb / m.n_rows : 0.0;
-  if (c->layout_policy == AMG_LAYOUT_WARP_ROWS) return false;
+  if (c->layout_policy == AMG_LAYOUT_WARP_ROWS || c->layout_policy == AMG_LAYOUT_ROW_LANES)
+    return false;
   if (c->layout_policy == AMG_LAYOUT_SELL_SHORT_ROWS) return avg <= 32.0;
   return m.n_rows >= 32 * 16 * c->num_sms && avg <= 32.0;
 }

@@ -42,15 +42,18 @@ def _hier(name):
     return _HIER[name]
 
 
-# every case runs with the warp-per-row kernels and with the SELL-32 layout
-@pytest.fixture(scope="module", params=[(n, lay) for n in sorted(CASES) for lay in ("warp", "sell")],
+LAYOUTS = {"warp": 2, "sell": 1, "rowlane": 3}
+
+
+# every case runs with each operator layout (warp per row, SELL-32, row lanes)
+@pytest.fixture(scope="module", params=[(n, lay) for n in sorted(CASES) for lay in LAYOUTS],
                 ids=lambda v: f"{v[0]}-{v[1]}")
 def case(request):
     amg = _amg()
     name, lay = request.param
     p, H = _hier(name)
     ctx = amg.Context(0)
-    ctx.set_layout_policy(amg.AMG_LAYOUT_WARP_ROWS if lay == "warp" else amg.AMG_LAYOUT_SELL_SHORT_ROWS)
+    ctx.set_layout_policy(LAYOUTS[lay])
     ctx.upload_hierarchy(H.A[0], H.P, amg.AMG_PREC_FP64)
     yield name, p, H, ctx
     ctx.close()
