@@ -21,7 +21,9 @@ import subprocess
 import sys
 import time
 
-for _v in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS"):
+# the CPU oracle runs on one core (BLAS threads off); OpenMP is left alone:
+# the library's host setup uses it
+for _v in ("OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS"):
     os.environ.setdefault(_v, "1")
 
 import numpy as np  # noqa: E402
@@ -112,8 +114,9 @@ class ClockSampler:
 
 
 def vcycle_launches(levels, prec):
-    """Kernels of one V-cycle: 5 per non-coarsest level, 1 coarsest, +2 casts."""
-    return 5 * (len(levels) - 1) + 1 + (2 if prec else 0)
+    """Kernels of one V-cycle: 5 per non-coarsest level and 1 coarsest (the
+    FP64<->FP32 casts of the mixed precisions are fused into level 0)."""
+    return 5 * (len(levels) - 1) + 1 + (2 if prec and len(levels) == 1 else 0)
 
 
 def algorithmic_bytes_per_iteration(levels, prec):
@@ -338,7 +341,7 @@ def main():
     it_mean = float(np.mean(its))
     per_it_bytes = algorithmic_bytes_per_iteration(levels, args.precision)
     solve_gbs = per_it_bytes * it_mean / (ms * 1e-3) / 1e9
-    launches = 1 + int(round(it_mean)) * (vcycle_launches(levels, args.precision) + 6)
+    launches = 1 + int(round(it_mean)) * (vcycle_launches(levels, args.precision) + 5)
 
     # precision variants (same prolongations, re-uploaded)
     variants = {}

@@ -197,14 +197,14 @@ int amg_set_pcg_graph(amg_ctx *ctx, int enable);
  * amg_upload_hierarchy / amg_setup:
  *   AMG_LAYOUT_AUTO             SELL-32 copy (one thread per block row) for
  *                               operators with >= 16 * 32 rows per SM and at
- *                               most 32 blocks per row; BSR row-lane kernels
- *                               (one lane per scalar row, no cross-lane
- *                               reduction) for the rest (default)
+ *                               most 32 blocks per row; warp-per-row BSR
+ *                               kernels (one warp streams a block row,
+ *                               shuffle reduction) for the rest (default)
  *   AMG_LAYOUT_SELL_SHORT_ROWS  SELL-32 for every operator with short rows,
- *                               row-lane kernels for the rest
- *   AMG_LAYOUT_WARP_ROWS        warp-per-row BSR kernels only (one warp
- *                               streams a block row, shuffle reduction)
- *   AMG_LAYOUT_ROW_LANES        row-lane BSR kernels only
+ *                               warp-per-row kernels for the rest
+ *   AMG_LAYOUT_WARP_ROWS        warp-per-row BSR kernels only
+ *   AMG_LAYOUT_ROW_LANES        row-lane BSR kernels only (one lane per
+ *                               scalar row of a block row, no reduction)
  * The result of every operator is the same up to the order of the sums. */
 enum {
   AMG_LAYOUT_AUTO = 0,

@@ -85,8 +85,11 @@ static const void *minv_of(const Level &L, int prec) {
   return prec == AMG_PREC_FP64 ? (const void *)L.minv64 : (const void *)L.minv32;
 }
 
-// Solve on level l: input b (level buffer or external), output y.
-static cudaError_t vcycle_level(Ctx *c, int l, const void *b, void *y) {
+// Solve on level l: input b (level buffer or external), output y.  In the
+// mixed precisions the finest level reads the FP64 residual r64 and writes
+// the FP64 result z64 directly (casts fused into its first / last kernel).
+static cudaError_t vcycle_level(Ctx *c, int l, const void *b, void *y, const double *r64 = nullptr,
+                                double *z64 = nullptr) {
   const int prec = c->precision;
   Level &L = c->levels[l];
   if (l == (int)c->levels.size() - 1) return launch_coarse_gemv(c, c->coarse_n, c->cinv, b, y, prec);
@@ -95,7 +98,10 @@ static cudaError_t vcycle_level(Ctx *c, int l, const void *b, void *y) {
   void *t = vb(L, prec, 't');
   const void *mi = minv_of(L, prec);
   // pre-smoothing from x = 0: x = M^+ b
-  AMG_CUDA_TRY(launch_blockdiag(c, L.A.n_rows, L.k, prec, mi, b, x));
+  if (r64)
+    AMG_CUDA_TRY(launch_blockdiag_entry(c, L.A.n_rows, L.k, L.minv32, r64, (float *)b, (float *)x));
+  else
+    AMG_CUDA_TRY(launch_blockdiag(c, L.A.n_rows, L.k, prec, mi, b, x));
   // residual t = b - A x
   AMG_CUDA_TRY(launch_bsr(c, L.A, prec, SPMV_RESID, x, b, nullptr, t));
   // restriction b_{l+1} = R t
@@ -105,6 +111,8 @@ static cudaError_t vcycle_level(Ctx *c, int l, const void *b, void *y) {
   // prolongation x += P e
   AMG_CUDA_TRY(launch_bsr(c, L.P, prec, SPMV_ADD, vb(Cn, prec, 'y'), nullptr, nullptr, x));
   // post-smoothing y = x + M^+ (b - A x)
+  if (z64)
+    return launch_smooth_out64(c, L.A, prec, (const float *)x, (const float *)b, L.minv32, z64);
   return launch_bsr(c, L.A, prec, SPMV_SMOOTH, x, b, mi, y);
 }
 
@@ -112,9 +120,12 @@ cudaError_t vcycle_launch(Ctx *c, const double *r, double *z) {
   if (c->precision == AMG_PREC_FP64) return vcycle_level(c, 0, r, z);
   Level &L0 = c->levels[0];
   const size_t n = (size_t)L0.A.n_rows * L0.k;
-  AMG_CUDA_TRY(launch_convert(c, n, r, AMG_PREC_FP64, L0.b32, AMG_PREC_FP32_VCYCLE));
-  AMG_CUDA_TRY(vcycle_level(c, 0, L0.b32, L0.y32));
-  return launch_convert(c, n, L0.y32, AMG_PREC_FP32_VCYCLE, z, AMG_PREC_FP64);
+  if (c->levels.size() == 1) {  // single level: the coarsest solve is FP64 anyway
+    AMG_CUDA_TRY(launch_convert(c, n, r, AMG_PREC_FP64, L0.b32, AMG_PREC_FP32_VCYCLE));
+    AMG_CUDA_TRY(vcycle_level(c, 0, L0.b32, L0.y32));
+    return launch_convert(c, n, L0.y32, AMG_PREC_FP32_VCYCLE, z, AMG_PREC_FP64);
+  }
+  return vcycle_level(c, 0, L0.b32, L0.y32, r, z);
 }
 
 }  // namespace amg

@@ -97,6 +97,10 @@ cudaError_t launch_bsr(const Ctx *c, const DevBSR &A, int prec, int mode, const 
                        const void *b, const void *minv, void *y);
 cudaError_t launch_blockdiag(const Ctx *c, int n, int k, int prec, const void *minv,
                              const void *b, void *y);
+cudaError_t launch_smooth_out64(const Ctx *c, const DevBSR &A, int prec, const float *x,
+                                const float *b, const float *minv, double *y);
+cudaError_t launch_blockdiag_entry(const Ctx *c, int n, int k, const float *minv, const double *r,
+                                   float *b, float *x);
 cudaError_t launch_coarse_gemv(const Ctx *c, int n, const double *cinv, const void *b, void *y,
                                int prec);
 cudaError_t launch_convert(const Ctx *c, size_t n, const void *src, int src_prec, void *dst,

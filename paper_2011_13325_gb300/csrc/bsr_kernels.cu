@@ -33,14 +33,88 @@ __device__ __forceinline__ float lds(const __nv_bfloat16 *p) {
   return __uint_as_float(((unsigned)u) << 16);
 }
 
-template <int BR, int BC, typename V, typename T, int MODE>
+// n consecutive values starting at p, streamed (values) or cached (vectors),
+// with the widest loads the alignment allows: a block row of BC values is
+// 2-element aligned whenever BC is even.
+template <int N, typename A>
+__device__ __forceinline__ void ldn_stream(const double *p, A *out) {
+  if (N % 2 == 0) {
+#pragma unroll
+    for (int i = 0; i < N; i += 2) {
+      const double2 v = __ldcs(reinterpret_cast<const double2 *>(p + i));
+      out[i] = (A)v.x;
+      out[i + 1] = (A)v.y;
+    }
+  } else {
+#pragma unroll
+    for (int i = 0; i < N; ++i) out[i] = (A)__ldcs(p + i);
+  }
+}
+template <int N, typename A>
+__device__ __forceinline__ void ldn_stream(const float *p, A *out) {
+  if (N % 2 == 0) {
+#pragma unroll
+    for (int i = 0; i < N; i += 2) {
+      const float2 v = __ldcs(reinterpret_cast<const float2 *>(p + i));
+      out[i] = (A)v.x;
+      out[i + 1] = (A)v.y;
+    }
+  } else {
+#pragma unroll
+    for (int i = 0; i < N; ++i) out[i] = (A)__ldcs(p + i);
+  }
+}
+template <int N, typename A>
+__device__ __forceinline__ void ldn_stream(const __nv_bfloat16 *p, A *out) {
+  if (N % 2 == 0) {
+#pragma unroll
+    for (int i = 0; i < N; i += 2) {
+      const unsigned u = __ldcs(reinterpret_cast<const unsigned *>(p + i));
+      out[i] = (A)__uint_as_float(u << 16);
+      out[i + 1] = (A)__uint_as_float(u & 0xffff0000u);
+    }
+  } else {
+#pragma unroll
+    for (int i = 0; i < N; ++i) out[i] = (A)lds(p + i);
+  }
+}
+template <int N, typename A>
+__device__ __forceinline__ void ldn_cached(const double *p, A *out) {
+  if (N % 2 == 0) {
+#pragma unroll
+    for (int i = 0; i < N; i += 2) {
+      const double2 v = __ldg(reinterpret_cast<const double2 *>(p + i));
+      out[i] = (A)v.x;
+      out[i + 1] = (A)v.y;
+    }
+  } else {
+#pragma unroll
+    for (int i = 0; i < N; ++i) out[i] = (A)__ldg(p + i);
+  }
+}
+template <int N, typename A>
+__device__ __forceinline__ void ldn_cached(const float *p, A *out) {
+  if (N % 2 == 0) {
+#pragma unroll
+    for (int i = 0; i < N; i += 2) {
+      const float2 v = __ldg(reinterpret_cast<const float2 *>(p + i));
+      out[i] = (A)v.x;
+      out[i + 1] = (A)v.y;
+    }
+  } else {
+#pragma unroll
+    for (int i = 0; i < N; ++i) out[i] = (A)__ldg(p + i);
+  }
+}
+
+template <int BR, int BC, typename V, typename T, int MODE, typename TO = T>
 __global__ void __launch_bounds__(256) bsr_warp_kernel(int n_rows, const int *__restrict__ rowptr,
                                                        const int *__restrict__ colidx,
                                                        const V *__restrict__ vals,
                                                        const T *__restrict__ x,
                                                        const T *__restrict__ b,
                                                        const T *__restrict__ minv,
-                                                       T *__restrict__ y) {
+                                                       TO *__restrict__ y) {
   using A = typename AccT<T>::type;
   constexpr int NB = 32 / BR;
   const int lane = threadIdx.x & 31;
@@ -56,25 +130,24 @@ __global__ void __launch_bounds__(256) bsr_warp_kernel(int n_rows, const int *__
       // two block steps per iteration keep more loads in flight
       for (; p + NB < e; p += 2 * NB) {
         const int c0 = __ldg(colidx + p), c1 = __ldg(colidx + p + NB);
-        const V *v0 = vals + ((size_t)p * BR + r) * BC;
-        const V *v1 = vals + ((size_t)(p + NB) * BR + r) * BC;
-        A a0[BC], a1[BC];
+        A a0[BC], a1[BC], x0[BC], x1[BC];
+        ldn_stream<BC>(vals + ((size_t)p * BR + r) * BC, a0);
+        ldn_stream<BC>(vals + ((size_t)(p + NB) * BR + r) * BC, a1);
+        ldn_cached<BC>(x + (size_t)c0 * BC, x0);
+        ldn_cached<BC>(x + (size_t)c1 * BC, x1);
 #pragma unroll
         for (int q = 0; q < BC; ++q) {
-          a0[q] = (A)lds(v0 + q);
-          a1[q] = (A)lds(v1 + q);
-        }
-#pragma unroll
-        for (int q = 0; q < BC; ++q) {
-          acc += a0[q] * (A)ld(x + (size_t)c0 * BC + q);
-          acc += a1[q] * (A)ld(x + (size_t)c1 * BC + q);
+          acc += a0[q] * x0[q];
+          acc += a1[q] * x1[q];
         }
       }
       if (p < e) {
         const int c0 = __ldg(colidx + p);
-        const V *v0 = vals + ((size_t)p * BR + r) * BC;
+        A a0[BC], x0[BC];
+        ldn_stream<BC>(vals + ((size_t)p * BR + r) * BC, a0);
+        ldn_cached<BC>(x + (size_t)c0 * BC, x0);
 #pragma unroll
-        for (int q = 0; q < BC; ++q) acc += (A)lds(v0 + q) * (A)ld(x + (size_t)c0 * BC + q);
+        for (int q = 0; q < BC; ++q) acc += a0[q] * x0[q];
       }
     }
 #pragma unroll
@@ -92,11 +165,11 @@ __global__ void __launch_bounds__(256) bsr_warp_kernel(int n_rows, const int *__
         A rq = __shfl_sync(0xffffffffu, res, q);
         if (lane < BR) upd += (A)minv[(o + lane) * BR + q] * rq;
       }
-      if (lane < BR) y[o + lane] = (T)((A)x[o + lane] + upd);
+      if (lane < BR) y[o + lane] = (TO)((A)x[o + lane] + upd);
     } else if (lane < BR) {
-      if (MODE == SPMV_SET) y[o + lane] = (T)acc;
-      if (MODE == SPMV_RESID) y[o + lane] = (T)((A)b[o + lane] - acc);
-      if (MODE == SPMV_ADD) y[o + lane] = (T)((A)y[o + lane] + acc);
+      if (MODE == SPMV_SET) y[o + lane] = (TO)acc;
+      if (MODE == SPMV_RESID) y[o + lane] = (TO)((A)b[o + lane] - acc);
+      if (MODE == SPMV_ADD) y[o + lane] = (TO)((A)y[o + lane] + acc);
     }
   }
 }
@@ -237,7 +310,7 @@ static cudaError_t rowlane_mode(const Ctx *c, const DevBSR &A, const V *vals, in
 // no cross-lane reduction is needed, and every FP64 lane does useful work
 // (on sm_103a each FP64 warp instruction occupies the SM's FP64 pipe for
 // many cycles, so idle or reducing lanes cost as much as useful ones).
-template <int BR, int BC, typename V, typename T, int MODE>
+template <int BR, int BC, typename V, typename T, int MODE, typename TO = T>
 __global__ void __launch_bounds__(256) sell_kernel(int n_rows, int n_slices,
                                                    const int *__restrict__ sell_ptr,
                                                    const int *__restrict__ sell_col,
@@ -245,7 +318,7 @@ __global__ void __launch_bounds__(256) sell_kernel(int n_rows, int n_slices,
                                                    const T *__restrict__ x,
                                                    const T *__restrict__ b,
                                                    const T *__restrict__ minv,
-                                                   T *__restrict__ y) {
+                                                   TO *__restrict__ y) {
   using A = typename AccT<T>::type;
   constexpr int E = BR * BC;
   const int slice = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
@@ -279,14 +352,14 @@ __global__ void __launch_bounds__(256) sell_kernel(int n_rows, int n_slices,
       A u = 0;
 #pragma unroll
       for (int q = 0; q < BR; ++q) u += (A)minv[(o + r) * BR + q] * res[q];
-      y[o + r] = (T)((A)x[o + r] + u);
+      y[o + r] = (TO)((A)x[o + r] + u);
     }
   } else {
 #pragma unroll
     for (int r = 0; r < BR; ++r) {
-      if (MODE == SPMV_SET) y[o + r] = (T)acc[r];
-      if (MODE == SPMV_RESID) y[o + r] = (T)((A)b[o + r] - acc[r]);
-      if (MODE == SPMV_ADD) y[o + r] = (T)((A)y[o + r] + acc[r]);
+      if (MODE == SPMV_SET) y[o + r] = (TO)acc[r];
+      if (MODE == SPMV_RESID) y[o + r] = (TO)((A)b[o + r] - acc[r]);
+      if (MODE == SPMV_ADD) y[o + r] = (TO)((A)y[o + r] + acc[r]);
     }
   }
 }
@@ -327,7 +400,7 @@ static cudaError_t bsr_prec(const Ctx *c, const DevBSR &A, int prec, int mode, c
       return sell_mode<BR, BC, float, float>(c, A, A.s32, mode, x, b, minv, y);
     return sell_mode<BR, BC, __nv_bfloat16, float>(c, A, A.s16, mode, x, b, minv, y);
   }
-  if (c->layout_policy == AMG_LAYOUT_WARP_ROWS) {
+  if (c->layout_policy != AMG_LAYOUT_ROW_LANES) {
     if (prec == AMG_PREC_FP64)
       return bsr_mode<BR, BC, double, double>(c, A, A.v64, mode, x, b, minv, y);
     if (prec == AMG_PREC_FP32_VCYCLE)
@@ -339,6 +412,71 @@ static cudaError_t bsr_prec(const Ctx *c, const DevBSR &A, int prec, int mode, c
   if (prec == AMG_PREC_FP32_VCYCLE)
     return rowlane_mode<BR, BC, float, float>(c, A, A.v32, mode, x, b, minv, y);
   return rowlane_mode<BR, BC, __nv_bfloat16, float>(c, A, A.v16, mode, x, b, minv, y);
+}
+
+// Post-smoothing of the finest level in the mixed precisions: FP32
+// arithmetic, result written as FP64 for the outer CG (saves a cast pass).
+template <int K, typename V>
+static cudaError_t smooth_out64_k(const Ctx *c, const DevBSR &A, const V *bsr_vals, const V *sell_vals,
+                                  const float *x, const float *b, const float *minv, double *y) {
+  if (A.sell_ptr) {
+    sell_kernel<K, K, V, float, SPMV_SMOOTH, double><<<(A.n_slices + 7) / 8, 256, 0, c->stream>>>(
+        A.n_rows, A.n_slices, A.sell_ptr, A.sell_col, sell_vals, x, b, minv, y);
+  } else {
+    bsr_warp_kernel<K, K, V, float, SPMV_SMOOTH, double><<<grid_for_rows(c, A.n_rows), 256, 0, c->stream>>>(
+        A.n_rows, A.rowptr, A.colidx, bsr_vals, x, b, minv, y);
+  }
+  return cudaGetLastError();
+}
+
+cudaError_t launch_smooth_out64(const Ctx *c, const DevBSR &A, int prec, const float *x,
+                                const float *b, const float *minv, double *y) {
+  if (A.n_rows == 0) return cudaSuccess;
+  if (A.br != A.bc || prec == AMG_PREC_FP64) return cudaErrorInvalidValue;
+  if (prec == AMG_PREC_FP32_VCYCLE) {
+    if (A.br == 2) return smooth_out64_k<2, float>(c, A, A.v32, A.s32, x, b, minv, y);
+    if (A.br == 3) return smooth_out64_k<3, float>(c, A, A.v32, A.s32, x, b, minv, y);
+  } else {
+    if (A.br == 2) return smooth_out64_k<2, __nv_bfloat16>(c, A, A.v16, A.s16, x, b, minv, y);
+    if (A.br == 3) return smooth_out64_k<3, __nv_bfloat16>(c, A, A.v16, A.s16, x, b, minv, y);
+  }
+  return cudaErrorInvalidValue;
+}
+
+// Pre-smoothing of the finest level in the mixed precisions: reads the FP64
+// CG residual, stores its FP32 copy b and x = M^+ b (FP32).
+template <int K>
+__global__ void blockdiag_entry_kernel(int n, const float *__restrict__ minv,
+                                       const double *__restrict__ r, float *__restrict__ b,
+                                       float *__restrict__ x) {
+  const size_t v = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (v >= (size_t)n) return;
+  float rb[K];
+#pragma unroll
+  for (int q = 0; q < K; ++q) {
+    rb[q] = (float)r[v * K + q];
+    b[v * K + q] = rb[q];
+  }
+#pragma unroll
+  for (int i = 0; i < K; ++i) {
+    float acc = 0.f;
+#pragma unroll
+    for (int q = 0; q < K; ++q) acc += minv[(v * K + i) * K + q] * rb[q];
+    x[v * K + i] = acc;
+  }
+}
+
+cudaError_t launch_blockdiag_entry(const Ctx *c, int n, int k, const float *minv, const double *r,
+                                   float *b, float *x) {
+  if (n == 0) return cudaSuccess;
+  const int g = (n + 255) / 256;
+  if (k == 2)
+    blockdiag_entry_kernel<2><<<g, 256, 0, c->stream>>>(n, minv, r, b, x);
+  else if (k == 3)
+    blockdiag_entry_kernel<3><<<g, 256, 0, c->stream>>>(n, minv, r, b, x);
+  else
+    return cudaErrorInvalidValue;
+  return cudaGetLastError();
 }
 
 cudaError_t launch_bsr(const Ctx *c, const DevBSR &A, int prec, int mode, const void *x,

@@ -11,7 +11,8 @@ namespace amg {
 
 constexpr int kRedThreads = 256;
 
-static int red_grid(const Ctx *c) { return c->num_sms * 8; }
+static int red_grid(const Ctx *c) { return c->num_sms * 8; }  // SpMV + dot kernels
+static int vec_grid(const Ctx *c) { return c->num_sms * 2; }  // pure vector reductions
 
 // Block-wide sum of NV values; returns the sums in thread 0.
 template <int NV>
@@ -369,8 +370,8 @@ static cudaError_t launch_body(Ctx *c, cudaGraphConditionalHandle h, int in_grap
   const size_t n = (size_t)L0.A.n_rows * BR;
   const int g = red_grid(c);
   AMG_CUDA_TRY(vcycle_launch(c, c->r, c->z));
-  pcg_dot_rz_kernel<<<g, kRedThreads, 0, c->stream>>>(n, c->r, c->z, c->zold, c->st, c->partials,
-                                                      c->counter);
+  pcg_dot_rz_kernel<<<vec_grid(c), kRedThreads, 0, c->stream>>>(n, c->r, c->z, c->zold, c->st,
+                                                                c->partials, c->counter);
   pcg_update_p_kernel<<<(unsigned)((n + 255) / 256), 256, 0, c->stream>>>(n, c->z, c->p, c->zold,
                                                                           c->st);
   if (L0.A.sell_ptr)
@@ -380,8 +381,8 @@ static cudaError_t launch_body(Ctx *c, cudaGraphConditionalHandle h, int in_grap
     pcg_spmv_dot_kernel<BR><<<g, kRedThreads, 0, c->stream>>>(L0.A.n_rows, L0.A.rowptr,
                                                               L0.A.colidx, L0.A.v64, c->p, c->q,
                                                               c->st, c->partials, c->counter);
-  pcg_update_xr_kernel<<<g, kRedThreads, 0, c->stream>>>(n, c->x, c->r, c->p, c->q, c->st,
-                                                         c->partials, c->counter);
+  pcg_update_xr_kernel<<<vec_grid(c), kRedThreads, 0, c->stream>>>(n, c->x, c->r, c->p, c->q,
+                                                                   c->st, c->partials, c->counter);
   pcg_guard_kernel<<<1, 1, 0, c->stream>>>(c->st, c->counter, h, in_graph);
   return cudaGetLastError();
 }
