@@ -367,13 +367,14 @@ __global__ void __launch_bounds__(256) sell_kernel(int n_rows, int n_slices,
 template <int BR, int BC, typename V, typename T>
 static cudaError_t sell_mode(const Ctx *c, const DevBSR &A, const V *vals, int mode, const void *x,
                              const void *b, const void *minv, void *y) {
-  const int g = (A.n_slices + 7) / 8;
+  // 64-thread blocks (two slices each) spread the rows evenly over the SMs
+  const int g = (A.n_slices + 1) / 2;
   const T *xx = (const T *)x;
   const T *bb = (const T *)b;
   const T *mm = (const T *)minv;
   T *yy = (T *)y;
 #define AMG_SELL_LAUNCH(M_)                                                                    \
-  sell_kernel<BR, BC, V, T, M_><<<g, 256, 0, c->stream>>>(A.n_rows, A.n_slices, A.sell_ptr,  \
+  sell_kernel<BR, BC, V, T, M_><<<g, 64, 0, c->stream>>>(A.n_rows, A.n_slices, A.sell_ptr,   \
                                                           A.sell_col, vals, xx, bb, mm, yy)
   switch (mode) {
     case SPMV_SET: AMG_SELL_LAUNCH(SPMV_SET); break;
@@ -420,7 +421,7 @@ template <int K, typename V>
 static cudaError_t smooth_out64_k(const Ctx *c, const DevBSR &A, const V *bsr_vals, const V *sell_vals,
                                   const float *x, const float *b, const float *minv, double *y) {
   if (A.sell_ptr) {
-    sell_kernel<K, K, V, float, SPMV_SMOOTH, double><<<(A.n_slices + 7) / 8, 256, 0, c->stream>>>(
+    sell_kernel<K, K, V, float, SPMV_SMOOTH, double><<<(A.n_slices + 1) / 2, 64, 0, c->stream>>>(
         A.n_rows, A.n_slices, A.sell_ptr, A.sell_col, sell_vals, x, b, minv, y);
   } else {
     bsr_warp_kernel<K, K, V, float, SPMV_SMOOTH, double><<<grid_for_rows(c, A.n_rows), 256, 0, c->stream>>>(

@@ -165,13 +165,20 @@ __global__ void __launch_bounds__(kRedThreads) pcg_init_sell_kernel(
   }
 }
 
+// q = A p and the per-block partial of p.q (64-thread blocks, two slices
+// each: fine-grained blocks balance the FP64 pipe load across SMs).  The
+// partials are summed, in block order, by the consumer (update_xr).
+constexpr int kSellThreads = 64;
+
 template <int BR>
-__global__ void __launch_bounds__(kRedThreads) pcg_spmv_dot_sell_kernel(
-    SellView A, const double *p, double *q, PcgState *st, double *partials, unsigned *counter) {
-  const int t = threadIdx.x & 31;
-  const int nw = (gridDim.x * blockDim.x) >> 5;
-  double v[1] = {0.0};
-  for (int s = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; s < A.n_slices; s += nw) {
+__global__ void __launch_bounds__(kSellThreads) pcg_spmv_dot_sell_kernel(SellView A,
+                                                                        const double *p, double *q,
+                                                                        double *partials) {
+  __shared__ double sh[kSellThreads / 32];
+  const int t = threadIdx.x & 31, w = threadIdx.x >> 5;
+  const int s = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  double v = 0.0;
+  if (s < A.n_slices) {
     double ap[BR];
     sell_row<BR>(s, t, A.ptr, A.col, A.v, p, ap);
     const int row = s * 32 + t;
@@ -180,20 +187,17 @@ __global__ void __launch_bounds__(kRedThreads) pcg_spmv_dot_sell_kernel(
       for (int c = 0; c < BR; ++c) {
         const size_t i = (size_t)row * BR + c;
         q[i] = ap[c];
-        v[0] += p[i] * ap[c];
+        v += p[i] * ap[c];
       }
     }
   }
-  double tot[1];
-  if (last_block_total<1>(v, partials, counter, tot) && threadIdx.x == 0) {
-    const double pq = tot[0];
-    st->pq = pq;
-    if (!(pq > 0.0) || !isfinite(pq)) {
-      st->status = AMG_ERR_NOT_SPD;
-      st->alpha = 0.0;
-    } else {
-      st->alpha = st->rho / pq;
-    }
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+  if (t == 0) sh[w] = v;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double b = 0.0;
+    for (int k = 0; k < kSellThreads / 32; ++k) b += sh[k];
+    partials[blockIdx.x] = b;
   }
 }
 
@@ -267,11 +271,11 @@ __global__ void pcg_update_p_kernel(size_t n, const double *z, double *p, double
   if (st->flexible) zold[i] = zi;
 }
 
-// q = A p ; pq = p.q ; alpha = rho / pq
+// q = A p ; p.q (last-block total written to *pq_out)
 template <int BR>
 __global__ void __launch_bounds__(kRedThreads) pcg_spmv_dot_kernel(
     int n_rows, const int *rowptr, const int *colidx, const double *vals, const double *p,
-    double *q, PcgState *st, double *partials, unsigned *counter) {
+    double *q, PcgState *st, double *partials, unsigned *counter, double *pq_out) {
   const int lane = threadIdx.x & 31;
   const int nwarps = (gridDim.x * blockDim.x) >> 5;
   double v[1] = {0.0};
@@ -296,37 +300,69 @@ __global__ void __launch_bounds__(kRedThreads) pcg_spmv_dot_kernel(
   }
 }
 
-// x += alpha p ; r -= alpha q ; rr = r.r
+// alpha = rho / p.q (p.q summed from the SpMV partials in block order, in
+// every block: deterministic, no atomics); x += alpha p ; r -= alpha q ;
+// per-block partials of r.r for the guard kernel.
 __global__ void __launch_bounds__(kRedThreads) pcg_update_xr_kernel(
     size_t n, double *x, double *r, const double *p, const double *q, PcgState *st,
-    double *partials, unsigned *counter) {
-  const double alpha = st->alpha;
-  double v[1] = {0.0};
+    const double *pq_partials, int n_pq, double *rr_partials) {
+  __shared__ double sh[kRedThreads / 32];
+  __shared__ double alpha_s;
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  double a = 0.0;
+  for (int b = threadIdx.x; b < n_pq; b += blockDim.x) a += pq_partials[b];
+  for (int o = 16; o > 0; o >>= 1) a += __shfl_down_sync(0xffffffffu, a, o);
+  if (lane == 0) sh[w] = a;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double pq = 0.0;
+    for (int k = 0; k < kRedThreads / 32; ++k) pq += sh[k];
+    const bool ok = (pq > 0.0) && isfinite(pq);
+    alpha_s = ok ? st->rho / pq : 0.0;
+    if (blockIdx.x == 0) {
+      st->pq = pq;
+      st->alpha = alpha_s;
+      if (!ok) st->status = AMG_ERR_NOT_SPD;
+    }
+  }
+  __syncthreads();
+  const double alpha = alpha_s;
+  double v = 0.0;
   const size_t stride = (size_t)gridDim.x * blockDim.x;
   for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) {
     x[i] += alpha * p[i];
     const double ri = r[i] - alpha * q[i];
     r[i] = ri;
-    v[0] += ri * ri;
+    v += ri * ri;
   }
-  double tot[1];
-  if (last_block_total<1>(v, partials, counter, tot) && threadIdx.x == 0) {
-    st->rr = tot[0];
-    st->it += 1;
-    if (!isfinite(tot[0]) && st->status == 0) st->status = AMG_ERR_NOT_SPD;
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+  __syncthreads();
+  if (lane == 0) sh[w] = v;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double b = 0.0;
+    for (int k = 0; k < kRedThreads / 32; ++k) b += sh[k];
+    rr_partials[blockIdx.x] = b;
   }
 }
 
-// Last node of every iteration (one thread): the only place the loop
-// condition is set inside the body.  An independent guard counter bounds the
-// loop even if a reduction failed to report, and the reduction counter is
-// re-armed.
-__global__ void pcg_guard_kernel(PcgState *st, unsigned *counter, cudaGraphConditionalHandle h,
-                                 int in_graph) {
+// Last node of every iteration (one warp): sums the r.r partials (block
+// order), counts the iteration and is the only place the loop condition is
+// set inside the body.  An independent guard counter bounds the loop, and
+// the counter of the last-block reductions is re-armed.
+__global__ void pcg_guard_kernel(PcgState *st, const double *rr_partials, int n_rr,
+                                 unsigned *counter, cudaGraphConditionalHandle h, int in_graph) {
+  double v = 0.0;
+  for (int b = threadIdx.x; b < n_rr; b += 32) v += rr_partials[b];
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+  if (threadIdx.x != 0) return;
+  st->rr = v;
+  st->it += 1;
   st->guard += 1;
   *counter = 0u;
-  const bool go = (st->rr > st->tol2) && isfinite(st->rr) && (st->it < st->maxit) &&
-                  (st->status == 0) && (st->guard < st->maxit);
+  if (!isfinite(v) && st->status == 0) st->status = AMG_ERR_NOT_SPD;
+  const bool go = (v > st->tol2) && isfinite(v) && (st->it < st->maxit) && (st->status == 0) &&
+                  (st->guard < st->maxit);
   if (in_graph) cudaGraphSetConditional(h, go ? 1u : 0u);
 }
 
@@ -341,7 +377,9 @@ cudaError_t pcg_alloc(Ctx *c) {
   }
   AMG_CUDA_TRY(dalloc((void **)&c->st, sizeof(PcgState)));
   AMG_CUDA_TRY(cudaMallocHost((void **)&c->st_host, sizeof(PcgState)));
-  AMG_CUDA_TRY(dalloc((void **)&c->partials, 4 * (size_t)red_grid(c) * sizeof(double)));
+  const int n_slices = (c->levels[0].A.n_rows + 31) / 32;
+  const size_t npart = 4 * (size_t)red_grid(c) + (size_t)(n_slices + 1) / 2 + 2 * (size_t)vec_grid(c);
+  AMG_CUDA_TRY(dalloc((void **)&c->partials, npart * sizeof(double)));
   AMG_CUDA_TRY(dalloc((void **)&c->counter, sizeof(unsigned)));
   AMG_CUDA_TRY(cudaMemsetAsync(c->counter, 0, sizeof(unsigned), c->stream));
   return cudaStreamSynchronize(c->stream);
@@ -368,22 +406,32 @@ template <int BR>
 static cudaError_t launch_body(Ctx *c, cudaGraphConditionalHandle h, int in_graph) {
   const Level &L0 = c->levels[0];
   const size_t n = (size_t)L0.A.n_rows * BR;
-  const int g = red_grid(c);
+  const int g = red_grid(c), gv = vec_grid(c);
+  // partial buffers: [0, 4g) last-block reductions, then p.q, then r.r
+  double *pq_part = c->partials + 4 * (size_t)g;
+  int n_pq;
   AMG_CUDA_TRY(vcycle_launch(c, c->r, c->z));
-  pcg_dot_rz_kernel<<<vec_grid(c), kRedThreads, 0, c->stream>>>(n, c->r, c->z, c->zold, c->st,
-                                                                c->partials, c->counter);
+  pcg_dot_rz_kernel<<<gv, kRedThreads, 0, c->stream>>>(n, c->r, c->z, c->zold, c->st, c->partials,
+                                                       c->counter);
   pcg_update_p_kernel<<<(unsigned)((n + 255) / 256), 256, 0, c->stream>>>(n, c->z, c->p, c->zold,
                                                                           c->st);
-  if (L0.A.sell_ptr)
-    pcg_spmv_dot_sell_kernel<BR><<<g, kRedThreads, 0, c->stream>>>(sell_view(L0.A), c->p, c->q,
-                                                                   c->st, c->partials, c->counter);
-  else
+  if (L0.A.sell_ptr) {
+    n_pq = (L0.A.n_slices + 1) / 2;
+    pcg_spmv_dot_sell_kernel<BR><<<n_pq, kSellThreads, 0, c->stream>>>(sell_view(L0.A), c->p,
+                                                                       c->q, pq_part);
+  } else {
+    // warp-per-row SpMV + dot with a last-block total: its block partial
+    // array holds the single total (n_pq = 1)
+    n_pq = 1;
     pcg_spmv_dot_kernel<BR><<<g, kRedThreads, 0, c->stream>>>(L0.A.n_rows, L0.A.rowptr,
                                                               L0.A.colidx, L0.A.v64, c->p, c->q,
-                                                              c->st, c->partials, c->counter);
-  pcg_update_xr_kernel<<<vec_grid(c), kRedThreads, 0, c->stream>>>(n, c->x, c->r, c->p, c->q,
-                                                                   c->st, c->partials, c->counter);
-  pcg_guard_kernel<<<1, 1, 0, c->stream>>>(c->st, c->counter, h, in_graph);
+                                                              c->st, c->partials, c->counter,
+                                                              pq_part);
+  }
+  double *rr_part = pq_part + (size_t)(L0.A.n_slices + 1) / 2 + 1;
+  pcg_update_xr_kernel<<<gv, kRedThreads, 0, c->stream>>>(n, c->x, c->r, c->p, c->q, c->st,
+                                                          pq_part, n_pq, rr_part);
+  pcg_guard_kernel<<<1, 32, 0, c->stream>>>(c->st, rr_part, gv, c->counter, h, in_graph);
   return cudaGetLastError();
 }
 
