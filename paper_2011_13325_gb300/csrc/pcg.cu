@@ -288,16 +288,7 @@ __global__ void __launch_bounds__(kRedThreads) pcg_spmv_dot_kernel(
     }
   }
   double tot[1];
-  if (last_block_total<1>(v, partials, counter, tot) && threadIdx.x == 0) {
-    const double pq = tot[0];
-    st->pq = pq;
-    if (!(pq > 0.0) || !isfinite(pq)) {
-      st->status = AMG_ERR_NOT_SPD;
-      st->alpha = 0.0;
-    } else {
-      st->alpha = st->rho / pq;
-    }
-  }
+  if (last_block_total<1>(v, partials, counter, tot) && threadIdx.x == 0) *pq_out = tot[0];
 }
 
 // alpha = rho / p.q (p.q summed from the SpMV partials in block order, in
