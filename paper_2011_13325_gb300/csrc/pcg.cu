@@ -291,14 +291,13 @@ __global__ void __launch_bounds__(kRedThreads) pcg_spmv_dot_kernel(
   if (last_block_total<1>(v, partials, counter, tot) && threadIdx.x == 0) *pq_out = tot[0];
 }
 
-// alpha = rho / p.q (p.q summed from the SpMV partials in block order, in
-// every block: deterministic, no atomics); x += alpha p ; r -= alpha q ;
-// per-block partials of r.r for the guard kernel.
-__global__ void __launch_bounds__(kRedThreads) pcg_update_xr_kernel(
-    size_t n, double *x, double *r, const double *p, const double *q, PcgState *st,
-    const double *pq_partials, int n_pq, double *rr_partials) {
-  __shared__ double sh[kRedThreads / 32];
-  __shared__ double alpha_s;
+// p.q from the SpMV's per-block partials (one block, fixed order:
+// deterministic, no atomics) and alpha = rho / p.q.
+constexpr int kFinThreads = 1024;
+__global__ void __launch_bounds__(kFinThreads) pcg_alpha_kernel(PcgState *st,
+                                                                const double *pq_partials,
+                                                                int n_pq) {
+  __shared__ double sh[kFinThreads / 32];
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
   double a = 0.0;
   for (int b = threadIdx.x; b < n_pq; b += blockDim.x) a += pq_partials[b];
@@ -307,17 +306,21 @@ __global__ void __launch_bounds__(kRedThreads) pcg_update_xr_kernel(
   __syncthreads();
   if (threadIdx.x == 0) {
     double pq = 0.0;
-    for (int k = 0; k < kRedThreads / 32; ++k) pq += sh[k];
+    for (int k = 0; k < kFinThreads / 32; ++k) pq += sh[k];
     const bool ok = (pq > 0.0) && isfinite(pq);
-    alpha_s = ok ? st->rho / pq : 0.0;
-    if (blockIdx.x == 0) {
-      st->pq = pq;
-      st->alpha = alpha_s;
-      if (!ok) st->status = AMG_ERR_NOT_SPD;
-    }
+    st->pq = pq;
+    st->alpha = ok ? st->rho / pq : 0.0;
+    if (!ok) st->status = AMG_ERR_NOT_SPD;
   }
-  __syncthreads();
-  const double alpha = alpha_s;
+}
+
+// x += alpha p ; r -= alpha q ; per-block partials of r.r for the guard.
+__global__ void __launch_bounds__(kRedThreads) pcg_update_xr_kernel(
+    size_t n, double *x, double *r, const double *p, const double *q, const PcgState *st,
+    double *rr_partials) {
+  __shared__ double sh[kRedThreads / 32];
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  const double alpha = st->alpha;
   double v = 0.0;
   const size_t stride = (size_t)gridDim.x * blockDim.x;
   for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) {
@@ -327,7 +330,6 @@ __global__ void __launch_bounds__(kRedThreads) pcg_update_xr_kernel(
     v += ri * ri;
   }
   for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
-  __syncthreads();
   if (lane == 0) sh[w] = v;
   __syncthreads();
   if (threadIdx.x == 0) {
@@ -420,8 +422,9 @@ static cudaError_t launch_body(Ctx *c, cudaGraphConditionalHandle h, int in_grap
                                                               pq_part);
   }
   double *rr_part = pq_part + (size_t)(L0.A.n_slices + 1) / 2 + 1;
+  pcg_alpha_kernel<<<1, kFinThreads, 0, c->stream>>>(c->st, pq_part, n_pq);
   pcg_update_xr_kernel<<<gv, kRedThreads, 0, c->stream>>>(n, c->x, c->r, c->p, c->q, c->st,
-                                                          pq_part, n_pq, rr_part);
+                                                          rr_part);
   pcg_guard_kernel<<<1, 32, 0, c->stream>>>(c->st, rr_part, gv, c->counter, h, in_graph);
   return cudaGetLastError();
 }

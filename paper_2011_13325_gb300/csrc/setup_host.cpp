@@ -14,8 +14,12 @@
 #include <stdint.h>
 #include <string.h>
 
+#include <stdio.h>
+#include <stdlib.h>
+
 #include <algorithm>
 #include <array>
+#include <chrono>
 #include <unordered_map>
 #include <vector>
 
@@ -1017,6 +1021,10 @@ static void smoothed_prolongation(const HostBSR &A, const Topo &T, const Coarsen
 
 // ------------------------------------------------------------------ level loop
 
+static double now_s() {
+  return std::chrono::duration<double>(std::chrono::steady_clock::now().time_since_epoch()).count();
+}
+
 int build_levels(const Problem &prob, const SetupParams &prm, LevelSink &sink, std::string &err) {
   const int d = prob.dim, n_all = prob.n_vertices;
   if (d != 2 && d != 3) {
@@ -1053,10 +1061,16 @@ int build_levels(const Problem &prob, const SetupParams &prm, LevelSink &sink, s
   const int cmax = prm.coarse_max > 0 ? prm.coarse_max
                                       : std::min(1000, std::max(64, (int)ceil(n0 / 1e4)));
   std::vector<char> bad_exact(A.n_rows, 0);
+  // AMG_SETUP_VERBOSE=1 prints the host time of every setup stage to stderr
+  const bool verbose = getenv("AMG_SETUP_VERBOSE") != nullptr;
   int level = 0;
   while (A.n_rows > cmax && level + 1 < prm.max_levels) {
     const bool first = level == 0;
+    double t0 = now_s();
     Coarsening cs = successive_matching(T, prm, first ? prm.passes_first : prm.passes_later);
+    if (verbose)
+      fprintf(stderr, "[amg setup] level %d: %d vertices -> %d agglomerates, matching %.2f s\n",
+              level, T.n, cs.nc, now_s() - t0);
     if (cs.nc == 0 || A.n_rows < prm.min_ratio * cs.nc) break;
     std::vector<char> bad(A.n_rows, 0);
     for (int r = 0; r < A.n_rows; ++r) {
@@ -1071,7 +1085,11 @@ int build_levels(const Problem &prob, const SetupParams &prm, LevelSink &sink, s
     }
     HostBSR P;
     std::vector<char> next_bad;
+    t0 = now_s();
     smoothed_prolongation(A, T, cs, rowmap, bad, first, prm, P, next_bad);
+    if (verbose)
+      fprintf(stderr, "[amg setup] level %d: prolongation %.2f s (%zu blocks)\n", level, now_s() - t0,
+              P.colidx.size());
     HostBSR Anext;
     if (sink.next(level, P, Anext) != 0) {
       err = "device Galerkin product failed";
