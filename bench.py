@@ -341,7 +341,7 @@ def main():
     it_mean = float(np.mean(its))
     per_it_bytes = algorithmic_bytes_per_iteration(levels, args.precision)
     solve_gbs = per_it_bytes * it_mean / (ms * 1e-3) / 1e9
-    launches = 1 + int(round(it_mean)) * (vcycle_launches(levels, args.precision) + 5)
+    launches = 1 + int(round(it_mean)) * (vcycle_launches(levels, args.precision) + 6)
 
     # precision variants (same prolongations, re-uploaded)
     variants = {}
