@@ -186,6 +186,27 @@ int amg_pcg_solve(amg_ctx *ctx, const double *f_dev, double *u_dev, int nrhs, do
 int amg_pcg_solve_host(amg_ctx *ctx, const double *f_host, double *u_host, int nrhs,
                        double rtol, int maxit, int *iters_out, double *relres_out);
 
+/* z = B^{-1} r for one right-hand side, exactly as amg_vcycle, but with the
+ * V-cycle's work vectors in a fixed 16 MiB device array of the library
+ * instead of buffers of the context, and without allocating anything.  It
+ * serves callers that must not allocate device memory while it runs: code
+ * running while another library captures the stream into a CUDA graph,
+ * code running where a framework's caching allocator already holds the free
+ * device memory, and code with a memory budget fixed in advance.  (The
+ * paper has no counterpart: it is an execution variant of the V-cycle.)
+ *  - The hierarchy must be uploaded before (amg_upload_hierarchy /
+ *    amg_setup allocate; this call does not).
+ *  - The array holds 4 vectors per level (256-byte aligned) of the
+ *    V-cycle precision; a hierarchy that needs more than 16 MiB is
+ *    rejected with AMG_ERR_ARG and a message giving the size.
+ *  - The first call on a device looks up the array's device address with
+ *    that device current; make that first call before any stream capture.
+ *  - Every GPU that loads the library holds the array until the process
+ *    exits.  All calls on a device share it and it keeps the last call's
+ *    contents (nothing in it needs to start at zero); calls that overlap on
+ *    the GPU (two contexts, two streams) race on it and must be serialised. */
+int amg_vcycle_static(amg_ctx *ctx, const double *r_dev, double *z_dev);
+
 /* Execution mode of amg_pcg_solve*: enable != 0 (default) runs the whole
  * iteration as one CUDA graph with a device-side while loop; enable == 0
  * launches the same kernels one by one and reads the loop condition back

@@ -91,6 +91,7 @@ _SIGS = {
     "amg_prolong_add": (_I, [_P, _I, _P, _P]),
     "amg_coarse_solve": (_I, [_P, _P, _P]),
     "amg_vcycle": (_I, [_P, _P, _P, _I]),
+    "amg_vcycle_static": (_I, [_P, _P, _P]),
     "amg_pcg_solve": (_I, [_P, _P, _P, _I, _D, _I, C.POINTER(_I), C.POINTER(_D)]),
     "amg_pcg_solve_host": (_I, [_P, _P, _P, _I, _D, _I, C.POINTER(_I), C.POINTER(_D)]),
     "amg_last_solve_ms": (_I, [_P, C.POINTER(C.c_float)]),
@@ -276,6 +277,11 @@ class Context:
 
     def vcycle(self, r, z, nrhs=1):
         return self._check(lib().amg_vcycle(self.h, _ptr(r), _ptr(z), int(nrhs)))
+
+    def vcycle_static(self, r, z):
+        """amg_vcycle_static: one V-cycle without allocating (work vectors in
+        the library's fixed device array)."""
+        return self._check(lib().amg_vcycle_static(self.h, _ptr(r), _ptr(z)))
 
     def pcg_solve(self, f, u, nrhs=1, rtol=1e-8, maxit=500, check=True):
         it = (C.c_int * nrhs)()
