@@ -21,10 +21,10 @@ import subprocess
 import sys
 import time
 
-# the CPU oracle runs on one core (BLAS threads off); OpenMP is left alone:
-# the library's host setup uses it
-for _v in ("OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS"):
-    os.environ.setdefault(_v, "1")
+# No thread-count variables are set here: on the Arm machine OpenBLAS's
+# OPENBLAS_NUM_THREADS=1 also pins the process-wide OpenMP thread count,
+# which the library's host setup uses.  The CPU oracle's solve phase is
+# single-threaded anyway (scipy.sparse products, numpy element-wise ops).
 
 import numpy as np  # noqa: E402
 
