@@ -316,6 +316,43 @@ int amg_prolongation_info(const amg_ctx *ctx, int level, int32_t *n_rows, int32_
 int amg_download_prolongation(amg_ctx *ctx, int level, int32_t *rowptr, int32_t *colidx,
                               double *vals);
 
+/* ------------------------------------------------------------------------
+ * Batched solve: many independent systems, several load cases each
+ * ---------------------------------------------------------------------- */
+
+typedef struct amg_batch amg_batch;
+
+/* Group n_systems contexts (each with an uploaded hierarchy, all on one
+ * device and with one V-cycle precision) for batched solves with nrhs load
+ * cases per system (nrhs = 1 or 6).  The contexts must outlive the batch and
+ * must not be re-uploaded while it exists.  The batch allocates its own
+ * multi-load-case work vectors and builds ONE CUDA graph in which every
+ * system is an independent branch: the system's FP64 PCG (Sec. 7) over its
+ * nrhs load cases runs in its own device-side while loop, preconditioned by
+ * the V-cycle applied to all load cases at once (every matrix block read
+ * serves all of them).  Errors: AMG_ERR_ARG, AMG_ERR_STATE (a context
+ * without hierarchy), AMG_ERR_CUDA. */
+int amg_batch_create(amg_batch **batch, amg_ctx *const *systems, int n_systems, int nrhs);
+void amg_batch_destroy(amg_batch *batch);
+const char *amg_batch_last_error(const amg_batch *batch);
+
+/* Layout of the stacked vectors: system s occupies [offset, offset +
+ * nrhs * n_dofs) with its nrhs load cases one after another (each n_dofs
+ * long); *total is the full length.  Any pointer may be NULL. */
+int amg_batch_layout(const amg_batch *batch, int s, int64_t *offset, int64_t *n_dofs,
+                     int64_t *total);
+
+/* Solve all systems and load cases with one graph launch.  f_dev / u_dev
+ * are stacked device vectors (amg_batch_layout); u_dev holds the initial
+ * guesses and receives the solutions.  Every load case stops when its
+ * recurrence residual reaches rtol * ||f|| (it is then frozen) or after
+ * maxit iterations.  iters_out / relres_out (n_systems * nrhs, may be NULL)
+ * receive per load case the iterations and final relative residual, ms_out
+ * the device time of the graph.  AMG_ERR_NO_CONVERGENCE / AMG_ERR_NOT_SPD
+ * if some load case failed. */
+int amg_batch_pcg_solve(amg_batch *batch, const double *f_dev, double *u_dev, double rtol,
+                        int maxit, int *iters_out, double *relres_out, float *ms_out);
+
 #ifdef __cplusplus
 }
 #endif

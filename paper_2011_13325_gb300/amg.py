@@ -104,6 +104,13 @@ _SIGS = {
     "amg_prolongation_info": (_I, [_P, _I, C.POINTER(C.c_int32), C.POINTER(C.c_int32),
                                    C.POINTER(C.c_int32), C.POINTER(C.c_int32), C.POINTER(C.c_int64)]),
     "amg_download_prolongation": (_I, [_P, _I, _P, _P, _P]),
+    "amg_batch_create": (_I, [C.POINTER(_P), C.POINTER(_P), _I, _I]),
+    "amg_batch_destroy": (None, [_P]),
+    "amg_batch_last_error": (C.c_char_p, [_P]),
+    "amg_batch_layout": (_I, [_P, _I, C.POINTER(C.c_int64), C.POINTER(C.c_int64),
+                              C.POINTER(C.c_int64)]),
+    "amg_batch_pcg_solve": (_I, [_P, _P, _P, _D, _I, C.POINTER(_I), C.POINTER(_D),
+                                 C.POINTER(C.c_float)]),
 }
 
 
@@ -320,3 +327,46 @@ class Context:
         ms = C.c_float()
         self._check(lib().amg_last_solve_ms(self.h, C.byref(ms)))
         return ms.value
+
+
+class Batch:
+    """amg_batch: independent systems (Contexts with uploaded hierarchies),
+    nrhs load cases each, solved by one graph launch."""
+
+    def __init__(self, contexts, nrhs=6):
+        self.contexts = list(contexts)          # keep them alive
+        self.nrhs = int(nrhs)
+        arr = (_P * len(self.contexts))(*[c.h for c in self.contexts])
+        self.h = _P()
+        s = lib().amg_batch_create(C.byref(self.h), arr, len(self.contexts), self.nrhs)
+        if s != AMG_OK:
+            raise AmgError(s, "amg_batch_create failed")
+
+    def close(self):
+        if self.h:
+            lib().amg_batch_destroy(self.h)
+            self.h = _P()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def layout(self, s):
+        o, n, t = C.c_int64(), C.c_int64(), C.c_int64()
+        st = lib().amg_batch_layout(self.h, int(s), C.byref(o), C.byref(n), C.byref(t))
+        if st != AMG_OK:
+            raise AmgError(st, "amg_batch_layout")
+        return o.value, n.value, t.value
+
+    def pcg_solve(self, f, u, rtol=1e-8, maxit=500, check=True):
+        m = len(self.contexts) * self.nrhs
+        it = (C.c_int * m)()
+        rr = (C.c_double * m)()
+        ms = C.c_float()
+        s = lib().amg_batch_pcg_solve(self.h, _ptr(f), _ptr(u), float(rtol), int(maxit), it, rr,
+                                      C.byref(ms))
+        if check and s != AMG_OK:
+            raise AmgError(s, lib().amg_batch_last_error(self.h).decode())
+        return s, list(it), list(rr), ms.value
