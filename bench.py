@@ -40,6 +40,9 @@ WORKLOADS = {
                  "clamped x=0, body force (0,-1); 2,112 dofs, 2x2 BSR"),
     "cube128jump": ("3D P1 elasticity, 128^3 vertices, 200 inclusion boxes E=10^U(-3,3), "
                     "nu U[0.25,0.45] (seed 3); 6.24M dofs"),
+    "batch64": ("64 independent 3D P1 elasticity boxes, vertices per axis U{16..48}, h=1/32, "
+                "E U[0.1,10], nu U[0.2,0.4] per system (seed 4), clamped x=0, 6 load cases "
+                "(unit body forces +-x, +-y, +-z) each"),
 }
 PREC_NAMES = {0: "fp64", 1: "fp32_vcycle", 2: "bf16_storage"}
 
@@ -119,35 +122,38 @@ def vcycle_launches(levels, prec):
     return 5 * (len(levels) - 1) + 1 + (2 if prec and len(levels) == 1 else 0)
 
 
-def algorithmic_bytes_per_iteration(levels, prec):
+def algorithmic_bytes_per_iteration(levels, prec, nr=1):
     """Bytes one PCG iteration must move at least once (matrices, smoother
-    blocks, vectors), from the actual level sizes."""
+    blocks, vectors), from the actual level sizes; with nr load cases solved
+    together the operators are read once and the vectors nr times."""
     w = {0: 8, 1: 4, 2: 2}[prec]          # matrix value bytes
     wv = 8 if prec == 0 else 4            # V-cycle vector / smoother bytes
     n0, k0 = levels[0]["n_rows"], levels[0]["block"]
     N0 = n0 * k0
     A0 = levels[0]["nnzb"] * (k0 * k0 * 8 + 4) + 4 * (n0 + 1)
-    total = A0 + N0 * 8 * 2                            # q = A p (p read, q written)
-    total += N0 * 8 * 2 + N0 * 8 * 3 + N0 * 8 * 6      # dots and updates
+    mat = A0
+    vec = N0 * 8 * 2                                   # q = A p (p read, q written)
+    vec += N0 * 8 * 2 + N0 * 8 * 3 + N0 * 8 * 6        # dots and updates
     for l, L in enumerate(levels):
         n, k = L["n_rows"], L["block"]
         N = n * k
         if l == len(levels) - 1:
-            total += (N * N) * 8 + 2 * N * wv
+            mat += (N * N) * 8
+            vec += 2 * N * wv
             continue
         Ab = L["nnzb"] * (k * k * w + 4) + 4 * (n + 1)
         kc = levels[l + 1]["block"]
         Pb = L["nnzb_P"] * (k * kc * w + 4) + 4 * (n + 1)
         Rb = L["nnzb_P"] * (k * kc * w + 4) + 4 * (levels[l + 1]["n_rows"] + 1)
         Mb = n * k * k * wv
-        total += Mb + 2 * N * wv                    # x = M b
-        total += Ab + 3 * N * wv                    # t = b - A x
-        total += Rb + N * wv + levels[l + 1]["n_rows"] * kc * wv
-        total += Pb + levels[l + 1]["n_rows"] * kc * wv + 2 * N * wv
-        total += Ab + Mb + 3 * N * wv               # y = x + M(b - A x)
+        Nc = levels[l + 1]["n_rows"] * kc
+        mat += 2 * Mb + 2 * Ab + Rb + Pb
+        vec += 2 * N * wv + 3 * N * wv              # x = M b ; t = b - A x
+        vec += N * wv + Nc * wv + Nc * wv + 2 * N * wv   # restriction, prolongation
+        vec += 3 * N * wv                           # y = x + M(b - A x)
     if prec:
-        total += N0 * (8 + 4) * 2
-    return total
+        vec += N0 * (8 + 4) * 2
+    return mat + nr * vec
 
 
 def spmv_bytes(L):
@@ -225,9 +231,14 @@ def main():
     ap.add_argument("--pcg-mode", default="graph", choices=["graph", "host"],
                     help="graph: whole PCG in one CUDA graph (default); host: the same kernels "
                          "launched one by one (per-kernel view for profilers)")
+    ap.add_argument("--systems", type=int, default=64,
+                    help="batch64: number of systems (the workload has 64)")
     args = ap.parse_args()
     if args.warmup < 3:
         raise SystemExit("--warmup must be >= 3")
+    if args.workload == "batch64":
+        # the 64 meshes are generated in a spawn pool before any CUDA call
+        problems = batch_problems(args.systems)
 
     import torch
     ws, rank, local = dist_env()
@@ -236,7 +247,11 @@ def main():
         torch.cuda.set_device(local)
         dist.init_process_group("nccl", device_id=torch.device("cuda", local))
     if args.impl == "reference":
+        if args.workload == "batch64":
+            return run_reference_batch(args, ws, rank, local, problems)
         return run_reference(args, ws, rank, local)
+    if args.workload == "batch64":
+        return run_batch(args, ws, rank, local, problems)
 
     from paper_2011_13325_gb300 import amg
     torch.cuda.set_device(local)
@@ -458,6 +473,270 @@ def run_reference(args, ws, rank, local):
             "cpu_baseline": {"value": round(v, 1), "unit": "ms", "cores": 1, "kind": "oracle",
                              "sample": f"each step: oracle PCG iterations for ~{budget:.0f} s, "
                                        f"scaled to {its[0]} iterations"},
+            "e2e": {"value": round(v, 1), "unit": "ms", "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    if ws > 1:
+        torch.distributed.destroy_process_group()
+
+
+# ---------------------------------------------------------------------------
+# batched workload: 64 systems x 6 load cases, one graph launch per step
+# ---------------------------------------------------------------------------
+
+def _batch_problem(spec):
+    from workloads import configs
+    return configs.batch_problem(spec)
+
+
+def batch_problems(n_systems):
+    import multiprocessing as mp
+    from workloads import configs
+    specs = configs.batch_specs(64)[:n_systems]
+    with mp.get_context("spawn").Pool(min(16, os.cpu_count() or 1)) as pool:
+        return pool.map(_batch_problem, specs, chunksize=1)
+
+
+def batch_setup(amg, problems, prec, local):
+    """Library setup of every system, side by side on the host cores (one
+    OpenMP thread per setup); returns the contexts and their prolongations."""
+    from concurrent.futures import ThreadPoolExecutor
+    ctxs = [amg.Context(local) for _ in problems]
+
+    def one(i):
+        ctxs[i].setup(problems[i], prec, host_threads=1)
+        return [ctxs[i].download_prolongation(l) for l in range(ctxs[i].n_levels - 1)]
+
+    with ThreadPoolExecutor(max_workers=min(16, os.cpu_count() or 1)) as ex:
+        P_lists = list(ex.map(one, range(len(problems))))
+    return ctxs, P_lists
+
+
+def batch_upload(amg, problems, P_lists, prec, local):
+    ctxs = []
+    for p, P_list in zip(problems, P_lists):
+        c = amg.Context(local)
+        Ps = [type("P", (), dict(n_rows=n, n_cols=m, rowptr=rp, colidx=ci, vals=v))
+              for (n, m, rp, ci, v) in P_list]
+        c.upload_hierarchy(p.A, Ps, prec)
+        ctxs.append(c)
+    return ctxs
+
+
+def stacked(B, problems):
+    total = B.layout(0)[2]
+    f = np.zeros(total)
+    for s, p in enumerate(problems):
+        off, n, _ = B.layout(s)
+        f[off:off + 6 * n] = p.b.reshape(-1)
+    return f
+
+
+def run_batch(args, ws, rank, local, problems):
+    import torch
+    from paper_2011_13325_gb300 import amg
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    prec = args.precision
+    t0 = time.perf_counter()
+    ctx_main, P_lists = batch_setup(amg, problems, prec, local)
+    torch.cuda.synchronize()
+    setup_s = time.perf_counter() - t0
+    levels_per_system = [[c.level_info(l) for l in range(c.n_levels)] for c in ctx_main]
+    B = amg.Batch(ctx_main, 6)
+    fh = stacked(B, problems)
+    f = torch.from_numpy(fh).to(dev)
+    u = torch.zeros_like(f)
+    total = f.numel()
+
+    def run(Bx, k, record):
+        times, its = [], None
+        for _ in range(k):
+            u.zero_()
+            torch.cuda.synchronize()
+            _, it, rr, ms = Bx.pcg_solve(f, u, rtol=args.rtol, maxit=1000)
+            if record:
+                times.append(ms)
+                its = it
+        return times, its
+
+    run(B, args.warmup, False)
+    if ws > 1:
+        torch.distributed.barrier()
+    torch.cuda.synchronize()
+    sampler = ClockSampler(local)
+    sampler.start()
+    time.sleep(0.15)
+    t_wall = time.perf_counter()
+    times, its = run(B, args.steps, True)
+    torch.cuda.synchronize()
+    wall = time.perf_counter() - t_wall
+    clocks = sampler.stop()
+    if ws > 1:
+        torch.distributed.barrier()
+    ms = float(np.mean(times))
+    if ws > 1:
+        t = torch.tensor([ms], device=dev)
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        ms = float(t.item())
+    uh = u.cpu().numpy()
+
+    # FP64 true residual of every load case (library residual kernel)
+    worst = 0.0
+    for s, c in enumerate(ctx_main):
+        off, n, _ = B.layout(s)
+        for j in range(6):
+            fj = f[off + j * n:off + (j + 1) * n]
+            uj = u[off + j * n:off + (j + 1) * n]
+            r = torch.empty_like(fj)
+            c.residual(0, fj, uj, r)
+            worst = max(worst, float(torch.linalg.norm(r) / torch.linalg.norm(fj)))
+
+    # the same batch with the FP64 V-cycle (one graph launch)
+    variants = {}
+    ctx64 = batch_upload(amg, problems, P_lists, 0, local) if prec != 0 else ctx_main
+    if prec != 0:
+        B64 = amg.Batch(ctx64, 6)
+        run(B64, 3, False)
+        t64, it64 = run(B64, args.steps, True)
+        variants["batch_fp64"] = {"ms": round(float(np.mean(t64)), 3), "iters_max": max(it64),
+                                  "iters_mean": round(float(np.mean(it64)), 2)}
+        B64.close()
+    # plain FP64 GPU PCG, one system and one load case at a time (384 graph
+    # launches per step), device time summed
+    seq_steps = 2
+    seq = []
+    seq_its = []
+    for step in range(1 + seq_steps):
+        tot = 0.0
+        for s, c in enumerate(ctx64):
+            off, n, _ = B.layout(s)
+            for j in range(6):
+                fj = f[off + j * n:off + (j + 1) * n]
+                uj = torch.zeros_like(fj)
+                _, it, _ = c.pcg_solve(fj, uj, rtol=args.rtol, maxit=1000)
+                tot += c.last_solve_ms()
+                if step == 1:
+                    seq_its.append(it[0])
+        if step >= 1:
+            seq.append(tot)
+    variants["sequential_fp64"] = {"ms": round(float(np.mean(seq)), 3),
+                                   "solves_per_step": 6 * len(ctx64),
+                                   "iters_mean": round(float(np.mean(seq_its)), 2),
+                                   "ms_ratio_to_main": round(float(np.mean(seq)) / ms, 2)}
+
+    # end to end: host buffers, copies inside the call and its timing
+    fpin = torch.from_numpy(fh).pin_memory()
+    upin = torch.zeros_like(fpin).pin_memory()
+    et = []
+    for k in range(2 + args.steps):
+        upin.zero_()
+        _, _, _, e_ms = B.pcg_solve_host(fpin, upin, rtol=args.rtol, maxit=1000)
+        if k >= 2:
+            et.append(e_ms)
+
+    per_step_bytes = 0
+    for s, levels in enumerate(levels_per_system):
+        it = its[s * 6:(s + 1) * 6]
+        per_step_bytes += algorithmic_bytes_per_iteration(levels, prec, nr=6) * max(it)
+    pk, pk_kind = peaks()
+    gbs = per_step_bytes / (ms * 1e-3) / 1e9
+    per_it, fixed = B.launches()
+    launches = fixed + max(its) * per_it
+    tuned = [ln for ln in B.describe().splitlines() if "lanes/row" in ln]
+    n_dofs = [levels[0]["n_rows"] * levels[0]["block"] for levels in levels_per_system]
+
+    cpu = None
+    if rank == 0 and ws == 1 and not args.no_cpu_baseline:
+        v, sample = oracle_batch_sample(problems, P_lists, its, budget_s=20.0)
+        cpu = {"value": round(v, 1), "unit": "ms", "cores": 1, "kind": "oracle", "sample": sample}
+
+    line = {
+        "metric": "batched AMG-PCG time-to-1e-8 (FP64 residual), 64 systems x 6 load cases",
+        "value": round(ms, 3), "unit": "ms", "n_gpus": ws, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": round(ms, 3), "higher_is_better": False,
+        "scaling": "weak", "vs_baseline": None,
+        "dtype": {0: "f64", 1: "f64 CG + f32 V-cycle", 2: "f64 CG + f32 V-cycle (bf16 storage)"}[prec],
+        "data": "synthetic",
+        "config": {"workload": "batch64", "description": WORKLOADS["batch64"],
+                   "systems": len(problems), "load_cases": 6, "dofs_total": int(sum(n_dofs)),
+                   "dofs_min_max": [int(min(n_dofs)), int(max(n_dofs))],
+                   "precision": PREC_NAMES[prec] + " V-cycle, fp64 CG (FP64 residual 1e-8)",
+                   "rtol": args.rtol,
+                   "l2": "inputs larger than L2 (operators of all systems > 1 GB)",
+                   "parallelism": f"replicas x{ws}"},
+        "iters_max": max(its), "iters_mean": round(float(np.mean(its)), 2),
+        "true_relres_max": worst, "setup_s": round(setup_s, 2),
+        "solve_gbs": round(gbs, 1), "bytes_per_step": int(per_step_bytes),
+        "roofline": {"bound": "hbm", "achieved": round(gbs, 1), "peak": pk["hbm_gbs"],
+                     "unit": "GB/s", "frac": round(gbs / pk["hbm_gbs"], 3), "traffic": None,
+                     "kernel": "whole batched solve (algorithmic bytes of every V-cycle and CG "
+                               "kernel / graph time)", "peak_kind": f"{pk_kind} copy"},
+        "wall_s_timed": round(wall, 3), "clocks": clocks, "variants": variants,
+        "e2e": {"value": round(float(np.mean(et)), 3), "unit": "ms",
+                "h2d_bytes_per_step": 2 * total * 8, "d2h_bytes_per_step": total * 8},
+        "gpu_launches": launches * args.steps, "gpu_launches_per_step": launches,
+        "autotuned_products": tuned,
+        "cpu_baseline": cpu,
+    }
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    B.close()
+    if ws > 1:
+        torch.distributed.destroy_process_group()
+
+
+def oracle_batch_sample(problems, P_lists, its, budget_s=20.0):
+    """Oracle PCG iterations on the first systems until ~budget_s of CPU
+    work; the cost per dof-iteration scales to every load case's actual
+    iteration count."""
+    from oracle import solve
+    spent, dof_its = 0.0, 0.0
+    used = 0
+    for s, (p, P_list) in enumerate(zip(problems, P_lists)):
+        H = oracle_hierarchy(p, P_list)
+        m = max(its[s * 6:(s + 1) * 6])
+        t0 = time.perf_counter()
+        solve.pcg(H, p.b[0], rtol=0.0, maxit=m)
+        spent += time.perf_counter() - t0
+        dof_its += m * p.b.shape[1]
+        used += 1
+        if spent >= budget_s:
+            break
+    per = spent / dof_its
+    want = sum(its[s * 6 + j] * problems[s].b.shape[1] for s in range(len(problems)) for j in range(6))
+    return per * want * 1e3, (f"oracle PCG of load case 0 on the first {used} systems "
+                              f"({spent:.1f} s), scaled per dof-iteration to all "
+                              f"{6 * len(problems)} load cases at their iteration counts")
+
+
+def run_reference_batch(args, ws, rank, local, problems):
+    import torch
+    if rank != 0:
+        if ws > 1:
+            torch.distributed.destroy_process_group()
+        return
+    from paper_2011_13325_gb300 import amg
+    ctxs, P_lists = batch_setup(amg, problems, amg.AMG_PREC_FP64, local)
+    B = amg.Batch(ctxs, 6)
+    f = torch.from_numpy(stacked(B, problems)).cuda(local)
+    _, its, _, _ = B.pcg_solve(f, torch.zeros_like(f), rtol=args.rtol, maxit=1000)
+    B.close()
+    budget = max(2.0, 60.0 / max(1, args.steps + args.warmup))
+    per_step, sample = [], ""
+    for s in range(args.warmup + args.steps):
+        v, sample = oracle_batch_sample(problems, P_lists, its, budget_s=budget)
+        if s >= args.warmup:
+            per_step.append(v)
+    v = float(np.mean(per_step))
+    line = {"impl": "reference",
+            "metric": "batched AMG-PCG time-to-1e-8 (FP64 residual), 64 systems x 6 load cases",
+            "value": round(v, 1), "unit": "ms", "n_gpus": ws, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": round(v, 1), "higher_is_better": False,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": "batch64", "description": WORKLOADS["batch64"]},
+            "cpu_baseline": {"value": round(v, 1), "unit": "ms", "cores": 1, "kind": "oracle",
+                             "sample": "each step: " + sample},
             "e2e": {"value": round(v, 1), "unit": "ms", "h2d_bytes_per_step": 0,
                     "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)

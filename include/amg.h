@@ -278,6 +278,8 @@ typedef struct {
  *               (0: min(1000, max(64, ceil(n_0 / 10^4))))
  *  min_ratio    stop when a level shrinks by less than this factor
  *  max_levels   upper bound on the number of levels
+ *  host_threads OpenMP threads of this call's host setup (0: the process
+ *               default); lets independent setups run side by side
  * A vertex is "standard" (real matrix row in P_s) when its row touches at
  * most cap agglomerates, does not couple to D and is kernel-exact; the
  * auxiliary rows use the own agglomerate and the 3 others with the largest
@@ -291,6 +293,7 @@ typedef struct {
   int32_t coarse_max;
   double min_ratio;
   int32_t max_levels;
+  int32_t host_threads;
 } amg_setup_params;
 
 /* Fill *p with the defaults listed above. */
@@ -326,15 +329,25 @@ typedef struct amg_batch amg_batch;
  * device and with one V-cycle precision) for batched solves with nrhs load
  * cases per system (nrhs = 1 or 6).  The contexts must outlive the batch and
  * must not be re-uploaded while it exists.  The batch allocates its own
- * multi-load-case work vectors and builds ONE CUDA graph in which every
- * system is an independent branch: the system's FP64 PCG (Sec. 7) over its
- * nrhs load cases runs in its own device-side while loop, preconditioned by
- * the V-cycle applied to all load cases at once (every matrix block read
- * serves all of them).  Errors: AMG_ERR_ARG, AMG_ERR_STATE (a context
- * without hierarchy), AMG_ERR_CUDA. */
+ * multi-load-case work vectors and builds ONE CUDA graph: a device-side
+ * while loop of FP64 PCG (Sec. 7) over all systems in lockstep, where every
+ * step (each V-cycle step of each level, each CG step) is one grouped launch
+ * covering every system, and every matrix block read serves all load cases.
+ * Creation also runs the autotuner: each grouped block-sparse product is
+ * timed with every tile (lanes per block row 32/16/8, warps per block 8/4)
+ * and the fastest is kept (amg_batch_describe lists the choices).  Errors:
+ * AMG_ERR_ARG, AMG_ERR_STATE (a context without hierarchy), AMG_ERR_CUDA. */
 int amg_batch_create(amg_batch **batch, amg_ctx *const *systems, int n_systems, int nrhs);
 void amg_batch_destroy(amg_batch *batch);
 const char *amg_batch_last_error(const amg_batch *batch);
+
+/* Text listing the grouped launches of the batch (init, one iteration,
+ * tail) with the tile the autotuner chose and its time; owned by the batch. */
+const char *amg_batch_describe(const amg_batch *batch);
+
+/* Kernel launches of one solve: *fixed + iterations * *per_iteration, where
+ * iterations is the largest iteration count over all load cases. */
+int amg_batch_launches(const amg_batch *batch, int32_t *per_iteration, int32_t *fixed);
 
 /* Layout of the stacked vectors: system s occupies [offset, offset +
  * nrhs * n_dofs) with its nrhs load cases one after another (each n_dofs
@@ -352,6 +365,12 @@ int amg_batch_layout(const amg_batch *batch, int s, int64_t *offset, int64_t *n_
  * if some load case failed. */
 int amg_batch_pcg_solve(amg_batch *batch, const double *f_dev, double *u_dev, double rtol,
                         int maxit, int *iters_out, double *relres_out, float *ms_out);
+
+/* amg_batch_pcg_solve with the stacked f / u in HOST memory (pinned for
+ * full copy speed): the copies to and from the device are part of the call
+ * and of *ms_out (end-to-end device time). */
+int amg_batch_pcg_solve_host(amg_batch *batch, const double *f_host, double *u_host, double rtol,
+                             int maxit, int *iters_out, double *relres_out, float *ms_out);
 
 #ifdef __cplusplus
 }

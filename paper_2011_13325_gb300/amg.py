@@ -59,7 +59,8 @@ class amg_setup_params(C.Structure):
     _fields_ = [("sigma", C.c_double), ("delta", C.c_int32), ("passes_first", C.c_int32),
                 ("passes_later", C.c_int32), ("omega", C.c_double), ("cap_S_first", C.c_int32),
                 ("cap_S_later", C.c_int32), ("cap_A", C.c_int32), ("coarse_max", C.c_int32),
-                ("min_ratio", C.c_double), ("max_levels", C.c_int32)]
+                ("min_ratio", C.c_double), ("max_levels", C.c_int32),
+                ("host_threads", C.c_int32)]
 
 
 class AmgError(RuntimeError):
@@ -107,10 +108,14 @@ _SIGS = {
     "amg_batch_create": (_I, [C.POINTER(_P), C.POINTER(_P), _I, _I]),
     "amg_batch_destroy": (None, [_P]),
     "amg_batch_last_error": (C.c_char_p, [_P]),
+    "amg_batch_describe": (C.c_char_p, [_P]),
+    "amg_batch_launches": (_I, [_P, C.POINTER(C.c_int32), C.POINTER(C.c_int32)]),
     "amg_batch_layout": (_I, [_P, _I, C.POINTER(C.c_int64), C.POINTER(C.c_int64),
                               C.POINTER(C.c_int64)]),
     "amg_batch_pcg_solve": (_I, [_P, _P, _P, _D, _I, C.POINTER(_I), C.POINTER(_D),
                                  C.POINTER(C.c_float)]),
+    "amg_batch_pcg_solve_host": (_I, [_P, _P, _P, _D, _I, C.POINTER(_I), C.POINTER(_D),
+                                      C.POINTER(C.c_float)]),
 }
 
 
@@ -353,6 +358,15 @@ class Batch:
         except Exception:
             pass
 
+    def describe(self):
+        return lib().amg_batch_describe(self.h).decode()
+
+    def launches(self):
+        """(kernels per iteration, fixed kernels per solve)."""
+        a, b = C.c_int32(), C.c_int32()
+        lib().amg_batch_launches(self.h, C.byref(a), C.byref(b))
+        return a.value, b.value
+
     def layout(self, s):
         o, n, t = C.c_int64(), C.c_int64(), C.c_int64()
         st = lib().amg_batch_layout(self.h, int(s), C.byref(o), C.byref(n), C.byref(t))
@@ -361,12 +375,19 @@ class Batch:
         return o.value, n.value, t.value
 
     def pcg_solve(self, f, u, rtol=1e-8, maxit=500, check=True):
+        """Stacked device vectors (torch tensors)."""
+        return self._solve(lib().amg_batch_pcg_solve, f, u, rtol, maxit, check)
+
+    def pcg_solve_host(self, f, u, rtol=1e-8, maxit=500, check=True):
+        """Stacked host vectors (numpy arrays or CPU tensors, pinned for speed)."""
+        return self._solve(lib().amg_batch_pcg_solve_host, f, u, rtol, maxit, check)
+
+    def _solve(self, fn, f, u, rtol, maxit, check):
         m = len(self.contexts) * self.nrhs
         it = (C.c_int * m)()
         rr = (C.c_double * m)()
         ms = C.c_float()
-        s = lib().amg_batch_pcg_solve(self.h, _ptr(f), _ptr(u), float(rtol), int(maxit), it, rr,
-                                      C.byref(ms))
+        s = fn(self.h, _ptr(f), _ptr(u), float(rtol), int(maxit), it, rr, C.byref(ms))
         if check and s != AMG_OK:
             raise AmgError(s, lib().amg_batch_last_error(self.h).decode())
         return s, list(it), list(rr), ms.value

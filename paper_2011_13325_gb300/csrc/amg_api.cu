@@ -762,6 +762,7 @@ void amg_default_setup_params(amg_setup_params *p) {
   p->coarse_max = d.coarse_max;
   p->min_ratio = d.min_ratio;
   p->max_levels = d.max_levels;
+  p->host_threads = d.host_threads;
 }
 
 int amg_setup(amg_ctx *h, const amg_problem *prob, const amg_setup_params *params, int precision,
@@ -791,9 +792,10 @@ int amg_setup(amg_ctx *h, const amg_problem *prob, const amg_setup_params *param
     prm.coarse_max = params->coarse_max;
     prm.min_ratio = params->min_ratio;
     prm.max_levels = params->max_levels;
+    prm.host_threads = params->host_threads;
   }
   if (!(prm.sigma > 0) || prm.passes_first < 1 || prm.passes_later < 1 || prm.cap_A < 1 ||
-      prm.max_levels < 1)
+      prm.max_levels < 1 || prm.host_threads < 0)
     return fail(c, AMG_ERR_ARG, "amg_setup: bad parameters");
   CUDA_OR_FAIL(c, cudaSetDevice(c->device), "cudaSetDevice");
   cudaStreamSynchronize(c->stream);

@@ -21,6 +21,10 @@
 #include <array>
 #include <chrono>
 #include <unordered_map>
+
+#ifdef _OPENMP
+#include <omp.h>
+#endif
 #include <vector>
 
 #include "setup_host.h"
@@ -1026,6 +1030,17 @@ static double now_s() {
 }
 
 int build_levels(const Problem &prob, const SetupParams &prm, LevelSink &sink, std::string &err) {
+#ifdef _OPENMP
+  // thread count of the OpenMP regions started by this (calling) thread only,
+  // restored on return: independent setups may run side by side on threads
+  struct ThreadScope {
+    int saved;
+    explicit ThreadScope(int n) : saved(omp_get_max_threads()) {
+      if (n > 0) omp_set_num_threads(n);
+    }
+    ~ThreadScope() { omp_set_num_threads(saved); }
+  } scope(prm.host_threads);
+#endif
   const int d = prob.dim, n_all = prob.n_vertices;
   if (d != 2 && d != 3) {
     err = "dim must be 2 or 3";

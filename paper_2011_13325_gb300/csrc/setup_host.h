@@ -46,6 +46,7 @@ struct SetupParams {
   int coarse_max = 0;
   double min_ratio = 1.5;
   int max_levels = 16;
+  int host_threads = 0;  // OpenMP threads of this call (0: the process default)
 };
 
 // Receives the levels as they are built: first(A_0), then for every level

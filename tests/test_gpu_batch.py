@@ -207,3 +207,30 @@ def test_batch_rejects_bad_arguments():
     with pytest.raises(amg.AmgError) as e:
         amg.Batch([ctxs[0], other], 6)
     assert e.value.code == amg.AMG_ERR_ARG
+
+
+def test_batch_host_entry_point_matches_device():
+    ctxs, B = _batch(1)
+    f = _stack(B, [p.b for p, _ in systems()])
+    u = torch.zeros_like(f)
+    _, it1, r1, ms1 = B.pcg_solve(f, u, rtol=1e-8)
+    fh = f.cpu().pin_memory()
+    uh = torch.zeros_like(fh).pin_memory()
+    _, it2, r2, ms2 = B.pcg_solve_host(fh, uh, rtol=1e-8)
+    assert it1 == it2 and r1 == r2 and ms2 > 0
+    assert torch.equal(u.cpu(), uh)
+
+
+def test_batch_schedule_is_grouped_and_tuned():
+    """One grouped launch per step for all systems: the launches per
+    iteration do not grow with the number of systems, and every product
+    stage carries the tile the autotuner chose."""
+    amg = _amg()
+    ctxs, B = _batch(1)
+    per_it, fixed = B.launches()
+    d = B.describe()
+    prods = [ln for ln in d.splitlines() if "lanes/row" in ln]
+    assert prods and all(any(f"{l} lanes/row" in ln for l in (32, 16, 8)) for ln in prods)
+    assert len([ln for ln in d.splitlines() if ln.startswith("iteration")]) == per_it
+    ctx1, B1 = ctxs[:2], amg.Batch(ctxs[:2], 6)
+    assert B1.launches()[0] <= per_it <= 40
