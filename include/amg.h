@@ -89,7 +89,7 @@ enum {
 /* Smoother on the finest level. */
 enum {
   AMG_SMOOTHER_L1_JACOBI = 0, /* block-l1 Jacobi (Sec. 7)                     */
-  AMG_SMOOTHER_LEARNED = 1    /* per-vertex blocks set by amg_set_fine_smoother */
+  AMG_SMOOTHER_LEARNED = 1    /* per-vertex blocks of amg_set_learned_smoother  */
 };
 
 /* Create a context on CUDA device `device`.  `cuda_stream` is a
@@ -371,6 +371,88 @@ int amg_batch_pcg_solve(amg_batch *batch, const double *f_dev, double *u_dev, do
  * and of *ms_out (end-to-end device time). */
 int amg_batch_pcg_solve_host(amg_batch *batch, const double *f_host, double *u_host, double rtol,
                              int maxit, int *iters_out, double *relres_out, float *ms_out);
+
+/* ------------------------------------------------------------------------
+ * Learned smoother of the finest level (an extension: the paper has no
+ * learned component; 3D elasticity, 3x3 blocks)
+ *
+ * A per-vertex MLP 13 -> 64 -> 64 -> 6 (ReLU) maps the features of vertex v
+ * to a lower-triangular factor L; the smoother block is
+ * B_v = (L L^T + 1e-6 I) / tr A_vv (SPD by construction) and replaces the
+ * block-l1 Jacobi block of level 0, damped by omega = 4 / (3 * 1.05 * lambda)
+ * with lambda the largest Ritz value of 30 Lanczos steps on B A (the
+ * smoother x += omega B r converges iff omega lambda_max(BA) < 2, which
+ * keeps the V-cycle an SPD preconditioner).
+ * Features (13, FP32): A_vv's 6 unique entries (00, 11, 22, 01, 02, 12) /
+ * tr A_vv; the same entries of sum_j c^{vj} t t^T over v's off-diagonal
+ * blocks (t = x_j - x_v, c^{vj} = mean |entry| of A_vj: the displacement
+ * part of the finest edge matrices of Thm. deng_elast and its Remark)
+ * / (tr A_vv * mean |t|^2); degree / 14.
+ * Training target (row-major 3x3): [(A_{N(v),N(v)})^{-1}]_{vv} * tr A_vv,
+ * N(v) = v and its neighbours (at most 15).
+ * Parameters (AMG_MLP_PARAMS floats): W1 (64 x 13, row-major), b1 (64),
+ * W2 (64 x 64), b2 (64), W3 (6 x 64), b3 (6); outputs L00, L10, L11, L20,
+ * L21, L22.  The network keeps FP32 master weights for Adam and computes
+ * with their BF16 copy, FP32 activations and FP32 accumulation.
+ * ---------------------------------------------------------------------- */
+
+#define AMG_MLP_PARAMS 5446
+
+typedef struct amg_mlp amg_mlp;
+
+/* Network on `device` with He-normal weights (splitmix64 stream from
+ * `seed`, Box-Muller) and zero biases.  Errors: AMG_ERR_ARG, AMG_ERR_CUDA. */
+int amg_mlp_create(amg_mlp **mlp, int device, uint64_t seed);
+void amg_mlp_destroy(amg_mlp *mlp);
+const char *amg_mlp_last_error(const amg_mlp *mlp);
+int amg_mlp_n_params(void);
+
+/* Copy the parameters to host `params` (AMG_MLP_PARAMS floats): the FP32
+ * master weights (working = 0) or the BF16 weights the kernels compute with,
+ * widened to FP32 (working = 1). */
+int amg_mlp_get_params(amg_mlp *mlp, float *params, int working);
+
+/* Set the master weights (host FP32), refresh the BF16 copy, clear Adam. */
+int amg_mlp_set_params(amg_mlp *mlp, const float *params);
+
+/* Features of the level-0 vertices of ctx: coords_host (n_0 x 3 FP64,
+ * host) are the vertex positions; X_dev receives n_0 x 13 FP32 (device),
+ * tr_dev (device, may be NULL) n_0 traces.  Errors: AMG_ERR_STATE (no
+ * hierarchy), AMG_ERR_ARG (not 3x3 blocks, a vertex without positive
+ * diagonal block), AMG_ERR_CUDA. */
+int amg_learned_features(amg_ctx *ctx, const double *coords_host, float *X_dev, double *tr_dev);
+
+/* Patch-inverse targets of the level-0 vertices (n_0 x 9, device; either
+ * pointer may be NULL), computed in FP64 (dense Cholesky per patch).
+ * AMG_ERR_ARG if a vertex has more than 15 neighbours or a singular patch. */
+int amg_learned_targets(amg_ctx *ctx, float *T32_dev, double *T64_dev);
+
+/* Mean loss (1/n) sum_v ||L L^T + 1e-6 I - T_v||_F^2 over n samples
+ * (X_dev n x 13, T_dev n x 9, device) and its gradient (host, may be NULL),
+ * with the BF16 weights. */
+int amg_mlp_loss_grad(amg_mlp *mlp, const float *X_dev, const float *T_dev, int64_t n, double *loss,
+                      float *grad_host);
+
+/* Adam (beta 0.9 / 0.999, eps 1e-8, step lr) over `epochs` passes of n
+ * samples in minibatches of `batch` (>= 32), the order of each pass a
+ * splitmix64 Fisher-Yates shuffle from `seed`; epoch_loss (host, may be
+ * NULL) receives the mean minibatch loss of every pass.  All on the device. */
+int amg_mlp_train(amg_mlp *mlp, const float *X_dev, const float *T_dev, int64_t n, int epochs, int batch,
+                  float lr, uint64_t seed, double *epoch_loss);
+
+/* Outputs (n x 6 FP32, device) of the network for n feature rows. */
+int amg_mlp_infer(amg_mlp *mlp, const float *X_dev, int64_t n, float *out_dev);
+
+/* Replace the level-0 smoother blocks of ctx by the damped learned blocks
+ * omega * B_v (features from coords_host as in amg_learned_features);
+ * lambda_out / omega_out (may be NULL) receive the Lanczos estimate and the
+ * damping.  The PCG graph stays valid (same buffers).  Errors: AMG_ERR_STATE
+ * (no hierarchy or one level), AMG_ERR_ARG, AMG_ERR_NOT_SPD, AMG_ERR_CUDA. */
+int amg_set_learned_smoother(amg_ctx *ctx, amg_mlp *mlp, const double *coords_host, double *lambda_out,
+                             double *omega_out);
+
+/* Restore the block-l1 Jacobi smoother of level 0. */
+int amg_reset_smoother(amg_ctx *ctx);
 
 #ifdef __cplusplus
 }

@@ -105,6 +105,19 @@ _SIGS = {
     "amg_prolongation_info": (_I, [_P, _I, C.POINTER(C.c_int32), C.POINTER(C.c_int32),
                                    C.POINTER(C.c_int32), C.POINTER(C.c_int32), C.POINTER(C.c_int64)]),
     "amg_download_prolongation": (_I, [_P, _I, _P, _P, _P]),
+    "amg_mlp_create": (_I, [C.POINTER(_P), _I, C.c_uint64]),
+    "amg_mlp_destroy": (None, [_P]),
+    "amg_mlp_last_error": (C.c_char_p, [_P]),
+    "amg_mlp_n_params": (_I, []),
+    "amg_mlp_get_params": (_I, [_P, _P, _I]),
+    "amg_mlp_set_params": (_I, [_P, _P]),
+    "amg_learned_features": (_I, [_P, _P, _P, _P]),
+    "amg_learned_targets": (_I, [_P, _P, _P]),
+    "amg_mlp_loss_grad": (_I, [_P, _P, _P, C.c_int64, C.POINTER(_D), _P]),
+    "amg_mlp_train": (_I, [_P, _P, _P, C.c_int64, _I, _I, C.c_float, C.c_uint64, _P]),
+    "amg_mlp_infer": (_I, [_P, _P, C.c_int64, _P]),
+    "amg_set_learned_smoother": (_I, [_P, _P, _P, C.POINTER(_D), C.POINTER(_D)]),
+    "amg_reset_smoother": (_I, [_P]),
     "amg_batch_create": (_I, [C.POINTER(_P), C.POINTER(_P), _I, _I]),
     "amg_batch_destroy": (None, [_P]),
     "amg_batch_last_error": (C.c_char_p, [_P]),
@@ -322,6 +335,27 @@ class Context:
         self._check(lib().amg_probe_fma_rate(self.h, C.byref(a), C.byref(b)))
         return a.value, b.value
 
+    def learned_features(self, coords, X, tr=None):
+        """Features (n_0 x 13 FP32 device tensor X) of the level-0 vertices at
+        host positions coords (n_0 x 3)."""
+        c = np.ascontiguousarray(coords, dtype=np.float64)
+        return self._check(lib().amg_learned_features(self.h, c.ctypes.data, _ptr(X), _ptr(tr)))
+
+    def learned_targets(self, T32=None, T64=None):
+        """Patch-inverse targets (n_0 x 9) into device tensors."""
+        return self._check(lib().amg_learned_targets(self.h, _ptr(T32), _ptr(T64)))
+
+    def set_learned_smoother(self, mlp, coords):
+        """Install the damped learned blocks at level 0; returns (lambda, omega)."""
+        c = np.ascontiguousarray(coords, dtype=np.float64)
+        lam, w = C.c_double(), C.c_double()
+        self._check(lib().amg_set_learned_smoother(self.h, mlp.h, c.ctypes.data, C.byref(lam),
+                                                   C.byref(w)))
+        return lam.value, w.value
+
+    def reset_smoother(self):
+        return self._check(lib().amg_reset_smoother(self.h))
+
     def set_layout_policy(self, policy: int):
         return self._check(lib().amg_set_layout_policy(self.h, int(policy)))
 
@@ -391,3 +425,62 @@ class Batch:
         if check and s != AMG_OK:
             raise AmgError(s, lib().amg_batch_last_error(self.h).decode())
         return s, list(it), list(rr), ms.value
+
+
+AMG_MLP_PARAMS = 5446
+
+
+class Mlp:
+    """amg_mlp: the learned smoother's network (FP32 master weights, BF16
+    working copy) with its device training."""
+
+    def __init__(self, device=0, seed=0):
+        self.h = _P()
+        s = lib().amg_mlp_create(C.byref(self.h), int(device), C.c_uint64(int(seed)))
+        if s != AMG_OK:
+            raise AmgError(s, "amg_mlp_create failed")
+
+    def close(self):
+        if self.h:
+            lib().amg_mlp_destroy(self.h)
+            self.h = _P()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def _check(self, s):
+        if s != AMG_OK:
+            raise AmgError(s, lib().amg_mlp_last_error(self.h).decode())
+        return s
+
+    def params(self, working=False):
+        out = np.zeros(AMG_MLP_PARAMS, dtype=np.float32)
+        self._check(lib().amg_mlp_get_params(self.h, out.ctypes.data, int(bool(working))))
+        return out
+
+    def set_params(self, p):
+        p = np.ascontiguousarray(p, dtype=np.float32)
+        if p.size != AMG_MLP_PARAMS:
+            raise ValueError("wrong number of parameters")
+        return self._check(lib().amg_mlp_set_params(self.h, p.ctypes.data))
+
+    def loss_grad(self, X, T, n=None):
+        n = int(X.shape[0]) if n is None else int(n)
+        loss = C.c_double()
+        g = np.zeros(AMG_MLP_PARAMS, dtype=np.float32)
+        self._check(lib().amg_mlp_loss_grad(self.h, _ptr(X), _ptr(T), n, C.byref(loss), g.ctypes.data))
+        return loss.value, g
+
+    def train(self, X, T, epochs=10, batch=4096, lr=1e-3, seed=0, n=None):
+        n = int(X.shape[0]) if n is None else int(n)
+        hist = np.zeros(max(epochs, 1))
+        self._check(lib().amg_mlp_train(self.h, _ptr(X), _ptr(T), n, int(epochs), int(batch),
+                                        float(lr), C.c_uint64(int(seed)), hist.ctypes.data))
+        return hist[:epochs]
+
+    def infer(self, X, out, n=None):
+        n = int(X.shape[0]) if n is None else int(n)
+        return self._check(lib().amg_mlp_infer(self.h, _ptr(X), n, _ptr(out)))
