@@ -40,6 +40,9 @@ WORKLOADS = {
                  "clamped x=0, body force (0,-1); 2,112 dofs, 2x2 BSR"),
     "cube128jump": ("3D P1 elasticity, 128^3 vertices, 200 inclusion boxes E=10^U(-3,3), "
                     "nu U[0.25,0.45] (seed 3); 6.24M dofs"),
+    "cube96nu": ("3D P1 elasticity, unit cube, 96^3 vertices (seed 5), E=1, nu per element "
+                 "U[0.3,0.45], clamped x=0, body force (0,0,-1); 2.65M dofs; level-0 smoother: the "
+                 "learned MLP trained on ten 32^3 meshes (seeds 100-109)"),
     "batch64": ("64 independent 3D P1 elasticity boxes, vertices per axis U{16..48}, h=1/32, "
                 "E U[0.1,10], nu U[0.2,0.4] per system (seed 4), clamped x=0, 6 load cases "
                 "(unit body forces +-x, +-y, +-z) each"),
@@ -55,6 +58,8 @@ def make_workload(name):
         return configs.square32()
     if name == "cube128jump":
         return configs.cube128jump()
+    if name == "cube96nu":
+        return configs.cube96nu()
     raise SystemExit(f"unknown workload {name}")
 
 
@@ -231,14 +236,22 @@ def main():
     ap.add_argument("--pcg-mode", default="graph", choices=["graph", "host"],
                     help="graph: whole PCG in one CUDA graph (default); host: the same kernels "
                          "launched one by one (per-kernel view for profilers)")
+    ap.add_argument("--smoother", default="auto", choices=["auto", "l1", "learned"],
+                    help="level-0 smoother (auto: learned for cube96nu, block-l1 Jacobi otherwise)")
+    ap.add_argument("--train-epochs", type=int, default=40)
     ap.add_argument("--systems", type=int, default=64,
                     help="batch64: number of systems (the workload has 64)")
     args = ap.parse_args()
     if args.warmup < 3:
         raise SystemExit("--warmup must be >= 3")
+    if args.smoother == "auto":
+        args.smoother = "learned" if args.workload == "cube96nu" else "l1"
     if args.workload == "batch64":
         # the 64 meshes are generated in a spawn pool before any CUDA call
         problems = batch_problems(args.systems)
+    train_problems = None
+    if args.smoother == "learned" and args.impl != "reference":
+        train_problems = training_problems()
 
     import torch
     ws, rank, local = dist_env()
@@ -275,6 +288,13 @@ def main():
     levels = []
     for l in range(ctx.n_levels):
         levels.append(ctx.level_info(l))
+    learned_info = None
+    if args.smoother == "learned":
+        net, learned_info = train_learned(amg, train_problems, local, epochs=args.train_epochs)
+        t0 = time.perf_counter()
+        lam, w = ctx.set_learned_smoother(net, problem.coords[problem.free])
+        learned_info.update(lambda_lanczos=lam, omega=w,
+                            install_s=round(time.perf_counter() - t0, 3))
     f = torch.from_numpy(np.ascontiguousarray(problem.b[0])).to(dev)
     u = torch.zeros_like(f)
 
@@ -362,7 +382,7 @@ def main():
     variants = {}
     P_list = [ctx.download_prolongation(l) for l in range(ctx.n_levels - 1)]
     if args.variants == "auto":
-        vlist = [p for p in (0, 1, 2) if p != args.precision]
+        vlist = [] if args.smoother == "learned" else [p for p in (0, 1, 2) if p != args.precision]
     else:
         vlist = [int(v) for v in args.variants.split(",") if v.strip()]
     for prec in vlist:
@@ -400,13 +420,34 @@ def main():
         et.append(e0.elapsed_time(e1))
     n_dof = int(f.numel())
 
+    fine_smoother = ctx.download_smoother(0) if args.smoother == "learned" else None
+    if args.smoother == "learned":
+        # the method's own block-l1 Jacobi on the same hierarchy and precision
+        ctx.reset_smoother()
+        run_steps(ctx, args.warmup, False)
+        tv, iv = run_steps(ctx, args.steps, True)
+        ctx.residual(0, f, u, res)
+        variants["l1_jacobi"] = {
+            "ms": round(float(np.mean(tv)), 3), "iters": float(np.mean(iv)),
+            "true_relres": float(torch.linalg.norm(res) / torch.linalg.norm(f)),
+            "ms_ratio_to_main": round(float(np.mean(tv)) / ms, 3)}
+
     cpu = None
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
-        H = oracle_hierarchy(problem, P_list)
-        cms, m, dt = time_oracle(H, problem.b[0], int(round(it_mean)))
-        cpu = {"value": round(cms, 1), "unit": "ms", "cores": 1, "kind": "oracle",
-               "sample": f"{m} oracle PCG iterations ({dt:.1f} s) on the same hierarchy, "
-                         f"scaled to {int(round(it_mean))} iterations"}
+        from numpy.linalg import LinAlgError
+        try:
+            H = oracle_hierarchy(problem, P_list)
+        except LinAlgError as e:
+            H = None
+            cpu = {"value": None, "unit": "ms", "cores": 1, "kind": "oracle",
+                   "unavailable": f"oracle coarsest Cholesky failed on this hierarchy: {e}"}
+        if H is not None:
+            if fine_smoother is not None:
+                H.Minv[0] = fine_smoother
+            cms, m, dt = time_oracle(H, problem.b[0], int(round(it_mean)))
+            cpu = {"value": round(cms, 1), "unit": "ms", "cores": 1, "kind": "oracle",
+                   "sample": f"{m} oracle PCG iterations ({dt:.1f} s) on the same hierarchy, "
+                             f"scaled to {int(round(it_mean))} iterations"}
 
     line = {
         "metric": "AMG-PCG time-to-1e-8 (FP64 residual), 3D elasticity",
@@ -433,6 +474,9 @@ def main():
         "gpu_launches": launches * args.steps, "gpu_launches_per_step": launches,
         "cpu_baseline": cpu,
     }
+    if learned_info is not None:
+        line["config"]["smoother"] = "learned MLP (level 0), block-l1 Jacobi below"
+        line["learned"] = learned_info
     if rank == 0:
         print(json.dumps(line), flush=True)
     ctx.close()
@@ -478,6 +522,53 @@ def run_reference(args, ws, rank, local):
     print(json.dumps(line), flush=True)
     if ws > 1:
         torch.distributed.destroy_process_group()
+
+
+# ---------------------------------------------------------------------------
+# learned smoother: training on the library's own patch-inverse targets
+# ---------------------------------------------------------------------------
+
+def _train_problem(seed):
+    from workloads import configs
+    return configs.training_meshes(seeds=[seed])[0]
+
+
+def training_problems():
+    import multiprocessing as mp
+    with mp.get_context("spawn").Pool(10) as pool:
+        return pool.map(_train_problem, list(range(100, 110)), chunksize=1)
+
+
+def train_learned(amg, problems, local, epochs=40, batch=1024, lr=2e-3):
+    """Features and FP64 patch-inverse targets of the training meshes (their
+    own hierarchies), then Adam on the device."""
+    import torch
+    t0 = time.perf_counter()
+    ctxs, _ = batch_setup(amg, problems, amg.AMG_PREC_FP64, local)
+    setup_s = time.perf_counter() - t0
+    sizes = [c.level_info(0)["n_rows"] for c in ctxs]
+    total = sum(sizes)
+    X = torch.zeros((total, 13), dtype=torch.float32, device=f"cuda:{local}")
+    T = torch.zeros((total, 9), dtype=torch.float32, device=f"cuda:{local}")
+    t0 = time.perf_counter()
+    off = 0
+    for c, p, n in zip(ctxs, problems, sizes):
+        c.learned_features(p.coords[p.free], X[off:off + n])
+        c.learned_targets(T32=T[off:off + n])
+        off += n
+    torch.cuda.synchronize()
+    data_s = time.perf_counter() - t0
+    for c in ctxs:
+        c.close()
+    net = amg.Mlp(local, seed=1)
+    l0, _ = net.loss_grad(X, T)
+    t0 = time.perf_counter()
+    hist = net.train(X, T, epochs=epochs, batch=batch, lr=lr, seed=2)
+    train_s = time.perf_counter() - t0
+    return net, {"meshes": len(problems), "samples": int(total), "epochs": epochs, "batch": batch,
+                 "lr": lr, "loss_initial": l0, "loss_final": float(hist[-1]),
+                 "setup_s": round(setup_s, 2), "features_targets_s": round(data_s, 3),
+                 "train_s": round(train_s, 3)}
 
 
 # ---------------------------------------------------------------------------
