@@ -193,6 +193,35 @@ def oracle_hierarchy(problem, P_list):
     return solve.prepare(A0, Ps)
 
 
+class EnergyError:
+    """Energy-norm error against a tight FP64 solve (rtol 1e-13) on the same
+    hierarchy (FP64 V-cycle, re-uploaded prolongations)."""
+
+    def __init__(self, amg, problem, P_list, f, local, stream):
+        import torch
+        self.c64 = amg.Context(local, stream.cuda_stream)
+        Ps = [type("P", (), dict(n_rows=n, n_cols=m, rowptr=rp, colidx=ci, vals=v))
+              for (n, m, rp, ci, v) in P_list]
+        self.c64.upload_hierarchy(problem.A, Ps, 0)
+        self.ue = torch.zeros_like(f)
+        _, it, rr = self.c64.pcg_solve(f, self.ue, rtol=1e-13, maxit=3000, check=False)
+        Au = torch.empty_like(f)
+        self.c64.spmv(0, self.ue, Au)
+        self.unorm2 = float(torch.dot(self.ue, Au))
+        self.reference = (f"FP64 V-cycle PCG to rtol 1e-13 on the same hierarchy ({it[0]} "
+                          f"iterations, relres {rr[0]:.1e})")
+
+    def __call__(self, u):
+        import torch
+        e = u - self.ue
+        Ae = torch.empty_like(e)
+        self.c64.spmv(0, e, Ae)
+        return float(torch.sqrt(torch.clamp(torch.dot(e, Ae), min=0.0) / self.unorm2))
+
+    def close(self):
+        self.c64.close()
+
+
 def time_oracle(H, f, gpu_iters, budget_s=15.0):
     """Times oracle PCG iterations on the same hierarchy until ~budget_s of
     CPU work; returns ms per full solve (scaled by the iteration count)."""
@@ -337,6 +366,9 @@ def main():
     res = torch.zeros_like(f)
     ctx.residual(0, f, u, res)
     true_rel = float(torch.linalg.norm(res) / torch.linalg.norm(f))
+    P_list = [ctx.download_prolongation(l) for l in range(ctx.n_levels - 1)]
+    eerr = EnergyError(amg, problem, P_list, f, local, stream)
+    accuracy = {"energy_error": eerr(u), "reference": eerr.reference}
 
     # A_0 SpMV (SELL-32, FP64), events per launch: FP64 on sm_103a is bound by
     # the FP64 pipe; report flops against the live FMA probe and bytes against HBM
@@ -380,7 +412,6 @@ def main():
 
     # precision variants (same prolongations, re-uploaded)
     variants = {}
-    P_list = [ctx.download_prolongation(l) for l in range(ctx.n_levels - 1)]
     if args.variants == "auto":
         vlist = [] if args.smoother == "learned" else [p for p in (0, 1, 2) if p != args.precision]
     else:
@@ -397,6 +428,7 @@ def main():
         variants[PREC_NAMES[prec]] = {
             "ms": round(float(np.mean(tv)), 3), "iters": float(np.mean(iv)),
             "true_relres": float(torch.linalg.norm(res) / torch.linalg.norm(f)),
+            "energy_error": eerr(u),
             "ms_ratio_to_main": round(float(np.mean(tv)) / ms, 3),
             "solve_gbs": round(algorithmic_bytes_per_iteration(levels, prec) * float(np.mean(iv)) /
                                (float(np.mean(tv)) * 1e-3) / 1e9, 1)}
@@ -430,6 +462,7 @@ def main():
         variants["l1_jacobi"] = {
             "ms": round(float(np.mean(tv)), 3), "iters": float(np.mean(iv)),
             "true_relres": float(torch.linalg.norm(res) / torch.linalg.norm(f)),
+            "energy_error": eerr(u),
             "ms_ratio_to_main": round(float(np.mean(tv)) / ms, 3)}
 
     cpu = None
@@ -464,7 +497,7 @@ def main():
                    "nnzb": [L["nnzb"] for L in levels],
                    "l2": "inputs larger than L2 (A_0 values 280 MB)",
                    "parallelism": f"replicas x{ws}"},
-        "iters": it_mean, "true_relres": true_rel, "setup_s": round(setup_s, 2), "setup_parts": setup_parts,
+        "iters": it_mean, "true_relres": true_rel, "accuracy": accuracy, "setup_s": round(setup_s, 2), "setup_parts": setup_parts,
         "generate_s": round(gen_s, 2), "solve_gbs": round(solve_gbs, 1),
         "bytes_per_iteration": int(per_it_bytes), "solves_per_s": round(ws * 1e3 / ms, 2),
         "wall_s_timed": round(wall, 3),
@@ -479,6 +512,7 @@ def main():
         line["learned"] = learned_info
     if rank == 0:
         print(json.dumps(line), flush=True)
+    eerr.close()
     ctx.close()
     if ws > 1:
         torch.distributed.destroy_process_group()
@@ -734,7 +768,7 @@ def run_batch(args, ws, rank, local, problems):
     gbs = per_step_bytes / (ms * 1e-3) / 1e9
     per_it, fixed = B.launches()
     launches = fixed + max(its) * per_it
-    tuned = [ln for ln in B.describe().splitlines() if "lanes/row" in ln]
+    tuned = [ln for ln in B.describe().splitlines() if "lanes/row" in ln or "SELL-32" in ln]
     n_dofs = [levels[0]["n_rows"] * levels[0]["block"] for levels in levels_per_system]
 
     cpu = None

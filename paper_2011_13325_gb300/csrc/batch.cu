@@ -27,6 +27,7 @@ struct SpmmOp {
   const void *vals, *x, *b, *minv;
   void *y;
   int sys;
+  const void *svals;  // SELL-32 values in the operator's precision (NULL: none)
 };
 
 struct Stage {
@@ -84,10 +85,10 @@ static int cdiv(long a, long b) { return (int)((a + b - 1) / b); }
 // ---------------------------------------------------------------------------
 static void build_spmm_items(Stage &S) {
   S.sp.clear();
-  const int rpb = S.wpb * (32 / S.lpr);
+  const int rpb = S.lpr ? S.wpb * (32 / S.lpr) : 0;
   int first = 0;
   for (const SpmmOp &o : S.ops) {
-    SpmmItem it;
+    SpmmItem it{};
     it.rowptr = o.A->rowptr;
     it.colidx = o.A->colidx;
     it.vals = o.vals;
@@ -98,7 +99,11 @@ static void build_spmm_items(Stage &S) {
     it.n_rows = o.A->n_rows;
     it.sys = o.sys;
     it.first_block = first;
-    first += cdiv(o.A->n_rows, rpb);
+    it.sell_ptr = o.A->sell_ptr;
+    it.sell_col = o.A->sell_col;
+    it.svals = o.svals;
+    it.n_slices = o.A->n_slices;
+    first += S.lpr ? cdiv(o.A->n_rows, rpb) : cdiv(o.A->n_slices, S.wpb);
     S.sp.push_back(it);
   }
   S.n_items = (int)S.sp.size();
@@ -164,6 +169,11 @@ static const void *vals_of(const DevBSR &A, int prec) {
   return prec == AMG_PREC_FP64 ? (const void *)A.v64
                                : prec == AMG_PREC_FP32_VCYCLE ? (const void *)A.v32 : (const void *)A.v16;
 }
+static const void *svals_of(const DevBSR &A, int prec) {
+  if (!A.sell_ptr) return nullptr;
+  return prec == AMG_PREC_FP64 ? (const void *)A.s64
+                               : prec == AMG_PREC_FP32_VCYCLE ? (const void *)A.s32 : (const void *)A.s16;
+}
 
 // the stages of init (r = f - A x), body (one PCG iteration with the
 // V-cycle) and tail (unpack)
@@ -176,7 +186,7 @@ static void build_stages(Batch *B) {
     std::vector<SpmmOp> ops;
     for (int s = 0; s < ns; ++s) {
       const DevBSR &A = B->ctx[s]->levels[0].A;
-      ops.push_back(SpmmOp{&A, A.v64, B->gsh[s].x, B->gsh[s].f, nullptr, B->gsh[s].r, s});
+      ops.push_back(SpmmOp{&A, A.v64, B->gsh[s].x, B->gsh[s].f, nullptr, B->gsh[s].r, s, svals_of(A, 0)});
     }
     add_spmm(B->init, "r = f - A_0 x", ops, SPMV_RESID, 0, 0);
   }
@@ -220,9 +230,9 @@ static void build_stages(Batch *B) {
         d.sys = s;
         dg.push_back({L.k, d});
         resid.push_back(SpmmOp{&L.A, vals_of(L.A, prec), B->vec[s].lx[l], bvec(s, l), nullptr,
-                               B->vec[s].lt[l], s});
+                               B->vec[s].lt[l], s, svals_of(L.A, prec)});
         restr.push_back(SpmmOp{&L.R, vals_of(L.R, prec), B->vec[s].lt[l], nullptr, nullptr,
-                               B->vec[s].lb[l + 1], s});
+                               B->vec[s].lb[l + 1], s, svals_of(L.R, prec)});
       } else if (l == Ls - 1) {
         CoarseItem ci{};
         ci.cinv = c->cinv;
@@ -286,10 +296,11 @@ static void build_stages(Batch *B) {
       if (l >= (int)c->levels.size() - 1) continue;
       const Level &L = c->levels[l];
       prol.push_back(SpmmOp{&L.P, vals_of(L.P, prec), B->vec[s].ly[l + 1], nullptr, nullptr,
-                            B->vec[s].lx[l], s});
+                            B->vec[s].lx[l], s, svals_of(L.P, prec)});
       smooth.push_back(SpmmOp{&L.A, vals_of(L.A, prec), B->vec[s].lx[l], bvec(s, l),
                               f64 ? (const void *)L.minv64 : (const void *)L.minv32,
-                              l == 0 ? (void *)B->gsh[s].z : B->vec[s].ly[l], s});
+                              l == 0 ? (void *)B->gsh[s].z : B->vec[s].ly[l], s,
+                              svals_of(L.A, prec)});
     }
     add_spmm(B->body, ls + " x += P y_c" + pn, prol, SPMV_ADD, prec, 0);
     add_spmm(B->body, ls + " y = x + M^+(b - A x)" + pn, smooth, SPMV_SMOOTH, prec,
@@ -306,7 +317,7 @@ static void build_stages(Batch *B) {
     std::vector<SpmmOp> ops;
     for (int s = 0; s < ns; ++s) {
       const DevBSR &A = B->ctx[s]->levels[0].A;
-      ops.push_back(SpmmOp{&A, A.v64, B->gsh[s].p, nullptr, nullptr, B->gsh[s].q, s});
+      ops.push_back(SpmmOp{&A, A.v64, B->gsh[s].p, nullptr, nullptr, B->gsh[s].q, s, svals_of(A, 0)});
     }
     add_spmm(B->body, "q = A_0 p", ops, SPMV_SET, 0, 0);
   }
@@ -391,15 +402,21 @@ static cudaError_t autotune(Batch *B) {
   }
   AMG_CUDA_TRY(cudaMemcpyAsync(B->st, B->st_host, sizeof(McgState) * B->ctx.size(),
                                cudaMemcpyHostToDevice, B->stream));
-  const int lprs[3] = {32, 16, 8}, wpbs[2] = {8, 4};
+  // candidates: (lanes per row, warps per block); (0, s): SELL-32, s slices
+  // per block, when every operator of the stage has its SELL copy
+  const int cand[8][2] = {{32, 8}, {32, 4}, {16, 8}, {16, 4}, {8, 8}, {8, 4}, {0, 4}, {0, 2}};
   for (auto *v : {&B->init, &B->body})
     for (Stage &S : *v) {
       if (S.kind != ST_SPMM) continue;
+      bool sell = gsell_supported(S.key.br, S.key.bc);
+      for (const SpmmOp &o : S.ops) sell = sell && o.svals && o.A->sell_ptr;
       float best = 1e30f;
       int bl = 32, bw = 8;
-      for (int lpr : lprs)
-        for (int wpb : wpbs) {
-          if (lpr < S.key.br) continue;
+      for (const auto &cw : cand) {
+        const int lpr = cw[0], wpb = cw[1];
+        if (lpr != 0 && lpr < S.key.br) continue;
+        if (lpr == 0 && !sell) continue;
+        {
           S.lpr = lpr;
           S.wpb = wpb;
           build_spmm_items(S);
@@ -418,6 +435,7 @@ static cudaError_t autotune(Batch *B) {
             bw = wpb;
           }
         }
+      }
       S.lpr = bl;
       S.wpb = bw;
       S.us = best * 1e3f / 3.f;
@@ -501,7 +519,10 @@ static std::string describe(const Batch *B) {
   for (auto *v : {&B->init, &B->body, &B->tail}) {
     const char *part = v == &B->init ? "init" : v == &B->body ? "iteration" : "tail";
     for (const Stage &S : *v) {
-      if (S.kind == ST_SPMM)
+      if (S.kind == ST_SPMM && S.lpr == 0)
+        snprintf(line, sizeof line, "%s: %s: %d systems, %d blocks, SELL-32 thread/row, %d slices/block, %.1f us\n",
+                 part, S.name.c_str(), S.n_items, S.grid, S.wpb, S.us);
+      else if (S.kind == ST_SPMM)
         snprintf(line, sizeof line, "%s: %s: %d systems, %d blocks, %d lanes/row, %d warps/block, %.1f us\n",
                  part, S.name.c_str(), S.n_items, S.grid, S.lpr, S.wpb, S.us);
       else
@@ -511,6 +532,21 @@ static std::string describe(const Batch *B) {
     }
   }
   return d;
+}
+
+// SELL-32 copies of every system's A_0 and P_0 (candidates of the tuner;
+// they also serve the system's own single-system kernels)
+static cudaError_t ensure_sell(Batch *B) {
+  for (Ctx *c : B->ctx) {
+    DevBSR *ops[2] = {&c->levels[0].A, c->levels.size() > 1 ? &c->levels[0].P : nullptr};
+    for (DevBSR *m : ops) {
+      if (!m || !m->nnzb || m->sell_ptr || !gsell_supported(m->br, m->bc)) continue;
+      AMG_CUDA_TRY(build_sell(c, *m));
+      if (c->precision != AMG_PREC_FP64) AMG_CUDA_TRY(make_low_precision(c, *m, c->precision));
+      AMG_CUDA_TRY(cudaStreamSynchronize(c->stream));
+    }
+  }
+  return cudaSuccess;
 }
 
 static cudaError_t create_buffers(Batch *B) {
@@ -659,6 +695,7 @@ int amg_batch_create(amg_batch **out, amg_ctx *const *systems, int n_systems, in
   B->precision = B->ctx[0]->precision;
   B->num_sms = B->ctx[0]->num_sms;
   cudaError_t e = cudaSetDevice(B->device);
+  if (e == cudaSuccess) e = ensure_sell(B);
   if (e == cudaSuccess) e = create_buffers(B);
   if (e == cudaSuccess) {
     build_stages(B);

@@ -144,10 +144,83 @@ __global__ void __launch_bounds__(256) gspmm_kernel(const SpmmItem *__restrict__
   }
 }
 
+// SELL-32 form: one thread per block row; slot j of a slice holds one block
+// per lane, element e of the 32 blocks contiguous (coalesced value loads)
+template <int BR, int BC, int NR, typename V, typename T, int MODE, typename TO>
+__global__ void __launch_bounds__(128) gsell_kernel(const SpmmItem *__restrict__ items, int n_items,
+                                                    const McgState *__restrict__ st) {
+  using A = typename GAcc<T>::type;
+  constexpr int E = BR * BC;
+  const int ii = find_item(items, n_items, blockIdx.x);
+  const SpmmItem &I = items[ii];
+  if (!st[I.sys].active) return;
+  const int slice = (blockIdx.x - I.first_block) * (blockDim.x >> 5) + (threadIdx.x >> 5);
+  if (slice >= I.n_slices) return;  // whole warp
+  const int t = threadIdx.x & 31;
+  const int row = slice * 32 + t;
+  const int j0 = __ldg(I.sell_ptr + slice), j1 = __ldg(I.sell_ptr + slice + 1);
+  const T *__restrict__ x = (const T *)I.x;
+  const V *__restrict__ sv = (const V *)I.svals;
+  A acc[BR][NR];
+#pragma unroll
+  for (int r = 0; r < BR; ++r)
+#pragma unroll
+    for (int j = 0; j < NR; ++j) acc[r][j] = 0;
+  for (int j = j0; j < j1; ++j) {
+    const int c = __ldg(I.sell_col + (size_t)j * 32 + t);
+    const V *v = sv + (size_t)j * E * 32 + t;
+    const T *xp = x + (size_t)c * BC * NR;
+#pragma unroll
+    for (int q = 0; q < BC; ++q) {
+      A xv[NR];
+      gld_nr<NR>(xp + q * NR, xv);
+#pragma unroll
+      for (int r = 0; r < BR; ++r) {
+        const A a = (A)glds(v + (r * BC + q) * 32);
+#pragma unroll
+        for (int jj = 0; jj < NR; ++jj) acc[r][jj] += a * xv[jj];
+      }
+    }
+  }
+  if (row >= I.n_rows) return;
+  const size_t o = (size_t)row * BR;
+  TO *__restrict__ y = (TO *)I.y;
+  const T *__restrict__ b = (const T *)I.b;
+  if (MODE == SPMV_SMOOTH) {
+    const T *__restrict__ minv = (const T *)I.minv;
+#pragma unroll
+    for (int jj = 0; jj < NR; ++jj) {
+      A res[BR];
+#pragma unroll
+      for (int r = 0; r < BR; ++r) res[r] = (A)b[(o + r) * NR + jj] - acc[r][jj];
+#pragma unroll
+      for (int r = 0; r < BR; ++r) {
+        A u = 0;
+#pragma unroll
+        for (int q = 0; q < BR; ++q) u += (A)minv[(o + r) * BR + q] * res[q];
+        y[(o + r) * NR + jj] = (TO)((A)x[(o + r) * NR + jj] + u);
+      }
+    }
+  } else {
+#pragma unroll
+    for (int r = 0; r < BR; ++r)
+#pragma unroll
+      for (int jj = 0; jj < NR; ++jj) {
+        const size_t i = (o + r) * NR + jj;
+        if (MODE == SPMV_SET) y[i] = (TO)acc[r][jj];
+        if (MODE == SPMV_RESID) y[i] = (TO)((A)b[i] - acc[r][jj]);
+        if (MODE == SPMV_ADD) y[i] = (TO)((A)y[i] + acc[r][jj]);
+      }
+  }
+}
+
 template <int BR, int BC, int NR, int LPR, typename V, typename T, int MODE, typename TO>
 static cudaError_t gspmm_go(int wpb, const SpmmItem *items, int n_items, int grid,
                             const McgState *st, cudaStream_t s) {
-  gspmm_kernel<BR, BC, NR, LPR, V, T, MODE, TO><<<grid, wpb * 32, 0, s>>>(items, n_items, st);
+  if constexpr (LPR == 0)
+    gsell_kernel<BR, BC, NR, V, T, MODE, TO><<<grid, wpb * 32, 0, s>>>(items, n_items, st);
+  else
+    gspmm_kernel<BR, BC, NR, LPR, V, T, MODE, TO><<<grid, wpb * 32, 0, s>>>(items, n_items, st);
   return cudaGetLastError();
 }
 
@@ -203,9 +276,19 @@ static cudaError_t gspmm_lpr(const SpmmKey &k, int wpb, const SpmmItem *items, i
   return cudaErrorInvalidValue;
 }
 
+bool gsell_supported(int br, int bc) {
+  return (br == 3 && bc == 3) || (br == 3 && bc == 6) || (br == 2 && bc == 2) || (br == 2 && bc == 3);
+}
+
 template <int BR, int BC, int NR>
 static cudaError_t gspmm_shape(const SpmmKey &k, int lpr, int wpb, const SpmmItem *items,
                                int n_items, int grid, const McgState *st, cudaStream_t s) {
+  constexpr bool sell_ok = (BR == 3 && BC == 3) || (BR == 3 && BC == 6) || (BR == 2 && BC == 2) ||
+                           (BR == 2 && BC == 3);
+  if (lpr == 0) {
+    if constexpr (sell_ok) return gspmm_lpr<BR, BC, NR, 0>(k, wpb, items, n_items, grid, st, s);
+    return cudaErrorInvalidValue;
+  }
   switch (lpr) {
     case 32: return gspmm_lpr<BR, BC, NR, 32>(k, wpb, items, n_items, grid, st, s);
     case 16: return gspmm_lpr<BR, BC, NR, 16>(k, wpb, items, n_items, grid, st, s);
@@ -233,7 +316,8 @@ static cudaError_t gspmm_nr(const SpmmKey &k, int lpr, int wpb, const SpmmItem *
 cudaError_t launch_gspmm(const SpmmKey &k, int nr, int lpr, int wpb, const SpmmItem *items,
                          int n_items, int grid, const McgState *st, cudaStream_t s) {
   if (grid <= 0 || n_items <= 0) return cudaSuccess;
-  if (wpb < 1 || wpb > 8 || lpr < k.br) return cudaErrorInvalidValue;
+  if (wpb < 1 || wpb > 8 || (lpr != 0 && lpr < k.br)) return cudaErrorInvalidValue;
+  if (lpr == 0 && wpb > 4) return cudaErrorInvalidValue;
   if (nr == 6) return gspmm_nr<6>(k, lpr, wpb, items, n_items, grid, st, s);
   if (nr == 1) return gspmm_nr<1>(k, lpr, wpb, items, n_items, grid, st, s);
   return cudaErrorInvalidValue;

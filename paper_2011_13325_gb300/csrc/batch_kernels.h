@@ -42,6 +42,10 @@ struct SpmmItem {
   const void *vals, *x, *b, *minv;
   void *y;
   int n_rows, sys, first_block;
+  // SELL-32 copy of the operator (thread per block row), if present
+  const int *sell_ptr, *sell_col;
+  const void *svals;
+  int n_slices;
 };
 struct DiagItem {
   const void *minv, *bin;
@@ -63,7 +67,10 @@ struct SpmmKey {
   int br, bc, vt, mode, to64;  // to64: FP64 output from an FP32 / BF16 operator
 };
 
-// lanes per row (32, 16 or 8) and warps per block (tile / schedule choice)
+// lanes per row (32, 16 or 8) and warps per block (tile / schedule choice);
+// lpr = 0: the SELL-32 copy, one thread per block row, wpb slices per block
+// (block shapes with gsell_supported only)
+bool gsell_supported(int br, int bc);
 cudaError_t launch_gspmm(const SpmmKey &k, int nr, int lpr, int wpb, const SpmmItem *items,
                          int n_items, int grid, const McgState *st, cudaStream_t s);
 // kind: 0 FP64; 1 FP64 input -> FP32 (+ FP32 copy of the input); 2 FP32

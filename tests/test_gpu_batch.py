@@ -229,8 +229,11 @@ def test_batch_schedule_is_grouped_and_tuned():
     ctxs, B = _batch(1)
     per_it, fixed = B.launches()
     d = B.describe()
-    prods = [ln for ln in d.splitlines() if "lanes/row" in ln]
-    assert prods and all(any(f"{l} lanes/row" in ln for l in (32, 16, 8)) for ln in prods)
+    prods = [ln for ln in d.splitlines() if "lanes/row" in ln or "SELL-32" in ln]
+    assert prods and all(any(f"{l} lanes/row" in ln for l in (32, 16, 8)) or "SELL-32" in ln
+                         for ln in prods)
+    # the FP64 CG product of every system is one of the tuned stages
+    assert any("q = A_0 p" in ln for ln in prods)
     assert len([ln for ln in d.splitlines() if ln.startswith("iteration")]) == per_it
     ctx1, B1 = ctxs[:2], amg.Batch(ctxs[:2], 6)
     assert B1.launches()[0] <= per_it <= 40
