@@ -105,7 +105,9 @@ def galerkin(P: Mat, A: Mat) -> Mat:
     # scatter the scalar entries into the structural blocks (sorted block keys)
     key_blocks = rows * nc + cols
     vals = np.zeros((cols.shape[0], k, k))
-    pos = np.searchsorted(key_blocks, (Cd.row // k) * nc + (Cd.col // k))
+    crow = Cd.row.astype(np.int64) // k   # 64-bit keys: nc^2 exceeds 2^31 beyond 46,340 rows
+    ccol = Cd.col.astype(np.int64) // k
+    pos = np.searchsorted(key_blocks, crow * nc + ccol)
     vals[pos, Cd.row % k, Cd.col % k] = Cd.data
     return Mat(nc, nc, S.indptr.astype(np.int64), cols, vals)
 

@@ -164,3 +164,28 @@ def test_pcg_recovers_manufactured_solution(which, request):
         err = np.sqrt(e @ solve.spmv(A, e)) / np.sqrt(ustar @ solve.spmv(A, ustar))
         assert err <= 1e-7
         assert hist[-1] <= 1e-12
+
+
+def test_galerkin_many_coarse_rows_keeps_block_keys():
+    """P = I on 50,000 block rows (nc^2 > 2^31): P^T A P must return A itself
+    (the block keys of the scatter need 64-bit arithmetic)."""
+    n, k = 50_000, 3
+    rng = np.random.default_rng(0)
+    rp = np.arange(n + 1, dtype=np.int64)
+    ci = np.arange(n, dtype=np.int64)
+    eye = np.tile(np.eye(k), (n, 1, 1))
+    P = solve.Mat(n, n, rp, ci, eye)
+    # A: diagonal blocks plus a coupling of row i to row n-1-i
+    rows, cols = [], []
+    for i in range(n):
+        j = n - 1 - i
+        rows += [i] * (1 if i == j else 2)
+        cols += sorted({i, j})
+    rows, cols = np.array(rows), np.array(cols)
+    Arp = np.zeros(n + 1, dtype=np.int64)
+    np.cumsum(np.bincount(rows, minlength=n), out=Arp[1:])
+    vals = rng.normal(size=(cols.shape[0], k, k))
+    A = solve.Mat(n, n, Arp, cols, vals)
+    C = solve.galerkin(P, A)
+    assert np.array_equal(C.rowptr, A.rowptr) and np.array_equal(C.colidx, A.colidx)
+    assert np.array_equal(C.vals, A.vals)
