@@ -261,6 +261,8 @@ def main():
                     help="comma list of other precisions timed for comparison ('auto': the two "
                          "others, '': none)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-accuracy", action="store_true",
+                    help="skip the tight FP64 reference solve (energy-norm errors); for profiling")
     ap.add_argument("--rtol", type=float, default=1e-8)
     ap.add_argument("--pcg-mode", default="graph", choices=["graph", "host"],
                     help="graph: whole PCG in one CUDA graph (default); host: the same kernels "
@@ -367,8 +369,11 @@ def main():
     ctx.residual(0, f, u, res)
     true_rel = float(torch.linalg.norm(res) / torch.linalg.norm(f))
     P_list = [ctx.download_prolongation(l) for l in range(ctx.n_levels - 1)]
-    eerr = EnergyError(amg, problem, P_list, f, local, stream)
-    accuracy = {"energy_error": eerr(u), "reference": eerr.reference}
+    if args.no_accuracy:
+        eerr, accuracy = (lambda _u: None), None
+    else:
+        eerr = EnergyError(amg, problem, P_list, f, local, stream)
+        accuracy = {"energy_error": eerr(u), "reference": eerr.reference}
 
     # A_0 SpMV (SELL-32, FP64), events per launch: FP64 on sm_103a is bound by
     # the FP64 pipe; report flops against the live FMA probe and bytes against HBM
@@ -512,7 +517,8 @@ def main():
         line["learned"] = learned_info
     if rank == 0:
         print(json.dumps(line), flush=True)
-    eerr.close()
+    if not args.no_accuracy:
+        eerr.close()
     ctx.close()
     if ws > 1:
         torch.distributed.destroy_process_group()
