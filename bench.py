@@ -176,10 +176,21 @@ def traffic_record():
         return None
     with open(p) as f:
         rec = json.load(f)
-    sha = hashlib.sha1(open(src, "rb").read()).hexdigest()
-    if rec.get("source_sha1") != sha:
+    if rec.get("kernel_source_sha1") != kernel_source_sha1(src, "sell_kernel"):
         return None
     return rec
+
+
+def kernel_source_sha1(path, name):
+    """SHA-1 of the source text of the __global__ function `name` (from its
+    template line to its closing brace): the traffic record stays valid while
+    that kernel is unchanged."""
+    import hashlib
+    text = open(path).read()
+    i = text.index(f" {name}(int n_rows")
+    start = text.rindex("template <", 0, i)
+    end = text.index("\n}\n", i) + 3
+    return hashlib.sha1(text[start:end].encode()).hexdigest()
 
 
 # ---------------------------------------------------------------------------
@@ -512,6 +523,7 @@ def main():
         "gpu_launches": launches * args.steps, "gpu_launches_per_step": launches,
         "cpu_baseline": cpu,
     }
+    line["kernels"] = [ln for ln in ctx.describe().splitlines()]
     if learned_info is not None:
         line["config"]["smoother"] = "learned MLP (level 0), block-l1 Jacobi below"
         line["learned"] = learned_info

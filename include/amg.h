@@ -226,14 +226,24 @@ int amg_set_pcg_graph(amg_ctx *ctx, int enable);
  *   AMG_LAYOUT_WARP_ROWS        warp-per-row BSR kernels only
  *   AMG_LAYOUT_ROW_LANES        row-lane BSR kernels only (one lane per
  *                               scalar row of a block row, no reduction)
+ *   AMG_LAYOUT_BLOCK_LANES      block-lane BSR kernels only (one warp per
+ *                               block row, one whole block per lane)
+ * Under AMG_LAYOUT_AUTO the upload also times, for every V-cycle operator
+ * without a SELL-32 copy, the warp-row, row-lane and block-lane kernels on
+ * the operator itself and keeps the fastest.
  * The result of every operator is the same up to the order of the sums. */
 enum {
   AMG_LAYOUT_AUTO = 0,
   AMG_LAYOUT_SELL_SHORT_ROWS = 1,
   AMG_LAYOUT_WARP_ROWS = 2,
-  AMG_LAYOUT_ROW_LANES = 3
+  AMG_LAYOUT_ROW_LANES = 3,
+  AMG_LAYOUT_BLOCK_LANES = 4
 };
 int amg_set_layout_policy(amg_ctx *ctx, int policy);
+
+/* Text listing every level operator with its size and the kernel that
+ * applies it (after the tuner); owned by ctx, valid until the next call. */
+const char *amg_describe(amg_ctx *ctx);
 
 /* Wall-clock seconds of the last amg_setup: [0] host setup (edge matrices,
  * Algorithm 1, prolongations), [1] device Galerkin products and transfers,

@@ -32,6 +32,7 @@ AMG_LAYOUT_AUTO = 0
 AMG_LAYOUT_SELL_SHORT_ROWS = 1
 AMG_LAYOUT_WARP_ROWS = 2
 AMG_LAYOUT_ROW_LANES = 3
+AMG_LAYOUT_BLOCK_LANES = 4
 AMG_SMOOTHER_L1_JACOBI = 0
 AMG_SMOOTHER_LEARNED = 1
 
@@ -105,6 +106,7 @@ _SIGS = {
     "amg_prolongation_info": (_I, [_P, _I, C.POINTER(C.c_int32), C.POINTER(C.c_int32),
                                    C.POINTER(C.c_int32), C.POINTER(C.c_int32), C.POINTER(C.c_int64)]),
     "amg_download_prolongation": (_I, [_P, _I, _P, _P, _P]),
+    "amg_describe": (C.c_char_p, [_P]),
     "amg_mlp_create": (_I, [C.POINTER(_P), _I, C.c_uint64]),
     "amg_mlp_destroy": (None, [_P]),
     "amg_mlp_last_error": (C.c_char_p, [_P]),
@@ -355,6 +357,9 @@ class Context:
 
     def reset_smoother(self):
         return self._check(lib().amg_reset_smoother(self.h))
+
+    def describe(self):
+        return lib().amg_describe(self.h).decode()
 
     def set_layout_policy(self, policy: int):
         return self._check(lib().amg_set_layout_policy(self.h, int(policy)))

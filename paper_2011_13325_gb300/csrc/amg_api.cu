@@ -276,6 +276,61 @@ static int finish(Ctx *c, const char *where) {
   return AMG_OK;
 }
 
+// Kernel tuner of the upload (AMG_LAYOUT_AUTO): every V-cycle operator that
+// has no SELL-32 copy is applied with the warp-row, row-lane and block-lane
+// kernels (one warm launch, then three timed) in the V-cycle precision, and
+// keeps the fastest.  The kernels differ only in the order of the sums.
+static cudaError_t tune_operators(Ctx *c) {
+  if (c->layout_policy != AMG_LAYOUT_AUTO) return cudaSuccess;
+  std::vector<DevBSR *> ops;
+  size_t nx = 0, ny = 0;
+  for (int l = 0; l + 1 < (int)c->levels.size(); ++l) {
+    Level &L = c->levels[l];
+    for (DevBSR *m : {&L.A, &L.P, &L.R}) {
+      if (!m->nnzb || m->sell_ptr) continue;
+      ops.push_back(m);
+      nx = std::max(nx, (size_t)m->n_cols * m->bc);
+      ny = std::max(ny, (size_t)m->n_rows * m->br);
+    }
+  }
+  if (ops.empty()) return cudaSuccess;
+  void *x = nullptr, *y = nullptr;
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  cudaError_t e = dalloc(&x, nx * sizeof(double));
+  if (e == cudaSuccess) e = dalloc(&y, ny * sizeof(double));
+  if (e == cudaSuccess) e = cudaMemsetAsync(x, 0, nx * sizeof(double), c->stream);
+  if (e == cudaSuccess) e = cudaEventCreate(&e0);
+  if (e == cudaSuccess) e = cudaEventCreate(&e1);
+  const int kerns[3] = {KERN_WARP_ROWS, KERN_ROW_LANES, KERN_BLOCK_LANES};
+  for (size_t i = 0; i < ops.size() && e == cudaSuccess; ++i) {
+    DevBSR &m = *ops[i];
+    float best = 1e30f;
+    int pick = KERN_WARP_ROWS;
+    for (int k : kerns) {
+      m.kern = k;
+      e = launch_bsr(c, m, c->precision, SPMV_SET, x, nullptr, nullptr, y);
+      if (e == cudaSuccess) e = cudaEventRecord(e0, c->stream);
+      for (int r = 0; r < 3 && e == cudaSuccess; ++r)
+        e = launch_bsr(c, m, c->precision, SPMV_SET, x, nullptr, nullptr, y);
+      if (e == cudaSuccess) e = cudaEventRecord(e1, c->stream);
+      if (e == cudaSuccess) e = cudaEventSynchronize(e1);
+      float ms = 0.f;
+      if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, e0, e1);
+      if (e != cudaSuccess) break;
+      if (ms < best) {
+        best = ms;
+        pick = k;
+      }
+    }
+    m.kern = pick;
+  }
+  if (e0) cudaEventDestroy(e0);
+  if (e1) cudaEventDestroy(e1);
+  dfree(x);
+  dfree(y);
+  return e;
+}
+
 // Smoothers, level vectors, low-precision copies, coarsest inverse, CG buffers.
 static int finalize_hierarchy(Ctx *c) {
   const int precision = c->precision;
@@ -292,6 +347,7 @@ static int finalize_hierarchy(Ctx *c) {
       if (L.R.nnzb) CUDA_OR_FAIL(c, make_low_precision(c, L.R, precision), "low precision R");
     }
   }
+  CUDA_OR_FAIL(c, tune_operators(c), "kernel tuner");
   CUDA_OR_FAIL(c, coarse_setup(c), "coarse setup");
   CUDA_OR_FAIL(c, pcg_alloc(c), "pcg buffers");
   return finish(c, "upload");
@@ -398,6 +454,30 @@ void amg_destroy(amg_ctx *h) {
 }
 
 const char *amg_last_error(const amg_ctx *h) { return h ? h->c.err.c_str() : "NULL context"; }
+
+const char *amg_describe(amg_ctx *h) {
+  if (!h) return "";
+  Ctx *c = &h->c;
+  static const char *kname[3] = {"warp rows", "row lanes", "block lanes"};
+  std::string d;
+  char line[256];
+  for (int l = 0; l < (int)c->levels.size(); ++l) {
+    const Level &L = c->levels[l];
+    const char *nm[3] = {"A", "P", "R"};
+    const DevBSR *ops[3] = {&L.A, &L.P, &L.R};
+    for (int i = 0; i < 3; ++i) {
+      const DevBSR &m = *ops[i];
+      if (!m.nnzb) continue;
+      const char *k = m.sell_ptr ? "SELL-32 (thread per block row)"
+                                 : kname[m.kern >= 0 && m.kern < 3 ? m.kern : 0];
+      snprintf(line, sizeof line, "level %d %s: %d x %d blocks of %dx%d, %lld stored, %s\n", l, nm[i],
+               m.n_rows, m.n_cols, m.br, m.bc, (long long)m.nnzb, k);
+      d += line;
+    }
+  }
+  c->desc = d;
+  return c->desc.c_str();
+}
 
 int amg_upload_hierarchy(amg_ctx *h, const amg_hierarchy *hier, int precision, int smoother) {
   if (!h) return AMG_ERR_ARG;
@@ -730,7 +810,7 @@ int amg_probe_fma_rate(amg_ctx *h, double *fp64_gflops, double *fp32_gflops) {
 
 int amg_set_layout_policy(amg_ctx *h, int policy) {
   if (!h) return AMG_ERR_ARG;
-  if (policy < AMG_LAYOUT_AUTO || policy > AMG_LAYOUT_ROW_LANES)
+  if (policy < AMG_LAYOUT_AUTO || policy > AMG_LAYOUT_BLOCK_LANES)
     return fail(&h->c, AMG_ERR_ARG, "unknown layout policy");
   h->c.layout_policy = policy;
   return AMG_OK;

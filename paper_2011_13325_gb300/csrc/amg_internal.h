@@ -14,6 +14,8 @@ namespace amg {
 
 // Device block-sparse-row matrix.  Values exist in FP64 always; FP32 / BF16
 // copies only for the mixed-precision V-cycles.
+enum BsrKernel { KERN_WARP_ROWS = 0, KERN_ROW_LANES = 1, KERN_BLOCK_LANES = 2 };
+
 struct DevBSR {
   int n_rows = 0, n_cols = 0, br = 0, bc = 0;
   int64_t nnzb = 0;
@@ -27,6 +29,8 @@ struct DevBSR {
   // slot j of lane t: column sell_col[j*32 + t], element q of its block at
   // s??[(j*br*bc + q)*32 + t] (every element of a slot is one coalesced
   // 32-wide row); padding slots have column 0 and zero values.
+  // kernel of the BSR form (set by the upload's tuner under AMG_LAYOUT_AUTO)
+  int kern = 0;  // KERN_WARP_ROWS / KERN_ROW_LANES / KERN_BLOCK_LANES
   int n_slices = 0;
   int64_t sell_slots = 0;
   int *sell_ptr = nullptr;
@@ -58,6 +62,7 @@ struct Ctx {
   bool own_stream = false;
   int num_sms = 0;
   std::string err;
+  std::string desc;  // amg_describe text
   std::vector<Level> levels;
   int precision = AMG_PREC_FP64;
   int smoother = AMG_SMOOTHER_L1_JACOBI;

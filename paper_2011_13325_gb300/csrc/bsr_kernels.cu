@@ -305,6 +305,114 @@ static cudaError_t rowlane_mode(const Ctx *c, const DevBSR &A, const V *vals, in
   return cudaGetLastError();
 }
 
+// Block-lane variant: one warp per block row; lane j takes the blocks j,
+// j + 32, ... of the row whole (all BR x BC values, contiguous, the widest
+// aligned loads) and keeps BR partial sums, which a butterfly reduction then
+// leaves on every lane.  Meant for long rows of large blocks (6x6 coarse
+// levels, restrictions), where one block-row element per lane spends most of
+// its loads on x entries that the lanes of the same block share.
+template <int E, bool W16>
+__device__ __forceinline__ void ldblock(const float *p, float *out) {
+  if constexpr (W16 && E % 4 == 0) {
+#pragma unroll
+    for (int i = 0; i < E; i += 4) {
+      const float4 v = __ldcs(reinterpret_cast<const float4 *>(p + i));
+      out[i] = v.x;
+      out[i + 1] = v.y;
+      out[i + 2] = v.z;
+      out[i + 3] = v.w;
+    }
+  } else {
+    ldn_stream<E>(p, out);
+  }
+}
+template <int E, bool W16>
+__device__ __forceinline__ void ldblock(const double *p, double *out) {
+  ldn_stream<E>(p, out);
+}
+template <int E, bool W16>
+__device__ __forceinline__ void ldblock(const __nv_bfloat16 *p, float *out) {
+  ldn_stream<E>(p, out);
+}
+
+template <int BR, int BC, typename V, typename T, int MODE>
+__global__ void __launch_bounds__(256) bsr_lblock_kernel(int n_rows, const int *__restrict__ rowptr,
+                                                         const int *__restrict__ colidx,
+                                                         const V *__restrict__ vals,
+                                                         const T *__restrict__ x,
+                                                         const T *__restrict__ b,
+                                                         const T *__restrict__ minv,
+                                                         T *__restrict__ y) {
+  using A = typename AccT<T>::type;
+  constexpr int E = BR * BC;
+  // a block starts 16-byte aligned when E * sizeof(V) is a multiple of 16
+  constexpr bool W16 = (E * sizeof(V)) % 16 == 0;
+  const int lane = threadIdx.x & 31;
+  const int nwarps = (gridDim.x * blockDim.x) >> 5;
+  for (int row = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; row < n_rows; row += nwarps) {
+    const int s = rowptr[row], e = rowptr[row + 1];
+    A acc[BR];
+#pragma unroll
+    for (int r = 0; r < BR; ++r) acc[r] = 0;
+    for (int p = s + lane; p < e; p += 32) {
+      const int c = __ldg(colidx + p);
+      A xv[BC], v[E];
+      ldn_cached<BC>(x + (size_t)c * BC, xv);
+      ldblock<E, W16>(vals + (size_t)p * E, v);
+#pragma unroll
+      for (int r = 0; r < BR; ++r)
+#pragma unroll
+        for (int q = 0; q < BC; ++q) acc[r] += v[r * BC + q] * xv[q];
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1)
+#pragma unroll
+      for (int r = 0; r < BR; ++r) acc[r] += __shfl_xor_sync(0xffffffffu, acc[r], o);
+    const size_t o = (size_t)row * BR;
+    if (lane >= BR) continue;
+    A mine = 0;  // acc[lane] without dynamic register indexing
+#pragma unroll
+    for (int r = 0; r < BR; ++r)
+      if (lane == r) mine = acc[r];
+    if (MODE == SPMV_SMOOTH) {
+      A upd = 0;
+#pragma unroll
+      for (int q = 0; q < BR; ++q) upd += (A)minv[(o + lane) * BR + q] * ((A)b[o + q] - acc[q]);
+      y[o + lane] = (T)((A)x[o + lane] + upd);
+    } else {
+      if (MODE == SPMV_SET) y[o + lane] = (T)mine;
+      if (MODE == SPMV_RESID) y[o + lane] = (T)((A)b[o + lane] - mine);
+      if (MODE == SPMV_ADD) y[o + lane] = (T)((A)y[o + lane] + mine);
+    }
+  }
+}
+
+template <int BR, int BC, typename V, typename T>
+static cudaError_t lblock_mode(const Ctx *c, const DevBSR &A, const V *vals, int mode, const void *x,
+                               const void *b, const void *minv, void *y) {
+  long want = ((long)A.n_rows + 7) / 8;
+  const long cap = (long)c->num_sms * 8;
+  if (want > cap) want = cap;
+  const int g = (int)(want < 1 ? 1 : want);
+  const T *xx = (const T *)x;
+  const T *bb = (const T *)b;
+  const T *mm = (const T *)minv;
+  T *yy = (T *)y;
+#define AMG_LB_LAUNCH(M_)                                                                        bsr_lblock_kernel<BR, BC, V, T, M_><<<g, 256, 0, c->stream>>>(A.n_rows, A.rowptr, A.colidx,                                                                  vals, xx, bb, mm, yy)
+  switch (mode) {
+    case SPMV_SET: AMG_LB_LAUNCH(SPMV_SET); break;
+    case SPMV_RESID: AMG_LB_LAUNCH(SPMV_RESID); break;
+    case SPMV_ADD: AMG_LB_LAUNCH(SPMV_ADD); break;
+    case SPMV_SMOOTH:
+      if (BR != BC) return cudaErrorInvalidValue;
+      AMG_LB_LAUNCH(SPMV_SMOOTH);
+      break;
+    default: return cudaErrorInvalidValue;
+  }
+#undef AMG_LB_LAUNCH
+  return cudaGetLastError();
+}
+
 // SELL-32 variant: one thread per block row, all lanes of a warp on 32
 // consecutive rows.  Every value load of a slot is a coalesced 32-wide row,
 // no cross-lane reduction is needed, and every FP64 lane does useful work
@@ -401,7 +509,17 @@ static cudaError_t bsr_prec(const Ctx *c, const DevBSR &A, int prec, int mode, c
       return sell_mode<BR, BC, float, float>(c, A, A.s32, mode, x, b, minv, y);
     return sell_mode<BR, BC, __nv_bfloat16, float>(c, A, A.s16, mode, x, b, minv, y);
   }
-  if (c->layout_policy != AMG_LAYOUT_ROW_LANES) {
+  int kern = A.kern;
+  if (c->layout_policy == AMG_LAYOUT_ROW_LANES) kern = KERN_ROW_LANES;
+  if (c->layout_policy == AMG_LAYOUT_BLOCK_LANES) kern = KERN_BLOCK_LANES;
+  if (kern == KERN_BLOCK_LANES) {
+    if (prec == AMG_PREC_FP64)
+      return lblock_mode<BR, BC, double, double>(c, A, A.v64, mode, x, b, minv, y);
+    if (prec == AMG_PREC_FP32_VCYCLE)
+      return lblock_mode<BR, BC, float, float>(c, A, A.v32, mode, x, b, minv, y);
+    return lblock_mode<BR, BC, __nv_bfloat16, float>(c, A, A.v16, mode, x, b, minv, y);
+  }
+  if (kern != KERN_ROW_LANES) {
     if (prec == AMG_PREC_FP64)
       return bsr_mode<BR, BC, double, double>(c, A, A.v64, mode, x, b, minv, y);
     if (prec == AMG_PREC_FP32_VCYCLE)
@@ -630,7 +748,8 @@ bool want_sell(const Ctx *c, const DevBSR &m) {
   // thread-per-row pays off when there are enough rows to fill the GPU with
   // warps (>= 16 warps per SM) and the rows are short
   const double avg = m.n_rows ? (double)m.nnzb / m.n_rows : 0.0;
-  if (c->layout_policy == AMG_LAYOUT_WARP_ROWS || c->layout_policy == AMG_LAYOUT_ROW_LANES)
+  if (c->layout_policy == AMG_LAYOUT_WARP_ROWS || c->layout_policy == AMG_LAYOUT_ROW_LANES ||
+      c->layout_policy == AMG_LAYOUT_BLOCK_LANES)
     return false;
   if (c->layout_policy == AMG_LAYOUT_SELL_SHORT_ROWS) return avg <= 32.0;
   return m.n_rows >= 32 * 16 * c->num_sms && avg <= 32.0;

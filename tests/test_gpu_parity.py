@@ -42,10 +42,11 @@ def _hier(name):
     return _HIER[name]
 
 
-LAYOUTS = {"warp": 2, "sell": 1, "rowlane": 3}
+LAYOUTS = {"auto": 0, "warp": 2, "sell": 1, "rowlane": 3, "blocklane": 4}
 
 
-# every case runs with each operator layout (warp per row, SELL-32, row lanes)
+# every case runs with each operator layout (tuned, warp per row, SELL-32,
+# row lanes, block lanes)
 @pytest.fixture(scope="module", params=[(n, lay) for n in sorted(CASES) for lay in LAYOUTS],
                 ids=lambda v: f"{v[0]}-{v[1]}")
 def case(request):
