@@ -450,6 +450,14 @@ def main():
                                (float(np.mean(tv)) * 1e-3) / 1e9, 1)}
         c2.close()
 
+    # the same solve with plain launches (no programmatic dependent launch)
+    ctx.set_launch_overlap(False)
+    run_steps(ctx, args.warmup, False)
+    tv, iv = run_steps(ctx, args.steps, True)
+    ctx.set_launch_overlap(True)
+    variants["no_launch_overlap"] = {"ms": round(float(np.mean(tv)), 3), "iters": float(np.mean(iv)),
+                                     "ms_ratio_to_main": round(float(np.mean(tv)) / ms, 3)}
+
     # end-to-end through the host entry point (H2D f, u0; D2H u inside)
     fh = torch.from_numpy(np.ascontiguousarray(problem.b[0])).pin_memory()
     uh = torch.zeros_like(fh).pin_memory()
@@ -524,6 +532,13 @@ def main():
         "cpu_baseline": cpu,
     }
     line["kernels"] = [ln for ln in ctx.describe().splitlines()]
+    # every V-cycle kernel: live time per launch vs its algorithmic bytes
+    kr = []
+    for lev, step, us_k, by in ctx.profile_vcycle(reps=20):
+        gbs_k = by / (us_k * 1e-6) / 1e9 if us_k > 0 else 0.0
+        kr.append({"level": lev, "step": step, "us": round(us_k, 2), "mbytes": round(by / 1e6, 2),
+                   "gbs": round(gbs_k, 1), "frac_hbm": round(gbs_k / pk["hbm_gbs"], 3)})
+    line["vcycle_kernels"] = kr
     if learned_info is not None:
         line["config"]["smoother"] = "learned MLP (level 0), block-l1 Jacobi below"
         line["learned"] = learned_info

@@ -214,6 +214,14 @@ int amg_vcycle_static(amg_ctx *ctx, const double *r_dev, double *z_dev);
  * see inside graphs with conditional nodes).  Results are identical. */
 int amg_set_pcg_graph(amg_ctx *ctx, int enable);
 
+/* Programmatic dependent launch of the solve-phase kernels (default on):
+ * every V-cycle and CG kernel waits at its start for the previous kernel of
+ * the stream to complete (griddepcontrol.wait) and lets the next one be
+ * scheduled at once, so that each launch overlaps its predecessor's tail.
+ * enable = 0 launches them plainly.  Results are identical.  If a graph
+ * build refuses the programmatic launches, the library turns them off. */
+int amg_set_launch_overlap(amg_ctx *ctx, int enable);
+
 /* Storage layout of the level operators, applied by the next
  * amg_upload_hierarchy / amg_setup:
  *   AMG_LAYOUT_AUTO             SELL-32 copy (one thread per block row) for
@@ -229,8 +237,9 @@ int amg_set_pcg_graph(amg_ctx *ctx, int enable);
  *   AMG_LAYOUT_BLOCK_LANES      block-lane BSR kernels only (one warp per
  *                               block row, one whole block per lane)
  * Under AMG_LAYOUT_AUTO the upload also times, for every V-cycle operator
- * without a SELL-32 copy, the warp-row, row-lane and block-lane kernels on
- * the operator itself and keeps the fastest.
+ * but a square one with a SELL-32 copy, the warp-row, row-lane and
+ * block-lane kernels (and the SELL-32 copy where there is one) on the
+ * operator itself and keeps the fastest.
  * The result of every operator is the same up to the order of the sums. */
 enum {
   AMG_LAYOUT_AUTO = 0,
@@ -240,6 +249,18 @@ enum {
   AMG_LAYOUT_BLOCK_LANES = 4
 };
 int amg_set_layout_policy(amg_ctx *ctx, int policy);
+
+/* Per-kernel timing of one V-cycle in the context's precision: every step
+ * (kind 0 pre-smoothing x = M^+ b, 1 residual t = b - A x, 2 restriction,
+ * 3 prolongation x += P y, 4 post-smoothing, 5 coarsest solve) of every
+ * level is launched reps times on the context's stream (after one warm
+ * launch) and timed with CUDA events; us receives microseconds per launch
+ * and bytes its algorithmic bytes (values, indices, row pointers, each
+ * input and output vector once).  The work vectors of the context are
+ * overwritten.  Up to max_entries entries are written; *n_entries receives
+ * the total. */
+int amg_profile_vcycle(amg_ctx *ctx, int reps, int32_t *level, int32_t *kind, double *us, double *bytes,
+                       int max_entries, int32_t *n_entries);
 
 /* Text listing every level operator with its size and the kernel that
  * applies it (after the tuner); owned by ctx, valid until the next call. */

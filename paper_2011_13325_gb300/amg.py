@@ -107,6 +107,8 @@ _SIGS = {
                                    C.POINTER(C.c_int32), C.POINTER(C.c_int32), C.POINTER(C.c_int64)]),
     "amg_download_prolongation": (_I, [_P, _I, _P, _P, _P]),
     "amg_describe": (C.c_char_p, [_P]),
+    "amg_set_launch_overlap": (_I, [_P, _I]),
+    "amg_profile_vcycle": (_I, [_P, _I, _P, _P, _P, _P, _I, C.POINTER(C.c_int32)]),
     "amg_mlp_create": (_I, [C.POINTER(_P), _I, C.c_uint64]),
     "amg_mlp_destroy": (None, [_P]),
     "amg_mlp_last_error": (C.c_char_p, [_P]),
@@ -361,8 +363,27 @@ class Context:
     def describe(self):
         return lib().amg_describe(self.h).decode()
 
+    PROFILE_KINDS = ("pre-smooth x = M^+ b", "residual t = b - A x", "restriction R t",
+                     "prolongation x += P y", "post-smooth", "coarsest solve")
+
+    def profile_vcycle(self, reps=20):
+        """[(level, step, us per launch, algorithmic bytes)] of one V-cycle."""
+        m = 8 * 64
+        lv = np.zeros(m, dtype=np.int32)
+        kd = np.zeros(m, dtype=np.int32)
+        us = np.zeros(m)
+        by = np.zeros(m)
+        n = C.c_int32()
+        self._check(lib().amg_profile_vcycle(self.h, int(reps), lv.ctypes.data, kd.ctypes.data,
+                                             us.ctypes.data, by.ctypes.data, m, C.byref(n)))
+        return [(int(lv[i]), self.PROFILE_KINDS[kd[i]], float(us[i]), float(by[i]))
+                for i in range(min(n.value, m))]
+
     def set_layout_policy(self, policy: int):
         return self._check(lib().amg_set_layout_policy(self.h, int(policy)))
+
+    def set_launch_overlap(self, enable: bool):
+        return self._check(lib().amg_set_launch_overlap(self.h, int(bool(enable))))
 
     def set_pcg_graph(self, enable: bool):
         return self._check(lib().amg_set_pcg_graph(self.h, int(bool(enable))))

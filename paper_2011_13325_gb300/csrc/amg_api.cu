@@ -116,6 +116,33 @@ static cudaError_t vcycle_level(Ctx *c, int l, const void *b, void *y, const dou
   return launch_bsr(c, L.A, prec, SPMV_SMOOTH, x, b, mi, y);
 }
 
+// One timed entry of amg_profile_vcycle: the kernel launch fn, repeated.
+template <typename F>
+static cudaError_t time_launch(Ctx *c, int reps, F fn, double *us) {
+  cudaEvent_t e0, e1;
+  AMG_CUDA_TRY(cudaEventCreate(&e0));
+  AMG_CUDA_TRY(cudaEventCreate(&e1));
+  cudaError_t e = fn();
+  if (e == cudaSuccess) e = cudaEventRecord(e0, c->stream);
+  for (int r = 0; r < reps && e == cudaSuccess; ++r) e = fn();
+  if (e == cudaSuccess) e = cudaEventRecord(e1, c->stream);
+  if (e == cudaSuccess) e = cudaEventSynchronize(e1);
+  float ms = 0.f;
+  if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, e0, e1);
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  *us = 1e3 * ms / reps;
+  return e;
+}
+
+// Algorithmic bytes of one application of m: values + column indices + row
+// pointers, the input vector once, the output once (twice when updated).
+static double op_bytes(const DevBSR &m, int prec, double wv, int out_rw) {
+  const double w = prec == AMG_PREC_FP64 ? 8.0 : prec == AMG_PREC_FP32_VCYCLE ? 4.0 : 2.0;
+  return (double)m.nnzb * (m.br * m.bc * w + 4.0) + 4.0 * (m.n_rows + 1) +
+         (double)m.n_cols * m.bc * wv + out_rw * (double)m.n_rows * m.br * wv;
+}
+
 cudaError_t vcycle_launch(Ctx *c, const double *r, double *z) {
   if (c->precision == AMG_PREC_FP64) return vcycle_level(c, 0, r, z);
   Level &L0 = c->levels[0];
@@ -276,50 +303,63 @@ static int finish(Ctx *c, const char *where) {
   return AMG_OK;
 }
 
-// Kernel tuner of the upload (AMG_LAYOUT_AUTO): every V-cycle operator that
-// has no SELL-32 copy is applied with the warp-row, row-lane and block-lane
-// kernels (one warm launch, then three timed) in the V-cycle precision, and
-// keeps the fastest.  The kernels differ only in the order of the sums.
+// Kernel tuner of the upload (AMG_LAYOUT_AUTO): every V-cycle operator (but
+// a square one with a SELL-32 copy) is applied with the warp-row, row-lane
+// and block-lane kernels and, where it has one, its SELL-32 copy (one warm
+// launch, then three timed) in the V-cycle precision, and keeps the
+// fastest.  The kernels differ only in the order of the sums.
 static cudaError_t tune_operators(Ctx *c) {
   if (c->layout_policy != AMG_LAYOUT_AUTO) return cudaSuccess;
-  std::vector<DevBSR *> ops;
+  // (operator, its mode in the V-cycle): A residual, P prolongation-add,
+  // R restriction
+  std::vector<std::pair<DevBSR *, int>> ops;
   size_t nx = 0, ny = 0;
   for (int l = 0; l + 1 < (int)c->levels.size(); ++l) {
     Level &L = c->levels[l];
-    for (DevBSR *m : {&L.A, &L.P, &L.R}) {
-      if (!m->nnzb || m->sell_ptr) continue;
-      ops.push_back(m);
+    const std::pair<DevBSR *, int> cand[3] = {{&L.A, SPMV_RESID}, {&L.P, SPMV_ADD}, {&L.R, SPMV_SET}};
+    for (const auto &om : cand) {
+      DevBSR *m = om.first;
+      // a square operator with a SELL-32 copy keeps it (A_0 is also the CG
+      // operator, whose FP64 kernels use that copy)
+      if (!m->nnzb || (m == &L.A && m->sell_ptr)) continue;
+      ops.push_back(om);
       nx = std::max(nx, (size_t)m->n_cols * m->bc);
       ny = std::max(ny, (size_t)m->n_rows * m->br);
     }
   }
   if (ops.empty()) return cudaSuccess;
-  void *x = nullptr, *y = nullptr;
+  void *x = nullptr, *y = nullptr, *b = nullptr;
   cudaEvent_t e0 = nullptr, e1 = nullptr;
   cudaError_t e = dalloc(&x, nx * sizeof(double));
   if (e == cudaSuccess) e = dalloc(&y, ny * sizeof(double));
+  if (e == cudaSuccess) e = dalloc(&b, ny * sizeof(double));
   if (e == cudaSuccess) e = cudaMemsetAsync(x, 0, nx * sizeof(double), c->stream);
+  if (e == cudaSuccess) e = cudaMemsetAsync(y, 0, ny * sizeof(double), c->stream);
+  if (e == cudaSuccess) e = cudaMemsetAsync(b, 0, ny * sizeof(double), c->stream);
   if (e == cudaSuccess) e = cudaEventCreate(&e0);
   if (e == cudaSuccess) e = cudaEventCreate(&e1);
-  const int kerns[3] = {KERN_WARP_ROWS, KERN_ROW_LANES, KERN_BLOCK_LANES};
+  const int kerns[4] = {KERN_SELL, KERN_WARP_ROWS, KERN_ROW_LANES, KERN_BLOCK_LANES};
   for (size_t i = 0; i < ops.size() && e == cudaSuccess; ++i) {
-    DevBSR &m = *ops[i];
+    DevBSR &m = *ops[i].first;
+    const int mode = ops[i].second;
     float best = 1e30f;
-    int pick = KERN_WARP_ROWS;
+    int pick = m.sell_ptr ? KERN_SELL : KERN_WARP_ROWS;
     for (int k : kerns) {
+      if (k == KERN_SELL && !m.sell_ptr) continue;
       m.kern = k;
-      e = launch_bsr(c, m, c->precision, SPMV_SET, x, nullptr, nullptr, y);
-      if (e == cudaSuccess) e = cudaEventRecord(e0, c->stream);
-      for (int r = 0; r < 3 && e == cudaSuccess; ++r)
-        e = launch_bsr(c, m, c->precision, SPMV_SET, x, nullptr, nullptr, y);
-      if (e == cudaSuccess) e = cudaEventRecord(e1, c->stream);
-      if (e == cudaSuccess) e = cudaEventSynchronize(e1);
-      float ms = 0.f;
-      if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, e0, e1);
-      if (e != cudaSuccess) break;
-      if (ms < best) {
-        best = ms;
-        pick = k;
+      // the operator's own V-cycle mode; best of two timed triples
+      e = launch_bsr(c, m, c->precision, mode, x, b, nullptr, y);
+      for (int trial = 0; trial < 2 && e == cudaSuccess; ++trial) {
+        e = cudaEventRecord(e0, c->stream);
+        for (int r = 0; r < 3 && e == cudaSuccess; ++r) e = launch_bsr(c, m, c->precision, mode, x, b, nullptr, y);
+        if (e == cudaSuccess) e = cudaEventRecord(e1, c->stream);
+        if (e == cudaSuccess) e = cudaEventSynchronize(e1);
+        float ms = 0.f;
+        if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, e0, e1);
+        if (e == cudaSuccess && ms < best) {
+          best = ms;
+          pick = k;
+        }
       }
     }
     m.kern = pick;
@@ -328,6 +368,7 @@ static cudaError_t tune_operators(Ctx *c) {
   if (e1) cudaEventDestroy(e1);
   dfree(x);
   dfree(y);
+  dfree(b);
   return e;
 }
 
@@ -455,6 +496,68 @@ void amg_destroy(amg_ctx *h) {
 
 const char *amg_last_error(const amg_ctx *h) { return h ? h->c.err.c_str() : "NULL context"; }
 
+int amg_profile_vcycle(amg_ctx *h, int reps, int32_t *level, int32_t *kind, double *us, double *bytes,
+                       int max_entries, int32_t *n_entries) {
+  if (!h || reps < 1 || max_entries < 0) return AMG_ERR_ARG;
+  Ctx *c = &h->c;
+  if (c->levels.empty()) return fail(c, AMG_ERR_STATE, "amg_profile_vcycle: no hierarchy uploaded");
+  CUDA_OR_FAIL(c, cudaSetDevice(c->device), "cudaSetDevice");
+  const int prec = c->precision;
+  const double wv = prec == AMG_PREC_FP64 ? 8.0 : 4.0;
+  const int nl = (int)c->levels.size();
+  int n = 0;
+  auto put = [&](int l, int k, double t, double b) {
+    if (n < max_entries) {
+      if (level) level[n] = l;
+      if (kind) kind[n] = k;
+      if (us) us[n] = t;
+      if (bytes) bytes[n] = b;
+    }
+    ++n;
+  };
+  for (int l = 0; l < nl; ++l) {
+    Level &L = c->levels[l];
+    const double N = (double)L.A.n_rows * L.k;
+    double t = 0.0;
+    void *b = vb(L, prec, 'b'), *x = vb(L, prec, 'x'), *tt = vb(L, prec, 't'), *y = vb(L, prec, 'y');
+    if (l == nl - 1) {
+      CUDA_OR_FAIL(c, time_launch(c, reps, [&] { return launch_coarse_gemv(c, c->coarse_n, c->cinv, b, y, prec); }, &t),
+                   "profile");
+      put(l, 5, t, (double)c->coarse_n * c->coarse_n * 8.0 + 2.0 * c->coarse_n * wv);
+      break;
+    }
+    Level &Cn = c->levels[l + 1];
+    const void *mi = minv_of(L, prec);
+    const bool entry = l == 0 && prec != AMG_PREC_FP64;  // FP64 residual in, FP64 z out
+    if (entry)
+      CUDA_OR_FAIL(c, time_launch(c, reps, [&] {
+        return launch_blockdiag_entry(c, L.A.n_rows, L.k, L.minv32, c->r, (float *)b, (float *)x); }, &t), "profile");
+    else
+      CUDA_OR_FAIL(c, time_launch(c, reps, [&] { return launch_blockdiag(c, L.A.n_rows, L.k, prec, mi, b, x); }, &t),
+                   "profile");
+    put(l, 0, t, N * L.k * wv + N * (entry ? 8.0 + 2 * wv : 2 * wv));
+    CUDA_OR_FAIL(c, time_launch(c, reps, [&] { return launch_bsr(c, L.A, prec, SPMV_RESID, x, b, nullptr, tt); }, &t),
+                 "profile");
+    put(l, 1, t, op_bytes(L.A, prec, wv, 1) + N * wv);
+    CUDA_OR_FAIL(c, time_launch(c, reps, [&] {
+      return launch_bsr(c, L.R, prec, SPMV_SET, tt, nullptr, nullptr, vb(Cn, prec, 'b')); }, &t), "profile");
+    put(l, 2, t, op_bytes(L.R, prec, wv, 1));
+    CUDA_OR_FAIL(c, time_launch(c, reps, [&] {
+      return launch_bsr(c, L.P, prec, SPMV_ADD, vb(Cn, prec, 'y'), nullptr, nullptr, x); }, &t), "profile");
+    put(l, 3, t, op_bytes(L.P, prec, wv, 2));
+    if (entry)
+      CUDA_OR_FAIL(c, time_launch(c, reps, [&] {
+        return launch_smooth_out64(c, L.A, prec, (const float *)x, (const float *)b, L.minv32, c->z); }, &t),
+                   "profile");
+    else
+      CUDA_OR_FAIL(c, time_launch(c, reps, [&] { return launch_bsr(c, L.A, prec, SPMV_SMOOTH, x, b, mi, y); }, &t),
+                   "profile");
+    put(l, 4, t, op_bytes(L.A, prec, wv, 0) + N * L.k * wv + N * wv + N * (entry ? 8.0 : wv));
+  }
+  if (n_entries) *n_entries = n;
+  return finish(c, "profile");
+}
+
 const char *amg_describe(amg_ctx *h) {
   if (!h) return "";
   Ctx *c = &h->c;
@@ -468,8 +571,12 @@ const char *amg_describe(amg_ctx *h) {
     for (int i = 0; i < 3; ++i) {
       const DevBSR &m = *ops[i];
       if (!m.nnzb) continue;
-      const char *k = m.sell_ptr ? "SELL-32 (thread per block row)"
-                                 : kname[m.kern >= 0 && m.kern < 3 ? m.kern : 0];
+      char k[96];
+      if (m.sell_ptr && m.kern == KERN_SELL)
+        snprintf(k, sizeof k, "SELL-32 (thread per block row, %.0f%% of the slots filled)",
+                 100.0 * (double)m.nnzb / (32.0 * (double)m.sell_slots));
+      else
+        snprintf(k, sizeof k, "%s", kname[m.kern >= 0 && m.kern < 3 ? m.kern : 0]);
       snprintf(line, sizeof line, "level %d %s: %d x %d blocks of %dx%d, %lld stored, %s\n", l, nm[i],
                m.n_rows, m.n_cols, m.br, m.bc, (long long)m.nnzb, k);
       d += line;
@@ -706,6 +813,21 @@ int amg_vcycle(amg_ctx *h, const double *r, double *z, int nrhs) {
   return finish(c, "vcycle");
 }
 
+// Build the PCG graph; if the capture or instantiation refuses the
+// programmatic launches, rebuild it with plain launches.
+static cudaError_t ensure_pcg_graph(Ctx *c) {
+  if (!c->pcg_graph || c->graph) return cudaSuccess;
+  cudaError_t e = pcg_build_graph(c);
+  if (e == cudaSuccess || !c->pdl) return e;
+  (void)cudaGetLastError();
+  if (c->graph) cudaGraphExecDestroy(c->graph);
+  if (c->graph_def) cudaGraphDestroy(c->graph_def);
+  c->graph = nullptr;
+  c->graph_def = nullptr;
+  c->pdl = false;
+  return pcg_build_graph(c);
+}
+
 static int pcg_one(Ctx *c, double rtol, int maxit, int *iters, double *relres) {
   c->st_host->rtol = rtol;
   c->st_host->maxit = maxit;
@@ -747,7 +869,7 @@ int amg_pcg_solve(amg_ctx *h, const double *f, double *u, int nrhs, double rtol,
   if (!f || !u || nrhs < 1 || !(rtol >= 0.0) || maxit < 0)
     return fail(c, AMG_ERR_ARG, "bad arguments");
   if (c->levels[0].k != 2 && c->levels[0].k != 3) return fail(c, AMG_ERR_ARG, "A0 block size");
-  if (c->pcg_graph && !c->graph) CUDA_OR_FAIL(c, pcg_build_graph(c), "pcg graph");
+  CUDA_OR_FAIL(c, ensure_pcg_graph(c), "pcg graph");
   const size_t n = (size_t)c->levels[0].A.n_rows * c->levels[0].k;
   c->last_ms = 0.f;
   int worst = AMG_OK;
@@ -775,7 +897,7 @@ int amg_pcg_solve_host(amg_ctx *h, const double *f, double *u, int nrhs, double 
   if (s) return s;
   if (!f || !u || nrhs < 1 || !(rtol >= 0.0) || maxit < 0)
     return fail(c, AMG_ERR_ARG, "bad arguments");
-  if (c->pcg_graph && !c->graph) CUDA_OR_FAIL(c, pcg_build_graph(c), "pcg graph");
+  CUDA_OR_FAIL(c, ensure_pcg_graph(c), "pcg graph");
   const size_t n = (size_t)c->levels[0].A.n_rows * c->levels[0].k;
   c->last_ms = 0.f;
   int worst = AMG_OK;
@@ -813,6 +935,19 @@ int amg_set_layout_policy(amg_ctx *h, int policy) {
   if (policy < AMG_LAYOUT_AUTO || policy > AMG_LAYOUT_BLOCK_LANES)
     return fail(&h->c, AMG_ERR_ARG, "unknown layout policy");
   h->c.layout_policy = policy;
+  return AMG_OK;
+}
+
+int amg_set_launch_overlap(amg_ctx *h, int enable) {
+  if (!h) return AMG_ERR_ARG;
+  Ctx *c = &h->c;
+  CUDA_OR_FAIL(c, cudaStreamSynchronize(c->stream), "sync");
+  c->pdl = enable != 0;
+  if (c->graph) cudaGraphExecDestroy(c->graph);
+  if (c->graph_def) cudaGraphDestroy(c->graph_def);
+  c->graph = nullptr;
+  c->graph_def = nullptr;
+  c->err.clear();
   return AMG_OK;
 }
 

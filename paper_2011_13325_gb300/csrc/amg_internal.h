@@ -14,7 +14,7 @@ namespace amg {
 
 // Device block-sparse-row matrix.  Values exist in FP64 always; FP32 / BF16
 // copies only for the mixed-precision V-cycles.
-enum BsrKernel { KERN_WARP_ROWS = 0, KERN_ROW_LANES = 1, KERN_BLOCK_LANES = 2 };
+enum BsrKernel { KERN_WARP_ROWS = 0, KERN_ROW_LANES = 1, KERN_BLOCK_LANES = 2, KERN_SELL = 3 };
 
 struct DevBSR {
   int n_rows = 0, n_cols = 0, br = 0, bc = 0;
@@ -29,8 +29,9 @@ struct DevBSR {
   // slot j of lane t: column sell_col[j*32 + t], element q of its block at
   // s??[(j*br*bc + q)*32 + t] (every element of a slot is one coalesced
   // 32-wide row); padding slots have column 0 and zero values.
-  // kernel of the BSR form (set by the upload's tuner under AMG_LAYOUT_AUTO)
-  int kern = 0;  // KERN_WARP_ROWS / KERN_ROW_LANES / KERN_BLOCK_LANES
+  // kernel choice (set by the upload's tuner under AMG_LAYOUT_AUTO); the
+  // SELL-32 copy is used when present unless the tuner picked a BSR kernel
+  int kern = KERN_SELL;  // KERN_WARP_ROWS / KERN_ROW_LANES / KERN_BLOCK_LANES / KERN_SELL
   int n_slices = 0;
   int64_t sell_slots = 0;
   int *sell_ptr = nullptr;
@@ -78,6 +79,7 @@ struct Ctx {
   unsigned *counter = nullptr;  // last-block counter
   int layout_policy = 0;        // AMG_LAYOUT_*: which operators get the SELL-32 copy
   bool pcg_graph = true;        // false: host-driven loop (same kernels, for profiling)
+  bool pdl = true;              // programmatic dependent launch of the solve kernels
   cudaGraphExec_t graph = nullptr;
   cudaGraph_t graph_def = nullptr;
   cudaEvent_t ev0 = nullptr, ev1 = nullptr;
@@ -86,6 +88,41 @@ struct Ctx {
   double *hbuf = nullptr;        // pinned staging for host solves
   size_t hbuf_len = 0;
 };
+
+
+// Programmatic dependent launch of the solve-phase kernels: such a kernel
+// starts with pdl_enter(), which waits until the previous grid of the stream
+// has completed with its writes visible (griddepcontrol.wait).  The
+// predecessor triggers the launch implicitly as its blocks exit (no explicit
+// early trigger: waiting blocks of the next grid would take SM slots from a
+// predecessor with several waves), so the next launch overlaps only the
+// predecessor's drain.  A no-op for a kernel launched without the
+// attribute.  pdl_enter() must be the first statement (a block that
+// returned before it would let a successor run early).
+#ifdef __CUDACC__
+__device__ __forceinline__ void pdl_enter() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+#endif
+
+// Launch on c's stream, with programmatic stream serialization if c->pdl.
+template <typename... P, typename... A>
+inline cudaError_t launch_k(const Ctx *c, void (*k)(P...), dim3 g, dim3 b, A &&... a) {
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = g;
+  cfg.blockDim = b;
+  cfg.dynamicSmemBytes = 0;
+  cfg.stream = c->stream;
+  cudaLaunchAttribute at[1];
+  at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  at[0].val.programmaticStreamSerializationAllowed = c->pdl ? 1 : 0;
+  cfg.attrs = at;
+  cfg.numAttrs = 1;
+  return cudaLaunchKernelEx(&cfg, k, static_cast<A &&>(a)...);
+}
+#define AMG_KLAUNCH(...)                          \
+  do {                                            \
+    const cudaError_t _le = launch_k(__VA_ARGS__); \
+    if (_le != cudaSuccess) return _le;           \
+  } while (0)
 
 // Device allocation helpers (all internal buffers are owned by the context).
 cudaError_t dalloc(void **p, size_t bytes);

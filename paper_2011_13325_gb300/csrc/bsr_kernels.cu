@@ -115,6 +115,7 @@ __global__ void __launch_bounds__(256) bsr_warp_kernel(int n_rows, const int *__
                                                        const T *__restrict__ b,
                                                        const T *__restrict__ minv,
                                                        TO *__restrict__ y) {
+  pdl_enter();
   using A = typename AccT<T>::type;
   constexpr int NB = 32 / BR;
   const int lane = threadIdx.x & 31;
@@ -191,21 +192,17 @@ static cudaError_t bsr_mode(const Ctx *c, const DevBSR &A, const V *vals, int mo
   T *yy = (T *)y;
   switch (mode) {
     case SPMV_SET:
-      bsr_warp_kernel<BR, BC, V, T, SPMV_SET>
-          <<<g, 256, 0, c->stream>>>(A.n_rows, A.rowptr, A.colidx, vals, xx, bb, mm, yy);
+      AMG_KLAUNCH(c, bsr_warp_kernel<BR, BC, V, T, SPMV_SET>, g, 256, A.n_rows, A.rowptr, A.colidx, vals, xx, bb, mm, yy);
       break;
     case SPMV_RESID:
-      bsr_warp_kernel<BR, BC, V, T, SPMV_RESID>
-          <<<g, 256, 0, c->stream>>>(A.n_rows, A.rowptr, A.colidx, vals, xx, bb, mm, yy);
+      AMG_KLAUNCH(c, bsr_warp_kernel<BR, BC, V, T, SPMV_RESID>, g, 256, A.n_rows, A.rowptr, A.colidx, vals, xx, bb, mm, yy);
       break;
     case SPMV_ADD:
-      bsr_warp_kernel<BR, BC, V, T, SPMV_ADD>
-          <<<g, 256, 0, c->stream>>>(A.n_rows, A.rowptr, A.colidx, vals, xx, bb, mm, yy);
+      AMG_KLAUNCH(c, bsr_warp_kernel<BR, BC, V, T, SPMV_ADD>, g, 256, A.n_rows, A.rowptr, A.colidx, vals, xx, bb, mm, yy);
       break;
     case SPMV_SMOOTH:
       if (BR != BC) return cudaErrorInvalidValue;
-      bsr_warp_kernel<BR, BC, V, T, SPMV_SMOOTH>
-          <<<g, 256, 0, c->stream>>>(A.n_rows, A.rowptr, A.colidx, vals, xx, bb, mm, yy);
+      AMG_KLAUNCH(c, bsr_warp_kernel<BR, BC, V, T, SPMV_SMOOTH>, g, 256, A.n_rows, A.rowptr, A.colidx, vals, xx, bb, mm, yy);
       break;
     default:
       return cudaErrorInvalidValue;
@@ -227,6 +224,7 @@ __global__ void __launch_bounds__(256) bsr_rowlane_kernel(int n_rows, const int 
                                                           const T *__restrict__ b,
                                                           const T *__restrict__ minv,
                                                           T *__restrict__ y) {
+  pdl_enter();
   using A = typename AccT<T>::type;
   constexpr int G = 32 / BR;
   const int lane = threadIdx.x & 31;
@@ -289,7 +287,7 @@ static cudaError_t rowlane_mode(const Ctx *c, const DevBSR &A, const V *vals, in
   const T *mm = (const T *)minv;
   T *yy = (T *)y;
 #define AMG_RL_LAUNCH(M_)                                                                      \
-  bsr_rowlane_kernel<BR, BC, V, T, M_><<<g, 256, 0, c->stream>>>(A.n_rows, A.rowptr, A.colidx, \
+  AMG_KLAUNCH(c, bsr_rowlane_kernel<BR, BC, V, T, M_>, g, 256, A.n_rows, A.rowptr, A.colidx, \
                                                                  vals, xx, bb, mm, yy)
   switch (mode) {
     case SPMV_SET: AMG_RL_LAUNCH(SPMV_SET); break;
@@ -343,6 +341,7 @@ __global__ void __launch_bounds__(256) bsr_lblock_kernel(int n_rows, const int *
                                                          const T *__restrict__ b,
                                                          const T *__restrict__ minv,
                                                          T *__restrict__ y) {
+  pdl_enter();
   using A = typename AccT<T>::type;
   constexpr int E = BR * BC;
   // a block starts 16-byte aligned when E * sizeof(V) is a multiple of 16
@@ -398,7 +397,7 @@ static cudaError_t lblock_mode(const Ctx *c, const DevBSR &A, const V *vals, int
   const T *bb = (const T *)b;
   const T *mm = (const T *)minv;
   T *yy = (T *)y;
-#define AMG_LB_LAUNCH(M_)                                                                        bsr_lblock_kernel<BR, BC, V, T, M_><<<g, 256, 0, c->stream>>>(A.n_rows, A.rowptr, A.colidx,                                                                  vals, xx, bb, mm, yy)
+#define AMG_LB_LAUNCH(M_)                                                                        AMG_KLAUNCH(c, bsr_lblock_kernel<BR, BC, V, T, M_>, g, 256, A.n_rows, A.rowptr, A.colidx,                                                                  vals, xx, bb, mm, yy)
   switch (mode) {
     case SPMV_SET: AMG_LB_LAUNCH(SPMV_SET); break;
     case SPMV_RESID: AMG_LB_LAUNCH(SPMV_RESID); break;
@@ -427,6 +426,7 @@ __global__ void __launch_bounds__(256) sell_kernel(int n_rows, int n_slices,
                                                    const T *__restrict__ b,
                                                    const T *__restrict__ minv,
                                                    TO *__restrict__ y) {
+  pdl_enter();
   using A = typename AccT<T>::type;
   constexpr int E = BR * BC;
   const int slice = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
@@ -482,7 +482,7 @@ static cudaError_t sell_mode(const Ctx *c, const DevBSR &A, const V *vals, int m
   const T *mm = (const T *)minv;
   T *yy = (T *)y;
 #define AMG_SELL_LAUNCH(M_)                                                                    \
-  sell_kernel<BR, BC, V, T, M_><<<g, 64, 0, c->stream>>>(A.n_rows, A.n_slices, A.sell_ptr,   \
+  AMG_KLAUNCH(c, sell_kernel<BR, BC, V, T, M_>, g, 64, A.n_rows, A.n_slices, A.sell_ptr,   \
                                                           A.sell_col, vals, xx, bb, mm, yy)
   switch (mode) {
     case SPMV_SET: AMG_SELL_LAUNCH(SPMV_SET); break;
@@ -502,14 +502,14 @@ template <int BR, int BC>
 static cudaError_t bsr_prec(const Ctx *c, const DevBSR &A, int prec, int mode, const void *x,
                             const void *b, const void *minv, void *y) {
   if (A.n_rows == 0) return cudaSuccess;
-  if (A.sell_ptr) {
+  if (A.sell_ptr && A.kern == KERN_SELL) {
     if (prec == AMG_PREC_FP64)
       return sell_mode<BR, BC, double, double>(c, A, A.s64, mode, x, b, minv, y);
     if (prec == AMG_PREC_FP32_VCYCLE)
       return sell_mode<BR, BC, float, float>(c, A, A.s32, mode, x, b, minv, y);
     return sell_mode<BR, BC, __nv_bfloat16, float>(c, A, A.s16, mode, x, b, minv, y);
   }
-  int kern = A.kern;
+  int kern = A.kern == KERN_SELL ? KERN_WARP_ROWS : A.kern;
   if (c->layout_policy == AMG_LAYOUT_ROW_LANES) kern = KERN_ROW_LANES;
   if (c->layout_policy == AMG_LAYOUT_BLOCK_LANES) kern = KERN_BLOCK_LANES;
   if (kern == KERN_BLOCK_LANES) {
@@ -538,11 +538,11 @@ static cudaError_t bsr_prec(const Ctx *c, const DevBSR &A, int prec, int mode, c
 template <int K, typename V>
 static cudaError_t smooth_out64_k(const Ctx *c, const DevBSR &A, const V *bsr_vals, const V *sell_vals,
                                   const float *x, const float *b, const float *minv, double *y) {
-  if (A.sell_ptr) {
-    sell_kernel<K, K, V, float, SPMV_SMOOTH, double><<<(A.n_slices + 1) / 2, 64, 0, c->stream>>>(
+  if (A.sell_ptr && A.kern == KERN_SELL) {
+    AMG_KLAUNCH(c, sell_kernel<K, K, V, float, SPMV_SMOOTH, double>, (A.n_slices + 1) / 2, 64, 
         A.n_rows, A.n_slices, A.sell_ptr, A.sell_col, sell_vals, x, b, minv, y);
   } else {
-    bsr_warp_kernel<K, K, V, float, SPMV_SMOOTH, double><<<grid_for_rows(c, A.n_rows), 256, 0, c->stream>>>(
+    AMG_KLAUNCH(c, bsr_warp_kernel<K, K, V, float, SPMV_SMOOTH, double>, grid_for_rows(c, A.n_rows), 256, 
         A.n_rows, A.rowptr, A.colidx, bsr_vals, x, b, minv, y);
   }
   return cudaGetLastError();
@@ -568,6 +568,7 @@ template <int K>
 __global__ void blockdiag_entry_kernel(int n, const float *__restrict__ minv,
                                        const double *__restrict__ r, float *__restrict__ b,
                                        float *__restrict__ x) {
+  pdl_enter();
   const size_t v = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (v >= (size_t)n) return;
   float rb[K];
@@ -590,9 +591,9 @@ cudaError_t launch_blockdiag_entry(const Ctx *c, int n, int k, const float *minv
   if (n == 0) return cudaSuccess;
   const int g = (n + 255) / 256;
   if (k == 2)
-    blockdiag_entry_kernel<2><<<g, 256, 0, c->stream>>>(n, minv, r, b, x);
+    AMG_KLAUNCH(c, blockdiag_entry_kernel<2>, g, 256, n, minv, r, b, x);
   else if (k == 3)
-    blockdiag_entry_kernel<3><<<g, 256, 0, c->stream>>>(n, minv, r, b, x);
+    AMG_KLAUNCH(c, blockdiag_entry_kernel<3>, g, 256, n, minv, r, b, x);
   else
     return cudaErrorInvalidValue;
   return cudaGetLastError();
@@ -617,6 +618,7 @@ cudaError_t launch_bsr(const Ctx *c, const DevBSR &A, int prec, int mode, const 
 template <int K, typename T>
 __global__ void blockdiag_kernel(int n, const T *__restrict__ minv, const T *__restrict__ b,
                                  T *__restrict__ y) {
+  pdl_enter();
   using A = typename AccT<T>::type;
   const size_t t = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (t >= (size_t)n * K) return;
@@ -634,10 +636,10 @@ static cudaError_t blockdiag_k(const Ctx *c, int n, int prec, const void *minv, 
   const int g = (int)((tot + 255) / 256);
   if (tot == 0) return cudaSuccess;
   if (prec == AMG_PREC_FP64)
-    blockdiag_kernel<K, double><<<g, 256, 0, c->stream>>>(n, (const double *)minv,
+    AMG_KLAUNCH(c, blockdiag_kernel<K, double>, g, 256, n, (const double *)minv,
                                                           (const double *)b, (double *)y);
   else
-    blockdiag_kernel<K, float><<<g, 256, 0, c->stream>>>(n, (const float *)minv,
+    AMG_KLAUNCH(c, blockdiag_kernel<K, float>, g, 256, n, (const float *)minv,
                                                          (const float *)b, (float *)y);
   return cudaGetLastError();
 }
@@ -655,6 +657,7 @@ cudaError_t launch_blockdiag(const Ctx *c, int n, int k, int prec, const void *m
 template <typename T>
 __global__ void coarse_gemv_kernel(int n, const double *__restrict__ cinv, const T *__restrict__ b,
                                    T *__restrict__ y) {
+  pdl_enter();
   const int lane = threadIdx.x & 31;
   const int row = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   if (row >= n) return;
@@ -671,14 +674,15 @@ cudaError_t launch_coarse_gemv(const Ctx *c, int n, const double *cinv, const vo
   if (n == 0) return cudaSuccess;
   const int g = (n + 7) / 8;
   if (prec == AMG_PREC_FP64)
-    coarse_gemv_kernel<double><<<g, 256, 0, c->stream>>>(n, cinv, (const double *)b, (double *)y);
+    AMG_KLAUNCH(c, coarse_gemv_kernel<double>, g, 256, n, cinv, (const double *)b, (double *)y);
   else
-    coarse_gemv_kernel<float><<<g, 256, 0, c->stream>>>(n, cinv, (const float *)b, (float *)y);
+    AMG_KLAUNCH(c, coarse_gemv_kernel<float>, g, 256, n, cinv, (const float *)b, (float *)y);
   return cudaGetLastError();
 }
 
 template <typename S, typename D>
 __global__ void convert_kernel(size_t n, const S *__restrict__ s, D *__restrict__ d) {
+  pdl_enter();
   const size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (i < n) d[i] = (D)s[i];
 }
@@ -689,9 +693,9 @@ cudaError_t launch_convert(const Ctx *c, size_t n, const void *src, int src_prec
   const int g = (int)((n + 255) / 256);
   const bool s64 = src_prec == AMG_PREC_FP64, d64 = dst_prec == AMG_PREC_FP64;
   if (s64 && !d64)
-    convert_kernel<double, float><<<g, 256, 0, c->stream>>>(n, (const double *)src, (float *)dst);
+    AMG_KLAUNCH(c, convert_kernel<double, float>, g, 256, n, (const double *)src, (float *)dst);
   else if (!s64 && d64)
-    convert_kernel<float, double><<<g, 256, 0, c->stream>>>(n, (const float *)src, (double *)dst);
+    AMG_KLAUNCH(c, convert_kernel<float, double>, g, 256, n, (const float *)src, (double *)dst);
   else
     return cudaErrorInvalidValue;
   return cudaGetLastError();

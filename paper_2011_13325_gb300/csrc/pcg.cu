@@ -132,6 +132,7 @@ template <int BR>
 __global__ void __launch_bounds__(kRedThreads) pcg_init_sell_kernel(
     SellView A, const double *f, const double *x, double *r, PcgState *st, double *partials,
     unsigned *counter, cudaGraphConditionalHandle h, int in_graph) {
+  pdl_enter();
   const int t = threadIdx.x & 31;
   const int nw = (gridDim.x * blockDim.x) >> 5;
   double v[2] = {0.0, 0.0};
@@ -174,6 +175,7 @@ template <int BR>
 __global__ void __launch_bounds__(kSellThreads) pcg_spmv_dot_sell_kernel(SellView A,
                                                                         const double *p, double *q,
                                                                         double *partials) {
+  pdl_enter();
   __shared__ double sh[kSellThreads / 32];
   const int t = threadIdx.x & 31, w = threadIdx.x >> 5;
   const int s = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
@@ -207,6 +209,7 @@ __global__ void __launch_bounds__(kRedThreads) pcg_init_kernel(
     int n_rows, const int *rowptr, const int *colidx, const double *vals, const double *f,
     const double *x, double *r, PcgState *st, double *partials, unsigned *counter,
     cudaGraphConditionalHandle h, int in_graph) {
+  pdl_enter();
   const int lane = threadIdx.x & 31;
   const int nwarps = (gridDim.x * blockDim.x) >> 5;
   double v[2] = {0.0, 0.0};
@@ -241,6 +244,7 @@ __global__ void __launch_bounds__(kRedThreads) pcg_dot_rz_kernel(size_t n, const
                                                                   const double *zold,
                                                                   PcgState *st, double *partials,
                                                                   unsigned *counter) {
+  pdl_enter();
   double v[2] = {0.0, 0.0};
   const size_t stride = (size_t)gridDim.x * blockDim.x;
   const bool flex = st->flexible != 0;
@@ -263,6 +267,7 @@ __global__ void __launch_bounds__(kRedThreads) pcg_dot_rz_kernel(size_t n, const
 // p = z + beta p ; z_old = z (flexible variant)
 __global__ void pcg_update_p_kernel(size_t n, const double *z, double *p, double *zold,
                                     const PcgState *st) {
+  pdl_enter();
   const size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= n) return;
   const double beta = st->beta;
@@ -276,6 +281,7 @@ template <int BR>
 __global__ void __launch_bounds__(kRedThreads) pcg_spmv_dot_kernel(
     int n_rows, const int *rowptr, const int *colidx, const double *vals, const double *p,
     double *q, PcgState *st, double *partials, unsigned *counter, double *pq_out) {
+  pdl_enter();
   const int lane = threadIdx.x & 31;
   const int nwarps = (gridDim.x * blockDim.x) >> 5;
   double v[1] = {0.0};
@@ -297,6 +303,7 @@ constexpr int kFinThreads = 1024;
 __global__ void __launch_bounds__(kFinThreads) pcg_alpha_kernel(PcgState *st,
                                                                 const double *pq_partials,
                                                                 int n_pq) {
+  pdl_enter();
   __shared__ double sh[kFinThreads / 32];
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
   double a = 0.0;
@@ -318,6 +325,7 @@ __global__ void __launch_bounds__(kFinThreads) pcg_alpha_kernel(PcgState *st,
 __global__ void __launch_bounds__(kRedThreads) pcg_update_xr_kernel(
     size_t n, double *x, double *r, const double *p, const double *q, const PcgState *st,
     double *rr_partials) {
+  pdl_enter();
   __shared__ double sh[kRedThreads / 32];
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
   const double alpha = st->alpha;
@@ -345,6 +353,7 @@ __global__ void __launch_bounds__(kRedThreads) pcg_update_xr_kernel(
 // the counter of the last-block reductions is re-armed.
 __global__ void pcg_guard_kernel(PcgState *st, const double *rr_partials, int n_rr,
                                  unsigned *counter, cudaGraphConditionalHandle h, int in_graph) {
+  pdl_enter();
   double v = 0.0;
   for (int b = threadIdx.x; b < n_rr; b += 32) v += rr_partials[b];
   for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
@@ -386,10 +395,10 @@ template <int BR>
 static cudaError_t launch_init(Ctx *c, cudaGraphConditionalHandle h, int in_graph) {
   const Level &L0 = c->levels[0];
   if (L0.A.sell_ptr)
-    pcg_init_sell_kernel<BR><<<red_grid(c), kRedThreads, 0, c->stream>>>(
+    AMG_KLAUNCH(c, pcg_init_sell_kernel<BR>, red_grid(c), kRedThreads, 
         sell_view(L0.A), c->f, c->x, c->r, c->st, c->partials, c->counter, h, in_graph);
   else
-    pcg_init_kernel<BR><<<red_grid(c), kRedThreads, 0, c->stream>>>(
+    AMG_KLAUNCH(c, pcg_init_kernel<BR>, red_grid(c), kRedThreads, 
         L0.A.n_rows, L0.A.rowptr, L0.A.colidx, L0.A.v64, c->f, c->x, c->r, c->st, c->partials,
         c->counter, h, in_graph);
   return cudaGetLastError();
@@ -404,28 +413,28 @@ static cudaError_t launch_body(Ctx *c, cudaGraphConditionalHandle h, int in_grap
   double *pq_part = c->partials + 4 * (size_t)g;
   int n_pq;
   AMG_CUDA_TRY(vcycle_launch(c, c->r, c->z));
-  pcg_dot_rz_kernel<<<gv, kRedThreads, 0, c->stream>>>(n, c->r, c->z, c->zold, c->st, c->partials,
+  AMG_KLAUNCH(c, pcg_dot_rz_kernel, gv, kRedThreads, n, c->r, c->z, c->zold, c->st, c->partials,
                                                        c->counter);
-  pcg_update_p_kernel<<<(unsigned)((n + 255) / 256), 256, 0, c->stream>>>(n, c->z, c->p, c->zold,
+  AMG_KLAUNCH(c, pcg_update_p_kernel, (unsigned)((n + 255) / 256), 256, n, c->z, c->p, c->zold,
                                                                           c->st);
   if (L0.A.sell_ptr) {
     n_pq = (L0.A.n_slices + 1) / 2;
-    pcg_spmv_dot_sell_kernel<BR><<<n_pq, kSellThreads, 0, c->stream>>>(sell_view(L0.A), c->p,
+    AMG_KLAUNCH(c, pcg_spmv_dot_sell_kernel<BR>, n_pq, kSellThreads, sell_view(L0.A), c->p,
                                                                        c->q, pq_part);
   } else {
     // warp-per-row SpMV + dot with a last-block total: its block partial
     // array holds the single total (n_pq = 1)
     n_pq = 1;
-    pcg_spmv_dot_kernel<BR><<<g, kRedThreads, 0, c->stream>>>(L0.A.n_rows, L0.A.rowptr,
+    AMG_KLAUNCH(c, pcg_spmv_dot_kernel<BR>, g, kRedThreads, L0.A.n_rows, L0.A.rowptr,
                                                               L0.A.colidx, L0.A.v64, c->p, c->q,
                                                               c->st, c->partials, c->counter,
                                                               pq_part);
   }
   double *rr_part = pq_part + (size_t)(L0.A.n_slices + 1) / 2 + 1;
-  pcg_alpha_kernel<<<1, kFinThreads, 0, c->stream>>>(c->st, pq_part, n_pq);
-  pcg_update_xr_kernel<<<gv, kRedThreads, 0, c->stream>>>(n, c->x, c->r, c->p, c->q, c->st,
+  AMG_KLAUNCH(c, pcg_alpha_kernel, 1, kFinThreads, c->st, pq_part, n_pq);
+  AMG_KLAUNCH(c, pcg_update_xr_kernel, gv, kRedThreads, n, c->x, c->r, c->p, c->q, c->st,
                                                           rr_part);
-  pcg_guard_kernel<<<1, 32, 0, c->stream>>>(c->st, rr_part, gv, c->counter, h, in_graph);
+  AMG_KLAUNCH(c, pcg_guard_kernel, 1, 32, c->st, rr_part, gv, c->counter, h, in_graph);
   return cudaGetLastError();
 }
 

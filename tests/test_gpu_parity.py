@@ -266,3 +266,36 @@ def test_errors_are_reported():
     s, its, rr = ctx.pcg_solve(dev(f), dev(np.zeros_like(f)), rtol=1e-8, maxit=500)
     assert s == amg.AMG_OK
     ctx.close()
+
+
+def test_profile_vcycle_covers_every_step(case):
+    name, p, H, ctx = case
+    prof = ctx.profile_vcycle(reps=2)
+    assert len(prof) == 5 * (H.n_levels - 1) + 1
+    assert all(us > 0 and by > 0 for _, _, us, by in prof)
+    assert prof[-1][1] == "coarsest solve" and prof[-1][0] == H.n_levels - 1
+    # the context stays usable: a V-cycle afterwards is unchanged
+    r = p.b[0]
+    z = dev(np.zeros_like(r))
+    ctx.vcycle(dev(r), z)
+    assert rel(host(z), solve.vcycle(H, r)) <= 1e-10
+
+
+def test_launch_overlap_gives_identical_results(case):
+    """Programmatic dependent launches change only when kernels are
+    scheduled: graph and host-loop solves with and without them agree
+    bitwise."""
+    name, p, H, ctx = case
+    f = dev(p.b[0])
+    outs = []
+    for overlap in (True, False):
+        ctx.set_launch_overlap(overlap)
+        for graph in (True, False):
+            ctx.set_pcg_graph(graph)
+            u = dev(np.zeros(p.b[0].shape[0]))
+            _, its, rr = ctx.pcg_solve(f, u, rtol=1e-8)
+            outs.append((its, rr, u))
+    ctx.set_pcg_graph(True)
+    ctx.set_launch_overlap(True)
+    for its, rr, u in outs[1:]:
+        assert its == outs[0][0] and rr == outs[0][1] and torch.equal(u, outs[0][2])
