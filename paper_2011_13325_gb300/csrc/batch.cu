@@ -85,7 +85,8 @@ static int cdiv(long a, long b) { return (int)((a + b - 1) / b); }
 // ---------------------------------------------------------------------------
 static void build_spmm_items(Stage &S) {
   S.sp.clear();
-  const int rpb = S.lpr ? S.wpb * (32 / S.lpr) : 0;
+  const int g = S.lpr < 0 ? -S.lpr : S.lpr;  // lanes per row (block lanes: -g)
+  const int rpb = g ? S.wpb * (32 / g) : 0;
   int first = 0;
   for (const SpmmOp &o : S.ops) {
     SpmmItem it{};
@@ -404,7 +405,9 @@ static cudaError_t autotune(Batch *B) {
                                cudaMemcpyHostToDevice, B->stream));
   // candidates: (lanes per row, warps per block); (0, s): SELL-32, s slices
   // per block, when every operator of the stage has its SELL copy
-  const int cand[8][2] = {{32, 8}, {32, 4}, {16, 8}, {16, 4}, {8, 8}, {8, 4}, {0, 4}, {0, 2}};
+  // (-g, w): block lanes, g lanes per block row, for 6x6 / 6x3 blocks
+  const int cand[12][2] = {{32, 8}, {32, 4}, {16, 8}, {16, 4}, {8, 8}, {8, 4},
+                           {0, 4},  {0, 2},  {-8, 8}, {-8, 4}, {-16, 8}, {-16, 4}};
   for (auto *v : {&B->init, &B->body})
     for (Stage &S : *v) {
       if (S.kind != ST_SPMM) continue;
@@ -414,8 +417,9 @@ static cudaError_t autotune(Batch *B) {
       int bl = 32, bw = 8;
       for (const auto &cw : cand) {
         const int lpr = cw[0], wpb = cw[1];
-        if (lpr != 0 && lpr < S.key.br) continue;
+        if (lpr > 0 && lpr < S.key.br) continue;
         if (lpr == 0 && !sell) continue;
+        if (lpr < 0 && !gblock_supported(S.key.br, S.key.bc)) continue;
         {
           S.lpr = lpr;
           S.wpb = wpb;
@@ -522,6 +526,9 @@ static std::string describe(const Batch *B) {
       if (S.kind == ST_SPMM && S.lpr == 0)
         snprintf(line, sizeof line, "%s: %s: %d systems, %d blocks, SELL-32 thread/row, %d slices/block, %.1f us\n",
                  part, S.name.c_str(), S.n_items, S.grid, S.wpb, S.us);
+      else if (S.kind == ST_SPMM && S.lpr < 0)
+        snprintf(line, sizeof line, "%s: %s: %d systems, %d blocks, block lanes %d lanes/row, %d warps/block, %.1f us\n",
+                 part, S.name.c_str(), S.n_items, S.grid, -S.lpr, S.wpb, S.us);
       else if (S.kind == ST_SPMM)
         snprintf(line, sizeof line, "%s: %s: %d systems, %d blocks, %d lanes/row, %d warps/block, %.1f us\n",
                  part, S.name.c_str(), S.n_items, S.grid, S.lpr, S.wpb, S.us);

@@ -214,11 +214,90 @@ __global__ void __launch_bounds__(128) gsell_kernel(const SpmmItem *__restrict__
   }
 }
 
+// Block-lane form for long rows of large blocks: G lanes per block row
+// (32 / G rows per warp); lane j of a row's group takes the blocks j, j + G,
+// ... whole (BR x BC values) for all NR load cases, and an xor butterfly
+// inside the group leaves every sum on every lane of the group.
+template <int BR, int BC, int NR, int G, typename V, typename T, int MODE, typename TO>
+__global__ void __launch_bounds__(256) gblock_kernel(const SpmmItem *__restrict__ items, int n_items,
+                                                     const McgState *__restrict__ st) {
+  using A = typename GAcc<T>::type;
+  constexpr int E = BR * BC;
+  constexpr int RPW = 32 / G;
+  const int ii = find_item(items, n_items, blockIdx.x);
+  const SpmmItem &I = items[ii];
+  if (!st[I.sys].active) return;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int grp = lane / G, gl = lane - grp * G;
+  const int row = ((blockIdx.x - I.first_block) * (blockDim.x >> 5) + warp) * RPW + grp;
+  const bool valid = row < I.n_rows;
+  const T *__restrict__ x = (const T *)I.x;
+  A acc[BR][NR];
+#pragma unroll
+  for (int r = 0; r < BR; ++r)
+#pragma unroll
+    for (int j = 0; j < NR; ++j) acc[r][j] = 0;
+  if (valid) {
+    const int s = __ldg(I.rowptr + row), e = __ldg(I.rowptr + row + 1);
+    const V *__restrict__ vals = (const V *)I.vals;
+    for (int p = s + gl; p < e; p += G) {
+      const int c = __ldg(I.colidx + p);
+      const V *v = vals + (size_t)p * E;
+      const T *xp = x + (size_t)c * BC * NR;
+#pragma unroll
+      for (int q = 0; q < BC; ++q) {
+        A xv[NR];
+        gld_nr<NR>(xp + q * NR, xv);
+#pragma unroll
+        for (int r = 0; r < BR; ++r) {
+          const A a = (A)glds(v + r * BC + q);
+#pragma unroll
+          for (int j = 0; j < NR; ++j) acc[r][j] += a * xv[j];
+        }
+      }
+    }
+  }
+#pragma unroll
+  for (int o = G / 2; o > 0; o >>= 1)
+#pragma unroll
+    for (int r = 0; r < BR; ++r)
+#pragma unroll
+      for (int j = 0; j < NR; ++j) acc[r][j] += __shfl_xor_sync(0xffffffffu, acc[r][j], o);
+  if (!valid || gl >= BR) return;
+  const size_t o = (size_t)row * BR;
+  TO *__restrict__ y = (TO *)I.y;
+  const T *__restrict__ b = (const T *)I.b;
+  if (MODE == SPMV_SMOOTH) {
+    const T *__restrict__ minv = (const T *)I.minv;
+#pragma unroll
+    for (int j = 0; j < NR; ++j) {
+      A upd = 0;
+#pragma unroll
+      for (int q = 0; q < BR; ++q) upd += (A)minv[(o + gl) * BR + q] * ((A)b[(o + q) * NR + j] - acc[q][j]);
+      y[(o + gl) * NR + j] = (TO)((A)x[(o + gl) * NR + j] + upd);
+    }
+  } else {
+#pragma unroll
+    for (int j = 0; j < NR; ++j) {
+      A mine = 0;  // acc[gl][j] without dynamic register indexing
+#pragma unroll
+      for (int r = 0; r < BR; ++r)
+        if (gl == r) mine = acc[r][j];
+      const size_t i = (o + gl) * NR + j;
+      if (MODE == SPMV_SET) y[i] = (TO)mine;
+      if (MODE == SPMV_RESID) y[i] = (TO)((A)b[i] - mine);
+      if (MODE == SPMV_ADD) y[i] = (TO)((A)y[i] + mine);
+    }
+  }
+}
+
 template <int BR, int BC, int NR, int LPR, typename V, typename T, int MODE, typename TO>
 static cudaError_t gspmm_go(int wpb, const SpmmItem *items, int n_items, int grid,
                             const McgState *st, cudaStream_t s) {
   if constexpr (LPR == 0)
     gsell_kernel<BR, BC, NR, V, T, MODE, TO><<<grid, wpb * 32, 0, s>>>(items, n_items, st);
+  else if constexpr (LPR < 0)
+    gblock_kernel<BR, BC, NR, -LPR, V, T, MODE, TO><<<grid, wpb * 32, 0, s>>>(items, n_items, st);
   else
     gspmm_kernel<BR, BC, NR, LPR, V, T, MODE, TO><<<grid, wpb * 32, 0, s>>>(items, n_items, st);
   return cudaGetLastError();
@@ -276,6 +355,8 @@ static cudaError_t gspmm_lpr(const SpmmKey &k, int wpb, const SpmmItem *items, i
   return cudaErrorInvalidValue;
 }
 
+bool gblock_supported(int br, int bc) { return br == 6 && (bc == 6 || bc == 3); }
+
 bool gsell_supported(int br, int bc) {
   return (br == 3 && bc == 3) || (br == 3 && bc == 6) || (br == 2 && bc == 2) || (br == 2 && bc == 3);
 }
@@ -287,6 +368,14 @@ static cudaError_t gspmm_shape(const SpmmKey &k, int lpr, int wpb, const SpmmIte
                            (BR == 2 && BC == 3);
   if (lpr == 0) {
     if constexpr (sell_ok) return gspmm_lpr<BR, BC, NR, 0>(k, wpb, items, n_items, grid, st, s);
+    return cudaErrorInvalidValue;
+  }
+  constexpr bool block_ok = BR == 6 && (BC == 6 || BC == 3);
+  if (lpr < 0) {
+    if constexpr (block_ok) {
+      if (lpr == -8) return gspmm_lpr<BR, BC, NR, -8>(k, wpb, items, n_items, grid, st, s);
+      if (lpr == -16) return gspmm_lpr<BR, BC, NR, -16>(k, wpb, items, n_items, grid, st, s);
+    }
     return cudaErrorInvalidValue;
   }
   switch (lpr) {
@@ -316,7 +405,7 @@ static cudaError_t gspmm_nr(const SpmmKey &k, int lpr, int wpb, const SpmmItem *
 cudaError_t launch_gspmm(const SpmmKey &k, int nr, int lpr, int wpb, const SpmmItem *items,
                          int n_items, int grid, const McgState *st, cudaStream_t s) {
   if (grid <= 0 || n_items <= 0) return cudaSuccess;
-  if (wpb < 1 || wpb > 8 || (lpr != 0 && lpr < k.br)) return cudaErrorInvalidValue;
+  if (wpb < 1 || wpb > 8 || (lpr > 0 && lpr < k.br)) return cudaErrorInvalidValue;
   if (lpr == 0 && wpb > 4) return cudaErrorInvalidValue;
   if (nr == 6) return gspmm_nr<6>(k, lpr, wpb, items, n_items, grid, st, s);
   if (nr == 1) return gspmm_nr<1>(k, lpr, wpb, items, n_items, grid, st, s);

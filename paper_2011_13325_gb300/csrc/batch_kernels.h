@@ -71,6 +71,9 @@ struct SpmmKey {
 // lpr = 0: the SELL-32 copy, one thread per block row, wpb slices per block
 // (block shapes with gsell_supported only)
 bool gsell_supported(int br, int bc);
+// lpr = -8 / -16: block lanes, 8 or 16 lanes per block row, one whole block
+// per lane (6x6 and 6x3 blocks only)
+bool gblock_supported(int br, int bc);
 cudaError_t launch_gspmm(const SpmmKey &k, int nr, int lpr, int wpb, const SpmmItem *items,
                          int n_items, int grid, const McgState *st, cudaStream_t s);
 // kind: 0 FP64; 1 FP64 input -> FP32 (+ FP32 copy of the input); 2 FP32
