@@ -251,6 +251,17 @@ def time_oracle(H, f, gpu_iters, budget_s=15.0):
 # ---------------------------------------------------------------------------
 
 
+def max_over_ranks(value, ws, device):
+    """The largest of every rank's value (the timing of a multi-replica run is
+    that of its slowest replica); the value itself for one rank."""
+    if ws <= 1:
+        return value
+    import torch
+    t = torch.tensor([float(value)], dtype=torch.float64, device=device)
+    torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+    return float(t.item())
+
+
 def dist_env():
     ws = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
@@ -369,11 +380,7 @@ def main():
     clocks = sampler.stop()
     if ws > 1:
         torch.distributed.barrier()
-    ms = float(np.mean(times))
-    if ws > 1:
-        t = torch.tensor([ms], device=dev)
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        ms = float(t.item())
+    ms = max_over_ranks(float(np.mean(times)), ws, dev)
 
     # final FP64 true residual (computed on the device by the library)
     res = torch.zeros_like(f)
@@ -732,11 +739,7 @@ def run_batch(args, ws, rank, local, problems):
     clocks = sampler.stop()
     if ws > 1:
         torch.distributed.barrier()
-    ms = float(np.mean(times))
-    if ws > 1:
-        t = torch.tensor([ms], device=dev)
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        ms = float(t.item())
+    ms = max_over_ranks(float(np.mean(times)), ws, dev)
     uh = u.cpu().numpy()
 
     # FP64 true residual of every load case (library residual kernel)

@@ -1,0 +1,85 @@
+"""Host-side logic of bench.py that needs no GPU: the max-over-ranks timing of
+a multi-replica run (two gloo ranks on the CPU), the algorithmic byte count
+per PCG iteration, and the kernel-source key of the recorded ncu traffic."""
+import os
+import socket
+
+import numpy as np
+import pytest
+
+import bench
+
+torch = pytest.importorskip("torch")
+
+
+def _free_port():
+    with socket.socket() as s:
+        s.bind(("127.0.0.1", 0))
+        return s.getsockname()[1]
+
+
+def _rank_main(rank, ws, port, values, out):
+    import torch.distributed as dist
+    dist.init_process_group("gloo", init_method=f"tcp://127.0.0.1:{port}", rank=rank, world_size=ws)
+    try:
+        out[rank] = bench.max_over_ranks(values[rank], ws, "cpu")
+        dist.barrier()
+    finally:
+        dist.destroy_process_group()
+
+
+def test_max_over_ranks_two_gloo_ranks():
+    import torch.multiprocessing as mp
+    ctx = mp.get_context("spawn")
+    mgr = ctx.Manager()
+    out = mgr.dict()
+    values = [3.25, 7.5]
+    port = _free_port()
+    procs = [ctx.Process(target=_rank_main, args=(r, 2, port, values, out)) for r in range(2)]
+    for p in procs:
+        p.start()
+    for p in procs:
+        p.join(timeout=120)
+        assert p.exitcode == 0
+    assert out[0] == out[1] == 7.5
+
+
+def test_max_over_ranks_single_rank_is_identity():
+    assert bench.max_over_ranks(1.5, 1, "cpu") == 1.5
+
+
+def test_algorithmic_bytes_count():
+    """Two levels (3x3 fine, 6x6 coarsest), FP64 and FP32 V-cycles, 1 and 6
+    load cases, against the terms written out by hand."""
+    lv = [dict(n_rows=10, block=3, nnzb=40, nnzb_P=12), dict(n_rows=2, block=6, nnzb=4, nnzb_P=0)]
+    n0, N0, N1 = 10, 30, 12
+    A0 = 40 * (9 * 8 + 4) + 4 * (n0 + 1)
+    for prec, w, wv in ((0, 8, 8), (1, 4, 4)):
+        mat = A0 + N1 * N1 * 8
+        Ab = 40 * (9 * w + 4) + 4 * 11
+        Pb = 12 * (18 * w + 4) + 4 * 11
+        Rb = 12 * (18 * w + 4) + 4 * 3
+        Mb = 10 * 9 * wv
+        mat += 2 * Mb + 2 * Ab + Pb + Rb
+        vec = N0 * 8 * 2 + N0 * 8 * 11 + 2 * N1 * wv + 11 * N0 * wv + 2 * N1 * wv
+        if prec:
+            vec += N0 * 12 * 2
+        for nr in (1, 6):
+            assert bench.algorithmic_bytes_per_iteration(lv, prec, nr) == mat + nr * vec
+
+
+def test_kernel_source_key_tracks_the_kernel(tmp_path):
+    src = os.path.join(os.path.dirname(bench.__file__), "paper_2011_13325_gb300", "csrc",
+                       "bsr_kernels.cu")
+    text = open(src).read()
+    h = bench.kernel_source_sha1(src, "sell_kernel")
+    assert h == bench.kernel_source_sha1(src, "sell_kernel")
+    # a change elsewhere keeps the key, a change inside the kernel does not
+    other = tmp_path / "a.cu"
+    other.write_text(text.replace("namespace amg {", "namespace amg {\n// note", 1))
+    assert bench.kernel_source_sha1(str(other), "sell_kernel") == h
+    i = text.index(" sell_kernel(int n_rows")
+    j = text.index("if (row >= n_rows) return;", i)
+    changed = tmp_path / "b.cu"
+    changed.write_text(text[:j] + "if (row >= n_rows + 0) return;" + text[j + len("if (row >= n_rows) return;"):])
+    assert bench.kernel_source_sha1(str(changed), "sell_kernel") != h
