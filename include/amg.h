@@ -239,7 +239,10 @@ int amg_set_launch_overlap(amg_ctx *ctx, int enable);
  * Under AMG_LAYOUT_AUTO the upload also times, for every V-cycle operator
  * but a square one with a SELL-32 copy, the warp-row, row-lane and
  * block-lane kernels (and the SELL-32 copy where there is one) on the
- * operator itself and keeps the fastest.
+ * operator itself and keeps the fastest.  With the environment variable
+ * AMG_TUNE_CACHE naming a file, choices recorded there are reused without
+ * timing and new ones appended (a profiled process then applies the kernels
+ * an earlier plain process chose).
  * The result of every operator is the same up to the order of the sums. */
 enum {
   AMG_LAYOUT_AUTO = 0,

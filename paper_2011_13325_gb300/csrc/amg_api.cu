@@ -308,21 +308,58 @@ static int finish(Ctx *c, const char *where) {
 // and block-lane kernels and, where it has one, its SELL-32 copy (one warm
 // launch, then three timed) in the V-cycle precision, and keeps the
 // fastest.  The kernels differ only in the order of the sums.
+// Optional tuning cache: with AMG_TUNE_CACHE naming a file, choices found
+// there (key: level, operator, rows, stored blocks, precision) are reused
+// without timing and new ones are appended, so that a later process (e.g. one
+// run under a profiler, where event timings are distorted) applies the same
+// kernels.
+static std::string tune_key(int l, char op, const DevBSR &m, int prec) {
+  char k[128];
+  snprintf(k, sizeof k, "L%d%c_%d_%lld_%dx%d_p%d", l, op, m.n_rows, (long long)m.nnzb, m.br, m.bc, prec);
+  return k;
+}
+
+static std::vector<std::pair<std::string, int>> load_tune_cache(const char *path) {
+  std::vector<std::pair<std::string, int>> out;
+  FILE *f = path ? fopen(path, "r") : nullptr;
+  if (!f) return out;
+  char key[128];
+  int k = 0;
+  while (fscanf(f, "%127s %d", key, &k) == 2)
+    if (k >= KERN_WARP_ROWS && k <= KERN_SELL) out.emplace_back(key, k);
+  fclose(f);
+  return out;
+}
+
 static cudaError_t tune_operators(Ctx *c) {
   if (c->layout_policy != AMG_LAYOUT_AUTO) return cudaSuccess;
+  const char *cache_path = getenv("AMG_TUNE_CACHE");
+  const auto cache = load_tune_cache(cache_path);
+  std::vector<std::pair<std::string, int>> fresh;
   // (operator, its mode in the V-cycle): A residual, P prolongation-add,
   // R restriction
   std::vector<std::pair<DevBSR *, int>> ops;
+  std::vector<std::string> keys;
   size_t nx = 0, ny = 0;
   for (int l = 0; l + 1 < (int)c->levels.size(); ++l) {
     Level &L = c->levels[l];
     const std::pair<DevBSR *, int> cand[3] = {{&L.A, SPMV_RESID}, {&L.P, SPMV_ADD}, {&L.R, SPMV_SET}};
-    for (const auto &om : cand) {
-      DevBSR *m = om.first;
+    const char names[3] = {'A', 'P', 'R'};
+    for (int i = 0; i < 3; ++i) {
+      DevBSR *m = cand[i].first;
       // a square operator with a SELL-32 copy keeps it (A_0 is also the CG
       // operator, whose FP64 kernels use that copy)
       if (!m->nnzb || (m == &L.A && m->sell_ptr)) continue;
-      ops.push_back(om);
+      const std::string key = tune_key(l, names[i], *m, c->precision);
+      bool hit = false;
+      for (const auto &kv : cache)
+        if (kv.first == key && (kv.second != KERN_SELL || m->sell_ptr)) {
+          m->kern = kv.second;
+          hit = true;
+        }
+      if (hit) continue;
+      ops.push_back(cand[i]);
+      keys.push_back(key);
       nx = std::max(nx, (size_t)m->n_cols * m->bc);
       ny = std::max(ny, (size_t)m->n_rows * m->br);
     }
@@ -363,12 +400,20 @@ static cudaError_t tune_operators(Ctx *c) {
       }
     }
     m.kern = pick;
+    fresh.emplace_back(keys[i], pick);
   }
   if (e0) cudaEventDestroy(e0);
   if (e1) cudaEventDestroy(e1);
   dfree(x);
   dfree(y);
   dfree(b);
+  if (e == cudaSuccess && cache_path && !fresh.empty()) {
+    FILE *f = fopen(cache_path, "a");
+    if (f) {
+      for (const auto &kv : fresh) fprintf(f, "%s %d\n", kv.first.c_str(), kv.second);
+      fclose(f);
+    }
+  }
   return e;
 }
 
