@@ -436,7 +436,10 @@ def main():
     # precision variants (same prolongations, re-uploaded)
     variants = {}
     if args.variants == "auto":
-        vlist = [] if args.smoother == "learned" else [p for p in (0, 1, 2) if p != args.precision]
+        # learned: the plain FP64 V-cycle with block-l1 Jacobi (the method without
+        # the extensions); otherwise the two other precisions
+        vlist = ([0] if args.precision != 0 else []) if args.smoother == "learned" else \
+            [p for p in (0, 1, 2) if p != args.precision]
     else:
         vlist = [int(v) for v in args.variants.split(",") if v.strip()]
     for prec in vlist:
