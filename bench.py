@@ -121,12 +121,6 @@ class ClockSampler:
                 "reasons": sorted(reasons), "samples": len(sm)}
 
 
-def vcycle_launches(levels, prec):
-    """Kernels of one V-cycle: 5 per non-coarsest level and 1 coarsest (the
-    FP64<->FP32 casts of the mixed precisions are fused into level 0)."""
-    return 5 * (len(levels) - 1) + 1 + (2 if prec and len(levels) == 1 else 0)
-
-
 def algorithmic_bytes_per_iteration(levels, prec, nr=1):
     """Bytes one PCG iteration must move at least once (matrices, smoother
     blocks, vectors), from the actual level sizes; with nr load cases solved
@@ -431,7 +425,8 @@ def main():
     it_mean = float(np.mean(its))
     per_it_bytes = algorithmic_bytes_per_iteration(levels, args.precision)
     solve_gbs = per_it_bytes * it_mean / (ms * 1e-3) / 1e9
-    launches = 1 + int(round(it_mean)) * (vcycle_launches(levels, args.precision) + 6)
+    per_it, fixed = ctx.pcg_launches()
+    launches = fixed + int(round(it_mean)) * per_it
 
     # precision variants (same prolongations, re-uploaded)
     variants = {}

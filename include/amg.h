@@ -222,6 +222,10 @@ int amg_set_pcg_graph(amg_ctx *ctx, int enable);
  * build refuses the programmatic launches, the library turns them off. */
 int amg_set_launch_overlap(amg_ctx *ctx, int enable);
 
+/* Kernel launches of one amg_pcg_solve (one right-hand side): *fixed +
+ * iterations * *per_iteration. */
+int amg_pcg_launches(const amg_ctx *ctx, int32_t *per_iteration, int32_t *fixed);
+
 /* Storage layout of the level operators, applied by the next
  * amg_upload_hierarchy / amg_setup:
  *   AMG_LAYOUT_AUTO             SELL-32 copy (one thread per block row) for

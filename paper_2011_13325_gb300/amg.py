@@ -108,6 +108,7 @@ _SIGS = {
     "amg_download_prolongation": (_I, [_P, _I, _P, _P, _P]),
     "amg_describe": (C.c_char_p, [_P]),
     "amg_set_launch_overlap": (_I, [_P, _I]),
+    "amg_pcg_launches": (_I, [_P, C.POINTER(C.c_int32), C.POINTER(C.c_int32)]),
     "amg_profile_vcycle": (_I, [_P, _I, _P, _P, _P, _P, _I, C.POINTER(C.c_int32)]),
     "amg_mlp_create": (_I, [C.POINTER(_P), _I, C.c_uint64]),
     "amg_mlp_destroy": (None, [_P]),
@@ -381,6 +382,12 @@ class Context:
 
     def set_layout_policy(self, policy: int):
         return self._check(lib().amg_set_layout_policy(self.h, int(policy)))
+
+    def pcg_launches(self):
+        """(kernels per PCG iteration, fixed kernels per solve)."""
+        a, b = C.c_int32(), C.c_int32()
+        self._check(lib().amg_pcg_launches(self.h, C.byref(a), C.byref(b)))
+        return a.value, b.value
 
     def set_launch_overlap(self, enable: bool):
         return self._check(lib().amg_set_launch_overlap(self.h, int(bool(enable))))

@@ -520,3 +520,18 @@ cudaError_t pcg_build_graph(Ctx *c) {
 }
 
 }  // namespace amg
+
+using namespace amg;
+
+extern "C" int amg_pcg_launches(const amg_ctx *h, int32_t *per_iteration, int32_t *fixed) {
+  if (!h) return AMG_ERR_ARG;
+  const Ctx *c = &h->c;
+  if (c->levels.empty()) return AMG_ERR_STATE;
+  const int nl = (int)c->levels.size();
+  int vc = 5 * (nl - 1) + 1;                              // V-cycle kernels
+  if (nl == 1 && c->precision != AMG_PREC_FP64) vc += 2;  // FP64 <-> FP32 casts
+  // r.z, p update, q = A p with p.q, alpha, x / r update with r.r, loop decision
+  if (per_iteration) *per_iteration = vc + 6;
+  if (fixed) *fixed = 1;
+  return AMG_OK;
+}
