@@ -92,7 +92,8 @@ enum {
   AMG_SMOOTHER_LEARNED = 1    /* per-vertex blocks of amg_set_learned_smoother  */
 };
 
-/* Create a context on CUDA device `device`.  `cuda_stream` is a
+/* Create a context (library plumbing, no counterpart in the paper) on CUDA
+ * device `device`.  `cuda_stream` is a
  * cudaStream_t owned by the caller (not the legacy default stream: the CG is
  * captured into a CUDA graph), or NULL to let the library create a blocking
  * stream, ordered with the legacy default stream.
@@ -100,10 +101,11 @@ enum {
  * AMG_ERR_CUDA. */
 int amg_create(amg_ctx **ctx, int device, void *cuda_stream);
 
-/* Release every device buffer, graph and owned stream.  NULL is a no-op. */
+/* Release every device buffer, graph and owned stream (plumbing).  NULL is
+ * a no-op. */
 void amg_destroy(amg_ctx *ctx);
 
-/* Message of the last failed call on ctx ("" if none). Valid until the next
+/* Message of the last failed call on ctx ("" if none; plumbing). Valid until the next
  * call on ctx. */
 const char *amg_last_error(const amg_ctx *ctx);
 
@@ -130,28 +132,29 @@ int amg_upload_hierarchy(amg_ctx *ctx, const amg_hierarchy *h, int precision, in
  * reported by amg_level_info(level+1).  0 <= level < n_levels-1. */
 int amg_galerkin(amg_ctx *ctx, int level, amg_bsr_out *out);
 
-/* Sizes of level `level`: block rows, block size and stored blocks of A_l,
- * and of P_l (0 on the coarsest level).  Any output pointer may be NULL. */
+/* Sizes of level `level` of the hierarchy (Sec. 3: A_l, P_l): block rows,
+ * block size and stored blocks of A_l, and of P_l (0 on the coarsest level).
+ * Any output pointer may be NULL. */
 int amg_level_info(const amg_ctx *ctx, int level, int32_t *n_rows, int32_t *block,
                    int64_t *nnzb_A, int64_t *nnzb_P, int32_t *n_levels);
 
-/* Copy A_level (as held on the device, FP64) to caller host arrays sized as
- * reported by amg_level_info. */
+/* Copy A_level (the Galerkin operator of Sec. 3, as held on the device,
+ * FP64) to caller host arrays sized as reported by amg_level_info. */
 int amg_download_matrix(amg_ctx *ctx, int level, int32_t *rowptr, int32_t *colidx, double *vals);
 
-/* Copy the smoother blocks M_v^+ of `level` (n_rows * k * k doubles,
- * row-major per block) to host memory `minv`. */
+/* Copy the smoother blocks M_v^+ of `level` (block-l1 Jacobi, Sec. 7;
+ * n_rows * k * k doubles, row-major per block) to host memory `minv`. */
 int amg_download_smoother(amg_ctx *ctx, int level, double *minv);
 
-/* Copy the coarsest-level inverse (A_L + I - E_L E_L^T)^{-1} (n x n doubles,
- * n = n_rows * k of the coarsest level) to host memory. */
+/* Copy the coarsest-level inverse (A_L + I - E_L E_L^T)^{-1} (Sec. 3.1;
+ * n x n doubles, n = n_rows * k of the coarsest level) to host memory. */
 int amg_download_coarse_inverse(amg_ctx *ctx, double *cinv);
 
 /* --- single steps of the V-cycle, FP64, device vectors of level `level` --- */
 
-/* y = A_l x (BSR SpMV). */
+/* y = A_l x (BSR SpMV with the level operator of Algorithm tg). */
 int amg_spmv(amg_ctx *ctx, int level, const double *x_dev, double *y_dev);
-/* r = b - A_l x. */
+/* r = b - A_l x (the residual of Algorithm tg). */
 int amg_residual(amg_ctx *ctx, int level, const double *b_dev, const double *x_dev, double *r_dev);
 /* One block-l1 Jacobi sweep x_out = x_in + M^+ (b - A_l x_in) (Algorithm tg,
  * pre- and post-smoothing; M symmetric so M^{-T} = M^{-1}).  x_in == NULL
@@ -180,7 +183,8 @@ int amg_vcycle(amg_ctx *ctx, const double *r_dev, double *z_dev, int nrhs);
 int amg_pcg_solve(amg_ctx *ctx, const double *f_dev, double *u_dev, int nrhs, double rtol,
                   int maxit, int *iters_out, double *relres_out);
 
-/* As amg_pcg_solve but f_host / u_host are host arrays (pinned or pageable);
+/* As amg_pcg_solve (PCG of Sec. 7) but f_host / u_host are host arrays
+ * (pinned or pageable);
  * the host->device copy of f and u and the device->host copy of u happen
  * inside the call on the context's stream (end-to-end use). */
 int amg_pcg_solve_host(amg_ctx *ctx, const double *f_host, double *u_host, int nrhs,
@@ -207,23 +211,26 @@ int amg_pcg_solve_host(amg_ctx *ctx, const double *f_host, double *u_host, int n
  *    the GPU (two contexts, two streams) race on it and must be serialised. */
 int amg_vcycle_static(amg_ctx *ctx, const double *r_dev, double *z_dev);
 
-/* Execution mode of amg_pcg_solve*: enable != 0 (default) runs the whole
+/* Execution mode of amg_pcg_solve* (the PCG of Sec. 7; no counterpart in
+ * the paper: a GPU scheduling choice): enable != 0 (default) runs the whole
  * iteration as one CUDA graph with a device-side while loop; enable == 0
  * launches the same kernels one by one and reads the loop condition back
  * after every iteration (a kernel-by-kernel view for profilers, which do not
  * see inside graphs with conditional nodes).  Results are identical. */
 int amg_set_pcg_graph(amg_ctx *ctx, int enable);
 
-/* Programmatic dependent launch of the solve-phase kernels (default on):
- * every V-cycle and CG kernel waits at its start for the previous kernel of
- * the stream to complete (griddepcontrol.wait) and lets the next one be
- * scheduled at once, so that each launch overlaps its predecessor's tail.
- * enable = 0 launches them plainly.  Results are identical.  If a graph
- * build refuses the programmatic launches, the library turns them off. */
+/* Programmatic dependent launch of the solve-phase kernels (no counterpart
+ * in the paper; default on): every V-cycle and CG kernel is launched with
+ * programmatic stream serialization and waits at its start for the previous
+ * kernel of the stream to complete (griddepcontrol.wait), so that its launch
+ * overlaps the predecessor's drain.  enable = 0 launches them plainly.
+ * Results are identical.  If a graph build refuses the programmatic
+ * launches, the library turns them off. */
 int amg_set_launch_overlap(amg_ctx *ctx, int enable);
 
-/* Kernel launches of one amg_pcg_solve (one right-hand side): *fixed +
- * iterations * *per_iteration. */
+/* Kernel launches of one amg_pcg_solve (one right-hand side; the V-cycle of
+ * Algorithm tg and the CG steps of Sec. 7): *fixed + iterations *
+ * *per_iteration. */
 int amg_pcg_launches(const amg_ctx *ctx, int32_t *per_iteration, int32_t *fixed);
 
 /* Storage layout of the level operators, applied by the next
@@ -257,7 +264,8 @@ enum {
 };
 int amg_set_layout_policy(amg_ctx *ctx, int policy);
 
-/* Per-kernel timing of one V-cycle in the context's precision: every step
+/* Per-kernel timing of one V-cycle (Algorithm tg) in the context's
+ * precision (a measurement aid, no counterpart in the paper): every step
  * (kind 0 pre-smoothing x = M^+ b, 1 residual t = b - A x, 2 restriction,
  * 3 prolongation x += P y, 4 post-smoothing, 5 coarsest solve) of every
  * level is launched reps times on the context's stream (after one warm
@@ -269,8 +277,9 @@ int amg_set_layout_policy(amg_ctx *ctx, int policy);
 int amg_profile_vcycle(amg_ctx *ctx, int reps, int32_t *level, int32_t *kind, double *us, double *bytes,
                        int max_entries, int32_t *n_entries);
 
-/* Text listing every level operator with its size and the kernel that
- * applies it (after the tuner); owned by ctx, valid until the next call. */
+/* Text listing every level operator (A_l, P_l, R_l of Sec. 3) with its
+ * size and the kernel that applies it (after the tuner); owned by ctx,
+ * valid until the next call. */
 const char *amg_describe(amg_ctx *ctx);
 
 /* Wall-clock seconds of the last amg_setup: [0] host setup (edge matrices,
@@ -284,7 +293,8 @@ int amg_setup_times(const amg_ctx *ctx, double *times4);
  * pipe on sm_103a, are reported).  Takes a few tens of milliseconds. */
 int amg_probe_fma_rate(amg_ctx *ctx, double *fp64_gflops, double *fp32_gflops);
 
-/* Cumulative device time (ms, CUDA events) of the last amg_pcg_solve* call. */
+/* Cumulative device time (ms, CUDA events) of the last amg_pcg_solve* call
+ * (the PCG of Sec. 7). */
 int amg_last_solve_ms(const amg_ctx *ctx, float *ms);
 
 
@@ -334,7 +344,7 @@ typedef struct {
   int32_t host_threads;
 } amg_setup_params;
 
-/* Fill *p with the defaults listed above. */
+/* Fill *p with the defaults listed above (the readings of Sec. 5, 6, 7). */
 void amg_default_setup_params(amg_setup_params *p);
 
 /* Build the hierarchy of `prob` on ctx: A_0 = A_full restricted to the free
@@ -348,12 +358,14 @@ void amg_default_setup_params(amg_setup_params *p);
 int amg_setup(amg_ctx *ctx, const amg_problem *prob, const amg_setup_params *params, int precision,
               int smoother);
 
-/* Size of P_level (0 <= level < n_levels-1): rows, columns, block dims and
+/* Size of P_level, the auxiliary smoothed prolongation (Def. aux_sp) built
+ * by amg_setup (0 <= level < n_levels-1): rows, columns, block dims and
  * stored blocks.  Any pointer may be NULL. */
 int amg_prolongation_info(const amg_ctx *ctx, int level, int32_t *n_rows, int32_t *n_cols,
                           int32_t *br, int32_t *bc, int64_t *nnzb);
 
-/* Copy P_level (FP64) to caller host arrays sized by amg_prolongation_info. */
+/* Copy P_level (Def. aux_sp, FP64) to caller host arrays sized by
+ * amg_prolongation_info. */
 int amg_download_prolongation(amg_ctx *ctx, int level, int32_t *rowptr, int32_t *colidx,
                               double *vals);
 
@@ -383,21 +395,25 @@ int amg_batch_create(amg_batch **batch, amg_ctx *const *systems, int n_systems, 
 void amg_batch_destroy(amg_batch *batch);
 const char *amg_batch_last_error(const amg_batch *batch);
 
-/* Text listing the grouped launches of the batch (init, one iteration,
- * tail) with the tile the autotuner chose and its time; owned by the batch. */
+/* Text listing the grouped launches of the batch (init, one iteration of
+ * the PCG of Sec. 7 with its V-cycle, tail) with the tile the autotuner
+ * chose and its time; owned by the batch. */
 const char *amg_batch_describe(const amg_batch *batch);
 
-/* Kernel launches of one solve: *fixed + iterations * *per_iteration, where
- * iterations is the largest iteration count over all load cases. */
+/* Kernel launches of one batched PCG solve (Sec. 7): *fixed + iterations *
+ * *per_iteration, where iterations is the largest iteration count over all
+ * load cases. */
 int amg_batch_launches(const amg_batch *batch, int32_t *per_iteration, int32_t *fixed);
 
-/* Layout of the stacked vectors: system s occupies [offset, offset +
+/* Layout of the stacked vectors (right-hand sides f and solutions u of
+ * A_0 u = f, Sec. 2, per system and load case): system s occupies [offset, offset +
  * nrhs * n_dofs) with its nrhs load cases one after another (each n_dofs
  * long); *total is the full length.  Any pointer may be NULL. */
 int amg_batch_layout(const amg_batch *batch, int s, int64_t *offset, int64_t *n_dofs,
                      int64_t *total);
 
-/* Solve all systems and load cases with one graph launch.  f_dev / u_dev
+/* Solve all systems and load cases by FP64 PCG with one V-cycle as
+ * preconditioner (Sec. 7) with one graph launch.  f_dev / u_dev
  * are stacked device vectors (amg_batch_layout); u_dev holds the initial
  * guesses and receives the solutions.  Every load case stops when its
  * recurrence residual reaches rtol * ||f|| (it is then frozen) or after
@@ -408,7 +424,7 @@ int amg_batch_layout(const amg_batch *batch, int s, int64_t *offset, int64_t *n_
 int amg_batch_pcg_solve(amg_batch *batch, const double *f_dev, double *u_dev, double rtol,
                         int maxit, int *iters_out, double *relres_out, float *ms_out);
 
-/* amg_batch_pcg_solve with the stacked f / u in HOST memory (pinned for
+/* amg_batch_pcg_solve (Sec. 7) with the stacked f / u in HOST memory (pinned for
  * full copy speed): the copies to and from the device are part of the call
  * and of *ms_out (end-to-end device time). */
 int amg_batch_pcg_solve_host(amg_batch *batch, const double *f_host, double *u_host, double rtol,
@@ -442,50 +458,53 @@ int amg_batch_pcg_solve_host(amg_batch *batch, const double *f_host, double *u_h
 
 typedef struct amg_mlp amg_mlp;
 
-/* Network on `device` with He-normal weights (splitmix64 stream from
+/* (Learned-smoother extension, no counterpart in the paper.)  Network on
+ * `device` with He-normal weights (splitmix64 stream from
  * `seed`, Box-Muller) and zero biases.  Errors: AMG_ERR_ARG, AMG_ERR_CUDA. */
 int amg_mlp_create(amg_mlp **mlp, int device, uint64_t seed);
 void amg_mlp_destroy(amg_mlp *mlp);
 const char *amg_mlp_last_error(const amg_mlp *mlp);
 int amg_mlp_n_params(void);
 
-/* Copy the parameters to host `params` (AMG_MLP_PARAMS floats): the FP32
+/* (Extension.)  Copy the parameters to host `params` (AMG_MLP_PARAMS floats): the FP32
  * master weights (working = 0) or the BF16 weights the kernels compute with,
  * widened to FP32 (working = 1). */
 int amg_mlp_get_params(amg_mlp *mlp, float *params, int working);
 
-/* Set the master weights (host FP32), refresh the BF16 copy, clear Adam. */
+/* (Extension.)  Set the master weights (host FP32), refresh the BF16 copy, clear Adam. */
 int amg_mlp_set_params(amg_mlp *mlp, const float *params);
 
-/* Features of the level-0 vertices of ctx: coords_host (n_0 x 3 FP64,
+/* (Extension; features from the finest edge matrices of Thm. deng_elast.)
+ * Features of the level-0 vertices of ctx: coords_host (n_0 x 3 FP64,
  * host) are the vertex positions; X_dev receives n_0 x 13 FP32 (device),
  * tr_dev (device, may be NULL) n_0 traces.  Errors: AMG_ERR_STATE (no
  * hierarchy), AMG_ERR_ARG (not 3x3 blocks, a vertex without positive
  * diagonal block), AMG_ERR_CUDA. */
 int amg_learned_features(amg_ctx *ctx, const double *coords_host, float *X_dev, double *tr_dev);
 
-/* Patch-inverse targets of the level-0 vertices (n_0 x 9, device; either
+/* (Extension.)  Patch-inverse targets of the level-0 vertices (n_0 x 9, device; either
  * pointer may be NULL), computed in FP64 (dense Cholesky per patch).
  * AMG_ERR_ARG if a vertex has more than 15 neighbours or a singular patch. */
 int amg_learned_targets(amg_ctx *ctx, float *T32_dev, double *T64_dev);
 
-/* Mean loss (1/n) sum_v ||L L^T + 1e-6 I - T_v||_F^2 over n samples
+/* (Extension.)  Mean loss (1/n) sum_v ||L L^T + 1e-6 I - T_v||_F^2 over n samples
  * (X_dev n x 13, T_dev n x 9, device) and its gradient (host, may be NULL),
  * with the BF16 weights. */
 int amg_mlp_loss_grad(amg_mlp *mlp, const float *X_dev, const float *T_dev, int64_t n, double *loss,
                       float *grad_host);
 
-/* Adam (beta 0.9 / 0.999, eps 1e-8, step lr) over `epochs` passes of n
+/* (Extension.)  Adam (beta 0.9 / 0.999, eps 1e-8, step lr) over `epochs` passes of n
  * samples in minibatches of `batch` (>= 32), the order of each pass a
  * splitmix64 Fisher-Yates shuffle from `seed`; epoch_loss (host, may be
  * NULL) receives the mean minibatch loss of every pass.  All on the device. */
 int amg_mlp_train(amg_mlp *mlp, const float *X_dev, const float *T_dev, int64_t n, int epochs, int batch,
                   float lr, uint64_t seed, double *epoch_loss);
 
-/* Outputs (n x 6 FP32, device) of the network for n feature rows. */
+/* (Extension.)  Outputs (n x 6 FP32, device) of the network for n feature rows. */
 int amg_mlp_infer(amg_mlp *mlp, const float *X_dev, int64_t n, float *out_dev);
 
-/* Replace the level-0 smoother blocks of ctx by the damped learned blocks
+/* (Extension; replaces the block-l1 Jacobi smoother of Sec. 7 on level 0.)
+ * Replace the level-0 smoother blocks of ctx by the damped learned blocks
  * omega * B_v (features from coords_host as in amg_learned_features);
  * lambda_out / omega_out (may be NULL) receive the Lanczos estimate and the
  * damping.  The PCG graph stays valid (same buffers).  Errors: AMG_ERR_STATE
@@ -493,7 +512,7 @@ int amg_mlp_infer(amg_mlp *mlp, const float *X_dev, int64_t n, float *out_dev);
 int amg_set_learned_smoother(amg_ctx *ctx, amg_mlp *mlp, const double *coords_host, double *lambda_out,
                              double *omega_out);
 
-/* Restore the block-l1 Jacobi smoother of level 0. */
+/* Restore the block-l1 Jacobi smoother (Sec. 7) of level 0. */
 int amg_reset_smoother(amg_ctx *ctx);
 
 #ifdef __cplusplus
