@@ -201,9 +201,12 @@ static cudaError_t bsr_mode(const Ctx *c, const DevBSR &A, const V *vals, int mo
       AMG_KLAUNCH(c, bsr_warp_kernel<BR, BC, V, T, SPMV_ADD>, g, 256, A.n_rows, A.rowptr, A.colidx, vals, xx, bb, mm, yy);
       break;
     case SPMV_SMOOTH:
-      if (BR != BC) return cudaErrorInvalidValue;
-      AMG_KLAUNCH(c, bsr_warp_kernel<BR, BC, V, T, SPMV_SMOOTH>, g, 256, A.n_rows, A.rowptr, A.colidx, vals, xx, bb, mm, yy);
-      break;
+      if constexpr (BR == BC) {
+        AMG_KLAUNCH(c, bsr_warp_kernel<BR, BC, V, T, SPMV_SMOOTH>, g, 256, A.n_rows, A.rowptr, A.colidx, vals, xx, bb, mm, yy);
+        break;
+      } else {
+        return cudaErrorInvalidValue;
+      }
     default:
       return cudaErrorInvalidValue;
   }
@@ -294,9 +297,12 @@ static cudaError_t rowlane_mode(const Ctx *c, const DevBSR &A, const V *vals, in
     case SPMV_RESID: AMG_RL_LAUNCH(SPMV_RESID); break;
     case SPMV_ADD: AMG_RL_LAUNCH(SPMV_ADD); break;
     case SPMV_SMOOTH:
-      if (BR != BC) return cudaErrorInvalidValue;
-      AMG_RL_LAUNCH(SPMV_SMOOTH);
-      break;
+      if constexpr (BR == BC) {
+        AMG_RL_LAUNCH(SPMV_SMOOTH);
+        break;
+      } else {
+        return cudaErrorInvalidValue;
+      }
     default: return cudaErrorInvalidValue;
   }
 #undef AMG_RL_LAUNCH
@@ -403,9 +409,12 @@ static cudaError_t lblock_mode(const Ctx *c, const DevBSR &A, const V *vals, int
     case SPMV_RESID: AMG_LB_LAUNCH(SPMV_RESID); break;
     case SPMV_ADD: AMG_LB_LAUNCH(SPMV_ADD); break;
     case SPMV_SMOOTH:
-      if (BR != BC) return cudaErrorInvalidValue;
-      AMG_LB_LAUNCH(SPMV_SMOOTH);
-      break;
+      if constexpr (BR == BC) {
+        AMG_LB_LAUNCH(SPMV_SMOOTH);
+        break;
+      } else {
+        return cudaErrorInvalidValue;
+      }
     default: return cudaErrorInvalidValue;
   }
 #undef AMG_LB_LAUNCH
@@ -489,9 +498,12 @@ static cudaError_t sell_mode(const Ctx *c, const DevBSR &A, const V *vals, int m
     case SPMV_RESID: AMG_SELL_LAUNCH(SPMV_RESID); break;
     case SPMV_ADD: AMG_SELL_LAUNCH(SPMV_ADD); break;
     case SPMV_SMOOTH:
-      if (BR != BC) return cudaErrorInvalidValue;
-      AMG_SELL_LAUNCH(SPMV_SMOOTH);
-      break;
+      if constexpr (BR == BC) {
+        AMG_SELL_LAUNCH(SPMV_SMOOTH);
+        break;
+      } else {
+        return cudaErrorInvalidValue;
+      }
     default: return cudaErrorInvalidValue;
   }
 #undef AMG_SELL_LAUNCH

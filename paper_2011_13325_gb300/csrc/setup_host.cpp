@@ -478,7 +478,7 @@ static double trace(int k, const double *A) {
 // Lemma mu2 (delta-stabilised pair measure)
 static double mu_p(const Topo &T, const std::vector<double> &Dh, int i, int j, int delta) {
   const int k = T.k, d = T.d;
-  double t[3], A[36], B[36], L[36], R[36], X[36], Y[36], H[36];
+  double t[3] = {0.0, 0.0, 0.0}, A[36], B[36], L[36], R[36], X[36], Y[36], H[36];
   half_shift(T, j, i, t);  // Q^{ji} = Q((x_i - x_j)/2)
   transport(d, t, Dh.data() + (size_t)i * k * k, A);
   half_shift(T, i, j, t);  // Q^{ij}
