@@ -557,7 +557,7 @@ def main():
 
 
 def run_reference(args, ws, rank, local):
-    """The CPU oracle on the machine's host cores, on the same workload and
+    """The CPU oracle on this machine's host cores, on the same workload and
     hierarchy, each step a bounded sample of oracle PCG iterations."""
     import torch
     if rank != 0:
