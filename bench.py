@@ -695,6 +695,50 @@ def stacked(B, problems):
     return f
 
 
+def batch_stage_roofline(levels_per_system, tuned, prec, hbm_gbs, nr=6):
+    """Per grouped product stage of the batch: its tuned time per launch (from
+    the tuner's CUDA events) against its algorithmic bytes over all systems
+    (values + indices + row pointers once, vectors of the nr load cases
+    once, updated outputs twice, smoother blocks for the smoothing)."""
+    import re
+    w = {0: 8, 1: 4, 2: 2}[prec]
+    wv = 8 if prec == 0 else 4
+    out = []
+    for ln in tuned:
+        m = re.search(r"(init|iteration): (.*?) (\d+)x(\d+): .* ([0-9.]+) us$", ln)
+        if not m:
+            continue
+        name, br, bc, us = m.group(2), int(m.group(3)), int(m.group(4)), float(m.group(5))
+        lv = re.search(r"level (\d+)", name)
+        total = 0.0
+        for levels in levels_per_system:
+            if "A_0" in name:            # FP64 CG operator (init residual, q = A p)
+                L = levels[0]
+                n, k = L["n_rows"], L["block"]
+                total += L["nnzb"] * (k * k * 8 + 4) + 4 * (n + 1) + (3 if "f -" in name else 2) * n * k * nr * 8
+                continue
+            l = int(lv.group(1))
+            if l >= len(levels) - 1:
+                continue
+            L, C = levels[l], levels[l + 1]
+            n, k, nc, kc = L["n_rows"], L["block"], C["n_rows"], C["block"]
+            if L["block"] != br and "A x" in name:
+                continue
+            if "t = b - A x" in name:
+                total += L["nnzb"] * (k * k * w + 4) + 4 * (n + 1) + 3 * n * k * nr * wv
+            elif "M^+(b - A x)" in name:
+                total += L["nnzb"] * (k * k * w + 4) + 4 * (n + 1) + 3 * n * k * nr * wv + n * k * k * wv
+            elif "b_c = R t" in name:
+                total += L["nnzb_P"] * (k * kc * w + 4) + 4 * (nc + 1) + (n * k + nc * kc) * nr * wv
+            elif "x += P y_c" in name:
+                total += L["nnzb_P"] * (k * kc * w + 4) + 4 * (n + 1) + (nc * kc + 2 * n * k) * nr * wv
+        if total and us > 0:
+            gbs = total / (us * 1e-6) / 1e9
+            out.append({"stage": name, "block": f"{br}x{bc}", "us": us, "mbytes": round(total / 1e6, 1),
+                        "gbs": round(gbs, 1), "frac_hbm": round(gbs / hbm_gbs, 3)})
+    return out
+
+
 def run_batch(args, ws, rank, local, problems):
     import torch
     from paper_2011_13325_gb300 import amg
@@ -851,6 +895,7 @@ def run_batch(args, ws, rank, local, problems):
                 "h2d_bytes_per_step": 2 * total * 8, "d2h_bytes_per_step": total * 8},
         "gpu_launches": launches * args.steps, "gpu_launches_per_step": launches,
         "autotuned_products": tuned,
+        "stage_kernels": batch_stage_roofline(levels_per_system, tuned, prec, pk["hbm_gbs"]),
         "cpu_baseline": cpu,
     }
     if rank == 0:

@@ -83,3 +83,22 @@ def test_kernel_source_key_tracks_the_kernel(tmp_path):
     changed = tmp_path / "b.cu"
     changed.write_text(text[:j] + "if (row >= n_rows + 0) return;" + text[j + len("if (row >= n_rows) return;"):])
     assert bench.kernel_source_sha1(str(changed), "sell_kernel") != h
+
+
+def test_batch_stage_roofline_bytes():
+    """One system, two levels: the residual and restriction stages of level 0
+    and the FP64 CG product, against the byte counts written out."""
+    lv = [[dict(n_rows=10, block=3, nnzb=40, nnzb_P=12), dict(n_rows=2, block=6, nnzb=4, nnzb_P=0)]]
+    tuned = ["iteration: level 0 t = b - A x (low precision) 3x3: 1 systems, 5 blocks, 32 lanes/row, "
+             "4 warps/block, 2.0 us",
+             "iteration: level 0 b_c = R t (low precision) 6x3: 1 systems, 5 blocks, SELL-32 thread/row, "
+             "2 slices/block, 1.0 us",
+             "iteration: q = A_0 p 3x3: 1 systems, 5 blocks, SELL-32 thread/row, 2 slices/block, 4.0 us"]
+    out = {r["stage"].split(" (")[0]: r for r in bench.batch_stage_roofline(lv, tuned, 1, 1000.0, nr=6)}
+    resid = 40 * (9 * 4 + 4) + 4 * 11 + 3 * 30 * 6 * 4
+    restr = 12 * (18 * 4 + 4) + 4 * 3 + (30 + 12) * 6 * 4
+    cg = 40 * (9 * 8 + 4) + 4 * 11 + 2 * 30 * 6 * 8
+    assert out["level 0 t = b - A x"]["mbytes"] == round(resid / 1e6, 1)
+    assert abs(out["level 0 t = b - A x"]["gbs"] - round(resid / 2e-6 / 1e9, 1)) < 1e-9
+    assert abs(out["level 0 b_c = R t"]["gbs"] - round(restr / 1e-6 / 1e9, 1)) < 1e-9
+    assert abs(out["q = A_0 p"]["gbs"] - round(cg / 4e-6 / 1e9, 1)) < 1e-9
