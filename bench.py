@@ -175,6 +175,22 @@ def traffic_record():
     return rec
 
 
+def scaled_traffic(rec, algorithmic_bytes):
+    """DRAM bytes per launch of the dominant kernel on this workload.  The
+    record holds one capture (cube64); on another workload the launch reads
+    each block and block row once as well, so its traffic grows with the
+    algorithmic bytes: the captured traffic is scaled by their ratio.
+    Returns (bytes, how it was obtained), or (None, None) without a record."""
+    if not rec:
+        return None, None
+    ref = rec["algorithmic_bytes_per_launch"]
+    if int(algorithmic_bytes) == int(ref):
+        return int(rec["bytes_per_launch"]), f"ncu capture ({rec.get('workload', 'same workload')})"
+    t = int(round(rec["bytes_per_launch"] * algorithmic_bytes / ref))
+    return t, (f"scaled from the {rec.get('workload', 'recorded')} ncu capture by algorithmic "
+               f"bytes ({algorithmic_bytes} / {ref})")
+
+
 def kernel_source_sha1(path, name):
     """SHA-1 of the source text of the __global__ function `name` (from its
     template line to its closing brace): the traffic record stays valid while
@@ -409,11 +425,11 @@ def main():
     k_flops = 2.0 * levels[0]["nnzb"] * levels[0]["block"] ** 2
     achieved_bw = k_bytes / (k_ms * 1e-3) / 1e9
     achieved_fl = k_flops / (k_ms * 1e-3) / 1e12
-    tr = traffic_record()
+    traffic, traffic_kind = scaled_traffic(traffic_record(), k_bytes)
     roofline = {"bound": "alu", "achieved": round(achieved_fl, 3),
                 "peak": round(fp64_gflops / 1e3, 3), "unit": "TFLOP/s",
                 "frac": round(achieved_fl / (fp64_gflops / 1e3), 3),
-                "traffic": tr["bytes_per_launch"] if tr else None,
+                "traffic": traffic, "traffic_kind": traffic_kind,
                 "kernel": "sell_kernel<3,3,f64> y = A_0 x (CG SpMV operator)",
                 "flops_per_launch": int(k_flops), "bytes_per_launch": int(k_bytes),
                 "us_per_launch": round(k_ms * 1e3, 2),

@@ -1,6 +1,7 @@
 """Host-side logic of bench.py that needs no GPU: the max-over-ranks timing of
 a multi-replica run (two gloo ranks on the CPU), the algorithmic byte count
-per PCG iteration, and the kernel-source key of the recorded ncu traffic."""
+per PCG iteration, the kernel-source key of the recorded ncu traffic and its
+scaling to another workload."""
 import os
 import socket
 
@@ -83,6 +84,25 @@ def test_kernel_source_key_tracks_the_kernel(tmp_path):
     changed = tmp_path / "b.cu"
     changed.write_text(text[:j] + "if (row >= n_rows + 0) return;" + text[j + len("if (row >= n_rows) return;"):])
     assert bench.kernel_source_sha1(str(changed), "sell_kernel") != h
+
+
+def test_traffic_is_scaled_to_the_workload():
+    """The recorded capture applies unchanged only to the workload it was
+    taken on; another workload gets it scaled by the algorithmic bytes."""
+    rec = {"workload": "cube64", "bytes_per_launch": 296559360,
+           "algorithmic_bytes_per_launch": 300257852}
+    t, kind = bench.scaled_traffic(rec, 300257852)
+    assert t == 296559360 and "capture (cube64)" in kind
+    # a launch with twice the algorithmic bytes: twice the traffic
+    t, kind = bench.scaled_traffic(rec, 2 * 300257852)
+    assert t == 2 * 296559360 and "scaled" in kind
+    # the committed record names its workload, and its traffic is close to
+    # (not far above) the algorithmic bytes of that launch
+    committed = bench.traffic_record()
+    if committed is not None:
+        assert committed["workload"] == "cube64"
+        assert committed["algorithmic_bytes_per_launch"] > committed["bytes_per_launch"] * 0.9
+    assert bench.scaled_traffic(None, 1) == (None, None)
 
 
 def test_batch_stage_roofline_bytes():
