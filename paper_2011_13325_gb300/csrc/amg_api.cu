@@ -31,6 +31,7 @@ void free_bsr(DevBSR &m) {
   dfree(m.v16);
   dfree(m.sell_ptr);
   dfree(m.sell_col);
+  dfree(m.sell_perm);
   dfree(m.s64);
   dfree(m.s32);
   dfree(m.s16);
@@ -618,7 +619,8 @@ const char *amg_describe(amg_ctx *h) {
       if (!m.nnzb) continue;
       char k[96];
       if (m.sell_ptr && m.kern == KERN_SELL)
-        snprintf(k, sizeof k, "SELL-32 (thread per block row, %.0f%% of the slots filled)",
+        snprintf(k, sizeof k, "SELL-32 (thread per block row,%s %.0f%% of the slots filled)",
+                 m.sell_perm ? " rows sorted by length," : "",
                  100.0 * (double)m.nnzb / (32.0 * (double)m.sell_slots));
       else
         snprintf(k, sizeof k, "%s", kname[m.kern >= 0 && m.kern < 3 ? m.kern : 0]);

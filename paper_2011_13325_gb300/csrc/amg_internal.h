@@ -29,6 +29,11 @@ struct DevBSR {
   // slot j of lane t: column sell_col[j*32 + t], element q of its block at
   // s??[(j*br*bc + q)*32 + t] (every element of a slot is one coalesced
   // 32-wide row); padding slots have column 0 and zero values.
+  // Rectangular operators (P_l, R_l, whose row lengths vary) have sorted
+  // slices: inside each window of 256 rows the rows are ordered by length,
+  // longest first, and lane t of slice s holds row sell_perm[32s + t]
+  // (n_rows on a padding lane); sell_perm is null where lane t of slice s
+  // holds row 32s + t (square operators, whose CG kernels assume that).
   // kernel choice (set by the upload's tuner under AMG_LAYOUT_AUTO); the
   // SELL-32 copy is used when present unless the tuner picked a BSR kernel
   int kern = KERN_SELL;  // KERN_WARP_ROWS / KERN_ROW_LANES / KERN_BLOCK_LANES / KERN_SELL
@@ -36,6 +41,7 @@ struct DevBSR {
   int64_t sell_slots = 0;
   int *sell_ptr = nullptr;
   int *sell_col = nullptr;
+  int *sell_perm = nullptr;
   double *s64 = nullptr;
   float *s32 = nullptr;
   __nv_bfloat16 *s16 = nullptr;

@@ -102,6 +102,7 @@ static void build_spmm_items(Stage &S) {
     it.first_block = first;
     it.sell_ptr = o.A->sell_ptr;
     it.sell_col = o.A->sell_col;
+    it.sell_perm = o.A->sell_perm;
     it.svals = o.svals;
     it.n_slices = o.A->n_slices;
     first += S.lpr ? cdiv(o.A->n_rows, rpb) : cdiv(o.A->n_slices, S.wpb);

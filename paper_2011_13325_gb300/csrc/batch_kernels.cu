@@ -145,7 +145,8 @@ __global__ void __launch_bounds__(256) gspmm_kernel(const SpmmItem *__restrict__
 }
 
 // SELL-32 form: one thread per block row; slot j of a slice holds one block
-// per lane, element e of the 32 blocks contiguous (coalesced value loads)
+// per lane, element e of the 32 blocks contiguous (coalesced value loads);
+// a sorted copy (rectangular operators) names each lane's row in sell_perm
 template <int BR, int BC, int NR, typename V, typename T, int MODE, typename TO>
 __global__ void __launch_bounds__(128) gsell_kernel(const SpmmItem *__restrict__ items, int n_items,
                                                     const McgState *__restrict__ st) {
@@ -157,7 +158,7 @@ __global__ void __launch_bounds__(128) gsell_kernel(const SpmmItem *__restrict__
   const int slice = (blockIdx.x - I.first_block) * (blockDim.x >> 5) + (threadIdx.x >> 5);
   if (slice >= I.n_slices) return;  // whole warp
   const int t = threadIdx.x & 31;
-  const int row = slice * 32 + t;
+  const int row = I.sell_perm ? __ldg(I.sell_perm + slice * 32 + t) : slice * 32 + t;
   const int j0 = __ldg(I.sell_ptr + slice), j1 = __ldg(I.sell_ptr + slice + 1);
   const T *__restrict__ x = (const T *)I.x;
   const V *__restrict__ sv = (const V *)I.svals;

@@ -42,8 +42,9 @@ struct SpmmItem {
   const void *vals, *x, *b, *minv;
   void *y;
   int n_rows, sys, first_block;
-  // SELL-32 copy of the operator (thread per block row), if present
-  const int *sell_ptr, *sell_col;
+  // SELL-32 copy of the operator (thread per block row), if present;
+  // sell_perm: row of each slice lane of a sorted copy (null: row 32s + t)
+  const int *sell_ptr, *sell_col, *sell_perm;
   const void *svals;
   int n_slices;
 };

@@ -481,6 +481,52 @@ __global__ void __launch_bounds__(256) sell_kernel(int n_rows, int n_slices,
   }
 }
 
+// The same for a sorted SELL-32 copy (rectangular operators: no smoothing
+// mode): lane t of a slice computes row perm[32 * slice + t] (n_rows on a
+// padding lane), so rows of similar length share a slice.
+template <int BR, int BC, typename V, typename T, int MODE>
+__global__ void __launch_bounds__(256) sell_perm_kernel(int n_rows, int n_slices,
+                                                        const int *__restrict__ sell_ptr,
+                                                        const int *__restrict__ sell_col,
+                                                        const int *__restrict__ perm,
+                                                        const V *__restrict__ vals,
+                                                        const T *__restrict__ x,
+                                                        const T *__restrict__ b,
+                                                        T *__restrict__ y) {
+  static_assert(MODE != SPMV_SMOOTH, "sorted slices serve rectangular operators only");
+  pdl_enter();
+  using A = typename AccT<T>::type;
+  constexpr int E = BR * BC;
+  const int slice = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  if (slice >= n_slices) return;
+  const int t = threadIdx.x & 31;
+  const int row = __ldg(perm + slice * 32 + t);
+  const int j0 = sell_ptr[slice], j1 = sell_ptr[slice + 1];
+  A acc[BR];
+#pragma unroll
+  for (int r = 0; r < BR; ++r) acc[r] = 0;
+#pragma unroll 2
+  for (int j = j0; j < j1; ++j) {
+    const int c = __ldg(sell_col + (size_t)j * 32 + t);
+    const V *v = vals + (size_t)j * E * 32 + t;
+    A xv[BC];
+#pragma unroll
+    for (int q = 0; q < BC; ++q) xv[q] = (A)ld(x + (size_t)c * BC + q);
+#pragma unroll
+    for (int r = 0; r < BR; ++r)
+#pragma unroll
+      for (int q = 0; q < BC; ++q) acc[r] += (A)lds(v + (r * BC + q) * 32) * xv[q];
+  }
+  if (row >= n_rows) return;
+  const size_t o = (size_t)row * BR;
+#pragma unroll
+  for (int r = 0; r < BR; ++r) {
+    if (MODE == SPMV_SET) y[o + r] = (T)acc[r];
+    if (MODE == SPMV_RESID) y[o + r] = (T)((A)b[o + r] - acc[r]);
+    if (MODE == SPMV_ADD) y[o + r] = (T)((A)y[o + r] + acc[r]);
+  }
+}
+
 template <int BR, int BC, typename V, typename T>
 static cudaError_t sell_mode(const Ctx *c, const DevBSR &A, const V *vals, int mode, const void *x,
                              const void *b, const void *minv, void *y) {
@@ -490,6 +536,19 @@ static cudaError_t sell_mode(const Ctx *c, const DevBSR &A, const V *vals, int m
   const T *bb = (const T *)b;
   const T *mm = (const T *)minv;
   T *yy = (T *)y;
+  if (A.sell_perm) {
+#define AMG_SELL_PERM_LAUNCH(M_)                                                                 \
+  AMG_KLAUNCH(c, sell_perm_kernel<BR, BC, V, T, M_>, g, 64, A.n_rows, A.n_slices, A.sell_ptr, \
+              A.sell_col, A.sell_perm, vals, xx, bb, yy)
+    switch (mode) {
+      case SPMV_SET: AMG_SELL_PERM_LAUNCH(SPMV_SET); break;
+      case SPMV_RESID: AMG_SELL_PERM_LAUNCH(SPMV_RESID); break;
+      case SPMV_ADD: AMG_SELL_PERM_LAUNCH(SPMV_ADD); break;
+      default: return cudaErrorInvalidValue;
+    }
+#undef AMG_SELL_PERM_LAUNCH
+    return cudaGetLastError();
+  }
 #define AMG_SELL_LAUNCH(M_)                                                                    \
   AMG_KLAUNCH(c, sell_kernel<BR, BC, V, T, M_>, g, 64, A.n_rows, A.n_slices, A.sell_ptr,   \
                                                           A.sell_col, vals, xx, bb, mm, yy)
@@ -727,8 +786,36 @@ __global__ void to_bf16_kernel(size_t n, const double *__restrict__ s, __nv_bflo
 // SELL-32 construction from the BSR arrays (device)
 // ---------------------------------------------------------------------------
 
+// Row order of a sorted SELL-32 copy: one 256-thread block per window of 256
+// rows ranks the window's rows by length, longest first (ties by row index),
+// so that the window's 8 slices each hold rows of similar length and little
+// padding.  perm[w*256 + rank] = row; lanes past the window's last row get
+// n_rows (padding).  Every slot below n_slots is written exactly once.
+__global__ void __launch_bounds__(256) sell_sort_kernel(int n_rows, int n_slots,
+                                                        const int *__restrict__ rowptr,
+                                                        int *__restrict__ perm) {
+  __shared__ int len[256];
+  const int i = threadIdx.x;
+  const int row = blockIdx.x * 256 + i;
+  const int l = row < n_rows ? rowptr[row + 1] - rowptr[row] : -1;
+  len[i] = l;
+  __syncthreads();
+  int rank = 0;
+  for (int j = 0; j < 256; ++j) {
+    const int lj = len[j];
+    rank += (lj > l) || (lj == l && j < i);
+  }
+  const int dst = blockIdx.x * 256 + rank;
+  if (dst < n_slots) perm[dst] = l >= 0 ? row : n_rows;
+}
+
+// the row held by lane t of a slice (identity order without perm)
+__device__ __forceinline__ int sell_lane_row(const int *__restrict__ perm, int slice, int t) {
+  return perm ? perm[slice * 32 + t] : slice * 32 + t;
+}
+
 __global__ void sell_width_kernel(int n_rows, int n_slices, const int *__restrict__ rowptr,
-                                  int *__restrict__ w) {
+                                  const int *__restrict__ perm, int *__restrict__ w) {
   const int s = blockIdx.x * blockDim.x + threadIdx.x;
   if (s > n_slices) return;
   if (s == n_slices) {
@@ -736,19 +823,22 @@ __global__ void sell_width_kernel(int n_rows, int n_slices, const int *__restric
     return;
   }
   int m = 0;
-  for (int r = s * 32; r < min(n_rows, s * 32 + 32); ++r) m = max(m, rowptr[r + 1] - rowptr[r]);
+  for (int t = 0; t < 32; ++t) {
+    const int r = sell_lane_row(perm, s, t);
+    if (r < n_rows) m = max(m, rowptr[r + 1] - rowptr[r]);
+  }
   w[s] = m;
 }
 
 template <int E>
 __global__ void sell_fill_kernel(int n_rows, int n_slices, const int *__restrict__ rowptr,
                                  const int *__restrict__ colidx, const double *__restrict__ vals,
-                                 const int *__restrict__ sell_ptr, int *__restrict__ sell_col,
-                                 double *__restrict__ s64) {
+                                 const int *__restrict__ sell_ptr, const int *__restrict__ perm,
+                                 int *__restrict__ sell_col, double *__restrict__ s64) {
   const int g = blockIdx.x * blockDim.x + threadIdx.x;
   const int slice = g >> 5, t = g & 31;
   if (slice >= n_slices) return;
-  const int row = slice * 32 + t;
+  const int row = sell_lane_row(perm, slice, t);
   const int rs = row < n_rows ? rowptr[row] : 0;
   const int len = row < n_rows ? rowptr[row + 1] - rs : 0;
   for (int j = sell_ptr[slice]; j < sell_ptr[slice + 1]; ++j) {
@@ -775,16 +865,26 @@ cudaError_t build_sell(Ctx *c, DevBSR &m) {
   const int E = m.br * m.bc;
   dfree(m.sell_ptr);
   dfree(m.sell_col);
+  dfree(m.sell_perm);
   dfree(m.s64);
   m.sell_ptr = nullptr;
   m.sell_col = nullptr;
+  m.sell_perm = nullptr;
   m.s64 = nullptr;
   m.n_slices = (m.n_rows + 31) / 32;
+  // rectangular operators (P_l, R_l) get length-sorted slices
+  if ((m.br != m.bc || m.n_rows != m.n_cols) && m.n_slices > 0) {
+    const int n_slots = m.n_slices * 32;
+    AMG_CUDA_TRY(dalloc((void **)&m.sell_perm, (size_t)n_slots * sizeof(int)));
+    sell_sort_kernel<<<(n_slots + 255) / 256, 256, 0, c->stream>>>(m.n_rows, n_slots, m.rowptr,
+                                                                   m.sell_perm);
+    AMG_CUDA_TRY(cudaGetLastError());
+  }
   AMG_CUDA_TRY(dalloc((void **)&m.sell_ptr, (size_t)(m.n_slices + 1) * sizeof(int)));
   int *total = nullptr;
   AMG_CUDA_TRY(dalloc((void **)&total, sizeof(int)));
   sell_width_kernel<<<(m.n_slices + 256) / 256, 256, 0, c->stream>>>(m.n_rows, m.n_slices, m.rowptr,
-                                                                     m.sell_ptr);
+                                                                     m.sell_perm, m.sell_ptr);
   AMG_CUDA_TRY(cudaGetLastError());
   AMG_CUDA_TRY(scan_exclusive(c, m.n_slices + 1, m.sell_ptr, total));
   int slots = 0;
@@ -799,7 +899,7 @@ cudaError_t build_sell(Ctx *c, DevBSR &m) {
   if (E == E_)                                                                          \
     sell_fill_kernel<E_><<<g, 256, 0, c->stream>>>(m.n_rows, m.n_slices, m.rowptr,     \
                                                    m.colidx, m.v64, m.sell_ptr,        \
-                                                   m.sell_col, m.s64);
+                                                   m.sell_perm, m.sell_col, m.s64);
   AMG_FILL(4) AMG_FILL(9) AMG_FILL(36) AMG_FILL(6) AMG_FILL(18)
 #undef AMG_FILL
   return cudaGetLastError();

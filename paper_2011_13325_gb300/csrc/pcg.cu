@@ -394,7 +394,7 @@ static SellView sell_view(const DevBSR &A) {
 template <int BR>
 static cudaError_t launch_init(Ctx *c, cudaGraphConditionalHandle h, int in_graph) {
   const Level &L0 = c->levels[0];
-  if (L0.A.sell_ptr)
+  if (L0.A.sell_ptr && !L0.A.sell_perm)
     AMG_KLAUNCH(c, pcg_init_sell_kernel<BR>, red_grid(c), kRedThreads, 
         sell_view(L0.A), c->f, c->x, c->r, c->st, c->partials, c->counter, h, in_graph);
   else
@@ -417,7 +417,7 @@ static cudaError_t launch_body(Ctx *c, cudaGraphConditionalHandle h, int in_grap
                                                        c->counter);
   AMG_KLAUNCH(c, pcg_update_p_kernel, (unsigned)((n + 255) / 256), 256, n, c->z, c->p, c->zold,
                                                                           c->st);
-  if (L0.A.sell_ptr) {
+  if (L0.A.sell_ptr && !L0.A.sell_perm) {
     n_pq = (L0.A.n_slices + 1) / 2;
     AMG_KLAUNCH(c, pcg_spmv_dot_sell_kernel<BR>, n_pq, kSellThreads, sell_view(L0.A), c->p,
                                                                        c->q, pq_part);

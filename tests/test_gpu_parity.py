@@ -299,3 +299,31 @@ def test_launch_overlap_gives_identical_results(case):
     ctx.set_launch_overlap(True)
     for its, rr, u in outs[1:]:
         assert its == outs[0][0] and rr == outs[0][1] and torch.equal(u, outs[0][2])
+
+
+def test_sell_layout_sorts_rectangular_operators():
+    """Under the SELL-32 layout the transfer operators P_l, R_l (rows of
+    varying length) get length-sorted slices and the square A_l keep rows in
+    order; the sorted copies fill more of their slots than rows in order
+    would, and a V-cycle through them matches the oracle."""
+    amg = _amg()
+    p, H = _hier("box_jump")
+    ctx = amg.Context(0)
+    ctx.set_layout_policy(amg.AMG_LAYOUT_SELL_SHORT_ROWS)
+    ctx.upload_hierarchy(H.A[0], H.P, amg.AMG_PREC_FP64)
+    lines = [ln for ln in ctx.describe().splitlines() if "SELL-32" in ln]
+    trans = [ln for ln in lines if " P:" in ln or " R:" in ln]
+    assert trans and all("rows sorted by length" in ln for ln in trans)
+    assert all("rows sorted" not in ln for ln in lines if " A:" in ln)
+    # fill of the sorted P_0 against the rows-in-order slice widths
+    P = H.P[0]
+    lens = np.diff(P.rowptr)
+    w_in_order = sum(int(lens[s:s + 32].max()) for s in range(0, len(lens), 32))
+    filled = float(next(ln for ln in trans if ln.startswith("level 0 P:"))
+                   .split("%")[0].rsplit(" ", 1)[1])
+    assert filled >= 100.0 * lens.sum() / (32 * w_in_order) - 0.5
+    r = p.b[0]
+    z = dev(np.zeros_like(r))
+    ctx.vcycle(dev(r), z)
+    assert rel(host(z), solve.vcycle(H, r)) <= 1e-10
+    ctx.close()
