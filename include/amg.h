@@ -254,6 +254,10 @@ int amg_pcg_launches(const amg_ctx *ctx, int32_t *per_iteration, int32_t *fixed)
  * AMG_TUNE_CACHE naming a file, choices recorded there are reused without
  * timing and new ones appended (a profiled process then applies the kernels
  * an earlier plain process chose).
+ * The SELL-32 copies of the transfer operators P_l, R_l (rows of varying
+ * length) hold, inside each window of 256 rows, the rows sorted by length,
+ * so that each slice of 32 rows carries little padding; square operators
+ * keep their rows in order.
  * The result of every operator is the same up to the order of the sums. */
 enum {
   AMG_LAYOUT_AUTO = 0,
