@@ -157,13 +157,39 @@ def exported_symbols():
     return list(_SIGS.keys())
 
 
-def _ptr(a):
-    """Device pointer of a torch tensor or host pointer of a numpy array."""
+def _ptr(a, where="argument", host=False, dtype="float64", n=None, device=None):
+    """Pointer of a flat array argument of a libamg call, after the checks
+    the C side cannot make: a device argument is a CUDA tensor (on `device`
+    when given), a host argument a numpy array or CPU tensor; the element
+    type is `dtype`, the storage C-contiguous, and at least `n` elements
+    long where the caller knows the length.  None passes through as NULL.
+    Raises TypeError / ValueError rather than hand the library a pointer it
+    would read or write past."""
     if a is None:
         return None
     if isinstance(a, np.ndarray):
-        return a.ctypes.data
-    return a.data_ptr()
+        if not host:
+            raise TypeError(f"{where}: needs a CUDA tensor, got a numpy array")
+        if a.dtype != np.dtype(dtype):
+            raise TypeError(f"{where}: needs {dtype} elements, got {a.dtype}")
+        if not a.flags.c_contiguous:
+            raise ValueError(f"{where}: the array must be C-contiguous")
+        size, ptr = a.size, a.ctypes.data
+    else:
+        if not hasattr(a, "data_ptr"):
+            raise TypeError(f"{where}: needs a torch tensor or numpy array, got {type(a).__name__}")
+        if bool(a.is_cuda) == bool(host):
+            raise TypeError(f"{where}: needs a {'CPU' if host else 'CUDA'} tensor, got one on {a.device}")
+        if not host and device is not None and a.device.index != int(device):
+            raise ValueError(f"{where}: tensor on {a.device}, the context is on cuda:{int(device)}")
+        if str(a.dtype) != f"torch.{dtype}":
+            raise TypeError(f"{where}: needs {dtype} elements, got {a.dtype}")
+        if not a.is_contiguous():
+            raise ValueError(f"{where}: the tensor must be contiguous")
+        size, ptr = a.numel(), a.data_ptr()
+    if n is not None and size < n:
+        raise ValueError(f"{where}: needs at least {n} elements, got {size}")
+    return ptr
 
 
 def bsr_struct(n_rows, n_cols, rowptr, colidx, vals, keep):
@@ -182,6 +208,7 @@ class Context:
 
     def __init__(self, device: int = 0, stream=None):
         self.h = _P()
+        self.device = int(device)
         s = lib().amg_create(C.byref(self.h), int(device), stream)
         if s != AMG_OK:
             raise AmgError(s, "amg_create failed")
@@ -201,6 +228,20 @@ class Context:
         if s != AMG_OK:
             raise AmgError(s, lib().amg_last_error(self.h).decode())
         return s
+
+    def _dofs(self, level):
+        """Scalar rows of a level, or None without a hierarchy or for a level
+        it does not have (the library then reports that error itself)."""
+        n, k = C.c_int32(), C.c_int32()
+        if lib().amg_level_info(self.h, int(level), C.byref(n), C.byref(k), None, None, None) != AMG_OK:
+            return None
+        return n.value * k.value
+
+    def _vec(self, a, where, level=0, count=1):
+        """Device pointer of an FP64 vector of `count` copies of a level's
+        unknowns (length checked when the hierarchy is there)."""
+        n = self._dofs(level)
+        return _ptr(a, where, n=None if n is None else n * int(count), device=self.device)
 
     # -- hierarchy ---------------------------------------------------------
     def upload_hierarchy(self, A0, P_list, precision=AMG_PREC_FP64, smoother=AMG_SMOOTHER_L1_JACOBI):
@@ -288,35 +329,45 @@ class Context:
 
     # -- single steps ------------------------------------------------------
     def spmv(self, level, x, y):
-        return self._check(lib().amg_spmv(self.h, int(level), _ptr(x), _ptr(y)))
+        return self._check(lib().amg_spmv(self.h, int(level), self._vec(x, "x", level),
+                                          self._vec(y, "y", level)))
 
     def residual(self, level, b, x, r):
-        return self._check(lib().amg_residual(self.h, int(level), _ptr(b), _ptr(x), _ptr(r)))
+        return self._check(lib().amg_residual(self.h, int(level), self._vec(b, "b", level),
+                                              self._vec(x, "x", level), self._vec(r, "r", level)))
 
     def smooth(self, level, b, x_in, x_out):
-        return self._check(lib().amg_smooth(self.h, int(level), _ptr(b), _ptr(x_in), _ptr(x_out)))
+        return self._check(lib().amg_smooth(self.h, int(level), self._vec(b, "b", level),
+                                            self._vec(x_in, "x_in", level),
+                                            self._vec(x_out, "x_out", level)))
 
     def restrict(self, level, r, bc):
-        return self._check(lib().amg_restrict(self.h, int(level), _ptr(r), _ptr(bc)))
+        return self._check(lib().amg_restrict(self.h, int(level), self._vec(r, "r", level),
+                                              self._vec(bc, "bc", level + 1)))
 
     def prolong_add(self, level, ec, x):
-        return self._check(lib().amg_prolong_add(self.h, int(level), _ptr(ec), _ptr(x)))
+        return self._check(lib().amg_prolong_add(self.h, int(level), self._vec(ec, "ec", level + 1),
+                                                 self._vec(x, "x", level)))
 
     def coarse_solve(self, b, x):
-        return self._check(lib().amg_coarse_solve(self.h, _ptr(b), _ptr(x)))
+        last = self.n_levels - 1
+        return self._check(lib().amg_coarse_solve(self.h, self._vec(b, "b", last),
+                                                  self._vec(x, "x", last)))
 
     def vcycle(self, r, z, nrhs=1):
-        return self._check(lib().amg_vcycle(self.h, _ptr(r), _ptr(z), int(nrhs)))
+        return self._check(lib().amg_vcycle(self.h, self._vec(r, "r", 0, nrhs),
+                                            self._vec(z, "z", 0, nrhs), int(nrhs)))
 
     def vcycle_static(self, r, z):
         """amg_vcycle_static: one V-cycle without allocating (work vectors in
         the library's fixed device array)."""
-        return self._check(lib().amg_vcycle_static(self.h, _ptr(r), _ptr(z)))
+        return self._check(lib().amg_vcycle_static(self.h, self._vec(r, "r"), self._vec(z, "z")))
 
     def pcg_solve(self, f, u, nrhs=1, rtol=1e-8, maxit=500, check=True):
         it = (C.c_int * nrhs)()
         rr = (C.c_double * nrhs)()
-        s = lib().amg_pcg_solve(self.h, _ptr(f), _ptr(u), int(nrhs), float(rtol), int(maxit), it, rr)
+        s = lib().amg_pcg_solve(self.h, self._vec(f, "f", 0, nrhs), self._vec(u, "u", 0, nrhs),
+                                int(nrhs), float(rtol), int(maxit), it, rr)
         if check:
             self._check(s)
         return s, list(it), list(rr)
@@ -324,8 +375,10 @@ class Context:
     def pcg_solve_host(self, f, u, nrhs=1, rtol=1e-8, maxit=500, check=True):
         it = (C.c_int * nrhs)()
         rr = (C.c_double * nrhs)()
-        s = lib().amg_pcg_solve_host(self.h, _ptr(f), _ptr(u), int(nrhs), float(rtol), int(maxit),
-                                     it, rr)
+        n = self._dofs(0)
+        n = None if n is None else n * int(nrhs)
+        s = lib().amg_pcg_solve_host(self.h, _ptr(f, "f", host=True, n=n), _ptr(u, "u", host=True, n=n),
+                                     int(nrhs), float(rtol), int(maxit), it, rr)
         if check:
             self._check(s)
         return s, list(it), list(rr)
@@ -344,15 +397,35 @@ class Context:
         """Features (n_0 x 13 FP32 device tensor X) of the level-0 vertices at
         host positions coords (n_0 x 3)."""
         c = np.ascontiguousarray(coords, dtype=np.float64)
-        return self._check(lib().amg_learned_features(self.h, c.ctypes.data, _ptr(X), _ptr(tr)))
+        n = self._n0()
+        if n is not None and c.size < 3 * n:
+            raise ValueError(f"coords: needs {n} x 3 positions, got {c.size} values")
+        return self._check(lib().amg_learned_features(
+            self.h, c.ctypes.data,
+            _ptr(X, "X", dtype="float32", n=None if n is None else 13 * n, device=self.device),
+            _ptr(tr, "tr", n=n, device=self.device)))
 
     def learned_targets(self, T32=None, T64=None):
         """Patch-inverse targets (n_0 x 9) into device tensors."""
-        return self._check(lib().amg_learned_targets(self.h, _ptr(T32), _ptr(T64)))
+        n = self._n0()
+        m = None if n is None else 9 * n
+        return self._check(lib().amg_learned_targets(
+            self.h, _ptr(T32, "T32", dtype="float32", n=m, device=self.device),
+            _ptr(T64, "T64", n=m, device=self.device)))
+
+    def _n0(self):
+        """Level-0 vertices (block rows), or None without a hierarchy."""
+        n = C.c_int32()
+        if lib().amg_level_info(self.h, 0, C.byref(n), None, None, None, None) != AMG_OK:
+            return None
+        return n.value
 
     def set_learned_smoother(self, mlp, coords):
         """Install the damped learned blocks at level 0; returns (lambda, omega)."""
         c = np.ascontiguousarray(coords, dtype=np.float64)
+        n = self._n0()
+        if n is not None and c.size < 3 * n:
+            raise ValueError(f"coords: needs {n} x 3 positions, got {c.size} values")
         lam, w = C.c_double(), C.c_double()
         self._check(lib().amg_set_learned_smoother(self.h, mlp.h, c.ctypes.data, C.byref(lam),
                                                    C.byref(w)))
@@ -443,18 +516,22 @@ class Batch:
 
     def pcg_solve(self, f, u, rtol=1e-8, maxit=500, check=True):
         """Stacked device vectors (torch tensors)."""
-        return self._solve(lib().amg_batch_pcg_solve, f, u, rtol, maxit, check)
+        return self._solve(lib().amg_batch_pcg_solve, f, u, rtol, maxit, check, host=False)
 
     def pcg_solve_host(self, f, u, rtol=1e-8, maxit=500, check=True):
         """Stacked host vectors (numpy arrays or CPU tensors, pinned for speed)."""
-        return self._solve(lib().amg_batch_pcg_solve_host, f, u, rtol, maxit, check)
+        return self._solve(lib().amg_batch_pcg_solve_host, f, u, rtol, maxit, check, host=True)
 
-    def _solve(self, fn, f, u, rtol, maxit, check):
+    def _solve(self, fn, f, u, rtol, maxit, check, host):
         m = len(self.contexts) * self.nrhs
         it = (C.c_int * m)()
         rr = (C.c_double * m)()
         ms = C.c_float()
-        s = fn(self.h, _ptr(f), _ptr(u), float(rtol), int(maxit), it, rr, C.byref(ms))
+        total = self.layout(0)[2] if self.contexts else None
+        dev = None if host or not self.contexts else self.contexts[0].device
+        s = fn(self.h, _ptr(f, "f", host=host, n=total, device=dev),
+               _ptr(u, "u", host=host, n=total, device=dev), float(rtol), int(maxit), it, rr,
+               C.byref(ms))
         if check and s != AMG_OK:
             raise AmgError(s, lib().amg_batch_last_error(self.h).decode())
         return s, list(it), list(rr), ms.value
@@ -504,16 +581,20 @@ class Mlp:
         n = int(X.shape[0]) if n is None else int(n)
         loss = C.c_double()
         g = np.zeros(AMG_MLP_PARAMS, dtype=np.float32)
-        self._check(lib().amg_mlp_loss_grad(self.h, _ptr(X), _ptr(T), n, C.byref(loss), g.ctypes.data))
+        self._check(lib().amg_mlp_loss_grad(self.h, _ptr(X, "X", dtype="float32", n=13 * n),
+                                            _ptr(T, "T", dtype="float32", n=9 * n), n,
+                                            C.byref(loss), g.ctypes.data))
         return loss.value, g
 
     def train(self, X, T, epochs=10, batch=4096, lr=1e-3, seed=0, n=None):
         n = int(X.shape[0]) if n is None else int(n)
         hist = np.zeros(max(epochs, 1))
-        self._check(lib().amg_mlp_train(self.h, _ptr(X), _ptr(T), n, int(epochs), int(batch),
+        self._check(lib().amg_mlp_train(self.h, _ptr(X, "X", dtype="float32", n=13 * n),
+                                        _ptr(T, "T", dtype="float32", n=9 * n), n, int(epochs), int(batch),
                                         float(lr), C.c_uint64(int(seed)), hist.ctypes.data))
         return hist[:epochs]
 
     def infer(self, X, out, n=None):
         n = int(X.shape[0]) if n is None else int(n)
-        return self._check(lib().amg_mlp_infer(self.h, _ptr(X), n, _ptr(out)))
+        return self._check(lib().amg_mlp_infer(self.h, _ptr(X, "X", dtype="float32", n=13 * n), n,
+                                               _ptr(out, "out", dtype="float32", n=6 * n)))
