@@ -167,3 +167,33 @@ def test_learned_smoother_coords(ctx):
     assert fake.calls[-1][0] == "amg_set_learned_smoother"
     with pytest.raises(ValueError):
         c.set_learned_smoother(net, np.zeros((9, 3)))
+
+
+def test_batch_vectors(monkeypatch):
+    """Stacked batch vectors: device entry wants CUDA tensors on the
+    contexts' GPU, host entry numpy / CPU tensors, both the full stacked
+    length that amg_batch_layout reports."""
+    fake = FakeLib()
+
+    def layout(h, s, off, n, total):
+        for p, v in ((off, 0), (n, 30), (total, 180)):
+            if p is not None:
+                p._obj.value = v
+        return amg.AMG_OK
+    fake.amg_batch_layout = layout
+    monkeypatch.setattr(amg, "lib", lambda: fake)
+    b = object.__new__(amg.Batch)
+    b.h = C.c_void_p(1)
+    b.nrhs = 6
+    b.contexts = [type("Cx", (), {"device": 0})()]
+    b.pcg_solve(FakeCuda(180), FakeCuda(180))
+    assert fake.calls[-1][0] == "amg_batch_pcg_solve"
+    b.pcg_solve_host(np.zeros(180), torch.zeros(180, dtype=torch.float64))
+    assert fake.calls[-1][0] == "amg_batch_pcg_solve_host"
+    with pytest.raises(ValueError):
+        b.pcg_solve(FakeCuda(179), FakeCuda(180))
+    with pytest.raises(TypeError):
+        b.pcg_solve_host(FakeCuda(180), np.zeros(180))
+    with pytest.raises(TypeError):
+        b.pcg_solve(np.zeros(180), FakeCuda(180))
+    b.h = C.c_void_p()
