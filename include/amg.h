@@ -10,7 +10,7 @@
  * restriction P^T r and the prolongation P e (Sec. 3, Algorithm tg) with the
  * auxiliary smoothed prolongation of Sec. 6 (Def. aux_sp), Galerkin coarse
  * matrices A_{l+1} = P_l^T A_l P_l (Sec. 6), and the regularised coarsest
- * solve of Sec. 3.1.
+ * solve of Sec. 3 after Lemma eet_is_diag.
  *
  * Conventions that hold for every entry point:
  *  - Every call returns an int status (AMG_OK or a negative AMG_ERR_*); the
@@ -115,9 +115,10 @@ const char *amg_last_error(const amg_ctx *ctx);
  *   - builds R_l = P_l^T explicitly (Sec. 3, restriction),
  *   - computes A_{l+1} = P_l^T A_l P_l on the device (Sec. 6, amg_galerkin),
  *   - computes the block-l1 smoother blocks M_v^+ (Sec. 7 and the pseudo
- *     smoother of Sec. 3.1) in FP64 on the device,
+ *     smoother of Sec. 3 after Lemma eet_is_diag) in FP64 on the device,
  *   - factorises the regularised coarsest matrix A_L + (I - E_L E_L^T)
- *     (Sec. 3.1) in FP64 on the device and stores its inverse,
+ *     (Sec. 3 after Lemma eet_is_diag) in FP64 on the device and stores
+ *     its inverse,
  *   - for AMG_PREC_FP32_VCYCLE / AMG_PREC_BF16_STORAGE, keeps FP32 / BF16
  *     copies of the level operators.
  * Replaces any previous hierarchy of ctx. */
@@ -146,8 +147,9 @@ int amg_download_matrix(amg_ctx *ctx, int level, int32_t *rowptr, int32_t *colid
  * n_rows * k * k doubles, row-major per block) to host memory `minv`. */
 int amg_download_smoother(amg_ctx *ctx, int level, double *minv);
 
-/* Copy the coarsest-level inverse (A_L + I - E_L E_L^T)^{-1} (Sec. 3.1;
- * n x n doubles, n = n_rows * k of the coarsest level) to host memory. */
+/* Copy the coarsest-level inverse (A_L + I - E_L E_L^T)^{-1} (Sec. 3 after
+ * Lemma eet_is_diag; n x n doubles, n = n_rows * k of the coarsest level)
+ * to host memory. */
 int amg_download_coarse_inverse(amg_ctx *ctx, double *cinv);
 
 /* --- single steps of the V-cycle, FP64, device vectors of level `level` --- */
@@ -164,7 +166,7 @@ int amg_smooth(amg_ctx *ctx, int level, const double *b_dev, const double *x_in_
 int amg_restrict(amg_ctx *ctx, int level, const double *r_dev, double *bc_dev);
 /* x_l += P_l e_{l+1} (prolongation and correction, Algorithm tg). */
 int amg_prolong_add(amg_ctx *ctx, int level, const double *ec_dev, double *x_dev);
-/* x = (A_L + I - E_L E_L^T)^{-1} b on the coarsest level (Sec. 3.1). */
+/* x = (A_L + I - E_L E_L^T)^{-1} b on the coarsest level (Sec. 3 after Lemma eet_is_diag). */
 int amg_coarse_solve(amg_ctx *ctx, const double *b_dev, double *x_dev);
 
 /* z = B^{-1} r: one V-cycle (Algorithm tg applied recursively, one pre- and

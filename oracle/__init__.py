@@ -16,7 +16,7 @@ Modules, each following the paper's section noted in its header:
 * ``prolongation`` Sec. 3 Def. pwp / pwp_el, Sec. 6 Def. aux_sp.
 * ``solve``       Sec. 3 Algorithm tg (two-grid / V-cycle), the block-l1
                   smoother of Sec. 7, the coarsest-level regularisation of
-                  Sec. 3.1, Galerkin products, PCG.
+                  Sec. 3 after Lemma eet_is_diag, Galerkin products, PCG.
 * ``hierarchy``   multi-level setup driver.
 * ``learned``     FP64 reference of the per-vertex learned smoother (MLP
                   forward/backward, patch-inverse targets).

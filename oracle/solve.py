@@ -10,10 +10,10 @@ TEST INFRASTRUCTURE ONLY (see ``oracle/__init__``).
 * Smoother: block version of the l1 smoother (Sec. 7): blocks are the dofs
   of one vertex, M_v = A_vv + diag(sum of |a_rc| over the columns c outside
   the block), applied as block Jacobi; singular M_v are pseudo-inverted
-  (Sec. 3.1, "pseudo smoother").
+  (Sec. 3 after Lemma eet_is_diag, "pseudo smoother").
 * Coarsest level: A_L + (I - E_L E_L^T) with E_L spanning the orthogonal
   complement of the kernels of the diagonal blocks (Lemma eet_is_diag and
-  the regularisation identity of Sec. 3.1), solved by Cholesky.
+  the regularisation identity of Sec. 3 after Lemma eet_is_diag), solved by Cholesky.
 * PCG with one V-cycle as preconditioner (Sec. 7).
 """
 from __future__ import annotations
@@ -152,7 +152,7 @@ def diag_kernels(A: Mat):
 
 
 def coarsest_matrix(A: Mat):
-    """Dense A_L + (I - E_L E_L^T) (Sec. 3.1)."""
+    """Dense A_L + (I - E_L E_L^T) (Sec. 3 after Lemma eet_is_diag)."""
     k = A.br
     Ad = A.scipy().toarray()
     for i, K in enumerate(diag_kernels(A)):

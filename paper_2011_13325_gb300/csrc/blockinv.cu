@@ -1,10 +1,10 @@
 // Setup kernels of the smoother and the coarsest level (FP64):
 //  - block-l1 smoother blocks M_v = A_vv + diag(sum_{c outside v} |a_rc|)
 //    (Sec. 7, block version of the l1 smoother) and their pseudo-inverse
-//    (Sec. 3.1, pseudo smoother: singular diagonal blocks are pseudo-inverted);
+//    (Sec. 3 after Lemma eet_is_diag, pseudo smoother: singular diagonal blocks are pseudo-inverted);
 //  - the regularised coarsest matrix A_L + (I - E_L E_L^T), E_L spanning the
 //    complement of the kernels of the diagonal blocks (Lemma eet_is_diag,
-//    Sec. 3.1), and its explicit inverse by Gauss-Jordan elimination.
+//    Sec. 3 after Lemma eet_is_diag), and its explicit inverse by Gauss-Jordan elimination.
 // Small symmetric eigenproblems use the cyclic Jacobi method (Golub & Van
 // Loan, "Matrix Computations", Sec. 8.5), written from the mathematics.
 #include <math.h>

@@ -1,5 +1,5 @@
 """Pins of the oracle's solve phase: Galerkin product, explicit transpose,
-block-l1 smoother, coarsest regularisation (Sec. 3.1), two-grid convergence
+block-l1 smoother, coarsest regularisation (Sec. 3 after Lemma eet_is_diag), two-grid convergence
 (Sec. 3, Algorithm tg), V-cycle symmetry and PCG on manufactured solutions."""
 import numpy as np
 import pytest
@@ -85,7 +85,7 @@ def test_block_l1_smoother_dominates_A(which, request):
 
 
 def test_coarsest_regularisation_identity(h3d):
-    """Sec. 3.1: (E A~ E^T + (I - E E^T))^{-1} = E A~^{-1} E^T + (I - E E^T)
+    """Sec. 3 after Lemma eet_is_diag: (E A~ E^T + (I - E E^T))^{-1} = E A~^{-1} E^T + (I - E E^T)
     with A~ = E^T A_L E and E spanning the complement of the block kernels."""
     _, H = h3d
     A = H.A[-1]
