@@ -397,71 +397,108 @@ static std::vector<double> aux_diagonal(const Topo &T) {
   return D;
 }
 
-// Thm. cemats for an agglomeration map (agg = -1 for D)
+// Thm. cemats for an agglomeration map (agg = -1 for D).  Every coarse
+// matrix is the sum of its fine contributions taken in a fixed order (a
+// coarse vertex: its fine vertex matrices by ascending vertex, then its
+// Dirichlet-coupled fine edges by ascending edge; a coarse edge: its fine
+// edges by ascending edge), so the result does not depend on the threads.
 static Topo coarse_topology(const Topo &T, const std::vector<int> &agg, int nc,
                             const std::vector<double> &xc, bool use_dir) {
   const int k = T.k, d = T.d;
+  const size_t kk = (size_t)k * k;
   Topo C;
   C.n = nc;
   C.d = d;
   C.k = k;
   C.pos = xc;
   C.dir.assign(nc, 0);
-  C.M.assign((size_t)nc * k * k, 0.0);
-  double t[3], X[36], Y[36];
-  for (int i = 0; i < T.n; ++i) {
-    const int I = agg[i];
-    if (I < 0) continue;
-    for (int a = 0; a < d; ++a) t[a] = T.pos[(size_t)i * d + a] - xc[(size_t)I * d + a];
-    transport(d, t, T.M.data() + (size_t)i * k * k, X);
-    for (int q = 0; q < k * k; ++q) C.M[(size_t)I * k * k + q] += X[q];
+  C.M.assign((size_t)nc * kk, 0.0);
+  const long long ne = (long long)T.ei.size();
+  // per fine edge: coarse edge key a * nc + b (a < b), or -1 (inside one
+  // agglomerate, between Dirichlet vertices, or not kept), or -2 - V (a
+  // Dirichlet coupling folded into coarse vertex V)
+  std::vector<long long> key(ne);
+#pragma omp parallel for schedule(static)
+  for (long long e = 0; e < ne; ++e) {
+    const int I = agg[T.ei[e]], J = agg[T.ej[e]];
+    if (I >= 0 && J >= 0)
+      key[e] = I == J ? -1 : (long long)std::min(I, J) * nc + std::max(I, J);
+    else if (use_dir && ((I >= 0) != (J >= 0)))
+      key[e] = -2 - (long long)(I >= 0 ? I : J);
+    else
+      key[e] = -1;
   }
-  std::unordered_map<long long, int> idx;
-  std::vector<std::array<double, 36>> acc;
-  std::vector<std::pair<int, int>> keys;
-  for (size_t e = 0; e < T.ei.size(); ++e) {
-    const int i = T.ei[e], j = T.ej[e];
-    const int I = agg[i], J = agg[j];
-    const double *E = T.E.data() + e * k * k;
-    if (I >= 0 && J >= 0) {
-      if (I == J) continue;
-      const int a = std::min(I, J), b = std::max(I, J);
+  // coarse vertex contributions: fine vertices, then Dirichlet edges
+  std::vector<int> vptr(nc + 1, 0), eptr(nc + 1, 0);
+  for (int i = 0; i < T.n; ++i)
+    if (agg[i] >= 0) ++vptr[agg[i] + 1];
+  for (long long e = 0; e < ne; ++e)
+    if (key[e] <= -2) ++eptr[-2 - key[e] + 1];
+  for (int I = 0; I < nc; ++I) {
+    vptr[I + 1] += vptr[I];
+    eptr[I + 1] += eptr[I];
+  }
+  std::vector<int> vlist(vptr[nc]), elist(eptr[nc]);
+  {
+    std::vector<int> fv(vptr.begin(), vptr.end() - 1), fe(eptr.begin(), eptr.end() - 1);
+    for (int i = 0; i < T.n; ++i)
+      if (agg[i] >= 0) vlist[fv[agg[i]]++] = i;
+    for (long long e = 0; e < ne; ++e)
+      if (key[e] <= -2) elist[fe[-2 - key[e]]++] = (int)e;
+  }
+#pragma omp parallel for schedule(dynamic, 64)
+  for (int I = 0; I < nc; ++I) {
+    double t[3], X[36];
+    double *MI = C.M.data() + (size_t)I * kk;
+    for (int p = vptr[I]; p < vptr[I + 1]; ++p) {
+      const int i = vlist[p];
+      for (int a = 0; a < d; ++a) t[a] = T.pos[(size_t)i * d + a] - xc[(size_t)I * d + a];
+      transport(d, t, T.M.data() + (size_t)i * kk, X);
+      for (size_t q = 0; q < kk; ++q) MI[q] += X[q];
+    }
+    for (int p = eptr[I]; p < eptr[I + 1]; ++p) {
+      const int e = elist[p], i = T.ei[e], j = T.ej[e];
+      const int v = agg[i] >= 0 ? i : j, w = agg[i] >= 0 ? j : i;
+      // Q^{v_I -> v_i, T} Q^{ij,T} E Q^{ij} Q^{v_I -> v_i}: one shift (x_i+x_j)/2 - x_I
+      for (int q = 0; q < d; ++q)
+        t[q] = 0.5 * (T.pos[(size_t)v * d + q] + T.pos[(size_t)w * d + q]) - xc[(size_t)I * d + q];
+      transport(d, t, T.E.data() + (size_t)e * kk, X);
+      for (size_t q = 0; q < kk; ++q) MI[q] += X[q];
+    }
+  }
+  // coarse edges: fine edges sorted by (coarse key, fine edge)
+  std::vector<int> ce;
+  for (long long e = 0; e < ne; ++e)
+    if (key[e] >= 0) ce.push_back((int)e);
+  std::sort(ce.begin(), ce.end(), [&](int a, int b) { return key[a] != key[b] ? key[a] < key[b] : a < b; });
+  std::vector<int> cptr;
+  for (size_t q = 0; q < ce.size(); ++q)
+    if (q == 0 || key[ce[q]] != key[ce[q - 1]]) cptr.push_back((int)q);
+  const int nce = (int)cptr.size();
+  cptr.push_back((int)ce.size());
+  C.ei.resize(nce);
+  C.ej.resize(nce);
+  C.E.assign((size_t)nce * kk, 0.0);
+#pragma omp parallel for schedule(dynamic, 256)
+  for (int c = 0; c < nce; ++c) {
+    const long long kc = key[ce[cptr[c]]];
+    const int a = (int)(kc / nc), b = (int)(kc % nc);
+    C.ei[c] = a;
+    C.ej[c] = b;
+    double t[3], X[36];
+    double *Ec = C.E.data() + (size_t)c * kk;
+    for (int p = cptr[c]; p < cptr[c + 1]; ++p) {
+      const int e = ce[p], i = T.ei[e], j = T.ej[e];
       // Q^{IJ->ij} = Q((x_i + x_j)/2 - (x_I + x_J)/2)
       for (int q = 0; q < d; ++q)
         t[q] = 0.5 * (T.pos[(size_t)i * d + q] + T.pos[(size_t)j * d + q]) -
                0.5 * (xc[(size_t)a * d + q] + xc[(size_t)b * d + q]);
-      transport(d, t, E, X);
-      const long long key = (long long)a * nc + b;
-      auto it = idx.find(key);
-      if (it == idx.end()) {
-        idx[key] = (int)acc.size();
-        std::array<double, 36> z;
-        z.fill(0.0);
-        for (int q = 0; q < k * k; ++q) z[q] = X[q];
-        acc.push_back(z);
-        keys.push_back({a, b});
-      } else {
-        for (int q = 0; q < k * k; ++q) acc[it->second][q] += X[q];
-      }
-    } else if (use_dir && ((I >= 0) != (J >= 0))) {
-      const int v = (I >= 0) ? i : j, w = (I >= 0) ? j : i, V = (I >= 0) ? I : J;
-      // Q^{v_I -> v_i, T} Q^{ij,T} E Q^{ij} Q^{v_I -> v_i}: one shift (x_i+x_j)/2 - x_I
-      for (int q = 0; q < d; ++q)
-        t[q] = 0.5 * (T.pos[(size_t)v * d + q] + T.pos[(size_t)w * d + q]) - xc[(size_t)V * d + q];
-      transport(d, t, E, Y);
-      for (int q = 0; q < k * k; ++q) C.M[(size_t)V * k * k + q] += Y[q];
+      transport(d, t, T.E.data() + (size_t)e * kk, X);
+      if (p == cptr[c])
+        for (size_t q = 0; q < kk; ++q) Ec[q] = X[q];
+      else
+        for (size_t q = 0; q < kk; ++q) Ec[q] += X[q];
     }
-  }
-  std::vector<int> order(keys.size());
-  for (size_t q = 0; q < order.size(); ++q) order[q] = (int)q;
-  std::sort(order.begin(), order.end(), [&](int a, int b) { return keys[a] < keys[b]; });
-  C.ei.resize(order.size());
-  C.ej.resize(order.size());
-  C.E.assign(order.size() * k * k, 0.0);
-  for (size_t q = 0; q < order.size(); ++q) {
-    C.ei[q] = keys[order[q]].first;
-    C.ej[q] = keys[order[q]].second;
-    for (int r = 0; r < k * k; ++r) C.E[q * k * k + r] = acc[order[q]][r];
   }
   C.build_adj();
   return C;
@@ -722,8 +759,9 @@ static Coarsening successive_matching(const Topo &T0, const SetupParams &prm, in
   std::vector<double> Dh0 = aux_diagonal(T0);
   Coarsening out;
   out.D = T0.dir;
+#pragma omp parallel for schedule(static)
   for (int v = 0; v < n; ++v)
-    if (!out.D[v]) {
+    if (!T0.dir[v]) {
       // mu_D(v) = lambda_max(D-hat_vv, M^v) (eq. mu_d)
       const double m = gen_lambda_max(k, Dh0.data() + (size_t)v * k * k, T0.M.data() + (size_t)v * k * k);
       if (m < sigma) out.D[v] = 1;
@@ -783,41 +821,56 @@ static Coarsening successive_matching(const Topo &T0, const SetupParams &prm, in
         gok = mu_g_below(T0, Dh0, uni, prm.delta, sigma) ? 1 : 0;
       }
     };
-    const int chunk = 2048;
+    // The greedy loop below decides pairs in iteration order; the measures
+    // it consults are evaluated ahead of it, in parallel: for every vertex of
+    // a chunk its first two live candidates (the first one usually
+    // succeeds), and where the loop needs a pair not evaluated yet, that
+    // pair together with the vertex's next live candidates.  The decisions
+    // are those of evaluating each pair when the loop reaches it.
+    const int chunk = 2048, ahead = 2, refill = 8;
     std::vector<Cand> cands;
+    struct Eval {
+      double mu;
+      int gok;
+    };
+    std::unordered_map<long long, Eval> done;
+    std::vector<std::array<int, 2>> tasks;
+    std::vector<Eval> res;
+    auto run_tasks = [&]() {
+      res.resize(tasks.size());
+#pragma omp parallel for schedule(dynamic, 1)
+      for (long long q = 0; q < (long long)tasks.size(); ++q)
+        evaluate(tasks[q][0], tasks[q][1], res[q].mu, res[q].gok);
+      for (size_t q = 0; q < tasks.size(); ++q) done[(long long)tasks[q][0] * m + tasks[q][1]] = res[q];
+      tasks.clear();
+    };
     for (size_t c0 = 0; c0 < order.size(); c0 += chunk) {
       const size_t c1 = std::min(order.size(), c0 + chunk);
-      // speculative parallel evaluation of the first eight live candidates
-      std::vector<std::array<int, 2>> tasks;
+      done.clear();
       for (size_t q = c0; q < c1; ++q) {
         const int ci = order[q];
         if (!inT[ci]) continue;
         candidates(ci, cands);
-        for (size_t u = 0; u < cands.size() && u < 8; ++u) tasks.push_back({ci, cands[u].cj});
+        for (size_t u = 0; u < cands.size() && u < (size_t)ahead; ++u) tasks.push_back({ci, cands[u].cj});
       }
-      std::vector<double> tmu(tasks.size());
-      std::vector<int> tg(tasks.size());
-#pragma omp parallel for schedule(dynamic, 8)
-      for (long long q = 0; q < (long long)tasks.size(); ++q) evaluate(tasks[q][0], tasks[q][1], tmu[q], tg[q]);
-      std::unordered_map<long long, size_t> done;
-      for (size_t q = 0; q < tasks.size(); ++q) done[(long long)tasks[q][0] * m + tasks[q][1]] = q;
+      run_tasks();
       for (size_t q = c0; q < c1; ++q) {
         const int ci = order[q];
         if (!inT[ci]) continue;
         inT[ci] = 0;
         candidates(ci, cands);
         bool matched = false;
-        for (const Cand &cd : cands) {
-          const int cj = cd.cj;
-          double mu;
-          int gok;
+        for (size_t u = 0; u < cands.size(); ++u) {
+          const int cj = cands[u].cj;
           auto it = done.find((long long)ci * m + cj);
-          if (it != done.end()) {
-            mu = tmu[it->second];
-            gok = tg[it->second];
-          } else {
-            evaluate(ci, cj, mu, gok);
+          if (it == done.end()) {
+            for (size_t w = u; w < cands.size() && tasks.size() < (size_t)refill; ++w)
+              if (!done.count((long long)ci * m + cands[w].cj)) tasks.push_back({ci, cands[w].cj});
+            run_tasks();
+            it = done.find((long long)ci * m + cj);
           }
+          const double mu = it->second.mu;
+          const int gok = it->second.gok;
           if (mu < sigma && gok) {
             groups.push_back({ci, cj});
             inT[cj] = 0;
