@@ -122,3 +122,29 @@ def test_batch_stage_roofline_bytes():
     assert abs(out["level 0 t = b - A x"]["gbs"] - round(resid / 2e-6 / 1e9, 1)) < 1e-9
     assert abs(out["level 0 b_c = R t"]["gbs"] - round(restr / 1e-6 / 1e9, 1)) < 1e-9
     assert abs(out["q = A_0 p"]["gbs"] - round(cg / 4e-6 / 1e9, 1)) < 1e-9
+
+
+def test_clock_sampler_parses_nvidia_smi_lines():
+    """Median SM clock, maximum, and the throttle reasons that were active
+    in any sample, from nvidia-smi's csv lines (the fields ClockSampler asks
+    for)."""
+    lines = "\n".join([
+        "0, 2070, 2070, 900.1, 0x0000000000000000, Not Active, Not Active, Not Active, Not Active",
+        "0, 1980, 2070, 1390.5, 0x0000000000000004, Not Active, Not Active, Not Active, Active",
+        "0, 2070, 2070, 1201.0, 0x0000000000000000, Not Active, Not Active, Not Active, Not Active",
+        "garbage line",
+    ])
+
+    class Proc:
+        def terminate(self):
+            pass
+
+        def communicate(self, timeout=None):
+            return lines, ""
+
+    s = bench.ClockSampler(0)
+    s.proc = Proc()
+    c = s.stop()
+    assert c == {"sm_mhz": 2070.0, "sm_max_mhz": 2070.0, "reasons": ["sw_power_cap"], "samples": 3}
+    s.proc = None
+    assert s.stop() is None
