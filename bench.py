@@ -21,9 +21,9 @@ import subprocess
 import sys
 import time
 
-# No thread-count variables are set here: on the Arm machine OpenBLAS's
-# OPENBLAS_NUM_THREADS=1 also pins the process-wide OpenMP thread count,
-# which the library's host setup uses.  The CPU oracle's solve phase is
+# No thread-count variables are set here: with some OpenBLAS builds (e.g. on
+# aarch64) OPENBLAS_NUM_THREADS=1 also pins the process-wide OpenMP thread
+# count, which the library's host setup uses.  The CPU oracle's solve phase is
 # single-threaded anyway (scipy.sparse products, numpy element-wise ops).
 
 import numpy as np  # noqa: E402
