@@ -961,11 +961,15 @@ static void smoothed_prolongation(const HostBSR &A, const Topo &T, const Coarsen
   P.rowptr.assign(nrows + 1, 0);
   P.colidx.clear();
   P.vals.clear();
-  std::vector<std::pair<int, std::array<double, 36>>> acc;
   const double om = prm.omega;
+  // rows are independent: each is built into its own buffers in parallel,
+  // then the buffers are concatenated in row order
+  std::vector<std::vector<int>> rcol(nrows);
+  std::vector<std::vector<double>> rval(nrows);
+#pragma omp parallel for schedule(dynamic, 256)
   for (int r = 0; r < nrows; ++r) {
     const int v = rowmap[r];
-    acc.clear();
+    std::vector<std::pair<int, std::array<double, 36>>> acc;
     double Dinv[36];
     if (!cs.D[v]) {
       std::vector<int> touched;
@@ -1062,12 +1066,16 @@ static void smoothed_prolongation(const HostBSR &A, const Topo &T, const Coarsen
     for (auto &pr : acc) {
       double X[36];
       mm(Dinv, pr.second.data(), X, kr, kr, k);
-      P.colidx.push_back(pr.first);
+      rcol[r].push_back(pr.first);
       for (int i = 0; i < kr * k; ++i) {
         const double base = (pr.first == Pcol[r]) ? Pt[r][i] : 0.0;
-        P.vals.push_back(base - om * X[i]);
+        rval[r].push_back(base - om * X[i]);
       }
     }
+  }
+  for (int r = 0; r < nrows; ++r) {
+    P.colidx.insert(P.colidx.end(), rcol[r].begin(), rcol[r].end());
+    P.vals.insert(P.vals.end(), rval[r].begin(), rval[r].end());
     P.rowptr[r + 1] = (int)P.colidx.size();
   }
   next_bad.assign(cs.nc, 0);
