@@ -23,8 +23,6 @@ def _rigid(x):
     W = np.zeros((n, 3, 6))
     for a in range(3):
         W[:, a, a] = 1
-        for b in range(3):
-            pass
     for r in range(3):
         e = np.zeros(3)
         e[r] = 1
@@ -75,3 +73,30 @@ def test_seeded_reproducible():
     a = make_problem((5, 5), seed=12)
     b = make_problem((5, 5), seed=12)
     assert np.array_equal(a.A.vals, b.A.vals) and np.array_equal(a.coords, b.coords)
+
+
+def test_jump_boxes_and_nu_per_element():
+    """Inclusion boxes: every element modulus is the background E or one of
+    the drawn 10^U(-3,3) values, inside [1e-3, 1e3], with several distinct
+    boxes present; the modulus of an element equals that of the last box
+    holding its centroid.  Per-element nu stays in its range.  Coefficient
+    jumps leave A symmetric and SPD."""
+    p = make_problem((9, 8, 7), seed=3, jump_boxes=40, nu_range=(0.25, 0.45))
+    E = p.E_el
+    assert np.all((E == 1.0) | ((E >= 1e-3) & (E <= 1e3)))
+    assert len(np.unique(E[E != 1.0])) >= 5
+    assert np.all((p.nu_el >= 0.25) & (p.nu_el <= 0.45))
+    # last box wins: redraw the boxes from the same stream and recheck
+    d = 3
+    brng = np.random.default_rng([3, 1])
+    ext = np.array([(s - 1) * p.h for s in p.shape])
+    centres = brng.uniform(0.0, 1.0, size=(40, d)) * ext
+    sides = brng.uniform(0.02, 0.2, size=(40, d)) * ext
+    moduli = 10.0 ** brng.uniform(-3.0, 3.0, size=40)
+    cen = p.coords[p.elements].mean(axis=1)
+    for e in np.random.default_rng(0).choice(len(E), 200, replace=False):
+        inside = [b for b in range(40) if np.all(np.abs(cen[e] - centres[b]) <= 0.5 * sides[b])]
+        assert E[e] == (moduli[inside[-1]] if inside else 1.0)
+    A = _csr(p.A).toarray()
+    assert np.abs(A - A.T).max() <= 1e-12 * np.abs(A).max()
+    assert np.linalg.eigvalsh(A).min() > 0
