@@ -34,6 +34,10 @@ class CoarsenParams:
     sigma: float = 30.0
     delta: int = 1
     passes: int = 5
+    # True: the comparison variant of Sec. 5's coefficient-jump figures, in
+    # which only the scalar measure mu_s is used (mu_p and mu_g are not
+    # computed; the first candidate is taken)
+    scalar_only: bool = False
 
 
 def cuthill_mckee(topo: Topology, active: np.ndarray):
@@ -85,6 +89,11 @@ def _match(Tc: Topology, order, sizes, members, level_topo, level_Dhat, level_nb
                 if m < p.sigma:
                     Ns.append((m, rank[cj], cj))
         matched = False
+        if p.scalar_only and Ns:
+            Ns.sort()
+            pairs.append((ci, Ns[0][2]))
+            inT[Ns[0][2]] = False
+            continue
         while Ns:
             Ns.sort()
             _, _, cj = Ns.pop(0)

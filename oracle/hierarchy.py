@@ -34,6 +34,7 @@ class SetupParams:
     coarse_max: int = 0          # 0: min(1000, max(64, ceil(n0/1e4)))
     min_ratio: float = 1.5
     max_levels: int = 16
+    scalar_only: bool = False    # Algorithm 1 with mu_s alone (Sec. 5 comparison)
 
 
 def rows_as_dicts(M: solve.Mat):
@@ -65,7 +66,8 @@ def setup(problem, params: SetupParams = SetupParams(), factor: bool = True):
     while A.n_rows > cmax and level + 1 < params.max_levels:
         first = level == 0
         cp = coarsening.CoarsenParams(sigma=params.sigma, delta=params.delta,
-                                      passes=params.passes_first if first else params.passes_later)
+                                      passes=params.passes_first if first else params.passes_later,
+                                      scalar_only=params.scalar_only)
         agg, n_c, xc, topo_c, D = coarsening.successive_matching(topo, cp)
         if n_c == 0 or A.n_rows < params.min_ratio * n_c:
             break

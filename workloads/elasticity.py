@@ -302,7 +302,7 @@ def _restrict(rowptr, colidx, vals, keep):
 def make_problem(shape: Sequence[int], seed: int, h: Optional[float] = None,
                  E: float = 1.0, nu: float = 0.3, forces=None,
                  jump_boxes: int = 0, nu_range=None, name: str = "",
-                 clamp: bool = True) -> Problem:
+                 clamp: bool = True, E_fn=None) -> Problem:
     """Build one seeded elasticity problem.
 
     ``shape`` is the number of vertices per axis (2 or 3 entries).  ``h``
@@ -314,7 +314,8 @@ def make_problem(shape: Sequence[int], seed: int, h: Optional[float] = None,
     sets its modulus, ``E`` elsewhere.  ``nu_range=(lo, hi)`` draws the
     Poisson ratio per element.  ``clamp=False`` keeps the pure Neumann
     problem (no Dirichlet vertices; A is then singular with the rigid-body
-    modes as its kernel).
+    modes as its kernel).  ``E_fn`` (optional) maps the element centroids
+    (n_el x d) to the element moduli, replacing ``E`` and the boxes.
     """
     shape = tuple(int(s) for s in shape)
     d = len(shape)
@@ -338,6 +339,8 @@ def make_problem(shape: Sequence[int], seed: int, h: Optional[float] = None,
         for bi in range(jump_boxes):
             inside = np.all(np.abs(cen - centres[bi]) <= 0.5 * sides[bi], axis=1)
             E_el[inside] = moduli[bi]
+    if E_fn is not None:
+        E_el = np.asarray(E_fn(coords[elements].mean(axis=1)), dtype=np.float64).reshape(n_el)
     if nu_range is not None:
         nrng = np.random.default_rng([seed, 2])
         nu_el = nrng.uniform(nu_range[0], nu_range[1], size=n_el)
