@@ -117,3 +117,12 @@ def test_dropped_delta_term(monkeypatch):
     orig = C.mu_p
     monkeypatch.setattr(C, "mu_p", lambda topo, Dhat, nbrs, i, j, delta=1: orig(topo, Dhat, nbrs, i, j, 0))
     _fails(tc.test_mu_p_equals_mu_g_on_coarse_neumann_level)
+
+
+def test_pair_measures_that_never_object(monkeypatch):
+    """mu_p and mu_g that accept every pair (e.g. a dropped harmonic-mean
+    term making the left side vanish) leave only mu_s: the two-grid
+    robustness pin across coefficient jumps must fail."""
+    monkeypatch.setattr(CO, "mu_p", lambda *a, **k: 0.0)
+    monkeypatch.setattr(CO, "mu_g", lambda *a, **k: 0.0)
+    _fails(tc.test_robust_criteria_keep_two_grid_conditioned_across_jumps)
