@@ -20,12 +20,21 @@ from workloads import configs, make_problem
 HERE = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(HERE, "..", "paper_2011_13325_gb300", "csrc")
 
+
+def _checker(c, nb=4):
+    """4 x 4 checkerboard of E = 10^4 and E = 1 boxes on the unit square."""
+    i = np.floor(c[:, 0] * nb).clip(0, nb - 1)
+    j = np.floor(c[:, 1] * nb).clip(0, nb - 1)
+    return np.where((i + j) % 2 == 1, 1e4, 1.0)
+
+
 CASES = {
     "square32": (lambda: configs.square32(), {}),
     "cube10": (lambda: make_problem((10, 10, 10), seed=2), {"coarse_max": 8}),
     "box_jump": (lambda: make_problem((9, 7, 8), seed=3, jump_boxes=6, nu_range=(0.25, 0.45)),
                  {"coarse_max": 6}),
     "rect2d_nu": (lambda: make_problem((41, 23), seed=9, nu_range=(0.3, 0.45)), {"coarse_max": 10}),
+    "checker2d": (lambda: make_problem((17, 17), seed=1, nu=0.25, E_fn=_checker), {"coarse_max": 4}),
 }
 
 
