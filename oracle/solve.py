@@ -218,8 +218,17 @@ def pcg(H: Hierarchy, f, rtol=1e-8, maxit=500, x0=None, precond=None):
     x = np.zeros_like(f) if x0 is None else x0.copy()
     r = f - spmv(A, x)
     nf = np.linalg.norm(f)
-    hist = [np.linalg.norm(r) / nf]
-    if hist[-1] <= rtol:
+
+    # relative residual; for f = 0 the stopping rule ||r|| <= rtol ||f||
+    # asks for r = 0, and ||r|| itself is recorded
+    def rel(r):
+        return np.linalg.norm(r) / nf if nf > 0 else np.linalg.norm(r)
+
+    def converged(h):
+        return h <= rtol if nf > 0 else h <= 0.0
+
+    hist = [rel(r)]
+    if converged(hist[-1]):
         return x, 0, hist
     p = None
     rho_old = None
@@ -234,8 +243,8 @@ def pcg(H: Hierarchy, f, rtol=1e-8, maxit=500, x0=None, precond=None):
         r = r - alpha * q
         rho_old = rho
         it += 1
-        hist.append(np.linalg.norm(r) / nf)
-        if hist[-1] <= rtol:
+        hist.append(rel(r))
+        if converged(hist[-1]):
             break
     return x, it, hist
 

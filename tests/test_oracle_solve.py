@@ -166,6 +166,24 @@ def test_pcg_recovers_manufactured_solution(which, request):
         assert hist[-1] <= 1e-12
 
 
+def test_pcg_degenerate_right_sides(h2d):
+    """f = 0 from x0 = 0: the stopping rule ||r|| <= rtol ||f|| holds at once
+    (0 iterations, x = 0).  A start at the solution of a manufactured
+    problem needs no iteration either, and a start on one side of the
+    solution converges to it."""
+    p, H = h2d
+    A = H.A[0]
+    n = A.n_rows * A.br
+    x, it, hist = solve.pcg(H, np.zeros(n), rtol=1e-8)
+    assert it == 0 and not x.any() and hist == [0.0]
+    ustar = np.random.default_rng(7).normal(size=n)
+    f = solve.spmv(A, ustar)
+    u, it, hist = solve.pcg(H, f, rtol=1e-8, x0=ustar)
+    assert it == 0 and hist[0] <= 1e-12
+    u, it, hist = solve.pcg(H, f, rtol=1e-10, x0=ustar + 1e-3)
+    assert 0 < it < 60 and np.abs(u - ustar).max() <= 1e-6
+
+
 def test_galerkin_many_coarse_rows_keeps_block_keys():
     """P = I on 50,000 block rows (nc^2 > 2^31): P^T A P must return A itself
     (the block keys of the scatter need 64-bit arithmetic)."""
