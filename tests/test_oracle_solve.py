@@ -184,6 +184,21 @@ def test_pcg_degenerate_right_sides(h2d):
     assert 0 < it < 60 and np.abs(u - ustar).max() <= 1e-6
 
 
+def test_one_level_hierarchy_is_an_exact_solve():
+    """A problem at or below the coarse size keeps one level: the V-cycle is
+    the regularised coarsest solve, which for an SPD A_0 (no kernel to
+    regularise) is A_0^{-1}, so PCG stops after one iteration."""
+    p = make_problem((4, 3), seed=1)
+    H = hierarchy.setup(p)
+    assert H.n_levels == 1
+    n = H.A[0].n_rows * H.A[0].br
+    V = np.column_stack([solve.vcycle(H, e) for e in np.eye(n)])
+    A = _dense(H.A[0])
+    np.testing.assert_allclose(V @ A, np.eye(n), atol=1e-12)
+    _, it, hist = solve.pcg(H, p.b[0], rtol=1e-12)
+    assert it == 1 and hist[-1] <= 1e-12
+
+
 def test_galerkin_many_coarse_rows_keeps_block_keys():
     """P = I on 50,000 block rows (nc^2 > 2^31): P^T A P must return A itself
     (the block keys of the scatter need 64-bit arithmetic)."""
