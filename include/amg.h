@@ -152,7 +152,10 @@ int amg_download_smoother(amg_ctx *ctx, int level, double *minv);
  * to host memory. */
 int amg_download_coarse_inverse(amg_ctx *ctx, double *cinv);
 
-/* --- single steps of the V-cycle, FP64, device vectors of level `level` --- */
+/* --- single steps of the V-cycle, FP64, device vectors of level `level` ---
+ * Errors of every single step: AMG_ERR_STATE without a hierarchy,
+ * AMG_ERR_ARG for a level out of range (restriction / prolongation: the
+ * coarsest level too) or a NULL required vector, AMG_ERR_CUDA. */
 
 /* y = A_l x (BSR SpMV with the level operator of Algorithm tg). */
 int amg_spmv(amg_ctx *ctx, int level, const double *x_dev, double *y_dev);
@@ -181,7 +184,12 @@ int amg_vcycle(amg_ctx *ctx, const double *r_dev, double *z_dev, int nrhs);
  * the device as one CUDA graph with a device-side while loop.  iters_out /
  * relres_out receive the iteration count and the final recurrence relative
  * residual per right-hand side (may be NULL).  For the mixed precisions the
- * CG uses the flexible (Polak-Ribiere) beta. */
+ * CG uses the flexible (Polak-Ribiere) beta.  f = 0 with u = 0 returns at
+ * once (0 iterations, relres 0).  Errors: AMG_ERR_STATE (no hierarchy),
+ * AMG_ERR_ARG (NULL vector, nrhs < 1, rtol < 0, maxit < 0),
+ * AMG_ERR_NOT_SPD (CG breakdown), AMG_ERR_NO_CONVERGENCE (u holds the last
+ * iterate), AMG_ERR_CUDA; with several right-hand sides the first failure
+ * is returned after all of them ran. */
 int amg_pcg_solve(amg_ctx *ctx, const double *f_dev, double *u_dev, int nrhs, double rtol,
                   int maxit, int *iters_out, double *relres_out);
 
