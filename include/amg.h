@@ -400,7 +400,8 @@ typedef struct amg_batch amg_batch;
  * Creation also runs the autotuner: each grouped block-sparse product is
  * timed with every tile (lanes per block row 32/16/8 x warps per block 8/4;
  * the SELL-32 copy with 4 or 2 slices per block for 2x2, 3x3, 2x3 and 3x6
- * blocks, which every system's A_0 and P_0 receive; block lanes, 8 or 16
+ * blocks, which every system's A_0 and P_0 receive, P_0's with
+ * length-sorted slices as in the single-system layout; block lanes, 8 or 16
  * lanes per block row with one whole block per lane, for 6x6 and 6x3
  * blocks) and the fastest is kept (amg_batch_describe lists the choices).
  * Errors: AMG_ERR_ARG, AMG_ERR_STATE (a context without hierarchy),
