@@ -148,3 +148,22 @@ def test_clock_sampler_parses_nvidia_smi_lines():
     assert c == {"sm_mhz": 2070.0, "sm_max_mhz": 2070.0, "reasons": ["sw_power_cap"], "samples": 3}
     s.proc = None
     assert s.stop() is None
+
+
+def test_reference_arm_oracle_timing_on_cpu():
+    """The reference arm's CPU pieces: the oracle hierarchy rebuilt from
+    downloaded prolongations (here the oracle's own) and the bounded
+    oracle PCG timing, scaled to the full iteration count."""
+    from oracle import hierarchy, solve
+    from workloads import configs
+    p = configs.square32()
+    H = hierarchy.setup(p)
+    P_list = [(P.n_rows, P.n_cols, P.rowptr.astype(np.int32), P.colidx.astype(np.int32), P.vals)
+              for P in H.P]
+    H2 = bench.oracle_hierarchy(p, P_list)
+    assert H2.n_levels == H.n_levels
+    _, its, _ = solve.pcg(H2, p.b[0], rtol=1e-8)
+    _, its_o, _ = solve.pcg(H, p.b[0], rtol=1e-8)
+    assert its == its_o
+    ms, m, dt = bench.time_oracle(H2, p.b[0], its, budget_s=0.2)
+    assert ms > 0 and 1 <= m <= its and dt > 0
