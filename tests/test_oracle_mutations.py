@@ -126,3 +126,16 @@ def test_pair_measures_that_never_object(monkeypatch):
     monkeypatch.setattr(CO, "mu_p", lambda *a, **k: 0.0)
     monkeypatch.setattr(CO, "mu_g", lambda *a, **k: 0.0)
     _fails(tc.test_robust_criteria_keep_two_grid_conditioned_across_jumps)
+
+
+@pytest.mark.parametrize("omega", [1.0, 4.0 / 3.0])
+def test_wrong_smoothing_damping(monkeypatch, omega):
+    """A damping other than the smoothed-aggregation one (undamped Jacobi,
+    or 4/3 from a spectral-radius estimate of 1) fails the energy pin."""
+    import dataclasses
+    orig = PR.smoothed
+
+    def wrong(A_rows, P_t, topo, agg, D, rowmap, bad, first, pp):
+        return orig(A_rows, P_t, topo, agg, D, rowmap, bad, first, dataclasses.replace(pp, omega=omega))
+    monkeypatch.setattr(PR, "smoothed", wrong)
+    _fails(tp.test_smoothing_lowers_prolongation_energy, (7, 7, 7))

@@ -99,3 +99,26 @@ def test_smoothed_prolongation_row_caps():
         assert cnt[kinds == "S"].max(initial=0) <= capS
         assert cnt[kinds == "A"].max(initial=0) <= 4
         assert cnt[kinds == "D"].max(initial=0) == 0
+
+
+@pytest.mark.parametrize("shape", [(17, 17), (7, 7, 7)])
+def test_smoothing_lowers_prolongation_energy(shape):
+    """Def. aux_sp smooths the tentative prolongation with one damped Jacobi
+    step on the auxiliary matrix; with the smoothed-aggregation damping
+    (omega = 2/3 for rho(D^-1 A) <= 2) it must lower the A-energy of every
+    coarse basis function, and of the whole prolongation well below half
+    (measured: 0.32-0.33 in total, at most 0.54 per column).  A damping of
+    1, 4/3 or 2 misses these bounds."""
+    from oracle import prolongation, solve
+    p = make_problem(shape, seed=2)
+    H = hierarchy.setup(p, hierarchy.SetupParams(max_levels=2, coarse_max=1))
+    rec = H.info["records"][0]
+    rp, ci, v = prolongation.to_bsr(rec["tentative"], H.P[0].n_cols, H.P[0].br, H.P[0].bc)
+    Pt = solve.Mat(H.P[0].n_rows, H.P[0].n_cols, rp, ci, v).scipy().toarray()
+    Ps = H.P[0].scipy().toarray()
+    A = H.A[0].scipy().toarray()
+    et = np.einsum("ij,ij->j", Pt, A @ Pt)
+    es = np.einsum("ij,ij->j", Ps, A @ Ps)
+    live = et > 1e-14 * et.max()
+    assert (es[live] / et[live]).max() < 0.6
+    assert es.sum() / et.sum() < 0.4
