@@ -66,8 +66,10 @@ def ctx(monkeypatch):
     c = object.__new__(amg.Context)
     c.h = C.c_void_p(1)
     c.device = 0
-    yield c, fake
-    c.h = C.c_void_p()
+    try:
+        yield c, fake
+    finally:
+        c.h = C.c_void_p()   # never hand the fake handle to the real library
 
 
 def test_device_vectors_pass_when_right(ctx):
@@ -132,10 +134,12 @@ def test_without_hierarchy_the_library_reports(monkeypatch):
     monkeypatch.setattr(amg, "lib", lambda: fake)
     c = object.__new__(amg.Context)
     c.h, c.device = C.c_void_p(1), 0
-    with pytest.raises(amg.AmgError) as e:
-        c.spmv(0, FakeCuda(4), FakeCuda(4))
-    assert e.value.code == amg.AMG_ERR_STATE
-    c.h = C.c_void_p()
+    try:
+        with pytest.raises(amg.AmgError) as e:
+            c.spmv(0, FakeCuda(4), FakeCuda(4))
+        assert e.value.code == amg.AMG_ERR_STATE
+    finally:
+        c.h = C.c_void_p()   # never hand the fake handle to the real library
 
 
 def test_learned_arrays(ctx):
@@ -186,6 +190,13 @@ def test_batch_vectors(monkeypatch):
     b.h = C.c_void_p(1)
     b.nrhs = 6
     b.contexts = [type("Cx", (), {"device": 0})()]
+    try:
+        _batch_checks(b, fake)
+    finally:
+        b.h = C.c_void_p()   # never hand the fake handle to the real library
+
+
+def _batch_checks(b, fake):
     b.pcg_solve(FakeCuda(180), FakeCuda(180))
     assert fake.calls[-1][0] == "amg_batch_pcg_solve"
     b.pcg_solve_host(np.zeros(180), torch.zeros(180, dtype=torch.float64))
@@ -196,4 +207,3 @@ def test_batch_vectors(monkeypatch):
         b.pcg_solve_host(FakeCuda(180), np.zeros(180))
     with pytest.raises(TypeError):
         b.pcg_solve(np.zeros(180), FakeCuda(180))
-    b.h = C.c_void_p()
