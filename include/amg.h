@@ -74,7 +74,9 @@ enum {
   AMG_ERR_CUDA = -2,           /* a CUDA runtime call failed                 */
   AMG_ERR_NOT_SPD = -3,        /* CG breakdown (p^T A p <= 0 or NaN)         */
   AMG_ERR_NO_CONVERGENCE = -4, /* maxit reached before rtol                  */
-  AMG_ERR_TIMEOUT = -5,        /* a bounded device wait ran out              */
+  AMG_ERR_TIMEOUT = -5,        /* reserved for a bounded device wait that
+                                  ran out; no entry point has such a wait,
+                                  so none returns it today                  */
   AMG_ERR_STATE = -6           /* call out of order (e.g. no hierarchy yet)  */
 };
 
@@ -203,18 +205,22 @@ int amg_pcg_solve_host(amg_ctx *ctx, const double *f_host, double *u_host, int n
 /* z = B^{-1} r for one right-hand side, exactly as amg_vcycle, but with the
  * V-cycle's work vectors in a fixed 16 MiB device array of the library
  * instead of buffers of the context, and without allocating anything.  It
- * serves callers that must not allocate device memory while it runs: code
- * running while another library captures the stream into a CUDA graph,
- * code running where a framework's caching allocator already holds the free
- * device memory, and code with a memory budget fixed in advance.  (The
+ * serves callers that cannot allocate device memory while it runs: code
+ * running where a framework's caching allocator already holds the free
+ * device memory (a cudaMalloc there fails or forces the framework to give
+ * back its cache), and code with a memory budget fixed in advance.  (The
  * paper has no counterpart: it is an execution variant of the V-cycle.)
  *  - The hierarchy must be uploaded before (amg_upload_hierarchy /
  *    amg_setup allocate; this call does not).
  *  - The array holds 4 vectors per level (256-byte aligned) of the
  *    V-cycle precision; a hierarchy that needs more than 16 MiB is
  *    rejected with AMG_ERR_ARG and a message giving the size.
- *  - The first call on a device looks up the array's device address with
- *    that device current; make that first call before any stream capture.
+ *  - The first call on a device is its set-up: it looks up the array's
+ *    device address with that device current.  Under lazy module loading
+ *    (the CUDA default) this also loads the array's module, and the driver
+ *    reserves its 16 MiB at that moment.  Make that first call before any
+ *    stream capture and while 16 MiB are free; later calls allocate nothing.
+ *  - The call returns after synchronising the context's stream.
  *  - Every GPU that loads the library holds the array until the process
  *    exits.  All calls on a device share it and it keeps the last call's
  *    contents (nothing in it needs to start at zero); calls that overlap on

@@ -2,13 +2,18 @@
 // fixed, file-scope device array instead of buffers of the context, for
 // callers that must not allocate device memory while they run it.
 //
-// Callers that cannot allocate: code that runs while another library is
-// capturing the stream into a CUDA graph (device allocation is not allowed
-// inside a capture), code that runs where a framework's caching allocator
-// already holds all free device memory, and code with a fixed memory budget
-// decided before it starts (real-time or embedded use).  The hierarchy must
-// have been uploaded before (amg_upload_hierarchy / amg_setup allocate);
-// this call itself allocates nothing.
+// Callers that cannot allocate: code that runs where a framework's caching
+// allocator already holds all free device memory (a cudaMalloc would fail or
+// force the framework to release its cache), and code with a memory budget
+// fixed before it starts (real-time or embedded use).  The hierarchy must
+// have been uploaded before (amg_upload_hierarchy / amg_setup allocate).
+//
+// The first call on a device is the set-up: it looks up the array's device
+// address (cudaGetSymbolAddress, with that device current).  With lazy module
+// loading (the CUDA default) that lookup also loads this file's device module,
+// and the driver reserves the array's 16 MiB then.  Make that first call
+// before any stream capture and while 16 MiB are free; every later call on
+// the device allocates nothing.
 #include <mutex>
 
 #include "amg_internal.h"
