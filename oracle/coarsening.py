@@ -69,6 +69,13 @@ def cuthill_mckee(topo: Topology, active: np.ndarray):
     return order
 
 
+def later_pass_order(m):
+    """Visiting order of passes 2, 3, ...: the previous pass's m agglomerates
+    (numbered pairs first, in the order they were formed, then singletons)
+    in reverse insertion order."""
+    return list(range(m - 1, -1, -1))
+
+
 def _match(Tc: Topology, order, sizes, members, level_topo, level_Dhat, level_nbrs, p):
     """One round of matching (procedure match_vertices)."""
     nbrs = Tc.adjacency()
@@ -145,7 +152,7 @@ def successive_matching(topo: Topology, p: CoarsenParams = CoarsenParams()):
         Tc = coarse_topology(Tc, cagg, m, xc, use_dirichlet=(k == 1))
         members = {gi: mem for gi, mem in enumerate(new_members)}
         sizes = {gi: len(mem) for gi, mem in enumerate(new_members)}
-        order = list(range(m - 1, -1, -1))
+        order = later_pass_order(m)
     agg = -np.ones(n, dtype=np.int64)
     for gi, mem in members.items():
         agg[mem] = gi

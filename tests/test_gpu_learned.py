@@ -3,9 +3,12 @@ BF16/FP32 MLP forward and backward, Adam training, Lanczos damping) against
 the FP64 oracle (oracle/learned.py).
 
 Tolerances: features 1e-6 relative (FP64 arithmetic, FP32 output); targets
-1e-10 (FP64); network outputs, loss and gradient 2e-3 relative to their norm
-(FP32 accumulation; the oracle evaluates the same BF16-rounded weights in
-FP64).
+1e-10 (FP64); network outputs 2e-5 relative to their norm and 1e-4 element by element,
+loss and gradient 2e-3 relative to their norm (gradient blocks also 1e-2
+element by element) (FP32 accumulation; the oracle evaluates the same
+BF16-rounded weights in FP64); V-cycle with the installed blocks 1e-10
+element by element; the trained network must take fewer PCG iterations than
+block-l1 Jacobi.
 """
 import copy
 
@@ -97,7 +100,10 @@ def test_forward_loss_and_gradient_match_oracle():
     out = torch.zeros((X.shape[0], 6), dtype=torch.float32, device="cuda")
     net.infer(X, out)
     out_o, _ = learned.forward(w, Xh)
-    assert np.linalg.norm(out.cpu().numpy() - out_o) <= 2e-5 * np.linalg.norm(out_o)
+    oh = out.cpu().numpy()
+    assert np.linalg.norm(oh - out_o) <= 2e-5 * np.linalg.norm(out_o)
+    # element by element: every output within 1e-4 of the largest
+    assert np.abs(oh - out_o).max() <= 1e-4 * np.abs(out_o).max()
     loss, g = net.loss_grad(X, T)
     loss_o, g_o = learned.loss_grad(w, Xh, Th)
     assert abs(loss - loss_o) <= 2e-3 * loss_o
@@ -106,6 +112,7 @@ def test_forward_loss_and_gradient_match_oracle():
     for name, sl in (("W1", slice(0, 832)), ("b1", slice(832, 896)), ("W2", slice(896, 4992)),
                      ("b2", slice(4992, 5056)), ("W3", slice(5056, 5440)), ("b3", slice(5440, 5446))):
         assert np.linalg.norm(g[sl] - g_o[sl]) <= 5e-3 * np.linalg.norm(g_o[sl]) + 1e-12, name
+        assert np.abs(g[sl] - g_o[sl]).max() <= 1e-2 * np.abs(g_o[sl]).max() + 1e-12, name
 
 
 def test_training_reduces_loss_deterministically():
@@ -151,7 +158,8 @@ def test_learned_smoother_installs_damped_spd_blocks():
     H2 = copy.copy(H)
     H2.Minv = list(H.Minv)
     H2.Minv[0] = M
-    assert np.linalg.norm(za - solve.vcycle(H2, a)) <= 1e-10 * np.linalg.norm(za)
+    zo = solve.vcycle(H2, a)
+    assert np.abs(za - zo).max() <= 1e-10 * np.abs(zo).max()
     f = c["p"].b[0]
     u = torch.zeros(n, dtype=torch.float64, device="cuda")
     s, its, rr = ctx.pcg_solve(torch.from_numpy(f).cuda(), u, rtol=1e-8, maxit=2000)
@@ -205,4 +213,4 @@ def test_trained_smoother_gain_over_block_l1_jacobi():
         ctx.close()
     print("iterations (block-l1 Jacobi, learned):", out)
     for prec, (a, b) in out.items():
-        assert b <= a, out
+        assert b < a, out     # a strict gain in both precisions

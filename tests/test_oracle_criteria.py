@@ -199,3 +199,58 @@ def test_robust_criteria_keep_two_grid_conditioned_across_jumps():
     robust, scalar = kappas
     assert robust < 30.0
     assert scalar > 50.0 * robust
+
+
+def _hand_topology(pos, edges, weights):
+    """A topology written out by hand: edge matrices w_e I_k, no vertex
+    weights (so mu_D = +inf and no vertex joins D)."""
+    pos = np.asarray(pos, dtype=np.float64)
+    k = T.kdim(pos.shape[1])
+    E = np.array([w * np.eye(k) for w in weights])
+    return T.Topology(pos=pos, edges=np.asarray(edges, dtype=np.int64), E=E,
+                      M=np.zeros((pos.shape[0], k, k)), dirichlet=np.zeros(pos.shape[0], bool))
+
+
+def _groups(agg):
+    return sorted(sorted(np.nonzero(agg == g)[0].tolist()) for g in set(agg.tolist()))
+
+
+def test_algorithm1_tries_the_candidate_of_minimal_mu_s_first():
+    """Algorithm 1 (Sec. 5.2), candidate choice, derived by hand on a 4-cycle
+    0-1-2-3-0 with edge traces 3 w (k = 3) for w01 = 1, w12 = w23 = w30 = 2;
+    sigma = 1e6 lets every mu_p / mu_g test pass, so only the choice and the
+    order decide.  Every vertex has degree 2: the Cuthill-McKee order starts
+    at vertex 0 (lowest id), then its neighbours by (degree, id): 1, 3, then 2.
+    The trace maxima are max over incident edges: 6 at every vertex, so
+    mu_s(0,1) = sqrt(6*6)/3 = 2 and mu_s(0,3) = sqrt(6*6)/6 = 1.  The minimal
+    mu_s pairs 0 with 3; vertex 1 is visited next and its only unmatched
+    neighbour is 2: agglomerates {0,3}, {1,2}.  Choosing the maximal mu_s
+    would give {0,1}, {2,3}."""
+    t = _hand_topology([(0, 0), (1, 0), (1, 1), (0, 1)], [(0, 1), (1, 2), (2, 3), (0, 3)],
+                       [1.0, 2.0, 2.0, 2.0])
+    tmax = C.trace_max(t, t.adjacency())
+    assert np.allclose(tmax, 6.0)
+    assert C.mu_s(tmax, 3.0, 0, 1) == 2.0 and C.mu_s(tmax, 6.0, 0, 3) == 1.0
+    agg, nc, _, _, D = coarsening.successive_matching(t, coarsening.CoarsenParams(sigma=1e6,
+                                                                                    passes=1))
+    assert not D.any() and nc == 2
+    assert _groups(agg) == [[0, 3], [1, 2]]
+
+
+def test_algorithm1_later_pass_visits_in_reverse_insertion_order():
+    """Algorithm 1 (Sec. 5.2), pass order, derived by hand on a zig-zag path
+    0-1-2-3-4-5 with equal edges (E = I), sigma = 1e6.  Pass 1 (Cuthill-McKee
+    from vertex 0, the lowest-id vertex of degree 1: 0,1,...,5) forms {0,1},
+    {2,3}, {4,5} in that order.  Pass 2 visits them in reverse insertion
+    order: {4,5} first, whose only neighbour is {2,3}, giving {2,3,4,5};
+    {0,1} is then left alone.  Visiting in insertion order would give
+    {0,1,2,3} and {4,5}.  Pairs are numbered before singletons, so the
+    merged agglomerate is coarse vertex 0."""
+    pos = [(i, 0.3 * (i % 2)) for i in range(6)]
+    t = _hand_topology(pos, [(i, i + 1) for i in range(5)], [1.0] * 5)
+    agg1, nc1, _, _, _ = coarsening.successive_matching(t, coarsening.CoarsenParams(sigma=1e6,
+                                                                                      passes=1))
+    assert agg1.tolist() == [0, 0, 1, 1, 2, 2]
+    agg2, nc2, _, _, _ = coarsening.successive_matching(t, coarsening.CoarsenParams(sigma=1e6,
+                                                                                      passes=2))
+    assert agg2.tolist() == [1, 1, 0, 0, 0, 0]

@@ -139,3 +139,17 @@ def test_wrong_smoothing_damping(monkeypatch, omega):
         return orig(A_rows, P_t, topo, agg, D, rowmap, bad, first, dataclasses.replace(pp, omega=omega))
     monkeypatch.setattr(PR, "smoothed", wrong)
     _fails(tp.test_smoothing_lowers_prolongation_energy, (7, 7, 7))
+
+
+def test_candidate_of_maximal_mu_s(monkeypatch):
+    """The text of Sec. 5.2 says 'maximizes'; the listing's minimal mu_s is
+    the reading taken.  Ordering candidates by 1/mu_s tries the maximal one
+    first and must fail the hand-derived pin."""
+    orig = C.mu_s
+    monkeypatch.setattr(CO, "mu_s", lambda tmax, tr, i, j: 1.0 / orig(tmax, tr, i, j))
+    _fails(tc.test_algorithm1_tries_the_candidate_of_minimal_mu_s_first)
+
+
+def test_later_pass_in_insertion_order(monkeypatch):
+    monkeypatch.setattr(CO, "later_pass_order", lambda m: list(range(m)))
+    _fails(tc.test_algorithm1_later_pass_visits_in_reverse_insertion_order)
