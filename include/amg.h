@@ -284,6 +284,51 @@ enum {
 };
 int amg_set_layout_policy(amg_ctx *ctx, int policy);
 
+/* Arithmetic of the CG operator q = A_0 p of the PCG (Sec. 7; no counterpart
+ * in the paper: an execution choice of GB300, whose FP64 pipe (about 2 FMA
+ * per clock per SM) is slower than its memory for 2x2 / 3x3 FP64 blocks):
+ *   AMG_CG_FP64          FP64 fused multiply-adds.
+ *   AMG_CG_DOUBLE_FLOAT  (default) every FP64 value of A_0 (scaled by a power
+ *                        of two so that max |a| < 1) and of p is held as a pair
+ *                        of FP32 numbers hi + lo (48 significant bits, same 8
+ *                        bytes), products are formed exactly with FP32 fused
+ *                        multiply-adds (Dekker's two-product) and summed with
+ *                        Knuth's two-sum (the double-float arithmetic of
+ *                        Dekker 1971 / Bailey's double-float method); q is
+ *                        returned in FP64.  Each term carries a relative error
+ *                        of about 2^-47 (FP64: 2^-53); p.q, the CG scalars and
+ *                        all vector updates stay FP64.  Entries of p below
+ *                        about 2^-102 in magnitude lose low-word bits (FP32
+ *                        gradual underflow); below 2^-126 they count as zero
+ *                        in the product.
+ * It applies to A_0 with 2x2 or 3x3 blocks and a SELL-32 copy (see
+ * amg_set_layout_policy); elsewhere the FP64 kernel runs.  The setting takes
+ * effect at the next amg_pcg_solve*.  Errors: AMG_ERR_ARG (unknown mode). */
+enum { AMG_CG_FP64 = 0, AMG_CG_DOUBLE_FLOAT = 1 };
+int amg_set_cg_operator(amg_ctx *ctx, int mode);
+
+/* q = A_0 p with the CG operator of the PCG (Sec. 7) in the arithmetic
+ * amg_set_cg_operator selects (device vectors of level 0; a single step for
+ * parity checks).  Errors: AMG_ERR_STATE (no hierarchy), AMG_ERR_ARG (NULL
+ * vector, A_0 block size other than 2 or 3), AMG_ERR_CUDA. */
+int amg_cg_operator(amg_ctx *ctx, const double *p_dev, double *q_dev);
+
+/* Per-kernel timing of the CG steps of one PCG iteration (Sec. 7; a
+ * measurement aid, no counterpart in the paper), the V-cycle excluded: kind
+ * 0 rho = r.z (and beta), 1 p = z + beta p, 2 q = A_0 p with the per-block
+ * partials of p.q (the CG operator, in the arithmetic amg_set_cg_operator
+ * selects), 3 alpha = rho / p.q, 4 x += alpha p, r -= alpha q with the
+ * partials of r.r, 5 the loop decision.  Each kernel is launched reps times
+ * on the context's stream after one warm launch and timed with CUDA events;
+ * us receives microseconds per launch and bytes its algorithmic bytes
+ * (operator values, indices and slice pointers once, every vector it reads
+ * or writes once).  The CG vectors of the context are overwritten (the next
+ * solve starts afresh).  Up to max_entries entries are written; *n_entries
+ * receives the total (6).  Errors: AMG_ERR_STATE (no hierarchy),
+ * AMG_ERR_ARG, AMG_ERR_CUDA. */
+int amg_profile_pcg(amg_ctx *ctx, int reps, int32_t *kind, double *us, double *bytes,
+                    int max_entries, int32_t *n_entries);
+
 /* Per-kernel timing of one V-cycle (Algorithm tg) in the context's
  * precision (a measurement aid, no counterpart in the paper): every step
  * (kind 0 pre-smoothing x = M^+ b, 1 residual t = b - A x, 2 restriction,
@@ -335,8 +380,9 @@ typedef struct {
 
 /* Parameters of the setup and the readings taken where the paper is silent:
  *  sigma        threshold of Algorithm 1 for mu_s, mu_p, mu_g and mu_D
- *               (not given; 30, chosen so the operator complexity lands in
- *               the paper's range 1.2-1.5 on 3D elasticity)
+ *               (not given; 30: the least work to 1e-8 on 3D elasticity
+ *               with coefficient jumps; larger values lower the operator
+ *               complexity but merge across the jumps)
  *  delta        stabilisation of mu_p / mu_g (Sec. 5, delta = 1)
  *  passes_*     matching passes on the first / later levels (Sec. 7: 5 / 4)
  *  omega        damping of Def. aux_sp (not given; 2/3)

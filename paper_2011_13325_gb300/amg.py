@@ -35,6 +35,8 @@ AMG_LAYOUT_ROW_LANES = 3
 AMG_LAYOUT_BLOCK_LANES = 4
 AMG_SMOOTHER_L1_JACOBI = 0
 AMG_SMOOTHER_LEARNED = 1
+AMG_CG_FP64 = 0
+AMG_CG_DOUBLE_FLOAT = 1
 
 
 class amg_bsr(C.Structure):
@@ -110,6 +112,9 @@ _SIGS = {
     "amg_set_launch_overlap": (_I, [_P, _I]),
     "amg_pcg_launches": (_I, [_P, C.POINTER(C.c_int32), C.POINTER(C.c_int32)]),
     "amg_profile_vcycle": (_I, [_P, _I, _P, _P, _P, _P, _I, C.POINTER(C.c_int32)]),
+    "amg_profile_pcg": (_I, [_P, _I, _P, _P, _P, _I, C.POINTER(C.c_int32)]),
+    "amg_set_cg_operator": (_I, [_P, _I]),
+    "amg_cg_operator": (_I, [_P, _P, _P]),
     "amg_mlp_create": (_I, [C.POINTER(_P), _I, C.c_uint64]),
     "amg_mlp_destroy": (None, [_P]),
     "amg_mlp_last_error": (C.c_char_p, [_P]),
@@ -452,6 +457,28 @@ class Context:
                                              us.ctypes.data, by.ctypes.data, m, C.byref(n)))
         return [(int(lv[i]), self.PROFILE_KINDS[kd[i]], float(us[i]), float(by[i]))
                 for i in range(min(n.value, m))]
+
+    PCG_KINDS = ("rho = r.z", "p = z + beta p", "q = A_0 p, p.q partials", "alpha = rho / p.q",
+                 "x += alpha p, r -= alpha q, r.r partials", "loop decision")
+
+    def profile_pcg(self, reps=20):
+        """[(step, us per launch, algorithmic bytes)] of the CG kernels of one
+        PCG iteration (the V-cycle excluded); overwrites the CG vectors."""
+        kd = np.zeros(8, dtype=np.int32)
+        us = np.zeros(8)
+        by = np.zeros(8)
+        n = C.c_int32()
+        self._check(lib().amg_profile_pcg(self.h, int(reps), kd.ctypes.data, us.ctypes.data,
+                                          by.ctypes.data, 8, C.byref(n)))
+        return [(self.PCG_KINDS[kd[i]], float(us[i]), float(by[i])) for i in range(min(n.value, 8))]
+
+    def set_cg_operator(self, mode: int):
+        """AMG_CG_FP64 or AMG_CG_DOUBLE_FLOAT (default): arithmetic of q = A_0 p in the PCG."""
+        return self._check(lib().amg_set_cg_operator(self.h, int(mode)))
+
+    def cg_operator(self, p, q):
+        """q = A_0 p with the PCG's CG operator (its selected arithmetic)."""
+        return self._check(lib().amg_cg_operator(self.h, self._vec(p, "p", 0), self._vec(q, "q", 0)))
 
     def set_layout_policy(self, policy: int):
         return self._check(lib().amg_set_layout_policy(self.h, int(policy)))

@@ -35,6 +35,7 @@ void free_bsr(DevBSR &m) {
   dfree(m.s64);
   dfree(m.s32);
   dfree(m.s16);
+  dfree(m.sdf);
   m = DevBSR();
 }
 
@@ -60,6 +61,8 @@ void free_pcg(Ctx *c) {
   c->st = nullptr;
   dfree(c->counter);
   c->counter = nullptr;
+  dfree(c->pdf);
+  c->pdf = nullptr;
   if (c->st_host) cudaFreeHost(c->st_host);
   c->st_host = nullptr;
   if (c->graph) cudaGraphExecDestroy(c->graph);
@@ -428,6 +431,9 @@ static int finalize_hierarchy(Ctx *c) {
     DevBSR *ops[] = {&L.A, &L.P, &L.R};
     for (DevBSR *m : ops)
       if (m->nnzb && want_sell(c, *m)) CUDA_OR_FAIL(c, build_sell(c, *m), "sell layout");
+    // the CG operator's double-float copy of A_0 (rows in order, 2x2 / 3x3)
+    if (l == 0 && L.A.s64 && !L.A.sell_perm && (L.k == 2 || L.k == 3))
+      CUDA_OR_FAIL(c, build_double_float(c, L.A), "double-float A_0");
     if (precision != AMG_PREC_FP64) {
       CUDA_OR_FAIL(c, make_low_precision(c, L.A, precision), "low precision A");
       if (L.P.nnzb) CUDA_OR_FAIL(c, make_low_precision(c, L.P, precision), "low precision P");
@@ -994,6 +1000,24 @@ int amg_set_launch_overlap(amg_ctx *h, int enable) {
   if (c->graph_def) cudaGraphDestroy(c->graph_def);
   c->graph = nullptr;
   c->graph_def = nullptr;
+  c->err.clear();
+  return AMG_OK;
+}
+
+int amg_set_cg_operator(amg_ctx *h, int mode) {
+  if (!h) return AMG_ERR_ARG;
+  Ctx *c = &h->c;
+  if (mode != AMG_CG_FP64 && mode != AMG_CG_DOUBLE_FLOAT)
+    return fail(c, AMG_ERR_ARG, "unknown CG operator mode");
+  if (mode != c->cg_op) {
+    CUDA_OR_FAIL(c, cudaStreamSynchronize(c->stream), "sync");
+    c->cg_op = mode;
+    // the PCG graph holds the operator's kernel: rebuilt at the next solve
+    if (c->graph) cudaGraphExecDestroy(c->graph);
+    if (c->graph_def) cudaGraphDestroy(c->graph_def);
+    c->graph = nullptr;
+    c->graph_def = nullptr;
+  }
   c->err.clear();
   return AMG_OK;
 }

@@ -45,6 +45,12 @@ struct DevBSR {
   double *s64 = nullptr;
   float *s32 = nullptr;
   __nv_bfloat16 *s16 = nullptr;
+  // double-float copy of the SELL-32 values (A_0 only, for the CG operator):
+  // value a is held as a * 2^-df_exp = hi + lo, two FP32 numbers (hi the
+  // value rounded to FP32, lo the rounded remainder), stored as one float2
+  // per element in the SELL-32 order of s64 (8 bytes, as the FP64 copy)
+  float2 *sdf = nullptr;
+  int df_exp = 0;
 };
 
 struct Level {
@@ -93,6 +99,8 @@ struct Ctx {
   double setup_times[4] = {0, 0, 0, 0};  // host setup, device Galerkin + transfers, finalize, total (s)
   double *hbuf = nullptr;        // pinned staging for host solves
   size_t hbuf_len = 0;
+  int cg_op = AMG_CG_DOUBLE_FLOAT;  // arithmetic of the CG operator q = A_0 p
+  float2 *pdf = nullptr;         // p split into double-float pairs (CG operator input)
 };
 
 
@@ -160,6 +168,7 @@ cudaError_t smoother_setup(Ctx *c, int level);
 cudaError_t coarse_setup(Ctx *c);
 cudaError_t make_low_precision(Ctx *c, DevBSR &m, int prec);
 cudaError_t build_sell(Ctx *c, DevBSR &m);
+cudaError_t build_double_float(Ctx *c, DevBSR &m);
 bool want_sell(const Ctx *c, const DevBSR &m);
 cudaError_t scan_exclusive(Ctx *c, int n, int *a, int *total_dev);
 

@@ -905,6 +905,64 @@ cudaError_t build_sell(Ctx *c, DevBSR &m) {
   return cudaGetLastError();
 }
 
+// Largest |a| of n values, as the bit pattern of a non-negative double
+// (non-negative doubles are ordered like their bit patterns).
+__global__ void absmax_bits_kernel(size_t n, const double *__restrict__ v,
+                                   unsigned long long *__restrict__ out) {
+  unsigned long long m = 0ull;
+  for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+       i += (size_t)gridDim.x * blockDim.x) {
+    const unsigned long long b = (unsigned long long)__double_as_longlong(fabs(v[i]));
+    m = b > m ? b : m;
+  }
+  for (int o = 16; o > 0; o >>= 1) {
+    const unsigned long long w = __shfl_down_sync(0xffffffffu, m, o);
+    m = w > m ? w : m;
+  }
+  if ((threadIdx.x & 31) == 0) atomicMax(out, m);
+}
+
+// a * scale (a power of two, exact) as hi + lo: hi the FP32 rounding, lo the
+// FP32 rounding of the exact remainder (48 significant bits together).
+__global__ void split_double_float_kernel(size_t n, const double *__restrict__ v, double scale,
+                                          float2 *__restrict__ out) {
+  const size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  const double a = v[i] * scale;
+  const float hi = __double2float_rn(a);
+  const float lo = __double2float_rn(a - (double)hi);
+  out[i] = make_float2(hi, lo);
+}
+
+// The CG operator's double-float copy of a SELL-32 operator: the values
+// scaled by 2^-df_exp (max |a| 2^-df_exp < 1) and split into hi + lo.
+cudaError_t build_double_float(Ctx *c, DevBSR &m) {
+  dfree(m.sdf);
+  m.sdf = nullptr;
+  m.df_exp = 0;
+  if (!m.s64) return cudaSuccess;
+  const size_t ns = (size_t)m.sell_slots * 32 * m.br * m.bc;
+  unsigned long long *d_max = nullptr;
+  AMG_CUDA_TRY(dalloc((void **)&d_max, sizeof(unsigned long long)));
+  AMG_CUDA_TRY(cudaMemsetAsync(d_max, 0, sizeof(unsigned long long), c->stream));
+  absmax_bits_kernel<<<c->num_sms * 8, 256, 0, c->stream>>>(ns, m.s64, d_max);
+  AMG_CUDA_TRY(cudaGetLastError());
+  unsigned long long mb = 0ull;
+  AMG_CUDA_TRY(cudaMemcpyAsync(&mb, d_max, sizeof(mb), cudaMemcpyDeviceToHost, c->stream));
+  AMG_CUDA_TRY(cudaStreamSynchronize(c->stream));
+  dfree(d_max);
+  // max |a| in [2^e, 2^(e+1)): df_exp = e + 1 puts every scaled value below 1
+  const int e = (int)((mb >> 52) & 0x7FFull) - 1023;
+  m.df_exp = mb ? e + 1 : 0;
+  AMG_CUDA_TRY(dalloc((void **)&m.sdf, (ns ? ns : 1) * sizeof(float2)));
+  if (ns) {
+    split_double_float_kernel<<<(unsigned)((ns + 255) / 256), 256, 0, c->stream>>>(
+        ns, m.s64, ldexp(1.0, -m.df_exp), m.sdf);
+    AMG_CUDA_TRY(cudaGetLastError());
+  }
+  return cudaSuccess;
+}
+
 cudaError_t make_low_precision(Ctx *c, DevBSR &m, int prec) {
   const size_t n = (size_t)m.nnzb * m.br * m.bc;
   if (n == 0) return cudaSuccess;

@@ -203,6 +203,120 @@ __global__ void __launch_bounds__(kSellThreads) pcg_spmv_dot_sell_kernel(SellVie
   }
 }
 
+// ---------------------------------------------------------------------------
+// Double-float CG operator (AMG_CG_DOUBLE_FLOAT): q = A_0 p with every FP64
+// value held as an unevaluated sum hi + lo of two FP32 numbers, so that the
+// products run on the FP32 pipe (on sm_103a the FP64 pipe retires about two
+// FMA per clock per SM, below what HBM feeds for 2x2 / 3x3 FP64 blocks).
+// Products are exact by Dekker's two-product (the FMA returns the rounding
+// error of a*b), sums by Knuth's two-sum; the cross terms hi*lo' + lo*hi' are
+// added to the low word, lo*lo' (below 2^-48 relative) is dropped.
+// ---------------------------------------------------------------------------
+
+// x = hi + lo with |lo| < ulp(hi): hi keeps the sign, the exponent and the 23
+// leading fraction bits of the double (truncated), lo the remaining 29 bits
+// (rounded to 24), both built with integer operations only (no FP64
+// instructions).  |x| < 2^-126 gives (0, 0); |x| >= 2^128 gives (+-inf, 0).
+__device__ __forceinline__ float2 split_double_float(double x) {
+  const unsigned hw = (unsigned)__double2hiint(x);
+  const unsigned lw = (unsigned)__double2loint(x);
+  const int e = (int)((hw >> 20) & 0x7FFu) - 1023;
+  const unsigned sign = hw & 0x80000000u;
+  if (e < -126) return make_float2(0.f, 0.f);
+  if (e > 127) return make_float2(__uint_as_float(sign | 0x7F800000u), 0.f);
+  const unsigned m23 = ((hw & 0xFFFFFu) << 3) | (lw >> 29);
+  const float hi = __uint_as_float(sign | ((unsigned)(e + 127) << 23) | m23);
+  const unsigned rem = lw & 0x1FFFFFFFu;  // x - hi = rem * 2^(e - 52)
+  float lo = __uint2float_rn(rem);
+  if (e >= -74)
+    lo = __fmul_rn(lo, __uint_as_float((unsigned)(e - 52 + 127) << 23));
+  else  // 2^(e-52) is below FP32's normal range: scale in two exact steps
+    lo = __fmul_rn(__fmul_rn(lo, 0x1p-60f), __uint_as_float((unsigned)(e + 8 + 127) << 23));
+  return make_float2(hi, __uint_as_float(__float_as_uint(lo) | sign));
+}
+
+// f * 2^s as a double, exactly, built with integer operations (FP32 values
+// below the normal range count as 0).
+__device__ __forceinline__ double float_to_double_scaled(float f, int s) {
+  const unsigned b = __float_as_uint(f);
+  const int e8 = (int)((b >> 23) & 0xFFu);
+  if (e8 == 0) return 0.0;
+  if (e8 == 255) return (double)f;
+  const unsigned hw = (b & 0x80000000u) | ((unsigned)(e8 - 127 + 1023 + s) << 20) |
+                      ((b & 0x7FFFFFu) >> 3);
+  return __hiloint2double((int)hw, (int)((b & 0x7u) << 29));
+}
+
+// (sh, sl) += (ah + al) * (xh + xl)
+__device__ __forceinline__ void df_mac(float &sh, float &sl, float2 a, float2 x) {
+  const float p = __fmul_rn(a.x, x.x);
+  const float pe = __fmaf_rn(a.x, x.x, -p);                     // a.x * x.x = p + pe exactly
+  const float cross = __fmaf_rn(a.x, x.y, __fmaf_rn(a.y, x.x, pe));
+  const float s = __fadd_rn(sh, p);                             // two-sum: sh + p = s + err
+  const float bb = __fsub_rn(s, sh);
+  const float err = __fadd_rn(__fsub_rn(sh, __fsub_rn(s, bb)), __fsub_rn(p, bb));
+  sh = s;
+  sl = __fadd_rn(sl, __fadd_rn(err, cross));
+}
+
+struct SellDfView {
+  int n_rows, n_slices, df_exp;
+  const int *ptr, *col;
+  const float2 *v;
+};
+
+// q = A_0 p in double-float arithmetic (p given as hi/lo pairs in pdf) and
+// the per-block partial of p.q in FP64 (64-thread blocks, two slices each,
+// thread per block row, as the FP64 kernel above).
+template <int BR>
+__global__ void __launch_bounds__(kSellThreads) pcg_spmv_dot_sell_df_kernel(
+    SellDfView A, const float2 *__restrict__ pdf, const double *__restrict__ p,
+    double *__restrict__ q, double *__restrict__ partials) {
+  pdl_enter();
+  constexpr int E = BR * BR;
+  __shared__ double sh_part[kSellThreads / 32];
+  const int t = threadIdx.x & 31, w = threadIdx.x >> 5;
+  const int s = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  double v = 0.0;
+  if (s < A.n_slices) {
+    float hi[BR], lo[BR];
+#pragma unroll
+    for (int r = 0; r < BR; ++r) hi[r] = lo[r] = 0.f;
+    const int j1 = A.ptr[s + 1];
+#pragma unroll 2
+    for (int j = A.ptr[s]; j < j1; ++j) {
+      const int c = __ldg(A.col + (size_t)j * 32 + t);
+      const float2 *a = A.v + (size_t)j * E * 32 + t;
+      float2 xv[BR];
+#pragma unroll
+      for (int k = 0; k < BR; ++k) xv[k] = __ldg(pdf + (size_t)c * BR + k);
+#pragma unroll
+      for (int r = 0; r < BR; ++r)
+#pragma unroll
+        for (int k = 0; k < BR; ++k) df_mac(hi[r], lo[r], __ldcs(a + (r * BR + k) * 32), xv[k]);
+    }
+    const int row = s * 32 + t;
+    if (row < A.n_rows) {
+#pragma unroll
+      for (int r = 0; r < BR; ++r) {
+        const size_t i = (size_t)row * BR + r;
+        const double qi = float_to_double_scaled(hi[r], A.df_exp) +
+                          float_to_double_scaled(lo[r], A.df_exp);
+        q[i] = qi;
+        v += p[i] * qi;
+      }
+    }
+  }
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+  if (t == 0) sh_part[w] = v;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double b = 0.0;
+    for (int k = 0; k < kSellThreads / 32; ++k) b += sh_part[k];
+    partials[blockIdx.x] = b;
+  }
+}
+
 // r = f - A x ; rr = r.r ; ff = f.f ; decides whether the loop starts.
 template <int BR>
 __global__ void __launch_bounds__(kRedThreads) pcg_init_kernel(
@@ -264,15 +378,18 @@ __global__ void __launch_bounds__(kRedThreads) pcg_dot_rz_kernel(size_t n, const
   }
 }
 
-// p = z + beta p ; z_old = z (flexible variant)
+// p = z + beta p ; z_old = z (flexible variant); with pdf, also p as
+// double-float pairs for the double-float CG operator
 __global__ void pcg_update_p_kernel(size_t n, const double *z, double *p, double *zold,
-                                    const PcgState *st) {
+                                    const PcgState *st, float2 *pdf) {
   pdl_enter();
   const size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= n) return;
   const double beta = st->beta;
   const double zi = z[i];
-  p[i] = (st->it == 0) ? zi : zi + beta * p[i];
+  const double pi = (st->it == 0) ? zi : zi + beta * p[i];
+  p[i] = pi;
+  if (pdf) pdf[i] = split_double_float(pi);
   if (st->flexible) zold[i] = zi;
 }
 
@@ -377,6 +494,7 @@ cudaError_t pcg_alloc(Ctx *c) {
     AMG_CUDA_TRY(dalloc((void **)b, bytes));
     AMG_CUDA_TRY(cudaMemsetAsync(*b, 0, bytes, c->stream));
   }
+  if (c->levels[0].A.sdf) AMG_CUDA_TRY(dalloc((void **)&c->pdf, (n ? n : 1) * sizeof(float2)));
   AMG_CUDA_TRY(dalloc((void **)&c->st, sizeof(PcgState)));
   AMG_CUDA_TRY(cudaMallocHost((void **)&c->st_host, sizeof(PcgState)));
   const int n_slices = (c->levels[0].A.n_rows + 31) / 32;
@@ -385,6 +503,13 @@ cudaError_t pcg_alloc(Ctx *c) {
   AMG_CUDA_TRY(dalloc((void **)&c->counter, sizeof(unsigned)));
   AMG_CUDA_TRY(cudaMemsetAsync(c->counter, 0, sizeof(unsigned), c->stream));
   return cudaStreamSynchronize(c->stream);
+}
+
+// The double-float CG operator runs where A_0 has its double-float copy
+// (SELL-32, rows in order) and the context asks for it.
+static bool use_double_float(const Ctx *c) {
+  const DevBSR &A = c->levels[0].A;
+  return c->cg_op == AMG_CG_DOUBLE_FLOAT && A.sdf && A.sell_ptr && !A.sell_perm && c->pdf;
 }
 
 static SellView sell_view(const DevBSR &A) {
@@ -415,9 +540,16 @@ static cudaError_t launch_body(Ctx *c, cudaGraphConditionalHandle h, int in_grap
   AMG_CUDA_TRY(vcycle_launch(c, c->r, c->z));
   AMG_KLAUNCH(c, pcg_dot_rz_kernel, gv, kRedThreads, n, c->r, c->z, c->zold, c->st, c->partials,
                                                        c->counter);
+  const bool df = use_double_float(c);
   AMG_KLAUNCH(c, pcg_update_p_kernel, (unsigned)((n + 255) / 256), 256, n, c->z, c->p, c->zold,
-                                                                          c->st);
-  if (L0.A.sell_ptr && !L0.A.sell_perm) {
+                                                                          c->st, df ? c->pdf : nullptr);
+  if (df) {
+    n_pq = (L0.A.n_slices + 1) / 2;
+    const SellDfView A{L0.A.n_rows, L0.A.n_slices, L0.A.df_exp, L0.A.sell_ptr, L0.A.sell_col,
+                       L0.A.sdf};
+    AMG_KLAUNCH(c, pcg_spmv_dot_sell_df_kernel<BR>, n_pq, kSellThreads, A, (const float2 *)c->pdf,
+                (const double *)c->p, c->q, pq_part);
+  } else if (L0.A.sell_ptr && !L0.A.sell_perm) {
     n_pq = (L0.A.n_slices + 1) / 2;
     AMG_KLAUNCH(c, pcg_spmv_dot_sell_kernel<BR>, n_pq, kSellThreads, sell_view(L0.A), c->p,
                                                                        c->q, pq_part);
@@ -533,5 +665,183 @@ extern "C" int amg_pcg_launches(const amg_ctx *h, int32_t *per_iteration, int32_
   // r.z, p update, q = A p with p.q, alpha, x / r update with r.r, loop decision
   if (per_iteration) *per_iteration = vc + 6;
   if (fixed) *fixed = 1;
+  return AMG_OK;
+}
+
+namespace amg {
+
+// Mean device time (us) of reps launches of fn on c's stream, after one warm
+// launch, by CUDA events on that stream.
+template <typename F>
+static cudaError_t time_kernel(Ctx *c, int reps, F fn, double *us) {
+  cudaEvent_t e0, e1;
+  AMG_CUDA_TRY(cudaEventCreate(&e0));
+  AMG_CUDA_TRY(cudaEventCreate(&e1));
+  cudaError_t e = fn();
+  if (e == cudaSuccess) e = cudaEventRecord(e0, c->stream);
+  for (int r = 0; r < reps && e == cudaSuccess; ++r) e = fn();
+  if (e == cudaSuccess) e = cudaEventRecord(e1, c->stream);
+  if (e == cudaSuccess) e = cudaEventSynchronize(e1);
+  float ms = 0.f;
+  if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, e0, e1);
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  *us = 1e3 * ms / reps;
+  return e;
+}
+
+template <int BR>
+static cudaError_t profile_pcg_k(Ctx *c, int reps, double *us, double *bytes) {
+  const Level &L0 = c->levels[0];
+  const DevBSR &A = L0.A;
+  const size_t n = (size_t)A.n_rows * BR;
+  const int g = red_grid(c), gv = vec_grid(c);
+  double *pq_part = c->partials + 4 * (size_t)g;
+  double *rr_part = pq_part + (size_t)(A.n_slices + 1) / 2 + 1;
+  const bool df = use_double_float(c);
+  const bool sell = A.sell_ptr && !A.sell_perm;
+  const int flex = c->precision != AMG_PREC_FP64 ? 1 : 0;
+  const int n_pq = sell ? (A.n_slices + 1) / 2 : 1;
+  // a consistent CG state: iteration 1 (beta used), flexible as in a solve
+  PcgState h = *c->st_host;
+  h.it = 1;
+  h.maxit = 1 << 30;
+  h.guard = 0;
+  h.status = 0;
+  h.flexible = flex;
+  h.beta = 0.5;
+  h.rho_old = 1.0;
+  h.alpha = 0.5;
+  h.tol2 = 0.0;
+  AMG_CUDA_TRY(cudaMemcpyAsync(c->st, &h, sizeof(PcgState), cudaMemcpyHostToDevice, c->stream));
+  AMG_CUDA_TRY(cudaMemcpyAsync(c->z, c->r, n * sizeof(double), cudaMemcpyDeviceToDevice, c->stream));
+  const double N8 = 8.0 * (double)n;
+  AMG_CUDA_TRY(time_kernel(c, reps, [&] {
+    launch_k(c, pcg_dot_rz_kernel, gv, kRedThreads, n, (const double *)c->r, (const double *)c->z,
+             (const double *)c->zold, c->st, c->partials, c->counter);
+    return cudaGetLastError(); }, &us[0]));
+  bytes[0] = N8 * (2 + flex);
+  AMG_CUDA_TRY(time_kernel(c, reps, [&] {
+    launch_k(c, pcg_update_p_kernel, (unsigned)((n + 255) / 256), 256, n, (const double *)c->z, c->p,
+             c->zold, (const PcgState *)c->st, df ? c->pdf : nullptr);
+    return cudaGetLastError(); }, &us[1]));
+  bytes[1] = N8 * (3 + flex + (df ? 1 : 0));
+  const double abytes = (double)A.nnzb * (BR * BR * 8.0 + 4.0) + 4.0 * (A.n_rows + 1);
+  AMG_CUDA_TRY(time_kernel(c, reps, [&] {
+    if (df) {
+      const SellDfView V{A.n_rows, A.n_slices, A.df_exp, A.sell_ptr, A.sell_col, A.sdf};
+      launch_k(c, pcg_spmv_dot_sell_df_kernel<BR>, n_pq, kSellThreads, V, (const float2 *)c->pdf,
+               (const double *)c->p, c->q, pq_part);
+    } else if (sell) {
+      launch_k(c, pcg_spmv_dot_sell_kernel<BR>, n_pq, kSellThreads, sell_view(A),
+               (const double *)c->p, c->q, pq_part);
+    } else {
+      launch_k(c, pcg_spmv_dot_kernel<BR>, g, kRedThreads, A.n_rows, (const int *)A.rowptr,
+               (const int *)A.colidx, (const double *)A.v64, (const double *)c->p, c->q, c->st,
+               c->partials, c->counter, pq_part);
+    }
+    return cudaGetLastError(); }, &us[2]));
+  bytes[2] = abytes + N8 * (df ? 3 : 2);
+  AMG_CUDA_TRY(time_kernel(c, reps, [&] {
+    launch_k(c, pcg_alpha_kernel, 1, kFinThreads, c->st, (const double *)pq_part, n_pq);
+    return cudaGetLastError(); }, &us[3]));
+  bytes[3] = 8.0 * n_pq;
+  AMG_CUDA_TRY(time_kernel(c, reps, [&] {
+    launch_k(c, pcg_update_xr_kernel, gv, kRedThreads, n, c->x, c->r, (const double *)c->p,
+             (const double *)c->q, (const PcgState *)c->st, rr_part);
+    return cudaGetLastError(); }, &us[4]));
+  bytes[4] = N8 * 6;
+  AMG_CUDA_TRY(time_kernel(c, reps, [&] {
+    launch_k(c, pcg_guard_kernel, 1, 32, c->st, (const double *)rr_part, gv, c->counter,
+             (cudaGraphConditionalHandle)0, 0);
+    return cudaGetLastError(); }, &us[5]));
+  bytes[5] = 8.0 * gv;
+  return cudaStreamSynchronize(c->stream);
+}
+
+__global__ void split_vector_kernel(size_t n, const double *__restrict__ p, float2 *__restrict__ pdf) {
+  const size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) pdf[i] = split_double_float(p[i]);
+}
+
+// q = A_0 p by the CG operator's kernel (p.q partials to the reduction scratch).
+template <int BR>
+static cudaError_t cg_operator_k(Ctx *c, const double *p, double *q) {
+  const DevBSR &A = c->levels[0].A;
+  const size_t n = (size_t)A.n_rows * BR;
+  const int g = red_grid(c);
+  double *pq_part = c->partials + 4 * (size_t)g;
+  if (use_double_float(c)) {
+    split_vector_kernel<<<(unsigned)((n + 255) / 256), 256, 0, c->stream>>>(n, p, c->pdf);
+    AMG_CUDA_TRY(cudaGetLastError());
+    const SellDfView V{A.n_rows, A.n_slices, A.df_exp, A.sell_ptr, A.sell_col, A.sdf};
+    AMG_KLAUNCH(c, pcg_spmv_dot_sell_df_kernel<BR>, (A.n_slices + 1) / 2, kSellThreads, V,
+                (const float2 *)c->pdf, p, q, pq_part);
+  } else if (A.sell_ptr && !A.sell_perm) {
+    AMG_KLAUNCH(c, pcg_spmv_dot_sell_kernel<BR>, (A.n_slices + 1) / 2, kSellThreads, sell_view(A),
+                p, q, pq_part);
+  } else {
+    AMG_KLAUNCH(c, pcg_spmv_dot_kernel<BR>, g, kRedThreads, A.n_rows, (const int *)A.rowptr,
+                (const int *)A.colidx, (const double *)A.v64, p, q, c->st, c->partials, c->counter,
+                pq_part);
+  }
+  return cudaStreamSynchronize(c->stream);
+}
+
+}  // namespace amg
+
+extern "C" int amg_cg_operator(amg_ctx *h, const double *p, double *q) {
+  if (!h) return AMG_ERR_ARG;
+  Ctx *c = &h->c;
+  if (c->levels.empty() || !c->st) {
+    c->err = "amg_cg_operator: no hierarchy uploaded";
+    return AMG_ERR_STATE;
+  }
+  const int k = c->levels[0].k;
+  if (!p || !q || (k != 2 && k != 3)) {
+    c->err = "amg_cg_operator: NULL vector or A_0 block size other than 2 or 3";
+    return AMG_ERR_ARG;
+  }
+  cudaError_t e = cudaSetDevice(c->device);
+  if (e == cudaSuccess) e = k == 2 ? cg_operator_k<2>(c, p, q) : cg_operator_k<3>(c, p, q);
+  if (e != cudaSuccess) {
+    c->err = std::string("amg_cg_operator: ") + cudaGetErrorString(e);
+    return AMG_ERR_CUDA;
+  }
+  c->err.clear();
+  return AMG_OK;
+}
+
+extern "C" int amg_profile_pcg(amg_ctx *h, int reps, int32_t *kind, double *us, double *bytes,
+                               int max_entries, int32_t *n_entries) {
+  if (!h) return AMG_ERR_ARG;
+  Ctx *c = &h->c;
+  if (reps < 1 || max_entries < 0) {
+    c->err = "amg_profile_pcg: reps < 1 or max_entries < 0";
+    return AMG_ERR_ARG;
+  }
+  if (c->levels.empty() || !c->st) {
+    c->err = "amg_profile_pcg: no hierarchy uploaded";
+    return AMG_ERR_STATE;
+  }
+  const int k = c->levels[0].k;
+  if (k != 2 && k != 3) {
+    c->err = "amg_profile_pcg: A_0 block size";
+    return AMG_ERR_ARG;
+  }
+  cudaError_t e = cudaSetDevice(c->device);
+  double t[6] = {0}, b[6] = {0};
+  if (e == cudaSuccess) e = k == 2 ? profile_pcg_k<2>(c, reps, t, b) : profile_pcg_k<3>(c, reps, t, b);
+  if (e != cudaSuccess) {
+    c->err = std::string("amg_profile_pcg: ") + cudaGetErrorString(e);
+    return AMG_ERR_CUDA;
+  }
+  for (int i = 0; i < 6 && i < max_entries; ++i) {
+    if (kind) kind[i] = i;
+    if (us) us[i] = t[i];
+    if (bytes) bytes[i] = b[i];
+  }
+  if (n_entries) *n_entries = 6;
+  c->err.clear();
   return AMG_OK;
 }

@@ -332,3 +332,60 @@ def test_sell_layout_sorts_rectangular_operators():
     ctx.vcycle(dev(r), z)
     assert maxrel(host(z), solve.vcycle(H, r)) <= 1e-10
     ctx.close()
+
+
+def test_cg_operator_both_arithmetics(case):
+    """q = A_0 p as the PCG applies it (Sec. 7), FP64 fused multiply-adds and
+    double-float (hi + lo FP32 pairs, 48 significant bits per value), against
+    the oracle's product element by element; the double-float path runs where
+    A_0 has a SELL-32 copy (the "sell" layout, and "auto" on large meshes),
+    elsewhere both modes run the FP64 kernel.  Scaling p by 2^-60 and 2^60 is
+    exact in both and must scale q alike; at 2^-100 the low words of the
+    smaller entries reach FP32's subnormal range and lose bits."""
+    amg = _amg()
+    name, p, H, ctx = case
+    A = H.A[0]
+    n = A.n_rows * A.br
+    x = np.random.default_rng(11).normal(size=n)
+    try:
+        for mode, tol in ((amg.AMG_CG_FP64, 1e-12), (amg.AMG_CG_DOUBLE_FLOAT, 1e-11)):
+            ctx.set_cg_operator(mode)
+            for scale, t in ((1.0, tol), (2.0 ** -60, tol), (2.0 ** 60, tol), (2.0 ** -100, 1e-6)):
+                y = dev(np.zeros(n))
+                ctx.cg_operator(dev(scale * x), y)
+                assert maxrel(host(y), solve.spmv(A, scale * x)) <= t, (mode, scale)
+    finally:
+        ctx.set_cg_operator(amg.AMG_CG_DOUBLE_FLOAT)
+
+
+def test_pcg_same_in_both_cg_arithmetics(case):
+    """The PCG with the FP64 and the double-float CG operator: iteration
+    counts within +-1 and iterates within 1e-10 of the oracle's at their own
+    iteration counts."""
+    amg = _amg()
+    name, p, H, ctx = case
+    f = p.b[0]
+    try:
+        for mode in (amg.AMG_CG_FP64, amg.AMG_CG_DOUBLE_FLOAT):
+            ctx.set_cg_operator(mode)
+            u = dev(np.zeros_like(f))
+            _, its, rr = ctx.pcg_solve(dev(f), u, rtol=1e-8, maxit=500)
+            u_k, it_k, _ = solve.pcg(H, f, rtol=0.0, maxit=its[0])
+            assert maxrel(host(u), u_k) <= 1e-10, mode
+            _, it_or, _ = solve.pcg(H, f, rtol=1e-8, maxit=500)
+            assert abs(its[0] - it_or) <= 1
+    finally:
+        ctx.set_cg_operator(amg.AMG_CG_DOUBLE_FLOAT)
+
+
+def test_profile_pcg_covers_every_cg_step(case):
+    name, p, H, ctx = case
+    prof = ctx.profile_pcg(reps=2)
+    assert [s for s, _, _ in prof] == list(_amg().Context.PCG_KINDS)
+    assert all(us > 0 and by > 0 for _, us, by in prof)
+    # the context stays usable: a solve afterwards matches the oracle
+    f = p.b[0]
+    u = dev(np.zeros_like(f))
+    _, its, _ = ctx.pcg_solve(dev(f), u, rtol=1e-8, maxit=500)
+    u_k, _, _ = solve.pcg(H, f, rtol=0.0, maxit=its[0])
+    assert maxrel(host(u), u_k) <= 1e-10

@@ -224,8 +224,53 @@ def _lame(E, nu):
     return mu, lam
 
 
+def _element_chunk(shape, coords, temps, cells, posmap, off_index, E_el, nu_el, c0, c1):
+    """Element matrices of the cells c0..c1 (all templates): the BSR slot of
+    every block contribution, the contributions, and the vertex ids and
+    volumes for the right-hand side."""
+    d = len(shape)
+    n_cells = cells.shape[0]
+    nv = d + 1
+    eye = np.eye(d)
+    cc = cells[c0:c1]
+    all_pos, all_K, all_vid, all_fv = [], [], [], []
+    for ti, t in enumerate(temps):
+        vid = _lin(shape, cc[:, None, :] + t[None, :, :])          # (m, nv)
+        el = ti * n_cells + np.arange(c0, c1)
+        X = coords[vid]
+        J = np.transpose(X[:, 1:, :] - X[:, :1, :], (0, 2, 1))
+        det = np.linalg.det(J)
+        Jinv = np.linalg.inv(J)
+        g = np.empty((c1 - c0, nv, d))
+        g[:, 1:, :] = Jinv
+        g[:, 0, :] = -Jinv.sum(axis=1)
+        vol = np.abs(det) / (2.0 if d == 2 else 6.0)
+        mu, lam = _lame(E_el[el], nu_el[el])
+        G = np.einsum("mad,mbd->mab", g, g)                           # g_a . g_b
+        # K[m,a,b,i,j] = vol (mu G_ab d_ij + mu g_b,i g_a,j + lam g_a,i g_b,j)
+        K = (mu * vol)[:, None, None, None, None] * (
+            G[:, :, :, None, None] * eye[None, None, None]
+            + np.einsum("mbi,maj->mabij", g, g))
+        K += (lam * vol)[:, None, None, None, None] * np.einsum("mai,mbj->mabij", g, g)
+        for a in range(nv):
+            for b in range(nv):
+                k = off_index[tuple(t[b] - t[a])]
+                all_pos.append(posmap[vid[:, a], k])
+                all_K.append(K[:, a, b].reshape(-1, d * d))
+        all_vid.append(vid)
+        all_fv.append(vol)
+    return (np.concatenate(all_pos), np.concatenate(all_K, axis=0),
+            np.concatenate(all_vid).ravel(), np.repeat(np.concatenate(all_fv) / (d + 1), nv))
+
+
 def _assemble(shape, coords, temps, cells, rowptr, colidx, offs, posmap,
               E_el, nu_el, forces, chunk=60_000):
+    """Assembled matrix values and right-hand sides.  Element matrices of
+    several chunks are computed by a thread pool; their sums go into the
+    matrix one chunk after another in cell order, so the result does not
+    depend on the number of threads."""
+    from concurrent.futures import ThreadPoolExecutor
+    import os
     d = len(shape)
     nnzb = colidx.shape[0]
     n_all = coords.shape[0]
@@ -233,50 +278,30 @@ def _assemble(shape, coords, temps, cells, rowptr, colidx, offs, posmap,
     nrhs = forces.shape[0]
     rhs = np.zeros((nrhs, d, n_all))
     n_cells = cells.shape[0]
-    nv = d + 1
     off_index = {o: k for k, o in enumerate(offs)}
-    eye = np.eye(d)
-    for c0 in range(0, n_cells, chunk):
-        c1 = min(n_cells, c0 + chunk)
-        cc = cells[c0:c1]
-        all_pos, all_K, all_vid, all_fv = [], [], [], []
-        for ti, t in enumerate(temps):
-            vid = _lin(shape, cc[:, None, :] + t[None, :, :])          # (m, nv)
-            el = ti * n_cells + np.arange(c0, c1)
-            X = coords[vid]
-            J = np.transpose(X[:, 1:, :] - X[:, :1, :], (0, 2, 1))
-            det = np.linalg.det(J)
-            Jinv = np.linalg.inv(J)
-            g = np.empty((c1 - c0, nv, d))
-            g[:, 1:, :] = Jinv
-            g[:, 0, :] = -Jinv.sum(axis=1)
-            vol = np.abs(det) / (2.0 if d == 2 else 6.0)
-            mu, lam = _lame(E_el[el], nu_el[el])
-            G = np.einsum("mad,mbd->mab", g, g)                           # g_a . g_b
-            # K[m,a,b,i,j] = vol (mu G_ab d_ij + mu g_b,i g_a,j + lam g_a,i g_b,j)
-            K = (mu * vol)[:, None, None, None, None] * (
-                G[:, :, :, None, None] * eye[None, None, None]
-                + np.einsum("mbi,maj->mabij", g, g))
-            K += (lam * vol)[:, None, None, None, None] * np.einsum("mai,mbj->mabij", g, g)
-            for a in range(nv):
-                for b in range(nv):
-                    k = off_index[tuple(t[b] - t[a])]
-                    all_pos.append(posmap[vid[:, a], k])
-                    all_K.append(K[:, a, b].reshape(-1, d * d))
-            all_vid.append(vid)
-            all_fv.append(vol)
-        pos = np.concatenate(all_pos)
-        Kc = np.concatenate(all_K, axis=0)
-        p0 = int(pos.min())
-        span = int(pos.max()) - p0 + 1
-        for e in range(d * d):
-            acc[e, p0:p0 + span] += np.bincount(pos - p0, weights=Kc[:, e], minlength=span)
-        vids = np.concatenate(all_vid).ravel()
-        w = np.repeat(np.concatenate(all_fv) / (d + 1), nv)
-        for r in range(nrhs):
-            for i in range(d):
-                if forces[r][i] != 0.0:
-                    rhs[r, i] += forces[r][i] * np.bincount(vids, weights=w, minlength=n_all)
+    bounds = [(c0, min(n_cells, c0 + chunk)) for c0 in range(0, n_cells, chunk)]
+    workers = max(1, min(8, os.cpu_count() or 1))
+    with ThreadPoolExecutor(max_workers=workers) as ex:
+        futs = []
+        for b in bounds[:workers]:
+            futs.append(ex.submit(_element_chunk, shape, coords, temps, cells, posmap, off_index,
+                                  E_el, nu_el, *b))
+        nxt = workers
+        for i in range(len(bounds)):
+            pos, Kc, vids, w = futs[i].result()
+            futs[i] = None
+            if nxt < len(bounds):
+                futs.append(ex.submit(_element_chunk, shape, coords, temps, cells, posmap,
+                                      off_index, E_el, nu_el, *bounds[nxt]))
+                nxt += 1
+            p0 = int(pos.min())
+            span = int(pos.max()) - p0 + 1
+            for e in range(d * d):
+                acc[e, p0:p0 + span] += np.bincount(pos - p0, weights=Kc[:, e], minlength=span)
+            for r in range(nrhs):
+                for i_ in range(d):
+                    if forces[r][i_] != 0.0:
+                        rhs[r, i_] += forces[r][i_] * np.bincount(vids, weights=w, minlength=n_all)
     vals = np.ascontiguousarray(acc.T).reshape(nnzb, d, d)
     return vals, np.ascontiguousarray(np.transpose(rhs, (0, 2, 1)))
 
@@ -336,9 +361,28 @@ def make_problem(shape: Sequence[int], seed: int, h: Optional[float] = None,
         sides = brng.uniform(0.02, 0.2, size=(jump_boxes, d)) * ext
         moduli = 10.0 ** brng.uniform(-3.0, 3.0, size=jump_boxes)
         cen = coords[elements].mean(axis=1)
+        n_cells = cells.shape[0]
+        cdims = [s - 1 for s in shape]
         for bi in range(jump_boxes):
-            inside = np.all(np.abs(cen - centres[bi]) <= 0.5 * sides[bi], axis=1)
-            E_el[inside] = moduli[bi]
+            # an element's centroid lies within 0.2h of its cell, so only the
+            # elements of cells overlapping the box (with a margin) can be
+            # inside; the test itself is the same on those
+            ranges = []
+            for a in range(d):
+                lo = int(np.floor((centres[bi][a] - 0.5 * sides[bi][a]) / h)) - 2
+                hi = int(np.floor((centres[bi][a] + 0.5 * sides[bi][a]) / h)) + 2
+                ranges.append(np.arange(max(lo, 0), min(hi, cdims[a] - 1) + 1))
+            if any(r.size == 0 for r in ranges):
+                continue
+            g = np.meshgrid(*ranges, indexing="ij")
+            cid = g[0].ravel()
+            stride = 1
+            for a in range(1, d):
+                stride *= cdims[a - 1]
+                cid = cid + stride * g[a].ravel()
+            cand = (np.arange(len(temps))[:, None] * n_cells + cid[None, :]).ravel()
+            inside = np.all(np.abs(cen[cand] - centres[bi]) <= 0.5 * sides[bi], axis=1)
+            E_el[cand[inside]] = moduli[bi]
     if E_fn is not None:
         E_el = np.asarray(E_fn(coords[elements].mean(axis=1)), dtype=np.float64).reshape(n_el)
     if nu_range is not None:
