@@ -153,3 +153,19 @@ def test_candidate_of_maximal_mu_s(monkeypatch):
 def test_later_pass_in_insertion_order(monkeypatch):
     monkeypatch.setattr(CO, "later_pass_order", lambda m: list(range(m)))
     _fails(tc.test_algorithm1_later_pass_visits_in_reverse_insertion_order)
+
+
+def test_c_oracle_with_transposed_blocks(monkeypatch):
+    """The C solve phase handed every square block transposed (a plausible
+    row/column-major mix-up) must fail the dense Galerkin pin."""
+    import oracle.csolve as CS
+    from tests import test_oracle_csolve as tcs
+    orig = CS._bsr
+
+    def transposed(M):
+        rp, ci, v = orig(M)
+        if v.ndim == 3 and v.shape[1] == v.shape[2]:
+            v = np.ascontiguousarray(np.transpose(v, (0, 2, 1)))
+        return rp, ci, v
+    monkeypatch.setattr(CS, "_bsr", transposed)
+    _fails(tcs.test_galerkin_equals_dense_triple_product)
