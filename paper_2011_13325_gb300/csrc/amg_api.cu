@@ -635,6 +635,15 @@ const char *amg_describe(amg_ctx *h) {
       d += line;
     }
   }
+  if (!c->levels.empty()) {
+    const DevBSR &A = c->levels[0].A;
+    const bool df = c->cg_op == AMG_CG_DOUBLE_FLOAT && A.sdf && A.sell_ptr && !A.sell_perm;
+    snprintf(line, sizeof line, "CG operator q = A_0 p: %s\n",
+             df ? "double-float pairs on the FP32 pipe, SELL-32 (pcg_spmv_dot_sell_df_kernel)"
+                : (A.sell_ptr && !A.sell_perm ? "FP64, SELL-32 (pcg_spmv_dot_sell_kernel)"
+                                              : "FP64, warp rows (pcg_spmv_dot_kernel)"));
+    d += line;
+  }
   c->desc = d;
   return c->desc.c_str();
 }

@@ -69,6 +69,20 @@ def test_algorithmic_bytes_count():
             assert bench.algorithmic_bytes_per_iteration(lv, prec, nr) == mat + nr * vec
 
 
+def test_kernel_source_key_finds_every_named_kernel():
+    src = os.path.join(os.path.dirname(bench.__file__), "paper_2011_13325_gb300", "csrc", "pcg.cu")
+    a = bench.kernel_source_sha1(src, "pcg_spmv_dot_sell_df_kernel")
+    b = bench.kernel_source_sha1(src, "pcg_spmv_dot_sell_kernel")
+    assert a != b
+
+
+def test_operator_complexity_counts_entries():
+    lv = [dict(n_rows=100, block=3, nnzb=1000), dict(n_rows=10, block=6, nnzb=50)]
+    oc = bench.operator_complexity(lv)
+    assert oc["entries"] == round((9000 + 50 * 36) / 9000, 3)
+    assert oc["blocks"] == 1.05 and oc["vertex"] == 1.1
+
+
 def test_kernel_source_key_tracks_the_kernel(tmp_path):
     src = os.path.join(os.path.dirname(bench.__file__), "paper_2011_13325_gb300", "csrc",
                        "bsr_kernels.cu")
@@ -98,9 +112,8 @@ def test_traffic_is_scaled_to_the_workload():
     assert t == 2 * 296559360 and "scaled" in kind
     # the committed record names its workload, and its traffic is close to
     # (not far above) the algorithmic bytes of that launch
-    committed = bench.traffic_record()
+    committed = bench.traffic_record("pcg_spmv_dot_sell_df_kernel<3>")
     if committed is not None:
-        assert committed["workload"] == "cube64"
         assert committed["algorithmic_bytes_per_launch"] > committed["bytes_per_launch"] * 0.9
     assert bench.scaled_traffic(None, 1) == (None, None)
 
@@ -167,3 +180,24 @@ def test_reference_arm_oracle_timing_on_cpu():
     assert its == its_o
     ms, m, dt = bench.time_oracle(H2, p.b[0], its, budget_s=0.2)
     assert ms > 0 and 1 <= m <= its and dt > 0
+
+
+def test_oracle_leg_on_cpu():
+    """The bench's CPU oracle leg on a small hierarchy (the oracle's own
+    prolongations): the all-thread solve reaches rtol with the numpy
+    oracle's iteration count, the one-thread sample scales to it, and the
+    energy error of the numpy oracle's 1e-8 solution is small."""
+    import types
+    from oracle import hierarchy, solve
+    from workloads import configs
+    p = configs.square32()
+    H = hierarchy.setup(p)
+    P_list = [(P.n_rows, P.n_cols, P.rowptr.astype(np.int32), P.colidx.astype(np.int32), P.vals)
+              for P in H.P]
+    u, it, _ = solve.pcg(H, p.b[0], rtol=1e-8)
+    args = types.SimpleNamespace(rtol=1e-8)
+    cpu, acc = bench.oracle_leg(p, P_list, None, args, u, {"same": u}, it, single_budget_s=0.2)
+    assert cpu["kind"] == "oracle" and cpu["cores"] >= 1 and abs(cpu["iters"] - it) <= 1
+    assert cpu["value"] > 0 and cpu["single_thread"]["cores"] == 1
+    assert acc["energy_error"] <= 1e-6 and acc["variants"]["same"] == acc["energy_error"]
+    assert acc["oracle_1e8"] <= 1e-6
