@@ -43,6 +43,12 @@ WORKLOADS = {
     "cube96nu": ("3D P1 elasticity, unit cube, 96^3 vertices (seed 5), E=1, nu per element "
                  "U[0.3,0.45], clamped x=0, body force (0,0,-1); 2.65M dofs; level-0 smoother: the "
                  "learned MLP trained on ten 32^3 meshes (seeds 100-109)"),
+    "beam": ("the paper's vector model problem (Sec. 7): 3D P1 elasticity on the beam "
+             "[0,10]x[0,1]^2, h=1/32 (321x33x33 vertices, seed 6), mu=1, lambda=0, clamped x=0, "
+             "body force (0,0,-1); 1.05M dofs"),
+    "jump11": ("the paper's difficult vector problem (Sec. 7): unit cube, 67^3 vertices (seed 7), "
+               "mu=lambda=1e4 in the eleven diagonal boxes [(i-1)/11,i/11]^3, 1 elsewhere, clamped "
+               "x=0, body force (0,0,-1); 888,822 dofs; 4 matching passes first, 3 later"),
     "batch64": ("64 independent 3D P1 elasticity boxes, vertices per axis U{16..48}, h=1/32, "
                 "E U[0.1,10], nu U[0.2,0.4] per system (seed 4), clamped x=0, 6 load cases "
                 "(unit body forces +-x, +-y, +-z) each"),
@@ -60,7 +66,17 @@ def make_workload(name):
         return configs.cube128jump()
     if name == "cube96nu":
         return configs.cube96nu()
+    if name == "beam":
+        return configs.beam()
+    if name == "jump11":
+        return configs.jump11()
     raise SystemExit(f"unknown workload {name}")
+
+
+def setup_params(name):
+    """amg_setup parameters the paper gives for this workload (Sec. 7)."""
+    from workloads import configs
+    return dict(configs.SETUP.get(name, {}))
 
 
 def peaks():
@@ -344,7 +360,7 @@ def run_single(args, ws, rank, local, train_problems):
     ctx.set_pcg_graph(args.pcg_mode == "graph")
     ctx.set_cg_operator(cg_mode)
     t0 = time.perf_counter()
-    ctx.setup(problem, args.precision)
+    ctx.setup(problem, args.precision, **setup_params(args.workload))
     torch.cuda.synchronize()
     setup_s = time.perf_counter() - t0
     setup_parts = {k: round(v, 2) for k, v in ctx.setup_times().items()}
@@ -648,7 +664,7 @@ def run_reference(args, ws, rank, local):
     from paper_2011_13325_gb300 import amg
     problem = make_workload(args.workload)
     ctx = amg.Context(local)
-    ctx.setup(problem, amg.AMG_PREC_FP64)
+    ctx.setup(problem, amg.AMG_PREC_FP64, **setup_params(args.workload))
     P_list = [ctx.download_prolongation(l) for l in range(ctx.n_levels - 1)]
     ctx.close()
     A0 = solve.mat_from(problem.A)

@@ -87,7 +87,7 @@ struct HostGalerkinSink : LevelSink {
 
 int main(int argc, char **argv) {
   if (argc < 3) {
-    fprintf(stderr, "usage: %s <dir> <coarse_max>\n", argv[0]);
+    fprintf(stderr, "usage: %s <dir> <coarse_max> [passes_first passes_later]\n", argv[0]);
     return 2;
   }
   const std::string dir = argv[1];
@@ -113,6 +113,10 @@ int main(int argc, char **argv) {
   pb.vals = vals.data();
   SetupParams prm;
   prm.coarse_max = atoi(argv[2]);
+  if (argc > 4) {  // matching passes on the first / later levels
+    prm.passes_first = atoi(argv[3]);
+    prm.passes_later = atoi(argv[4]);
+  }
   HostGalerkinSink sink;
   std::string err;
   if (build_levels(pb, prm, sink, err) != 0) {

@@ -30,6 +30,12 @@ CASES = {
     # 3D 9x7x8 jump coefficients + per-element nu (ragged sizes)
     "box_jump": lambda: (make_problem((9, 7, 8), seed=3, jump_boxes=6, nu_range=(0.25, 0.45)),
                          hierarchy.SetupParams(coarse_max=6)),
+    # Sec. 7's vector model problem: beam [0,10] x [0,1]^2, mu = 1, lambda = 0
+    "beam": lambda: (configs.beam(4), hierarchy.SetupParams(coarse_max=8)),
+    # Sec. 7's difficult problem: eleven diagonal boxes with mu = lambda = 10^4
+    # (one cell per box side), 4 passes on the first level and 3 later
+    "jump11": lambda: (configs.jump11(12), hierarchy.SetupParams(coarse_max=8, passes_first=4,
+                                                                  passes_later=3)),
 }
 
 

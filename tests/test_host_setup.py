@@ -35,6 +35,8 @@ CASES = {
                  {"coarse_max": 6}),
     "rect2d_nu": (lambda: make_problem((41, 23), seed=9, nu_range=(0.3, 0.45)), {"coarse_max": 10}),
     "checker2d": (lambda: make_problem((17, 17), seed=1, nu=0.25, E_fn=_checker), {"coarse_max": 4}),
+    "beam": (lambda: configs.beam(4), {"coarse_max": 8}),
+    "jump11": (lambda: configs.jump11(12), {"coarse_max": 8, "passes_first": 4, "passes_later": 3}),
 }
 
 
@@ -100,7 +102,9 @@ def test_host_setup_matches_oracle_setup(harness, tmp_path, name, threads):
     p, kw, H = _oracle(name)
     _write_problem(p, str(tmp_path))
     env = dict(os.environ, OMP_NUM_THREADS=str(threads))
-    r = subprocess.run([harness, str(tmp_path), str(kw.get("coarse_max", 0))], capture_output=True,
+    r = subprocess.run([harness, str(tmp_path), str(kw.get("coarse_max", 0)),
+                        str(kw.get("passes_first", 5)), str(kw.get("passes_later", 4))],
+                       capture_output=True,
                        text=True, env=env, timeout=300)
     assert r.returncode == 0, r.stderr
     Ps = _read_prolongations(str(tmp_path))

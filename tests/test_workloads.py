@@ -100,3 +100,25 @@ def test_jump_boxes_and_nu_per_element():
     A = _csr(p.A).toarray()
     assert np.abs(A - A.T).max() <= 1e-12 * np.abs(A).max()
     assert np.linalg.eigvalsh(A).min() > 0
+
+
+def test_paper_workloads_beam_and_eleven_boxes():
+    """Sec. 7's vector model problem (beam [0,10] x [0,1]^2, clamped at
+    x = 0, mu = 1, lambda = 0) and the difficult problem (eleven diagonal
+    boxes [(i-1)/11, i/11]^3 with mu = lambda = 10^4, 1 elsewhere)."""
+    from workloads import configs
+    p = configs.beam(4)
+    assert p.shape == (41, 5, 5) and abs(p.coords[:, 0].max() - 10.0) < 1e-12
+    assert np.allclose(p.coords[:, 1:].max(axis=0), 1.0)
+    assert p.n_free == 41 * 25 - 25 and np.all(p.nu_el == 0.0) and np.all(p.E_el == 1.0)
+    q = configs.jump11(23)              # two cells per box side
+    cen = q.coords[q.elements].mean(axis=1)
+    k = np.floor(cen * 11).clip(0, 10)
+    inside = (k[:, 0] == k[:, 1]) & (k[:, 1] == k[:, 2])
+    mu = q.E_el / (1.0 + q.nu_el)       # the paper's mu (= 2 mu of the Hooke law)
+    lam = q.E_el * q.nu_el / ((1 + q.nu_el) * (1 - 2 * q.nu_el))
+    assert np.allclose(mu[inside], 1e4) and np.allclose(mu[~inside], 1.0)
+    assert np.allclose(lam, mu)         # mu = lambda in the paper's form
+    # every one of the eleven boxes holds elements (48 per box at 2 cells per side)
+    assert sorted(np.unique(k[inside, 0]).astype(int).tolist()) == list(range(11))
+    assert inside.sum() == 11 * 8 * 6

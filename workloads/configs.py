@@ -15,6 +15,18 @@ which are not available: same operator (P1 linear elasticity, Problem
   body forces), seed 4.
 * ``cube96nu``  3D unit cube, 96^3 vertices, E=1, nu per element U[0.3,0.45],
   seed 5; the learned smoother trains on ten 32^3 meshes (seeds 100..109).
+
+The paper's own three workloads (Sec. 7), on structured perturbed meshes:
+
+* ``beam``      the vector model problem: the beam [0,10] x [0,1]^2 clamped
+  at x = 0 with mu = 1, lambda = 0 (E = 1, nu = 0 in the Hooke law
+  2 mu eps:eps + lambda div div, whose 2 mu is the paper's mu); default
+  h = 1/32 -> 321 x 33 x 33 vertices, 348,480 free, 1.05M dofs; seed 6.
+* ``jump11``    the difficult vector problem: the unit cube clamped at x = 0,
+  mu = lambda = 10^4 in the eleven diagonal boxes [(i-1)/11, i/11]^3 and
+  mu = lambda = 1 elsewhere (nu = 1/3, E = 4/3 mu); default 67^3 vertices
+  (six cells per box side), 296,274 free, 888,822 dofs; seed 7.
+Body forces are not given in the paper; both use (0, 0, -1).
 """
 from __future__ import annotations
 
@@ -68,3 +80,31 @@ def cube96nu(n: int = 96, seed: int = 5):
 def training_meshes(n: int = 32, seeds=range(100, 110)):
     return [make_problem((n, n, n), seed=s, E=1.0, forces=[[0.0, 0.0, -1.0]],
                          nu_range=(0.3, 0.45), name=f"train{n}_{s}") for s in seeds]
+
+
+BEAM_LENGTH = 10
+
+
+def beam(m: int = 32, seed: int = 6):
+    """The beam [0,10] x [0,1]^2 with h = 1/m (10m+1 x m+1 x m+1 vertices)."""
+    return make_problem((BEAM_LENGTH * m + 1, m + 1, m + 1), seed=seed, h=1.0 / m, E=1.0, nu=0.0,
+                        forces=[[0.0, 0.0, -1.0]], name=f"beam{m}")
+
+
+def jump11_modulus(c, mu_in=1e4, mu_out=1.0, nu=1.0 / 3.0, boxes=11):
+    """E per element centroid c: mu_in inside the union of the boxes
+    [(i-1)/boxes, i/boxes]^3, mu_out elsewhere, as E = mu (1 + nu)."""
+    idx = np.floor(np.asarray(c) * boxes).clip(0, boxes - 1)
+    inside = (idx[:, 0] == idx[:, 1]) & (idx[:, 1] == idx[:, 2])
+    return np.where(inside, mu_in, mu_out) * (1.0 + nu)
+
+
+def jump11(n: int = 67, seed: int = 7):
+    """The difficult vector problem on n^3 vertices of the unit cube."""
+    return make_problem((n, n, n), seed=seed, nu=1.0 / 3.0, forces=[[0.0, 0.0, -1.0]],
+                        E_fn=jump11_modulus, name=f"jump11_{n}")
+
+
+# Setup parameters the paper states per workload (Sec. 7); the rest are the
+# defaults (5 passes on the first level and 4 later, caps 8 / 6 / 4).
+SETUP = {"jump11": {"passes_first": 4, "passes_later": 3}}
