@@ -10,7 +10,12 @@ TEST INFRASTRUCTURE ONLY (see ``oracle/__init__``).
 * Smoother: block version of the l1 smoother (Sec. 7): blocks are the dofs
   of one vertex, M_v = A_vv + diag(sum of |a_rc| over the columns c outside
   the block), applied as block Jacobi; singular M_v are pseudo-inverted
-  (Sec. 3 after Lemma eet_is_diag, "pseudo smoother").
+  (Sec. 3 after Lemma eet_is_diag, "pseudo smoother").  The other form of
+  the l1 smoothers the paper cites, hybrid Gauss-Seidel, is read for one
+  device as block Gauss-Seidel over the colour classes of a distance-1
+  colouring (a class plays the part of a processor's block; the l1 term
+  covers couplings inside a class, of which a distance-1 colouring has
+  none): forward sweep before, backward sweep after the coarse correction.
 * Coarsest level: A_L + (I - E_L E_L^T) with E_L spanning the orthogonal
   complement of the kernels of the diagonal blocks (Lemma eet_is_diag and
   the regularisation identity of Sec. 3 after Lemma eet_is_diag), solved by Cholesky.
@@ -125,6 +130,39 @@ def block_l1_inverse(A: Mat):
     return batched_pinv(Mv, KERNEL_RTOL)
 
 
+def greedy_colouring(A: Mat):
+    """Distance-1 colouring of the block graph of A: block rows in index
+    order, each takes the smallest colour that none of its already coloured
+    neighbours holds.  Rows of one colour never couple."""
+    n = A.n_rows
+    col = -np.ones(n, dtype=np.int64)
+    for i in range(n):
+        nb = A.colidx[A.rowptr[i]:A.rowptr[i + 1]]
+        used = set(col[nb].tolist())
+        c = 0
+        while c in used:
+            c += 1
+        col[i] = c
+    return col
+
+
+def hybrid_gs_inverse(A: Mat, colour):
+    """(M_v)^+ of the block-l1 hybrid Gauss-Seidel smoother: M_v = A_vv +
+    diag_r(sum of |a_rc| over the columns c of the other rows of v's own
+    colour), the couplings a colour-parallel sweep treats Jacobi-wise; with a
+    distance-1 colouring there are none and M_v = A_vv."""
+    n, k = A.n_rows, A.br
+    rows = np.repeat(np.arange(n), np.diff(A.rowptr))
+    diag = A.colidx == rows
+    Mv = np.zeros((n, k, k))
+    Mv[rows[diag]] = A.vals[diag]
+    same = (~diag) & (colour[A.colidx] == colour[rows])
+    l1 = np.zeros((n, k))
+    np.add.at(l1, rows[same], np.abs(A.vals[same]).sum(axis=2))
+    Mv[:, np.arange(k), np.arange(k)] += l1
+    return batched_pinv(Mv, KERNEL_RTOL)
+
+
 def batched_pinv(B, rtol):
     """Symmetric pseudo-inverse of every block (eigenvalues <= rtol * max|w| dropped)."""
     w, V = np.linalg.eigh(0.5 * (B + np.transpose(B, (0, 2, 1))))
@@ -168,20 +206,30 @@ class Hierarchy:
     Minv: list = dataclasses.field(default_factory=list)
     coarse_chol: object = None
     info: dict = dataclasses.field(default_factory=dict)
+    smoother: str = "l1_jacobi"           # or "hybrid_gs"
+    colour: list = dataclasses.field(default_factory=list)
 
     @property
     def n_levels(self):
         return len(self.A)
 
 
-def prepare(A0: Mat, P: List[Mat]) -> Hierarchy:
-    """Galerkin coarse matrices, explicit R = P^T, smoothers, coarsest factor."""
+def prepare(A0: Mat, P: List[Mat], smoother: str = "l1_jacobi") -> Hierarchy:
+    """Galerkin coarse matrices, explicit R = P^T, smoothers, coarsest factor.
+    smoother: "l1_jacobi" (block-l1 Jacobi) or "hybrid_gs" (block-l1 hybrid
+    Gauss-Seidel over the colour classes of greedy_colouring)."""
     A = [A0]
     for Pl in P:
         A.append(galerkin(Pl, A[-1]))
-    H = Hierarchy(A=A, P=list(P))
+    H = Hierarchy(A=A, P=list(P), smoother=smoother)
     H.R = [transpose(Pl) for Pl in P]
-    H.Minv = [block_l1_inverse(Al) for Al in A[:-1]]
+    if smoother == "hybrid_gs":
+        H.colour = [greedy_colouring(Al) for Al in A[:-1]]
+        H.Minv = [hybrid_gs_inverse(Al, c) for Al, c in zip(A[:-1], H.colour)]
+    elif smoother == "l1_jacobi":
+        H.Minv = [block_l1_inverse(Al) for Al in A[:-1]]
+    else:
+        raise ValueError(f"unknown smoother {smoother}")
     H.coarse_chol = sla.cho_factor(coarsest_matrix(A[-1]), lower=True)
     return H
 
@@ -193,6 +241,24 @@ def smooth(A: Mat, Minv, b, x=None):
     return x + block_apply(Minv, b - spmv(A, x))
 
 
+def gs_sweep(A: Mat, Minv, colour, b, x=None, forward=True):
+    """One block-l1 hybrid Gauss-Seidel sweep: the colour classes in
+    increasing (forward) or decreasing (backward) order; the rows of a class
+    take x_v <- x_v + M_v^+ (b - A x)_v with x as updated by the classes
+    before (Jacobi-wise inside a class).  x = None starts from x = 0."""
+    n, k = A.n_rows, A.br
+    x = np.zeros(n * k) if x is None else x.copy()
+    As = A.scipy()
+    ncol = int(colour.max()) + 1 if n else 0
+    order = range(ncol) if forward else range(ncol - 1, -1, -1)
+    for c in order:
+        rows = np.nonzero(colour == c)[0]
+        dofs = (rows[:, None] * k + np.arange(k)).ravel()
+        r = (b[dofs] - As[dofs] @ x).reshape(-1, k)
+        x[dofs] += np.einsum("nij,nj->ni", Minv[rows], r).ravel()
+    return x
+
+
 def coarse_solve(H: Hierarchy, b):
     return sla.cho_solve(H.coarse_chol, b)
 
@@ -202,6 +268,14 @@ def vcycle(H: Hierarchy, b, level=0):
     if level == H.n_levels - 1:
         return coarse_solve(H, b)
     A, Minv = H.A[level], H.Minv[level]
+    if H.smoother == "hybrid_gs":
+        # forward sweep before, backward sweep after: the post-smoother is the
+        # adjoint of the pre-smoother, so the V-cycle stays symmetric
+        col = H.colour[level]
+        x = gs_sweep(A, Minv, col, b, None, forward=True)
+        bc = spmv(H.R[level], b - spmv(A, x))
+        x = x + spmv(H.P[level], vcycle(H, bc, level + 1))
+        return gs_sweep(A, Minv, col, b, x, forward=False)
     x = smooth(A, Minv, b)
     r = b - spmv(A, x)
     bc = spmv(H.R[level], r)

@@ -169,3 +169,25 @@ def test_c_oracle_with_transposed_blocks(monkeypatch):
         return rp, ci, v
     monkeypatch.setattr(CS, "_bsr", transposed)
     _fails(tcs.test_galerkin_equals_dense_triple_product)
+
+
+def test_gauss_seidel_post_sweep_not_reversed(monkeypatch):
+    """Both sweeps forward: the V-cycle is no longer symmetric."""
+    from tests import test_oracle_gs as tg
+    orig = S.gs_sweep
+    monkeypatch.setattr(S, "gs_sweep", lambda A, M, c, b, x=None, forward=True: orig(A, M, c, b, x, True))
+    _fails(tg.test_gs_vcycle_symmetric_positive_and_two_grid_contracts)
+
+
+def test_gauss_seidel_with_stale_values(monkeypatch):
+    """A sweep that reads the values from before the sweep (block Jacobi
+    with the Gauss-Seidel blocks) fails the splitting pin."""
+    from tests import test_oracle_gs as tg
+
+    def jacobi_like(A, Minv, colour, b, x=None, forward=True):
+        n, k = A.n_rows, A.br
+        x0 = np.zeros(n * k) if x is None else x.copy()
+        r = (b - A.scipy() @ x0).reshape(n, k)
+        return x0 + np.einsum("nij,nj->ni", Minv, r).ravel()
+    monkeypatch.setattr(S, "gs_sweep", jacobi_like)
+    _fails(tg.test_sweep_equals_block_triangular_splitting)
