@@ -88,10 +88,29 @@ enum {
   AMG_PREC_BF16_STORAGE = 2   /* as FP32 but A_l, P_l, R_l stored in BF16     */
 };
 
-/* Smoother on the finest level. */
+/* Smoother of the V-cycle.
+ *  AMG_SMOOTHER_L1_JACOBI  block-l1 Jacobi (Sec. 7) on every level.
+ *  AMG_SMOOTHER_LEARNED    level 0 uses the blocks of amg_set_learned_smoother
+ *                          (set by that call, not accepted by the uploads).
+ *  AMG_SMOOTHER_HYBRID_GS  block-l1 hybrid Gauss-Seidel, the other form of the
+ *                          l1 smoothers Sec. 7 cites, read for one device:
+ *                          the block rows of every level are coloured at
+ *                          upload (greedy, rows in index order, each the
+ *                          smallest colour no already coloured neighbour
+ *                          holds: a distance-1 colouring) and a sweep visits
+ *                          the colour classes in order, every row of a class
+ *                          x_v <- x_v + M_v^+ (b - A x)_v with the values of
+ *                          the classes before (one kernel per class); M_v =
+ *                          A_vv + diag of the |entries| coupling v to rows of
+ *                          its own class (none for a distance-1 colouring).
+ *                          Forward sweep before the coarse correction,
+ *                          backward sweep after it (the V-cycle stays
+ *                          symmetric).  Not available to amg_batch_create,
+ *                          amg_vcycle_static or amg_set_learned_smoother. */
 enum {
-  AMG_SMOOTHER_L1_JACOBI = 0, /* block-l1 Jacobi (Sec. 7)                     */
-  AMG_SMOOTHER_LEARNED = 1    /* per-vertex blocks of amg_set_learned_smoother  */
+  AMG_SMOOTHER_L1_JACOBI = 0,
+  AMG_SMOOTHER_LEARNED = 1,
+  AMG_SMOOTHER_HYBRID_GS = 2
 };
 
 /* Create a context (library plumbing, no counterpart in the paper) on CUDA
@@ -178,6 +197,12 @@ int amg_coarse_solve(amg_ctx *ctx, const double *b_dev, double *x_dev);
  * one post-smoothing sweep, zero initial guess) on the finest level, in the
  * context's precision.  nrhs vectors stored one after another. */
 int amg_vcycle(amg_ctx *ctx, const double *r_dev, double *z_dev, int nrhs);
+
+/* Colour of every block row of level `level` under AMG_SMOOTHER_HYBRID_GS
+ * (colour_out: n_rows int32, host; may be NULL) and the number of colours.
+ * 0 <= level < n_levels - 1.  Errors: AMG_ERR_STATE (no hierarchy or another
+ * smoother), AMG_ERR_ARG. */
+int amg_smoother_colouring(amg_ctx *ctx, int level, int32_t *colour_out, int32_t *n_colours);
 
 /* Solve A_0 u = f by FP64 PCG with one V-cycle as preconditioner (Sec. 7).
  * u_dev holds the initial guess on entry and the solution on return.  Stops
@@ -456,8 +481,8 @@ typedef struct amg_batch amg_batch;
  * length-sorted slices as in the single-system layout; block lanes, 8 or 16
  * lanes per block row with one whole block per lane, for 6x6 and 6x3
  * blocks) and the fastest is kept (amg_batch_describe lists the choices).
- * Errors: AMG_ERR_ARG, AMG_ERR_STATE (a context without hierarchy),
- * AMG_ERR_CUDA. */
+ * Errors: AMG_ERR_ARG (also: a context with AMG_SMOOTHER_HYBRID_GS),
+ * AMG_ERR_STATE (a context without hierarchy), AMG_ERR_CUDA. */
 int amg_batch_create(amg_batch **batch, amg_ctx *const *systems, int n_systems, int nrhs);
 void amg_batch_destroy(amg_batch *batch);
 const char *amg_batch_last_error(const amg_batch *batch);

@@ -35,6 +35,7 @@ AMG_LAYOUT_ROW_LANES = 3
 AMG_LAYOUT_BLOCK_LANES = 4
 AMG_SMOOTHER_L1_JACOBI = 0
 AMG_SMOOTHER_LEARNED = 1
+AMG_SMOOTHER_HYBRID_GS = 2
 AMG_CG_FP64 = 0
 AMG_CG_DOUBLE_FLOAT = 1
 
@@ -114,6 +115,7 @@ _SIGS = {
     "amg_profile_vcycle": (_I, [_P, _I, _P, _P, _P, _P, _I, C.POINTER(C.c_int32)]),
     "amg_profile_pcg": (_I, [_P, _I, _P, _P, _P, _I, C.POINTER(C.c_int32)]),
     "amg_set_cg_operator": (_I, [_P, _I]),
+    "amg_smoother_colouring": (_I, [_P, _I, _P, C.POINTER(C.c_int32)]),
     "amg_cg_operator": (_I, [_P, _P, _P]),
     "amg_mlp_create": (_I, [C.POINTER(_P), _I, C.c_uint64]),
     "amg_mlp_destroy": (None, [_P]),
@@ -471,6 +473,15 @@ class Context:
         self._check(lib().amg_profile_pcg(self.h, int(reps), kd.ctypes.data, us.ctypes.data,
                                           by.ctypes.data, 8, C.byref(n)))
         return [(self.PCG_KINDS[kd[i]], float(us[i]), float(by[i])) for i in range(min(n.value, 8))]
+
+    def smoother_colouring(self, level):
+        """(colour of every block row of `level`, number of colours) under
+        the hybrid Gauss-Seidel smoother."""
+        info = self.level_info(level)
+        col = np.zeros(max(info["n_rows"], 1), dtype=np.int32)
+        nc = C.c_int32()
+        self._check(lib().amg_smoother_colouring(self.h, int(level), col.ctypes.data, C.byref(nc)))
+        return col[:info["n_rows"]], nc.value
 
     def set_cg_operator(self, mode: int):
         """AMG_CG_FP64 or AMG_CG_DOUBLE_FLOAT (default): arithmetic of q = A_0 p in the PCG."""

@@ -44,7 +44,8 @@ void free_levels(Ctx *c) {
     free_bsr(L.A);
     free_bsr(L.P);
     free_bsr(L.R);
-    void *ptrs[] = {L.minv64, L.minv32, L.b64, L.x64, L.t64, L.y64, L.b32, L.x32, L.t32, L.y32};
+    void *ptrs[] = {L.minv64, L.minv32, L.b64, L.x64, L.t64, L.y64, L.b32, L.x32, L.t32, L.y32,
+                    L.gs_colour, L.gs_rows};
     for (void *p : ptrs) dfree(p);
   }
   c->levels.clear();
@@ -101,6 +102,22 @@ static cudaError_t vcycle_level(Ctx *c, int l, const void *b, void *y, const dou
   void *x = vb(L, prec, 'x');
   void *t = vb(L, prec, 't');
   const void *mi = minv_of(L, prec);
+  if (c->smoother == AMG_SMOOTHER_HYBRID_GS) {
+    const size_t n = (size_t)L.A.n_rows * L.k;
+    const size_t w = prec == AMG_PREC_FP64 ? sizeof(double) : sizeof(float);
+    if (r64) AMG_CUDA_TRY(launch_convert(c, n, r64, AMG_PREC_FP64, (void *)b, AMG_PREC_FP32_VCYCLE));
+    // forward sweep from x = 0
+    AMG_CUDA_TRY(cudaMemsetAsync(x, 0, n * w, c->stream));
+    AMG_CUDA_TRY(launch_gs_sweep(c, L, prec, b, x, true));
+    AMG_CUDA_TRY(launch_bsr(c, L.A, prec, SPMV_RESID, x, b, nullptr, t));
+    AMG_CUDA_TRY(launch_bsr(c, L.R, prec, SPMV_SET, t, nullptr, nullptr, vb(Cn, prec, 'b')));
+    AMG_CUDA_TRY(vcycle_level(c, l + 1, vb(Cn, prec, 'b'), vb(Cn, prec, 'y')));
+    AMG_CUDA_TRY(launch_bsr(c, L.P, prec, SPMV_ADD, vb(Cn, prec, 'y'), nullptr, nullptr, x));
+    // backward sweep (the adjoint of the forward one)
+    AMG_CUDA_TRY(launch_gs_sweep(c, L, prec, b, x, false));
+    if (z64) return launch_convert(c, n, x, AMG_PREC_FP32_VCYCLE, z64, AMG_PREC_FP64);
+    return cudaMemcpyAsync(y, x, n * w, cudaMemcpyDeviceToDevice, c->stream);
+  }
   // pre-smoothing from x = 0: x = M^+ b
   if (r64)
     AMG_CUDA_TRY(launch_blockdiag_entry(c, L.A.n_rows, L.k, L.minv32, r64, (float *)b, (float *)x));
@@ -426,6 +443,8 @@ static int finalize_hierarchy(Ctx *c) {
   const int precision = c->precision;
   for (int l = 0; l < (int)c->levels.size(); ++l) {
     Level &L = c->levels[l];
+    if (l + 1 < (int)c->levels.size() && c->smoother == AMG_SMOOTHER_HYBRID_GS)
+      CUDA_OR_FAIL(c, gs_prepare(c, l), "colouring");
     if (l + 1 < (int)c->levels.size()) CUDA_OR_FAIL(c, smoother_setup(c, l), "smoother setup");
     CUDA_OR_FAIL(c, alloc_level_vectors(c, L), "level vectors");
     DevBSR *ops[] = {&L.A, &L.P, &L.R};
@@ -581,13 +600,21 @@ int amg_profile_vcycle(amg_ctx *h, int reps, int32_t *level, int32_t *kind, doub
     Level &Cn = c->levels[l + 1];
     const void *mi = minv_of(L, prec);
     const bool entry = l == 0 && prec != AMG_PREC_FP64;  // FP64 residual in, FP64 z out
-    if (entry)
+    const bool gs = c->smoother == AMG_SMOOTHER_HYBRID_GS;
+    // a hybrid Gauss-Seidel sweep reads every block and writes x once
+    const double gs_bytes = op_bytes(L.A, prec, wv, 1) + N * L.k * wv + N * wv;
+    if (gs) {
+      CUDA_OR_FAIL(c, time_launch(c, reps, [&] {
+        cudaError_t e = cudaMemsetAsync(x, 0, (size_t)N * (size_t)wv, c->stream);
+        return e == cudaSuccess ? launch_gs_sweep(c, L, prec, b, x, true) : e; }, &t), "profile");
+      put(l, 0, t, gs_bytes);
+    } else if (entry)
       CUDA_OR_FAIL(c, time_launch(c, reps, [&] {
         return launch_blockdiag_entry(c, L.A.n_rows, L.k, L.minv32, c->r, (float *)b, (float *)x); }, &t), "profile");
     else
       CUDA_OR_FAIL(c, time_launch(c, reps, [&] { return launch_blockdiag(c, L.A.n_rows, L.k, prec, mi, b, x); }, &t),
                    "profile");
-    put(l, 0, t, N * L.k * wv + N * (entry ? 8.0 + 2 * wv : 2 * wv));
+    if (!gs) put(l, 0, t, N * L.k * wv + N * (entry ? 8.0 + 2 * wv : 2 * wv));
     CUDA_OR_FAIL(c, time_launch(c, reps, [&] { return launch_bsr(c, L.A, prec, SPMV_RESID, x, b, nullptr, tt); }, &t),
                  "profile");
     put(l, 1, t, op_bytes(L.A, prec, wv, 1) + N * wv);
@@ -597,6 +624,12 @@ int amg_profile_vcycle(amg_ctx *h, int reps, int32_t *level, int32_t *kind, doub
     CUDA_OR_FAIL(c, time_launch(c, reps, [&] {
       return launch_bsr(c, L.P, prec, SPMV_ADD, vb(Cn, prec, 'y'), nullptr, nullptr, x); }, &t), "profile");
     put(l, 3, t, op_bytes(L.P, prec, wv, 2));
+    if (gs) {
+      CUDA_OR_FAIL(c, time_launch(c, reps, [&] { return launch_gs_sweep(c, L, prec, b, x, false); }, &t),
+                   "profile");
+      put(l, 4, t, gs_bytes);
+      continue;
+    }
     if (entry)
       CUDA_OR_FAIL(c, time_launch(c, reps, [&] {
         return launch_smooth_out64(c, L.A, prec, (const float *)x, (const float *)b, L.minv32, c->z); }, &t),
@@ -655,7 +688,8 @@ int amg_upload_hierarchy(amg_ctx *h, const amg_hierarchy *hier, int precision, i
     return fail(c, AMG_ERR_ARG, "hierarchy: need n_levels >= 1 and P for n_levels > 1");
   if (precision < AMG_PREC_FP64 || precision > AMG_PREC_BF16_STORAGE)
     return fail(c, AMG_ERR_ARG, "unknown precision");
-  if (smoother != AMG_SMOOTHER_L1_JACOBI) return fail(c, AMG_ERR_ARG, "unknown smoother");
+  if (smoother != AMG_SMOOTHER_L1_JACOBI && smoother != AMG_SMOOTHER_HYBRID_GS)
+    return fail(c, AMG_ERR_ARG, "unknown smoother");
   const amg_bsr &A0 = hier->A0;
   int s = validate_bsr(c, A0, "A0");
   if (s) return s;
@@ -1068,7 +1102,8 @@ int amg_setup(amg_ctx *h, const amg_problem *prob, const amg_setup_params *param
     return fail(c, AMG_ERR_ARG, "amg_setup: bad problem");
   if (precision < AMG_PREC_FP64 || precision > AMG_PREC_BF16_STORAGE)
     return fail(c, AMG_ERR_ARG, "unknown precision");
-  if (smoother != AMG_SMOOTHER_L1_JACOBI) return fail(c, AMG_ERR_ARG, "unknown smoother");
+  if (smoother != AMG_SMOOTHER_L1_JACOBI && smoother != AMG_SMOOTHER_HYBRID_GS)
+    return fail(c, AMG_ERR_ARG, "unknown smoother");
   const amg_bsr &A = prob->A_full;
   int s = validate_bsr(c, A, "A_full");
   if (s) return s;

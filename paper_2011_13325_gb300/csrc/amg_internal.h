@@ -61,6 +61,11 @@ struct Level {
   // V-cycle work vectors (n * k), FP64 and FP32 sets
   double *b64 = nullptr, *x64 = nullptr, *t64 = nullptr, *y64 = nullptr;
   float *b32 = nullptr, *x32 = nullptr, *t32 = nullptr, *y32 = nullptr;
+  // hybrid Gauss-Seidel: colour of every block row (device), the rows ordered
+  // by colour then index (device), and the class offsets (host, n_colours+1)
+  int *gs_colour = nullptr;
+  int *gs_rows = nullptr;
+  std::vector<int> gs_ptr;
 };
 
 // Scalars of the device-resident PCG iteration.
@@ -165,6 +170,11 @@ cudaError_t launch_convert(const Ctx *c, size_t n, const void *src, int src_prec
 // setup kernels
 cudaError_t galerkin_device(Ctx *c, int level);
 cudaError_t smoother_setup(Ctx *c, int level);
+// hybrid Gauss-Seidel: colouring of level l (host greedy, uploaded), and one
+// sweep over the colour classes (forward or backward) updating x in place
+cudaError_t gs_prepare(Ctx *c, int level);
+cudaError_t launch_gs_sweep(const Ctx *c, const Level &L, int prec, const void *b, void *x,
+                            bool forward);
 cudaError_t coarse_setup(Ctx *c);
 cudaError_t make_low_precision(Ctx *c, DevBSR &m, int prec);
 cudaError_t build_sell(Ctx *c, DevBSR &m);

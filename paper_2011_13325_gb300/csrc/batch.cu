@@ -694,6 +694,8 @@ int amg_batch_create(amg_batch **out, amg_ctx *const *systems, int n_systems, in
     if (s > 0 && (systems[s]->c.device != systems[0]->c.device ||
                   systems[s]->c.precision != systems[0]->c.precision))
       return AMG_ERR_ARG;
+    // the grouped V-cycle runs the block-l1 Jacobi (or learned) smoother only
+    if (systems[s]->c.smoother == AMG_SMOOTHER_HYBRID_GS) return AMG_ERR_ARG;
   }
   amg_batch *hb = new amg_batch();
   Batch *B = &hb->b;

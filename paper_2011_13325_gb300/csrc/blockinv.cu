@@ -59,10 +59,12 @@ __device__ void jacobi_eig(double *a, double *v) {
 }
 
 // One thread per block row: assemble M_v, eigen-decompose, pseudo-invert.
+// With colour (hybrid Gauss-Seidel) the l1 term sums only the couplings to
+// rows of v's own colour class; without it (block-l1 Jacobi), all of them.
 template <int K>
 __global__ void l1_pinv_kernel(int n, const int *__restrict__ rowptr, const int *__restrict__ colidx,
                                const double *__restrict__ vals, double *__restrict__ minv,
-                               float *__restrict__ minv32) {
+                               float *__restrict__ minv32, const int *__restrict__ colour) {
   const int v = blockIdx.x * blockDim.x + threadIdx.x;
   if (v >= n) return;
   double a[K * K], e[K * K], l1[K];
@@ -72,7 +74,7 @@ __global__ void l1_pinv_kernel(int n, const int *__restrict__ rowptr, const int 
     const double *blk = vals + (size_t)p * K * K;
     if (colidx[p] == v) {
       for (int i = 0; i < K * K; ++i) a[i] += blk[i];
-    } else {
+    } else if (!colour || colour[colidx[p]] == colour[v]) {
       for (int r = 0; r < K; ++r)
         for (int c = 0; c < K; ++c) l1[r] += fabs(blk[r * K + c]);
     }
@@ -114,12 +116,13 @@ cudaError_t smoother_setup(Ctx *c, int level) {
   if (n == 0) return cudaSuccess;
   const int g = (n + 127) / 128;
   float *m32 = (c->precision != AMG_PREC_FP64) ? L.minv32 : nullptr;
+  const int *col = c->smoother == AMG_SMOOTHER_HYBRID_GS ? L.gs_colour : nullptr;
   if (k == 2)
-    l1_pinv_kernel<2><<<g, 128, 0, c->stream>>>(n, L.A.rowptr, L.A.colidx, L.A.v64, L.minv64, m32);
+    l1_pinv_kernel<2><<<g, 128, 0, c->stream>>>(n, L.A.rowptr, L.A.colidx, L.A.v64, L.minv64, m32, col);
   else if (k == 3)
-    l1_pinv_kernel<3><<<g, 128, 0, c->stream>>>(n, L.A.rowptr, L.A.colidx, L.A.v64, L.minv64, m32);
+    l1_pinv_kernel<3><<<g, 128, 0, c->stream>>>(n, L.A.rowptr, L.A.colidx, L.A.v64, L.minv64, m32, col);
   else if (k == 6)
-    l1_pinv_kernel<6><<<g, 128, 0, c->stream>>>(n, L.A.rowptr, L.A.colidx, L.A.v64, L.minv64, m32);
+    l1_pinv_kernel<6><<<g, 128, 0, c->stream>>>(n, L.A.rowptr, L.A.colidx, L.A.v64, L.minv64, m32, col);
   else
     return cudaErrorInvalidValue;
   return cudaGetLastError();

@@ -918,6 +918,8 @@ int amg_set_learned_smoother(amg_ctx *h, amg_mlp *m, const double *coords_host, 
   int s = check_fine(c, "amg_set_learned_smoother");
   if (s) return s;
   if (c->levels.size() < 2) return cfail(c, AMG_ERR_STATE, "amg_set_learned_smoother: one-level hierarchy");
+  if (c->smoother == AMG_SMOOTHER_HYBRID_GS)
+    return cfail(c, AMG_ERR_STATE, "amg_set_learned_smoother: the context uses the hybrid Gauss-Seidel smoother");
   if (m->device != c->device) return cfail(c, AMG_ERR_ARG, "network and context on different devices");
   CCUDA(c, cudaSetDevice(c->device), "cudaSetDevice");
   Level &L = c->levels[0];
@@ -976,7 +978,7 @@ int amg_reset_smoother(amg_ctx *h) {
     CCUDA(c, smoother_setup(c, 0), "smoother setup");
     CCUDA(c, cudaStreamSynchronize(c->stream), "smoother setup");
   }
-  c->smoother = AMG_SMOOTHER_L1_JACOBI;
+  if (c->smoother == AMG_SMOOTHER_LEARNED) c->smoother = AMG_SMOOTHER_L1_JACOBI;
   c->err.clear();
   return AMG_OK;
 }

@@ -662,6 +662,13 @@ extern "C" int amg_pcg_launches(const amg_ctx *h, int32_t *per_iteration, int32_
   const int nl = (int)c->levels.size();
   int vc = 5 * (nl - 1) + 1;                              // V-cycle kernels
   if (nl == 1 && c->precision != AMG_PREC_FP64) vc += 2;  // FP64 <-> FP32 casts
+  if (c->smoother == AMG_SMOOTHER_HYBRID_GS && nl > 1) {
+    // per level: one kernel per colour class and sweep instead of the two
+    // Jacobi kernels (the zero start and the result copy are memory nodes)
+    vc = 1;
+    for (int l = 0; l + 1 < nl; ++l) vc += 3 + 2 * ((int)c->levels[l].gs_ptr.size() - 1);
+    if (c->precision != AMG_PREC_FP64) vc += 2;  // FP64 <-> FP32 casts of level 0
+  }
   // r.z, p update, q = A p with p.q, alpha, x / r update with r.r, loop decision
   if (per_iteration) *per_iteration = vc + 6;
   if (fixed) *fixed = 1;

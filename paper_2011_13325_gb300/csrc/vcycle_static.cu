@@ -94,6 +94,10 @@ extern "C" int amg_vcycle_static(amg_ctx *h, const double *r_dev, double *z_dev)
     c->err = "amg_vcycle_static: NULL vector";
     return AMG_ERR_ARG;
   }
+  if (c->smoother == AMG_SMOOTHER_HYBRID_GS) {
+    c->err = "amg_vcycle_static: runs the block-l1 Jacobi and learned smoothers only";
+    return AMG_ERR_ARG;
+  }
   const int nl = (int)c->levels.size();
   if (nl > 32) {
     c->err = "amg_vcycle_static: more than 32 levels";
