@@ -211,7 +211,11 @@ int amg_smoother_colouring(amg_ctx *ctx, int level, int32_t *colour_out, int32_t
  * the device as one CUDA graph with a device-side while loop.  iters_out /
  * relres_out receive the iteration count and the final recurrence relative
  * residual per right-hand side (may be NULL).  For the mixed precisions the
- * CG uses the flexible (Polak-Ribiere) beta.  f = 0 with u = 0 returns at
+ * CG uses the flexible (Polak-Ribiere) beta.  With the double-float CG
+ * operator (amg_set_cg_operator), a recurrence residual that meets the
+ * tolerance is replaced by the true residual f - A_0 u computed with the FP64
+ * operator, and the iteration stops only if that one meets the tolerance
+ * (else it continues from it); relres_out then reports the true residual.  f = 0 with u = 0 returns at
  * once (0 iterations, relres 0).  Errors: AMG_ERR_STATE (no hierarchy),
  * AMG_ERR_ARG (NULL vector, nrhs < 1, rtol < 0, maxit < 0),
  * AMG_ERR_NOT_SPD (CG breakdown), AMG_ERR_NO_CONVERGENCE (u holds the last

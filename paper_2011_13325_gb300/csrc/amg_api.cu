@@ -931,6 +931,8 @@ static int pcg_one(Ctx *c, double rtol, int maxit, int *iters, double *relres) {
   c->st_host->it = 0;
   c->st_host->status = 0;
   c->st_host->guard = 0;
+  c->st_host->replace = 0;
+  c->st_host->replaced = 0;
   CUDA_OR_FAIL(c, cudaMemcpyAsync(c->st, c->st_host, sizeof(PcgState), cudaMemcpyHostToDevice,
                                   c->stream), "pcg state");
   CUDA_OR_FAIL(c, cudaEventRecord(c->ev0, c->stream), "event");

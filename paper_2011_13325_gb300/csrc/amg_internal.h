@@ -72,6 +72,8 @@ struct Level {
 struct PcgState {
   double rr, ff, tol2, rho, rho_old, alpha, beta, pq, rtol;
   int it, maxit, status, flexible, guard;
+  int replace;     // 1: the recurrence residual met the tolerance, recompute it
+  int replaced;    // residual replacements of this solve
 };
 
 struct Ctx {

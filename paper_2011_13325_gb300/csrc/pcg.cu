@@ -468,8 +468,13 @@ __global__ void __launch_bounds__(kRedThreads) pcg_update_xr_kernel(
 // order), counts the iteration and is the only place the loop condition is
 // set inside the body.  An independent guard counter bounds the loop, and
 // the counter of the last-block reductions is re-armed.
+// With verify (the double-float CG operator), a recurrence residual that
+// meets the tolerance is not trusted: the guard asks the replacement kernel
+// that follows to recompute r = f - A x with the FP64 operator and to take
+// the loop decision on that true residual.
 __global__ void pcg_guard_kernel(PcgState *st, const double *rr_partials, int n_rr,
-                                 unsigned *counter, cudaGraphConditionalHandle h, int in_graph) {
+                                 unsigned *counter, cudaGraphConditionalHandle h, int in_graph,
+                                 int verify) {
   pdl_enter();
   double v = 0.0;
   for (int b = threadIdx.x; b < n_rr; b += 32) v += rr_partials[b];
@@ -482,7 +487,47 @@ __global__ void pcg_guard_kernel(PcgState *st, const double *rr_partials, int n_
   if (!isfinite(v) && st->status == 0) st->status = AMG_ERR_NOT_SPD;
   const bool go = (v > st->tol2) && isfinite(v) && (st->it < st->maxit) && (st->status == 0) &&
                   (st->guard < st->maxit);
-  if (in_graph) cudaGraphSetConditional(h, go ? 1u : 0u);
+  st->replace = (verify && !go && isfinite(v) && v <= st->tol2 && st->status == 0) ? 1 : 0;
+  if (in_graph && !st->replace) cudaGraphSetConditional(h, go ? 1u : 0u);
+}
+
+// Residual replacement (van der Vorst and Ye's strategy, applied where the
+// recurrence residual meets the tolerance): r = f - A_0 x with the FP64
+// operator, r.r by a last-block total, and the loop decision on it.  Every
+// block returns at once unless the guard asked for it.
+template <int BR>
+__global__ void __launch_bounds__(kRedThreads) pcg_replace_kernel(
+    SellView A, const double *f, const double *x, double *r, PcgState *st, double *partials,
+    unsigned *counter, cudaGraphConditionalHandle h, int in_graph) {
+  pdl_enter();
+  if (!st->replace) return;
+  const int t = threadIdx.x & 31;
+  const int nw = (gridDim.x * blockDim.x) >> 5;
+  double v[1] = {0.0};
+  for (int s = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; s < A.n_slices; s += nw) {
+    double ax[BR];
+    sell_row<BR>(s, t, A.ptr, A.col, A.v, x, ax);
+    const int row = s * 32 + t;
+    if (row < A.n_rows) {
+#pragma unroll
+      for (int q = 0; q < BR; ++q) {
+        const size_t i = (size_t)row * BR + q;
+        const double ri = f[i] - ax[q];
+        r[i] = ri;
+        v[0] += ri * ri;
+      }
+    }
+  }
+  double tot[1];
+  if (last_block_total<1>(v, partials, counter, tot) && threadIdx.x == 0) {
+    st->rr = tot[0];
+    st->replace = 0;
+    st->replaced += 1;
+    if (!isfinite(tot[0]) && st->status == 0) st->status = AMG_ERR_NOT_SPD;
+    const bool go = (tot[0] > st->tol2) && isfinite(tot[0]) && (st->it < st->maxit) &&
+                    (st->status == 0) && (st->guard < st->maxit);
+    if (in_graph) cudaGraphSetConditional(h, go ? 1u : 0u);
+  }
 }
 
 cudaError_t pcg_alloc(Ctx *c) {
@@ -566,7 +611,10 @@ static cudaError_t launch_body(Ctx *c, cudaGraphConditionalHandle h, int in_grap
   AMG_KLAUNCH(c, pcg_alpha_kernel, 1, kFinThreads, c->st, pq_part, n_pq);
   AMG_KLAUNCH(c, pcg_update_xr_kernel, gv, kRedThreads, n, c->x, c->r, c->p, c->q, c->st,
                                                           rr_part);
-  AMG_KLAUNCH(c, pcg_guard_kernel, 1, 32, c->st, rr_part, gv, c->counter, h, in_graph);
+  AMG_KLAUNCH(c, pcg_guard_kernel, 1, 32, c->st, rr_part, gv, c->counter, h, in_graph, df ? 1 : 0);
+  if (df)
+    AMG_KLAUNCH(c, pcg_replace_kernel<BR>, g, kRedThreads, sell_view(L0.A), (const double *)c->f,
+                (const double *)c->x, c->r, c->st, c->partials, c->counter, h, in_graph);
   return cudaGetLastError();
 }
 
@@ -669,8 +717,10 @@ extern "C" int amg_pcg_launches(const amg_ctx *h, int32_t *per_iteration, int32_
     for (int l = 0; l + 1 < nl; ++l) vc += 3 + 2 * ((int)c->levels[l].gs_ptr.size() - 1);
     if (c->precision != AMG_PREC_FP64) vc += 2;  // FP64 <-> FP32 casts of level 0
   }
-  // r.z, p update, q = A p with p.q, alpha, x / r update with r.r, loop decision
-  if (per_iteration) *per_iteration = vc + 6;
+  // r.z, p update, q = A p with p.q, alpha, x / r update with r.r, loop
+  // decision (and the residual replacement kernel with the double-float
+  // operator, which returns at once except at convergence)
+  if (per_iteration) *per_iteration = vc + 6 + (use_double_float(c) ? 1 : 0);
   if (fixed) *fixed = 1;
   return AMG_OK;
 }
@@ -760,7 +810,7 @@ static cudaError_t profile_pcg_k(Ctx *c, int reps, double *us, double *bytes) {
   bytes[4] = N8 * 6;
   AMG_CUDA_TRY(time_kernel(c, reps, [&] {
     launch_k(c, pcg_guard_kernel, 1, 32, c->st, (const double *)rr_part, gv, c->counter,
-             (cudaGraphConditionalHandle)0, 0);
+             (cudaGraphConditionalHandle)0, 0, 0);
     return cudaGetLastError(); }, &us[5]));
   bytes[5] = 8.0 * gv;
   return cudaStreamSynchronize(c->stream);

@@ -395,3 +395,31 @@ def test_profile_pcg_covers_every_cg_step(case):
     _, its, _ = ctx.pcg_solve(dev(f), u, rtol=1e-8, maxit=500)
     u_k, _, _ = solve.pcg(H, f, rtol=0.0, maxit=its[0])
     assert maxrel(host(u), u_k) <= 1e-10
+
+
+def test_double_float_operator_stops_on_the_true_residual():
+    """On a coefficient-jump problem (E over six decades) the double-float CG
+    operator's rounding (about 2^-48 per term) opens a gap between the
+    recurrence and the true residual; the residual replacement at
+    convergence recomputes f - A u with the FP64 operator and stops only on
+    it: the true FP64 residual (oracle product) meets rtol, and the iteration
+    count stays within 3 of the FP64 operator's."""
+    amg = _amg()
+    p = make_problem((24, 24, 24), seed=3, jump_boxes=60, nu_range=(0.25, 0.45))
+    H = hierarchy.setup(p, hierarchy.SetupParams())
+    f = p.b[0]
+    out = {}
+    for mode in (amg.AMG_CG_FP64, amg.AMG_CG_DOUBLE_FLOAT):
+        ctx = amg.Context(0)
+        ctx.set_layout_policy(amg.AMG_LAYOUT_SELL_SHORT_ROWS)
+        ctx.set_cg_operator(mode)
+        ctx.upload_hierarchy(H.A[0], H.P, amg.AMG_PREC_FP32_VCYCLE)
+        u = dev(np.zeros_like(f))
+        _, its, rr = ctx.pcg_solve(dev(f), u, rtol=1e-8, maxit=500)
+        true = np.linalg.norm(f - solve.spmv(H.A[0], host(u))) / np.linalg.norm(f)
+        out[mode] = (its[0], rr[0], true)
+        ctx.close()
+    it64, _, _ = out[amg.AMG_CG_FP64]
+    itdf, rrdf, truedf = out[amg.AMG_CG_DOUBLE_FLOAT]
+    assert truedf <= 1.001e-8 and abs(rrdf - truedf) <= 1e-3 * truedf, out
+    assert abs(itdf - it64) <= 3, out
