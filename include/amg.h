@@ -423,6 +423,13 @@ typedef struct {
  *  max_levels   upper bound on the number of levels
  *  host_threads OpenMP threads of this call's host setup (0: the process
  *               default); lets independent setups run side by side
+ *  device_setup 1 (default): the coarse edge / vertex matrices (Thm.
+ *               cemats) and the auxiliary smoothed prolongation (Def.
+ *               aux_sp) are built on the device for the agglomerates that
+ *               Algorithm 1 finds on the host; 0: on the host
+ *  keep_topology 1: keep the coarse topologies the device stages build, for
+ *               amg_download_topology (host memory: a level's edge and
+ *               vertex matrices); 0 (default): drop them
  * A vertex is "standard" (real matrix row in P_s) when its row touches at
  * most cap agglomerates, does not couple to D and is kernel-exact; the
  * auxiliary rows use the own agglomerate and the 3 others with the largest
@@ -437,6 +444,8 @@ typedef struct {
   double min_ratio;
   int32_t max_levels;
   int32_t host_threads;
+  int32_t device_setup;
+  int32_t keep_topology;
 } amg_setup_params;
 
 /* Fill *p with the defaults listed above (the readings of Sec. 5, 6, 7). */
@@ -452,6 +461,21 @@ void amg_default_setup_params(amg_setup_params *p);
  * AMG_ERR_CUDA. */
 int amg_setup(amg_ctx *ctx, const amg_problem *prob, const amg_setup_params *params, int precision,
               int smoother);
+
+/* Wall-clock seconds of the last amg_setup's device stages, split into the
+ * Galerkin products with their transfers and the coarse edge / vertex
+ * matrices with the smoothed prolongation (either pointer may be NULL). */
+int amg_setup_device_split(const amg_ctx *ctx, double *galerkin_s, double *topology_prolongation_s);
+
+/* The coarse topology of level `level` (>= 1) built by amg_setup's device
+ * stages (Thm. cemats: edge matrices E^{IJ} of the coarse edges (ei < ej),
+ * vertex matrices M^I, vertex positions = agglomerate centroids), kept when
+ * amg_setup_params.keep_topology was set.  Sizes first (NULL arrays): n
+ * vertices, m edges, k x k blocks; then ei / ej (m), E (m k k), M (n k k),
+ * pos (n d) into caller host arrays (any may be NULL).  Errors:
+ * AMG_ERR_STATE (nothing kept for that level), AMG_ERR_ARG. */
+int amg_download_topology(amg_ctx *ctx, int level, int32_t *n_vertices, int64_t *n_edges, int32_t *k,
+                          int32_t *ei, int32_t *ej, double *E, double *M, double *pos);
 
 /* Size of P_level, the auxiliary smoothed prolongation (Def. aux_sp) built
  * by amg_setup (0 <= level < n_levels-1): rows, columns, block dims and

@@ -64,7 +64,8 @@ class amg_setup_params(C.Structure):
                 ("passes_later", C.c_int32), ("omega", C.c_double), ("cap_S_first", C.c_int32),
                 ("cap_S_later", C.c_int32), ("cap_A", C.c_int32), ("coarse_max", C.c_int32),
                 ("min_ratio", C.c_double), ("max_levels", C.c_int32),
-                ("host_threads", C.c_int32)]
+                ("host_threads", C.c_int32), ("device_setup", C.c_int32),
+                ("keep_topology", C.c_int32)]
 
 
 class AmgError(RuntimeError):
@@ -104,6 +105,9 @@ _SIGS = {
     "amg_set_layout_policy": (_I, [_P, _I]),
     "amg_probe_fma_rate": (_I, [_P, C.POINTER(C.c_double), C.POINTER(C.c_double)]),
     "amg_setup_times": (_I, [_P, C.POINTER(C.c_double)]),
+    "amg_setup_device_split": (_I, [_P, C.POINTER(C.c_double), C.POINTER(C.c_double)]),
+    "amg_download_topology": (_I, [_P, _I, C.POINTER(C.c_int32), C.POINTER(C.c_int64),
+                                   C.POINTER(C.c_int32), _P, _P, _P, _P, _P]),
     "amg_default_setup_params": (None, [C.POINTER(amg_setup_params)]),
     "amg_setup": (_I, [_P, C.POINTER(amg_problem), C.POINTER(amg_setup_params), _I, _I]),
     "amg_prolongation_info": (_I, [_P, _I, C.POINTER(C.c_int32), C.POINTER(C.c_int32),
@@ -393,7 +397,28 @@ class Context:
     def setup_times(self):
         t = (C.c_double * 4)()
         self._check(lib().amg_setup_times(self.h, t))
-        return dict(host_s=t[0], device_s=t[1], finalize_s=t[2], total_s=t[3])
+        g, tp = C.c_double(), C.c_double()
+        self._check(lib().amg_setup_device_split(self.h, C.byref(g), C.byref(tp)))
+        return dict(host_s=t[0], device_s=t[1], finalize_s=t[2], total_s=t[3],
+                    device_galerkin_s=g.value, device_topology_prolongation_s=tp.value)
+
+    def download_topology(self, level):
+        """(pos, edges (m x 2), E (m x k x k), M (n x k x k)) of the coarse
+        topology of `level` kept by amg_setup(keep_topology=1)."""
+        n, m, k = C.c_int32(), C.c_int64(), C.c_int32()
+        self._check(lib().amg_download_topology(self.h, int(level), C.byref(n), C.byref(m), C.byref(k),
+                                                None, None, None, None, None))
+        n, m, k = n.value, m.value, k.value
+        d = 2 if k == 3 else 3
+        ei = np.zeros(max(m, 1), dtype=np.int32)
+        ej = np.zeros(max(m, 1), dtype=np.int32)
+        E = np.zeros((max(m, 1), k, k))
+        M = np.zeros((max(n, 1), k, k))
+        pos = np.zeros((max(n, 1), d))
+        self._check(lib().amg_download_topology(self.h, int(level), None, None, None, ei.ctypes.data,
+                                                ej.ctypes.data, E.ctypes.data, M.ctypes.data,
+                                                pos.ctypes.data))
+        return pos[:n], np.stack([ei[:m], ej[:m]], axis=1), E[:m], M[:n]
 
     def probe_fma_rate(self):
         a, b = C.c_double(), C.c_double()

@@ -471,10 +471,51 @@ static double wall_s() {
   return std::chrono::duration<double>(std::chrono::steady_clock::now().time_since_epoch()).count();
 }
 
+namespace amg {
+cudaError_t device_coarse_topology(Ctx *c, const amgsetup::Topo &T, const std::vector<int> &agg, int nc,
+                                   const std::vector<double> &xc, amgsetup::Topo &C);
+cudaError_t device_prolongation(Ctx *c, int level, const amgsetup::Topo &T, const std::vector<int> &agg,
+                                const std::vector<char> &dflag, int nc, const std::vector<double> &xc,
+                                const std::vector<int> &rowmap, const std::vector<char> &bad, bool first,
+                                const amgsetup::SetupParams &prm, amgsetup::HostBSR &Ph,
+                                std::vector<char> &next_bad, int *handled);
+}  // namespace amg
+
 struct DeviceSink : amgsetup::LevelSink {
   Ctx *c;
-  double device_s = 0.0;
+  double device_s = 0.0, device_setup_s = 0.0;
+  bool device = true, keep = false;
+  std::vector<char> p_on_device;  // per level: P_l already built on the device
   explicit DeviceSink(Ctx *cc) : c(cc) {}
+  bool device_stages() const override { return device; }
+  int coarse_topology(int level, const amgsetup::Topo &T, const std::vector<int> &agg, int nc,
+                      const std::vector<double> &xc, amgsetup::Topo &out) override {
+    const double t0 = wall_s();
+    const cudaError_t e = device_coarse_topology(c, T, agg, nc, xc, out);
+    device_setup_s += wall_s() - t0;
+    if (e != cudaSuccess) return -1;
+    if (keep) {
+      if ((int)c->topo.size() < level + 2) c->topo.resize(level + 2);
+      c->topo[level + 1] = out;
+    }
+    return 0;
+  }
+  int prolongation(int level, const amgsetup::HostBSR &A, const amgsetup::Topo &T,
+                   const std::vector<int> &agg, const std::vector<char> &D, int nc,
+                   const std::vector<double> &xc, const std::vector<int> &rowmap,
+                   const std::vector<char> &bad, bool first, const amgsetup::SetupParams &prm,
+                   amgsetup::HostBSR &P, std::vector<char> &next_bad, int *handled) override {
+    (void)A;
+    const double t0 = wall_s();
+    if ((int)c->levels.size() < level + 2) c->levels.resize(level + 2);
+    const cudaError_t e = device_prolongation(c, level, T, agg, D, nc, xc, rowmap, bad, first, prm, P,
+                                              next_bad, handled);
+    device_setup_s += wall_s() - t0;
+    if (e != cudaSuccess) return -1;
+    if ((int)p_on_device.size() < level + 1) p_on_device.resize(level + 1, 0);
+    p_on_device[level] = *handled ? 1 : 0;
+    return 0;
+  }
   int first(const amgsetup::HostBSR &A) override {
     c->levels.clear();
     c->levels.resize(1);
@@ -495,8 +536,9 @@ struct DeviceSink : amgsetup::LevelSink {
     Level &L = c->levels[level];
     amg_bsr pv = {P.n_rows, P.n_cols, P.br, P.bc, (int64_t)P.colidx.size(), P.rowptr.data(),
                   P.colidx.data(), P.vals.data()};
-    if (upload_bsr(c, L.P, P.n_rows, P.n_cols, P.br, P.bc, pv.nnzb, P.rowptr.data(),
-                   P.colidx.data(), P.vals.data()) != cudaSuccess)
+    const bool on_dev = level < (int)p_on_device.size() && p_on_device[level];
+    if (!on_dev && upload_bsr(c, L.P, P.n_rows, P.n_cols, P.br, P.bc, pv.nnzb, P.rowptr.data(),
+                              P.colidx.data(), P.vals.data()) != cudaSuccess)
       return -1;
     if (upload_transpose(c, L.R, pv) != cudaSuccess) return -1;
     if (galerkin_device(c, level) != cudaSuccess) return -1;
@@ -1021,6 +1063,34 @@ int amg_setup_times(const amg_ctx *h, double *times4) {
   return AMG_OK;
 }
 
+int amg_setup_device_split(const amg_ctx *h, double *galerkin_s, double *topology_prolongation_s) {
+  if (!h) return AMG_ERR_ARG;
+  if (galerkin_s) *galerkin_s = h->c.setup_times[1] - h->c.setup_times[4];
+  if (topology_prolongation_s) *topology_prolongation_s = h->c.setup_times[4];
+  return AMG_OK;
+}
+
+int amg_download_topology(amg_ctx *h, int level, int32_t *n_vertices, int64_t *n_edges, int32_t *k,
+                          int32_t *ei, int32_t *ej, double *E, double *M, double *pos) {
+  if (!h) return AMG_ERR_ARG;
+  Ctx *c = &h->c;
+  if (level < 1 || level >= (int)c->topo.size() || c->topo[level].n == 0)
+    return fail(c, AMG_ERR_STATE, "amg_download_topology: no kept topology of that level (amg_setup "
+                                  "with keep_topology and the device stages)");
+  const amgsetup::Topo &T = c->topo[level];
+  const size_t kk = (size_t)T.k * T.k;
+  if (n_vertices) *n_vertices = T.n;
+  if (n_edges) *n_edges = (int64_t)T.ei.size();
+  if (k) *k = T.k;
+  if (ei) std::copy(T.ei.begin(), T.ei.end(), ei);
+  if (ej) std::copy(T.ej.begin(), T.ej.end(), ej);
+  if (E) std::copy(T.E.begin(), T.E.begin() + T.ei.size() * kk, E);
+  if (M) std::copy(T.M.begin(), T.M.begin() + (size_t)T.n * kk, M);
+  if (pos) std::copy(T.pos.begin(), T.pos.end(), pos);
+  c->err.clear();
+  return AMG_OK;
+}
+
 int amg_probe_fma_rate(amg_ctx *h, double *fp64_gflops, double *fp32_gflops) {
   if (!h || !fp64_gflops || !fp32_gflops) return AMG_ERR_ARG;
   Ctx *c = &h->c;
@@ -1094,6 +1164,8 @@ void amg_default_setup_params(amg_setup_params *p) {
   p->min_ratio = d.min_ratio;
   p->max_levels = d.max_levels;
   p->host_threads = d.host_threads;
+  p->device_setup = 1;
+  p->keep_topology = 0;
 }
 
 int amg_setup(amg_ctx *h, const amg_problem *prob, const amg_setup_params *params, int precision,
@@ -1144,6 +1216,9 @@ int amg_setup(amg_ctx *h, const amg_problem *prob, const amg_setup_params *param
   pb.colidx = A.colidx;
   pb.vals = A.vals;
   DeviceSink sink(c);
+  sink.device = !params || params->device_setup != 0;
+  sink.keep = params && params->keep_topology != 0;
+  c->topo.clear();
   std::string err;
   const double t0 = wall_s();
   if (amgsetup::build_levels(pb, prm, sink, err) != 0) {
@@ -1153,10 +1228,11 @@ int amg_setup(amg_ctx *h, const amg_problem *prob, const amg_setup_params *param
   const double t1 = wall_s();
   const int rc = finalize_hierarchy(c);
   const double t2 = wall_s();
-  c->setup_times[0] = (t1 - t0) - sink.device_s;
-  c->setup_times[1] = sink.device_s;
+  c->setup_times[0] = (t1 - t0) - sink.device_s - sink.device_setup_s;
+  c->setup_times[1] = sink.device_s + sink.device_setup_s;
   c->setup_times[2] = t2 - t1;
   c->setup_times[3] = t2 - t0;
+  c->setup_times[4] = sink.device_setup_s;
   return rc;
 }
 

@@ -9,6 +9,7 @@
 #include <vector>
 
 #include "../../include/amg.h"
+#include "setup_host.h"
 
 namespace amg {
 
@@ -103,7 +104,13 @@ struct Ctx {
   cudaGraph_t graph_def = nullptr;
   cudaEvent_t ev0 = nullptr, ev1 = nullptr;
   float last_ms = 0.f;
-  double setup_times[4] = {0, 0, 0, 0};  // host setup, device Galerkin + transfers, finalize, total (s)
+  // host setup, device stages (Galerkin, transfers, coarse topology,
+  // prolongation), finalize, total, and the coarse topology + prolongation
+  // part of the device stages (s)
+  double setup_times[5] = {0, 0, 0, 0, 0};
+  // coarse topologies built by the device stages of amg_setup (kept when
+  // asked for, level l >= 1 at index l)
+  std::vector<amgsetup::Topo> topo;
   double *hbuf = nullptr;        // pinned staging for host solves
   size_t hbuf_len = 0;
   int cg_op = AMG_CG_DOUBLE_FLOAT;  // arithmetic of the CG operator q = A_0 p

@@ -753,7 +753,10 @@ struct Coarsening {
   std::vector<char> D;
 };
 
-static Coarsening successive_matching(const Topo &T0, const SetupParams &prm, int passes) {
+// final_topology = false leaves the coarse edge / vertex matrices of the
+// last pass to the caller (positions only).
+static Coarsening successive_matching(const Topo &T0, const SetupParams &prm, int passes,
+                                      bool final_topology = true) {
   const int n = T0.n, k = T0.k, d = T0.d;
   const double sigma = prm.sigma;
   std::vector<double> Dh0 = aux_diagonal(T0);
@@ -895,8 +898,17 @@ static Coarsening successive_matching(const Topo &T0, const SetupParams &prm, in
         for (int a = 0; a < d; ++a) xc[(size_t)g * d + a] += T0.pos[(size_t)v * d + a];
       for (int a = 0; a < d; ++a) xc[(size_t)g * d + a] /= (double)nm[g].size();
     }
-    Topo next = coarse_topology(*Tc, cagg, mc, xc, pass == 1);
-    cur = std::move(next);
+    if (pass == passes && !final_topology) {
+      Topo next;
+      next.n = mc;
+      next.d = d;
+      next.k = k;
+      next.pos = xc;
+      cur = std::move(next);
+    } else {
+      Topo next = coarse_topology(*Tc, cagg, mc, xc, pass == 1);
+      cur = std::move(next);
+    }
     Tc = &cur;
     members = std::move(nm);
     order.resize(mc);
@@ -1143,11 +1155,16 @@ int build_levels(const Problem &prob, const SetupParams &prm, LevelSink &sink, s
   while (A.n_rows > cmax && level + 1 < prm.max_levels) {
     const bool first = level == 0;
     double t0 = now_s();
-    Coarsening cs = successive_matching(T, prm, first ? prm.passes_first : prm.passes_later);
+    const bool dev = sink.device_stages();
+    Coarsening cs = successive_matching(T, prm, first ? prm.passes_first : prm.passes_later, !dev);
     if (verbose)
       fprintf(stderr, "[amg setup] level %d: %d vertices -> %d agglomerates, matching %.2f s\n",
               level, T.n, cs.nc, now_s() - t0);
     if (cs.nc == 0 || A.n_rows < prm.min_ratio * cs.nc) break;
+    if (dev && sink.coarse_topology(level, T, cs.agg, cs.nc, cs.xc, cs.coarse) != 0) {
+      err = "device coarse edge / vertex matrices failed";
+      return -1;
+    }
     std::vector<char> bad(A.n_rows, 0);
     for (int r = 0; r < A.n_rows; ++r) {
       bool couples = false;
@@ -1162,7 +1179,13 @@ int build_levels(const Problem &prob, const SetupParams &prm, LevelSink &sink, s
     HostBSR P;
     std::vector<char> next_bad;
     t0 = now_s();
-    smoothed_prolongation(A, T, cs, rowmap, bad, first, prm, P, next_bad);
+    int handled = 0;
+    if (dev && sink.prolongation(level, A, T, cs.agg, cs.D, cs.nc, cs.xc, rowmap, bad, first, prm, P,
+                                 next_bad, &handled) != 0) {
+      err = "device smoothed prolongation failed";
+      return -1;
+    }
+    if (!handled) smoothed_prolongation(A, T, cs, rowmap, bad, first, prm, P, next_bad);
     if (verbose)
       fprintf(stderr, "[amg setup] level %d: prolongation %.2f s (%zu blocks)\n", level, now_s() - t0,
               P.colidx.size());

@@ -51,10 +51,30 @@ struct SetupParams {
 
 // Receives the levels as they are built: first(A_0), then for every level
 // the prolongation P_l; it must return A_{l+1} = P_l^T A_l P_l on the host.
+// A sink with device_stages() true also builds, for the agglomerates of
+// Algorithm 1, the coarse edge / vertex matrices (coarse_topology) and the
+// smoothed prolongation (prolongation: sets *handled = 1 when it built P
+// and next_bad, else the host builds them); each returns 0 or an error.
 struct LevelSink {
   virtual ~LevelSink() {}
   virtual int first(const HostBSR &A0) = 0;
   virtual int next(int level, const HostBSR &P, HostBSR &A_next) = 0;
+  virtual bool device_stages() const { return false; }
+  virtual int coarse_topology(int level, const Topo &T, const std::vector<int> &agg, int nc,
+                              const std::vector<double> &xc, Topo &out) {
+    (void)level; (void)T; (void)agg; (void)nc; (void)xc; (void)out;
+    return -1;
+  }
+  virtual int prolongation(int level, const HostBSR &A, const Topo &T, const std::vector<int> &agg,
+                           const std::vector<char> &D, int nc, const std::vector<double> &xc,
+                           const std::vector<int> &rowmap, const std::vector<char> &bad, bool first,
+                           const SetupParams &prm, HostBSR &P, std::vector<char> &next_bad,
+                           int *handled) {
+    (void)level; (void)A; (void)T; (void)agg; (void)D; (void)nc; (void)xc; (void)rowmap; (void)bad;
+    (void)first; (void)prm; (void)P; (void)next_bad;
+    *handled = 0;
+    return 0;
+  }
 };
 
 Topo finest_topology(int d, int n, const double *coords, const uint8_t *dirichlet,

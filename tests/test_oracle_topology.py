@@ -143,3 +143,23 @@ def test_galerkin_of_aux_matrix_is_coarse_aux_matrix(shape, clamp):
             assert np.abs(tc.M).max() > 0  # Dirichlet edges became vertex matrices
         else:
             assert np.abs(tc.M).max() == 0
+
+
+@pytest.mark.parametrize("shape,kw", [((13, 11), {"coarse_max": 3}), ((7, 6, 5), {"coarse_max": 4}),
+                                      ((9, 7, 8), {"coarse_max": 6})])
+def test_coarse_topology_in_one_step_equals_pass_by_pass(shape, kw):
+    """Kernel transfers compose (Q(a) Q(b) = Q(a + b)), so Thm. cemats applied
+    once from a level's topology to the final agglomerates of Algorithm 1
+    gives the coarse topology Algorithm 1 built pass by pass (edges exact,
+    matrices to rounding)."""
+    from oracle import hierarchy
+    p = make_problem(shape, seed=3, jump_boxes=4 if len(shape) == 3 else 0)
+    H = hierarchy.setup(p, hierarchy.SetupParams(**kw), factor=False)
+    recs = H.info["records"]
+    assert len(recs) >= 2
+    for l in range(len(recs) - 1):
+        rec, seq = recs[l], recs[l + 1]["topo"]
+        one = T.coarse_topology(rec["topo"], rec["agg"], rec["xc"].shape[0], rec["xc"])
+        np.testing.assert_array_equal(one.edges, seq.edges)
+        assert np.abs(one.E - seq.E).max() <= 1e-12 * np.abs(seq.E).max()
+        assert np.abs(one.M - seq.M).max() <= 1e-12 * max(np.abs(seq.M).max(), 1e-300)
