@@ -286,9 +286,10 @@ def main():
     ap.add_argument("--precision", type=int, default=1, choices=[0, 1, 2],
                     help="V-cycle precision of the timed path: 0 fp64, 1 fp32 (default), 2 bf16 "
                          "storage; the CG is FP64 in all three")
-    ap.add_argument("--cg-operator", default="double_float", choices=["double_float", "fp64"],
-                    help="arithmetic of the CG operator q = A_0 p (both FP64-accurate; default "
-                         "double-float pairs on the FP32 pipe)")
+    ap.add_argument("--cg-operator", default="auto", choices=["auto", "double_float", "fp64"],
+                    help="arithmetic of the CG operator q = A_0 p: auto (default: double-float "
+                         "pairs on the FP32 pipe with the FP32 / BF16 V-cycles, FP64 with the "
+                         "FP64 V-cycle), double_float, fp64")
     ap.add_argument("--variants", default="auto",
                     help="comma list of other precisions timed for comparison ('auto': the two "
                          "others, '': none)")
@@ -350,7 +351,8 @@ def run_single(args, ws, rank, local, train_problems):
     # capture is not allowed on the legacy default stream)
     stream = torch.cuda.Stream(dev)
     torch.cuda.set_stream(stream)
-    cg_mode = amg.AMG_CG_DOUBLE_FLOAT if args.cg_operator == "double_float" else amg.AMG_CG_FP64
+    cg_mode = {"auto": amg.AMG_CG_AUTO, "double_float": amg.AMG_CG_DOUBLE_FLOAT,
+               "fp64": amg.AMG_CG_FP64}[args.cg_operator]
 
     t0 = time.perf_counter()
     problem = make_workload(args.workload)
@@ -452,7 +454,8 @@ def run_single(args, ws, rank, local, train_problems):
         variants[PREC_NAMES[prec]] = variant(c2, PREC_NAMES[prec], prec)
         c2.close()
     # the timed configuration with the other CG operator arithmetic
-    other = amg.AMG_CG_FP64 if cg_mode == amg.AMG_CG_DOUBLE_FLOAT else amg.AMG_CG_DOUBLE_FLOAT
+    main_df = "pcg_spmv_dot_sell_df_kernel" in ctx.describe()
+    other = amg.AMG_CG_FP64 if main_df else amg.AMG_CG_DOUBLE_FLOAT
     ctx.set_cg_operator(other)
     variants["cg_operator_" + ("fp64" if other == amg.AMG_CG_FP64 else "double_float")] = \
         variant(ctx, "other_cg_operator")

@@ -212,10 +212,10 @@ int amg_smoother_colouring(amg_ctx *ctx, int level, int32_t *colour_out, int32_t
  * relres_out receive the iteration count and the final recurrence relative
  * residual per right-hand side (may be NULL).  For the mixed precisions the
  * CG uses the flexible (Polak-Ribiere) beta.  With the double-float CG
- * operator (amg_set_cg_operator), a recurrence residual that meets the
- * tolerance is replaced by the true residual f - A_0 u computed with the FP64
- * operator, and the iteration stops only if that one meets the tolerance
- * (else it continues from it); relres_out then reports the true residual.  f = 0 with u = 0 returns at
+ * operator (amg_set_cg_operator) the residual is replaced by the true one
+ * f - A_0 u (FP64 operator) at every 10^3 drop of its norm and when it meets
+ * the tolerance, and the iteration stops only when the true residual meets
+ * it; relres_out then reports the true residual.  f = 0 with u = 0 returns at
  * once (0 iterations, relres 0).  Errors: AMG_ERR_STATE (no hierarchy),
  * AMG_ERR_ARG (NULL vector, nrhs < 1, rtol < 0, maxit < 0),
  * AMG_ERR_NOT_SPD (CG breakdown), AMG_ERR_NO_CONVERGENCE (u holds the last
@@ -317,7 +317,7 @@ int amg_set_layout_policy(amg_ctx *ctx, int policy);
  * in the paper: an execution choice of GB300, whose FP64 pipe (about 2 FMA
  * per clock per SM) is slower than its memory for 2x2 / 3x3 FP64 blocks):
  *   AMG_CG_FP64          FP64 fused multiply-adds.
- *   AMG_CG_DOUBLE_FLOAT  (default) every FP64 value of A_0 (scaled by a power
+ *   AMG_CG_DOUBLE_FLOAT  every FP64 value of A_0 (scaled by a power
  *                        of two so that max |a| < 1) and of p is held as a pair
  *                        of FP32 numbers hi + lo (48 significant bits, same 8
  *                        bytes), products are formed exactly with FP32 fused
@@ -330,10 +330,17 @@ int amg_set_layout_policy(amg_ctx *ctx, int policy);
  *                        about 2^-102 in magnitude lose low-word bits (FP32
  *                        gradual underflow); below 2^-126 they count as zero
  *                        in the product.
+ *   AMG_CG_AUTO          (default) double-float with the FP32 / BF16-storage
+ *                        V-cycles, FP64 with the FP64 V-cycle.
  * It applies to A_0 with 2x2 or 3x3 blocks and a SELL-32 copy (see
- * amg_set_layout_policy); elsewhere the FP64 kernel runs.  The setting takes
- * effect at the next amg_pcg_solve*.  Errors: AMG_ERR_ARG (unknown mode). */
-enum { AMG_CG_FP64 = 0, AMG_CG_DOUBLE_FLOAT = 1 };
+ * amg_set_layout_policy); elsewhere the FP64 kernel runs.  With the
+ * double-float operator the PCG replaces the recurrence residual by the true
+ * one, f - A_0 u with the FP64 operator, whenever r.r has dropped by 10^6
+ * since the start or the last replacement and when it meets the tolerance
+ * (residual replacement, van der Vorst and Ye); the stop is decided on the
+ * true residual.  The setting takes effect at the next amg_pcg_solve*.
+ * Errors: AMG_ERR_ARG (unknown mode). */
+enum { AMG_CG_FP64 = 0, AMG_CG_DOUBLE_FLOAT = 1, AMG_CG_AUTO = 2 };
 int amg_set_cg_operator(amg_ctx *ctx, int mode);
 
 /* q = A_0 p with the CG operator of the PCG (Sec. 7) in the arithmetic

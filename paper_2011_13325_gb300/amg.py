@@ -38,6 +38,7 @@ AMG_SMOOTHER_LEARNED = 1
 AMG_SMOOTHER_HYBRID_GS = 2
 AMG_CG_FP64 = 0
 AMG_CG_DOUBLE_FLOAT = 1
+AMG_CG_AUTO = 2
 
 
 class amg_bsr(C.Structure):
@@ -509,7 +510,8 @@ class Context:
         return col[:info["n_rows"]], nc.value
 
     def set_cg_operator(self, mode: int):
-        """AMG_CG_FP64 or AMG_CG_DOUBLE_FLOAT (default): arithmetic of q = A_0 p in the PCG."""
+        """AMG_CG_FP64, AMG_CG_DOUBLE_FLOAT or AMG_CG_AUTO (default: double-float with the
+        FP32 / BF16 V-cycles): arithmetic of q = A_0 p in the PCG."""
         return self._check(lib().amg_set_cg_operator(self.h, int(mode)))
 
     def cg_operator(self, p, q):

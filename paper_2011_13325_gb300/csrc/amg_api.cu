@@ -712,7 +712,9 @@ const char *amg_describe(amg_ctx *h) {
   }
   if (!c->levels.empty()) {
     const DevBSR &A = c->levels[0].A;
-    const bool df = c->cg_op == AMG_CG_DOUBLE_FLOAT && A.sdf && A.sell_ptr && !A.sell_perm;
+    const bool df = (c->cg_op == AMG_CG_DOUBLE_FLOAT ||
+                     (c->cg_op == AMG_CG_AUTO && c->precision != AMG_PREC_FP64)) &&
+                    A.sdf && A.sell_ptr && !A.sell_perm;
     snprintf(line, sizeof line, "CG operator q = A_0 p: %s\n",
              df ? "double-float pairs on the FP32 pipe, SELL-32 (pcg_spmv_dot_sell_df_kernel)"
                 : (A.sell_ptr && !A.sell_perm ? "FP64, SELL-32 (pcg_spmv_dot_sell_kernel)"
@@ -1122,7 +1124,7 @@ int amg_set_launch_overlap(amg_ctx *h, int enable) {
 int amg_set_cg_operator(amg_ctx *h, int mode) {
   if (!h) return AMG_ERR_ARG;
   Ctx *c = &h->c;
-  if (mode != AMG_CG_FP64 && mode != AMG_CG_DOUBLE_FLOAT)
+  if (mode != AMG_CG_FP64 && mode != AMG_CG_DOUBLE_FLOAT && mode != AMG_CG_AUTO)
     return fail(c, AMG_ERR_ARG, "unknown CG operator mode");
   if (mode != c->cg_op) {
     CUDA_OR_FAIL(c, cudaStreamSynchronize(c->stream), "sync");

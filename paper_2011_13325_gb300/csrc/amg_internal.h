@@ -73,8 +73,9 @@ struct Level {
 struct PcgState {
   double rr, ff, tol2, rho, rho_old, alpha, beta, pq, rtol;
   int it, maxit, status, flexible, guard;
-  int replace;     // 1: the recurrence residual met the tolerance, recompute it
+  int replace;     // 1: recompute the residual as f - A x (FP64 operator)
   int replaced;    // residual replacements of this solve
+  double rr_ref;   // r.r at the start or the last replacement
 };
 
 struct Ctx {
@@ -113,7 +114,7 @@ struct Ctx {
   std::vector<amgsetup::Topo> topo;
   double *hbuf = nullptr;        // pinned staging for host solves
   size_t hbuf_len = 0;
-  int cg_op = AMG_CG_DOUBLE_FLOAT;  // arithmetic of the CG operator q = A_0 p
+  int cg_op = AMG_CG_AUTO;       // arithmetic of the CG operator q = A_0 p
   float2 *pdf = nullptr;         // p split into double-float pairs (CG operator input)
 };
 

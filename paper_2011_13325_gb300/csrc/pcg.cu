@@ -10,6 +10,9 @@
 namespace amg {
 
 constexpr int kRedThreads = 256;
+// residual replacement of the double-float CG operator: every drop of r.r by
+// this factor (r by 10^3) since the last replacement
+constexpr double kReplaceDrop = 1e-6;
 
 static int red_grid(const Ctx *c) { return c->num_sms * 8; }  // SpMV + dot kernels
 static int vec_grid(const Ctx *c) { return c->num_sms * 2; }  // pure vector reductions
@@ -154,6 +157,7 @@ __global__ void __launch_bounds__(kRedThreads) pcg_init_sell_kernel(
   double tot[2];
   if (last_block_total<2>(v, partials, counter, tot) && threadIdx.x == 0) {
     st->rr = tot[0];
+    st->rr_ref = tot[0];
     st->ff = tot[1];
     st->tol2 = st->rtol * st->rtol * tot[1];
     st->it = 0;
@@ -340,6 +344,7 @@ __global__ void __launch_bounds__(kRedThreads) pcg_init_kernel(
   double tot[2];
   if (last_block_total<2>(v, partials, counter, tot) && threadIdx.x == 0) {
     st->rr = tot[0];
+    st->rr_ref = tot[0];
     st->ff = tot[1];
     st->tol2 = st->rtol * st->rtol * tot[1];
     st->it = 0;
@@ -468,10 +473,13 @@ __global__ void __launch_bounds__(kRedThreads) pcg_update_xr_kernel(
 // order), counts the iteration and is the only place the loop condition is
 // set inside the body.  An independent guard counter bounds the loop, and
 // the counter of the last-block reductions is re-armed.
-// With verify (the double-float CG operator), a recurrence residual that
-// meets the tolerance is not trusted: the guard asks the replacement kernel
-// that follows to recompute r = f - A x with the FP64 operator and to take
-// the loop decision on that true residual.
+// With verify (the double-float CG operator) the recurrence residual drifts
+// from the true one by the operator's rounding, most of it from the early
+// iterations, whose terms are largest.  So the guard asks the replacement
+// kernel that follows to recompute r = f - A x with the FP64 operator
+// whenever r.r has dropped by kReplaceDrop since the last replacement, and
+// when it meets the tolerance; the loop decision is then taken on the true
+// residual.
 __global__ void pcg_guard_kernel(PcgState *st, const double *rr_partials, int n_rr,
                                  unsigned *counter, cudaGraphConditionalHandle h, int in_graph,
                                  int verify) {
@@ -485,9 +493,10 @@ __global__ void pcg_guard_kernel(PcgState *st, const double *rr_partials, int n_
   st->guard += 1;
   *counter = 0u;
   if (!isfinite(v) && st->status == 0) st->status = AMG_ERR_NOT_SPD;
-  const bool go = (v > st->tol2) && isfinite(v) && (st->it < st->maxit) && (st->status == 0) &&
-                  (st->guard < st->maxit);
-  st->replace = (verify && !go && isfinite(v) && v <= st->tol2 && st->status == 0) ? 1 : 0;
+  const bool ok = isfinite(v) && (st->status == 0);
+  const bool more = (st->it < st->maxit) && (st->guard < st->maxit);
+  const bool go = (v > st->tol2) && ok && more;
+  st->replace = (verify && ok && (v <= st->tol2 || (more && v <= kReplaceDrop * st->rr_ref))) ? 1 : 0;
   if (in_graph && !st->replace) cudaGraphSetConditional(h, go ? 1u : 0u);
 }
 
@@ -521,6 +530,7 @@ __global__ void __launch_bounds__(kRedThreads) pcg_replace_kernel(
   double tot[1];
   if (last_block_total<1>(v, partials, counter, tot) && threadIdx.x == 0) {
     st->rr = tot[0];
+    st->rr_ref = tot[0];
     st->replace = 0;
     st->replaced += 1;
     if (!isfinite(tot[0]) && st->status == 0) st->status = AMG_ERR_NOT_SPD;
@@ -554,7 +564,9 @@ cudaError_t pcg_alloc(Ctx *c) {
 // (SELL-32, rows in order) and the context asks for it.
 static bool use_double_float(const Ctx *c) {
   const DevBSR &A = c->levels[0].A;
-  return c->cg_op == AMG_CG_DOUBLE_FLOAT && A.sdf && A.sell_ptr && !A.sell_perm && c->pdf;
+  const bool want = c->cg_op == AMG_CG_DOUBLE_FLOAT ||
+                    (c->cg_op == AMG_CG_AUTO && c->precision != AMG_PREC_FP64);
+  return want && A.sdf && A.sell_ptr && !A.sell_perm && c->pdf;
 }
 
 static SellView sell_view(const DevBSR &A) {
