@@ -53,8 +53,12 @@ def setup(problem, params: SetupParams = SetupParams(), factor: bool = True):
     factor (for singular Neumann problems).
     """
     Af = problem.A_full
-    topo = topology.finest_topology(problem.coords, Af.rowptr, Af.colidx, Af.vals,
-                                    problem.dirichlet)
+    if getattr(problem, "k", problem.dim) == 1:
+        topo = topology.finest_topology_scalar(problem.coords, Af.rowptr, Af.colidx, Af.vals,
+                                               problem.dirichlet)
+    else:
+        topo = topology.finest_topology(problem.coords, Af.rowptr, Af.colidx, Af.vals,
+                                        problem.dirichlet)
     A = solve.mat_from(problem.A)
     rowmap = np.asarray(problem.free, dtype=np.int64)
     n0 = A.n_rows

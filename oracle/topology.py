@@ -26,6 +26,9 @@ def skew(t) -> np.ndarray:
     (the paper's 1-based t_1..t_3 are read as t_0..t_2).
     """
     t = np.asarray(t, dtype=np.float64)
+    if t.shape[0] == 1:
+        # the scalar problem (k = kdim(1) = 1): no rotations, Q = 1
+        return np.zeros((1, 0))
     if t.shape[0] == 2:
         return np.array([[-t[1]], [t[0]]])
     return np.array([[0.0, -t[2], t[1]],
@@ -111,6 +114,30 @@ def finest_topology(coords, A_rowptr, A_colidx, A_vals, dirichlet) -> Topology:
     M = np.zeros((n, k, k))
     return Topology(pos=coords, edges=np.stack([ei, ej], axis=1).astype(np.int64), E=E, M=M,
                     dirichlet=np.asarray(dirichlet, dtype=bool).copy())
+
+
+def finest_topology_scalar(coords, A_rowptr, A_colidx, A_vals, dirichlet) -> Topology:
+    """Finest-level edge and vertex weights of the scalar problem (Sec. 4,
+    after Def. deng: E^{ij} = |A_ij|, M^i = max{0, A_ii - sum_{j != i} |A_ij|}
+    over the full (Neumann) matrix, which split an M-matrix exactly).  The
+    kernel transfers of the scalar problem are the identity (k = 1); the
+    topology expresses this with one coordinate per vertex (kdim(1) = 1), the
+    first one of the mesh."""
+    coords = np.asarray(coords, dtype=np.float64)
+    n = coords.shape[0]
+    rows = np.repeat(np.arange(n), np.diff(A_rowptr))
+    vals = np.asarray(A_vals, dtype=np.float64).reshape(-1)
+    cols = np.asarray(A_colidx)
+    upper = cols > rows
+    off = cols != rows
+    E = np.abs(vals[upper]).reshape(-1, 1, 1)
+    diag = np.zeros(n)
+    np.add.at(diag, rows[~off], vals[~off])
+    absoff = np.zeros(n)
+    np.add.at(absoff, rows[off], np.abs(vals[off]))
+    M = np.maximum(0.0, diag - absoff).reshape(n, 1, 1)
+    return Topology(pos=coords[:, :1].copy(), edges=np.stack([rows[upper], cols[upper]], axis=1).astype(np.int64),
+                    E=E, M=M, dirichlet=np.asarray(dirichlet, dtype=bool).copy())
 
 
 def edge_form(xi, xj, Eij):

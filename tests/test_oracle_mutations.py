@@ -191,3 +191,19 @@ def test_gauss_seidel_with_stale_values(monkeypatch):
         return x0 + np.einsum("nij,nj->ni", Minv, r).ravel()
     monkeypatch.setattr(S, "gs_sweep", jacobi_like)
     _fails(tg.test_sweep_equals_block_triangular_splitting)
+
+
+def test_scalar_edge_weights_with_sign(monkeypatch):
+    """E^{ij} = A_ij instead of |A_ij| (negative weights) fails the exact
+    M-matrix splitting pin."""
+    from tests import test_oracle_scalar as tsc
+    orig = T.finest_topology_scalar
+
+    def signed(coords, rp, ci, vals, dirichlet):
+        t = orig(coords, rp, ci, vals, dirichlet)
+        rows = np.repeat(np.arange(coords.shape[0]), np.diff(rp))
+        upper = np.asarray(ci) > rows
+        t.E = np.asarray(vals, dtype=np.float64).reshape(-1)[upper].reshape(-1, 1, 1)
+        return t
+    monkeypatch.setattr(T, "finest_topology_scalar", signed)
+    _fails(tsc.test_weights_split_an_m_matrix_exactly)

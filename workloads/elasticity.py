@@ -86,6 +86,12 @@ class Problem:
     E_el: np.ndarray            # (n_el,) Young's modulus per element
     nu_el: np.ndarray           # (n_el,) Poisson ratio per element
     name: str = ""
+    dofs: int = 0               # dofs per vertex: 0 means dim (elasticity), 1 scalar
+
+    @property
+    def k(self) -> int:
+        """Dofs per vertex (block size of A)."""
+        return self.dofs or self.dim
 
     @property
     def n_all(self) -> int:
@@ -97,7 +103,7 @@ class Problem:
 
     @property
     def ndof(self) -> int:
-        return self.n_free * self.dim
+        return self.n_free * self.k
 
 
 # --------------------------------------------------------------------------
