@@ -405,13 +405,18 @@ int amg_last_solve_ms(const amg_ctx *ctx, float *ms);
  * phase exactly as amg_upload_hierarchy does.
  * ---------------------------------------------------------------------- */
 
-/* The problem of Sec. 2 before the Dirichlet elimination. */
+/* The problem of Sec. 2 before the Dirichlet elimination: elasticity
+ * (Problem epseps, block = dim or 0) or the scalar problem (Problem gg,
+ * block = 1, 1 x 1 blocks; its kernel transfers are the identity and its
+ * finest edge / vertex weights E^{ij} = |A_ij|, M^i = max{0, A_ii -
+ * sum_{j != i} |A_ij|}, Sec. 4). */
 typedef struct {
-  int32_t dim;              /* 2 or 3 (elasticity, dim x dim blocks)             */
+  int32_t dim;              /* spatial dimension, 2 or 3                          */
   int32_t n_vertices;       /* all mesh vertices, Dirichlet ones included         */
   const double *coords;     /* n_vertices * dim vertex positions (host)           */
   const uint8_t *dirichlet; /* n_vertices flags, 1 = clamped vertex (may be NULL) */
   amg_bsr A_full;           /* stiffness matrix over all vertices (Neumann)       */
+  int32_t block;            /* dofs per vertex: 0 or dim (elasticity), 1 (scalar) */
 } amg_problem;
 
 /* Parameters of the setup and the readings taken where the paper is silent:
@@ -437,6 +442,11 @@ typedef struct {
  *  keep_topology 1: keep the coarse topologies the device stages build, for
  *               amg_download_topology (host memory: a level's edge and
  *               vertex matrices); 0 (default): drop them
+ *  scalar_only  1: Algorithm 1 with the scalar measure mu_s alone (the
+ *               candidate of minimal mu_s is taken; the paper's choice for
+ *               the scalar problem and the comparison of Sec. 5); 0 (default)
+ * The device stages run for elasticity (2D / 3D); the scalar problem builds
+ * its coarse topology and prolongation on the host.
  * A vertex is "standard" (real matrix row in P_s) when its row touches at
  * most cap agglomerates, does not couple to D and is kernel-exact; the
  * auxiliary rows use the own agglomerate and the 3 others with the largest
@@ -453,6 +463,7 @@ typedef struct {
   int32_t host_threads;
   int32_t device_setup;
   int32_t keep_topology;
+  int32_t scalar_only;
 } amg_setup_params;
 
 /* Fill *p with the defaults listed above (the readings of Sec. 5, 6, 7). */

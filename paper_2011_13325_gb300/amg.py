@@ -57,7 +57,7 @@ class amg_hierarchy(C.Structure):
 
 class amg_problem(C.Structure):
     _fields_ = [("dim", C.c_int32), ("n_vertices", C.c_int32), ("coords", C.POINTER(C.c_double)),
-                ("dirichlet", C.POINTER(C.c_uint8)), ("A_full", amg_bsr)]
+                ("dirichlet", C.POINTER(C.c_uint8)), ("A_full", amg_bsr), ("block", C.c_int32)]
 
 
 class amg_setup_params(C.Structure):
@@ -66,7 +66,7 @@ class amg_setup_params(C.Structure):
                 ("cap_S_later", C.c_int32), ("cap_A", C.c_int32), ("coarse_max", C.c_int32),
                 ("min_ratio", C.c_double), ("max_levels", C.c_int32),
                 ("host_threads", C.c_int32), ("device_setup", C.c_int32),
-                ("keep_topology", C.c_int32)]
+                ("keep_topology", C.c_int32), ("scalar_only", C.c_int32)]
 
 
 class AmgError(RuntimeError):
@@ -281,7 +281,8 @@ class Context:
         pr = amg_problem(int(problem.dim), int(coords.shape[0]),
                          coords.ctypes.data_as(C.POINTER(C.c_double)),
                          dmask.ctypes.data_as(C.POINTER(C.c_uint8)),
-                         bsr_struct(Af.n_rows, Af.n_cols, Af.rowptr, Af.colidx, Af.vals, keep))
+                         bsr_struct(Af.n_rows, Af.n_cols, Af.rowptr, Af.colidx, Af.vals, keep),
+                         int(getattr(problem, "k", problem.dim)))
         return self._check(lib().amg_setup(self.h, C.byref(pr), C.byref(prm), int(precision),
                                            int(smoother)))
 

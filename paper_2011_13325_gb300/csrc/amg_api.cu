@@ -200,7 +200,7 @@ static int cuda_fail(Ctx *c, cudaError_t e, const char *where) {
     if (_e != cudaSuccess) return cuda_fail(c, _e, where); \
   } while (0)
 
-static bool block_ok(int b) { return b == 2 || b == 3 || b == 6; }
+static bool block_ok(int b) { return b == 1 || b == 2 || b == 3 || b == 6; }
 
 static int validate_bsr(Ctx *c, const amg_bsr &m, const char *name) {
   char buf[256];
@@ -451,7 +451,7 @@ static int finalize_hierarchy(Ctx *c) {
     for (DevBSR *m : ops)
       if (m->nnzb && want_sell(c, *m)) CUDA_OR_FAIL(c, build_sell(c, *m), "sell layout");
     // the CG operator's double-float copy of A_0 (rows in order, 2x2 / 3x3)
-    if (l == 0 && L.A.s64 && !L.A.sell_perm && (L.k == 2 || L.k == 3))
+    if (l == 0 && L.A.s64 && !L.A.sell_perm && (L.k == 1 || L.k == 2 || L.k == 3))
       CUDA_OR_FAIL(c, build_double_float(c, L.A), "double-float A_0");
     if (precision != AMG_PREC_FP64) {
       CUDA_OR_FAIL(c, make_low_precision(c, L.A, precision), "low precision A");
@@ -737,8 +737,8 @@ int amg_upload_hierarchy(amg_ctx *h, const amg_hierarchy *hier, int precision, i
   const amg_bsr &A0 = hier->A0;
   int s = validate_bsr(c, A0, "A0");
   if (s) return s;
-  if (A0.br != A0.bc || A0.n_rows != A0.n_cols || (A0.br != 2 && A0.br != 3))
-    return fail(c, AMG_ERR_ARG, "A0 must be square with 2x2 or 3x3 blocks");
+  if (A0.br != A0.bc || A0.n_rows != A0.n_cols || (A0.br != 1 && A0.br != 2 && A0.br != 3))
+    return fail(c, AMG_ERR_ARG, "A0 must be square with 1x1, 2x2 or 3x3 blocks");
   // every row of A0 needs a diagonal block with positive diagonal entries
   for (int i = 0; i < A0.n_rows; ++i) {
     const double *blk = nullptr;
@@ -1010,7 +1010,7 @@ int amg_pcg_solve(amg_ctx *h, const double *f, double *u, int nrhs, double rtol,
   if (s) return s;
   if (!f || !u || nrhs < 1 || !(rtol >= 0.0) || maxit < 0)
     return fail(c, AMG_ERR_ARG, "bad arguments");
-  if (c->levels[0].k != 2 && c->levels[0].k != 3) return fail(c, AMG_ERR_ARG, "A0 block size");
+  if (c->levels[0].k < 1 || c->levels[0].k > 3) return fail(c, AMG_ERR_ARG, "A0 block size");
   CUDA_OR_FAIL(c, ensure_pcg_graph(c), "pcg graph");
   const size_t n = (size_t)c->levels[0].A.n_rows * c->levels[0].k;
   c->last_ms = 0.f;
@@ -1168,6 +1168,7 @@ void amg_default_setup_params(amg_setup_params *p) {
   p->host_threads = d.host_threads;
   p->device_setup = 1;
   p->keep_topology = 0;
+  p->scalar_only = 0;
 }
 
 int amg_setup(amg_ctx *h, const amg_problem *prob, const amg_setup_params *params, int precision,
@@ -1183,8 +1184,10 @@ int amg_setup(amg_ctx *h, const amg_problem *prob, const amg_setup_params *param
   const amg_bsr &A = prob->A_full;
   int s = validate_bsr(c, A, "A_full");
   if (s) return s;
-  if (A.n_rows != prob->n_vertices || A.n_cols != A.n_rows || A.br != prob->dim || A.bc != prob->dim)
-    return fail(c, AMG_ERR_ARG, "A_full must be n_vertices x n_vertices with dim x dim blocks");
+  const int blk = prob->block ? prob->block : prob->dim;
+  if (blk != 1 && blk != prob->dim) return fail(c, AMG_ERR_ARG, "amg_setup: block must be 0, 1 or dim");
+  if (A.n_rows != prob->n_vertices || A.n_cols != A.n_rows || A.br != blk || A.bc != blk)
+    return fail(c, AMG_ERR_ARG, "A_full must be n_vertices x n_vertices with block x block blocks");
   amgsetup::SetupParams prm;
   if (params) {
     prm.sigma = params->sigma;
@@ -1199,6 +1202,7 @@ int amg_setup(amg_ctx *h, const amg_problem *prob, const amg_setup_params *param
     prm.min_ratio = params->min_ratio;
     prm.max_levels = params->max_levels;
     prm.host_threads = params->host_threads;
+    prm.scalar_only = params->scalar_only != 0;
   }
   if (!(prm.sigma > 0) || prm.passes_first < 1 || prm.passes_later < 1 || prm.cap_A < 1 ||
       prm.max_levels < 1 || prm.host_threads < 0)
@@ -1211,6 +1215,7 @@ int amg_setup(amg_ctx *h, const amg_problem *prob, const amg_setup_params *param
   c->smoother = smoother;
   amgsetup::Problem pb;
   pb.dim = prob->dim;
+  pb.block = blk;
   pb.n_vertices = prob->n_vertices;
   pb.coords = prob->coords;
   pb.dirichlet = prob->dirichlet;
@@ -1218,7 +1223,7 @@ int amg_setup(amg_ctx *h, const amg_problem *prob, const amg_setup_params *param
   pb.colidx = A.colidx;
   pb.vals = A.vals;
   DeviceSink sink(c);
-  sink.device = !params || params->device_setup != 0;
+  sink.device = (!params || params->device_setup != 0) && blk != 1;
   sink.keep = params && params->keep_topology != 0;
   c->topo.clear();
   std::string err;

@@ -75,7 +75,9 @@ cudaError_t smoother_setup(Ctx *c, int level) {
   const int g = (n + 127) / 128;
   float *m32 = (c->precision != AMG_PREC_FP64) ? L.minv32 : nullptr;
   const int *col = c->smoother == AMG_SMOOTHER_HYBRID_GS ? L.gs_colour : nullptr;
-  if (k == 2)
+  if (k == 1)
+    l1_pinv_kernel<1><<<g, 128, 0, c->stream>>>(n, L.A.rowptr, L.A.colidx, L.A.v64, L.minv64, m32, col);
+  else if (k == 2)
     l1_pinv_kernel<2><<<g, 128, 0, c->stream>>>(n, L.A.rowptr, L.A.colidx, L.A.v64, L.minv64, m32, col);
   else if (k == 3)
     l1_pinv_kernel<3><<<g, 128, 0, c->stream>>>(n, L.A.rowptr, L.A.colidx, L.A.v64, L.minv64, m32, col);
@@ -160,7 +162,9 @@ cudaError_t coarse_setup(Ctx *c) {
   AMG_CUDA_TRY(dalloc((void **)&c->cinv, (size_t)N * N * sizeof(double)));
   AMG_CUDA_TRY(cudaMemsetAsync(c->cinv, 0, (size_t)N * N * sizeof(double), c->stream));
   const int g = (n + 127) / 128;
-  if (k == 2)
+  if (k == 1)
+    coarse_dense_kernel<1><<<g, 128, 0, c->stream>>>(n, L.A.rowptr, L.A.colidx, L.A.v64, c->cinv);
+  else if (k == 2)
     coarse_dense_kernel<2><<<g, 128, 0, c->stream>>>(n, L.A.rowptr, L.A.colidx, L.A.v64, c->cinv);
   else if (k == 3)
     coarse_dense_kernel<3><<<g, 128, 0, c->stream>>>(n, L.A.rowptr, L.A.colidx, L.A.v64, c->cinv);

@@ -624,9 +624,11 @@ cudaError_t launch_smooth_out64(const Ctx *c, const DevBSR &A, int prec, const f
   if (A.n_rows == 0) return cudaSuccess;
   if (A.br != A.bc || prec == AMG_PREC_FP64) return cudaErrorInvalidValue;
   if (prec == AMG_PREC_FP32_VCYCLE) {
+    if (A.br == 1) return smooth_out64_k<1, float>(c, A, A.v32, A.s32, x, b, minv, y);
     if (A.br == 2) return smooth_out64_k<2, float>(c, A, A.v32, A.s32, x, b, minv, y);
     if (A.br == 3) return smooth_out64_k<3, float>(c, A, A.v32, A.s32, x, b, minv, y);
   } else {
+    if (A.br == 1) return smooth_out64_k<1, __nv_bfloat16>(c, A, A.v16, A.s16, x, b, minv, y);
     if (A.br == 2) return smooth_out64_k<2, __nv_bfloat16>(c, A, A.v16, A.s16, x, b, minv, y);
     if (A.br == 3) return smooth_out64_k<3, __nv_bfloat16>(c, A, A.v16, A.s16, x, b, minv, y);
   }
@@ -661,7 +663,9 @@ cudaError_t launch_blockdiag_entry(const Ctx *c, int n, int k, const float *minv
                                    float *b, float *x) {
   if (n == 0) return cudaSuccess;
   const int g = (n + 255) / 256;
-  if (k == 2)
+  if (k == 1)
+    AMG_KLAUNCH(c, blockdiag_entry_kernel<1>, g, 256, n, minv, r, b, x);
+  else if (k == 2)
     AMG_KLAUNCH(c, blockdiag_entry_kernel<2>, g, 256, n, minv, r, b, x);
   else if (k == 3)
     AMG_KLAUNCH(c, blockdiag_entry_kernel<3>, g, 256, n, minv, r, b, x);
@@ -674,6 +678,7 @@ cudaError_t launch_bsr(const Ctx *c, const DevBSR &A, int prec, int mode, const 
                        const void *b, const void *minv, void *y) {
 #define AMG_BSR_CASE(R_, C_) \
   if (A.br == R_ && A.bc == C_) return bsr_prec<R_, C_>(c, A, prec, mode, x, b, minv, y);
+  AMG_BSR_CASE(1, 1)
   AMG_BSR_CASE(2, 2)
   AMG_BSR_CASE(3, 3)
   AMG_BSR_CASE(6, 6)
@@ -717,6 +722,7 @@ static cudaError_t blockdiag_k(const Ctx *c, int n, int prec, const void *minv, 
 
 cudaError_t launch_blockdiag(const Ctx *c, int n, int k, int prec, const void *minv, const void *b,
                              void *y) {
+  if (k == 1) return blockdiag_k<1>(c, n, prec, minv, b, y);
   if (k == 2) return blockdiag_k<2>(c, n, prec, minv, b, y);
   if (k == 3) return blockdiag_k<3>(c, n, prec, minv, b, y);
   if (k == 6) return blockdiag_k<6>(c, n, prec, minv, b, y);
@@ -900,7 +906,7 @@ cudaError_t build_sell(Ctx *c, DevBSR &m) {
     sell_fill_kernel<E_><<<g, 256, 0, c->stream>>>(m.n_rows, m.n_slices, m.rowptr,     \
                                                    m.colidx, m.v64, m.sell_ptr,        \
                                                    m.sell_perm, m.sell_col, m.s64);
-  AMG_FILL(4) AMG_FILL(9) AMG_FILL(36) AMG_FILL(6) AMG_FILL(18)
+  AMG_FILL(1) AMG_FILL(4) AMG_FILL(9) AMG_FILL(36) AMG_FILL(6) AMG_FILL(18)
 #undef AMG_FILL
   return cudaGetLastError();
 }

@@ -201,6 +201,7 @@ static cudaError_t spgemm_dispatch(Ctx *c, const DevBSR &L, const DevBSR &R, Dev
   if (L.bc != R.br) return cudaErrorInvalidValue;
 #define AMG_SPGEMM_CASE(a, b, d) \
   if (L.br == a && L.bc == b && R.bc == d) return spgemm<a, b, d>(c, L, R, C);
+  AMG_SPGEMM_CASE(1, 1, 1)
   AMG_SPGEMM_CASE(2, 2, 3)
   AMG_SPGEMM_CASE(3, 2, 3)
   AMG_SPGEMM_CASE(3, 3, 6)

@@ -140,6 +140,7 @@ cudaError_t launch_gs_sweep(const Ctx *c, const Level &L, int prec, const void *
                             bool forward) {
   if (L.A.n_rows == 0) return cudaSuccess;
   switch (L.k) {
+    case 1: return gs_sweep_prec<1>(c, L, prec, b, x, forward);
     case 2: return gs_sweep_prec<2>(c, L, prec, b, x, forward);
     case 3: return gs_sweep_prec<3>(c, L, prec, b, x, forward);
     case 6: return gs_sweep_prec<6>(c, L, prec, b, x, forward);

@@ -631,11 +631,13 @@ static cudaError_t launch_body(Ctx *c, cudaGraphConditionalHandle h, int in_grap
 }
 
 static cudaError_t capture_init(Ctx *c, int k, cudaGraphConditionalHandle h) {
-  return k == 2 ? launch_init<2>(c, h, 1) : k == 3 ? launch_init<3>(c, h, 1) : cudaErrorInvalidValue;
+  return k == 1 ? launch_init<1>(c, h, 1) : k == 2 ? launch_init<2>(c, h, 1)
+         : k == 3 ? launch_init<3>(c, h, 1) : cudaErrorInvalidValue;
 }
 
 static cudaError_t capture_body(Ctx *c, int k, cudaGraphConditionalHandle h) {
-  return k == 2 ? launch_body<2>(c, h, 1) : k == 3 ? launch_body<3>(c, h, 1) : cudaErrorInvalidValue;
+  return k == 1 ? launch_body<1>(c, h, 1) : k == 2 ? launch_body<2>(c, h, 1)
+         : k == 3 ? launch_body<3>(c, h, 1) : cudaErrorInvalidValue;
 }
 
 static bool host_go(const PcgState &s) {
@@ -646,14 +648,15 @@ static bool host_go(const PcgState &s) {
 // read back after every iteration (no graph; used for per-kernel profiling).
 cudaError_t pcg_host_loop(Ctx *c) {
   const int k = c->levels[0].k;
-  if (k != 2 && k != 3) return cudaErrorInvalidValue;
-  AMG_CUDA_TRY(k == 2 ? launch_init<2>(c, 0, 0) : launch_init<3>(c, 0, 0));
+  if (k != 1 && k != 2 && k != 3) return cudaErrorInvalidValue;
+  AMG_CUDA_TRY(k == 1 ? launch_init<1>(c, 0, 0) : k == 2 ? launch_init<2>(c, 0, 0) : launch_init<3>(c, 0, 0));
   AMG_CUDA_TRY(cudaMemcpyAsync(c->st_host, c->st, sizeof(PcgState), cudaMemcpyDeviceToHost,
                                c->stream));
   AMG_CUDA_TRY(cudaStreamSynchronize(c->stream));
   bool go = c->st_host->rr > c->st_host->tol2 && c->st_host->maxit > 0 && isfinite(c->st_host->rr);
   while (go) {
-    AMG_CUDA_TRY(k == 2 ? launch_body<2>(c, 0, 0) : launch_body<3>(c, 0, 0));
+    AMG_CUDA_TRY(k == 1 ? launch_body<1>(c, 0, 0) : k == 2 ? launch_body<2>(c, 0, 0)
+                        : launch_body<3>(c, 0, 0));
     AMG_CUDA_TRY(cudaMemcpyAsync(c->st_host, c->st, sizeof(PcgState), cudaMemcpyDeviceToHost,
                                  c->stream));
     AMG_CUDA_TRY(cudaStreamSynchronize(c->stream));
@@ -867,12 +870,13 @@ extern "C" int amg_cg_operator(amg_ctx *h, const double *p, double *q) {
     return AMG_ERR_STATE;
   }
   const int k = c->levels[0].k;
-  if (!p || !q || (k != 2 && k != 3)) {
-    c->err = "amg_cg_operator: NULL vector or A_0 block size other than 2 or 3";
+  if (!p || !q || (k != 1 && k != 2 && k != 3)) {
+    c->err = "amg_cg_operator: NULL vector or A_0 block size other than 1, 2 or 3";
     return AMG_ERR_ARG;
   }
   cudaError_t e = cudaSetDevice(c->device);
-  if (e == cudaSuccess) e = k == 2 ? cg_operator_k<2>(c, p, q) : cg_operator_k<3>(c, p, q);
+  if (e == cudaSuccess)
+    e = k == 1 ? cg_operator_k<1>(c, p, q) : k == 2 ? cg_operator_k<2>(c, p, q) : cg_operator_k<3>(c, p, q);
   if (e != cudaSuccess) {
     c->err = std::string("amg_cg_operator: ") + cudaGetErrorString(e);
     return AMG_ERR_CUDA;
@@ -894,13 +898,15 @@ extern "C" int amg_profile_pcg(amg_ctx *h, int reps, int32_t *kind, double *us, 
     return AMG_ERR_STATE;
   }
   const int k = c->levels[0].k;
-  if (k != 2 && k != 3) {
+  if (k != 1 && k != 2 && k != 3) {
     c->err = "amg_profile_pcg: A_0 block size";
     return AMG_ERR_ARG;
   }
   cudaError_t e = cudaSetDevice(c->device);
   double t[6] = {0}, b[6] = {0};
-  if (e == cudaSuccess) e = k == 2 ? profile_pcg_k<2>(c, reps, t, b) : profile_pcg_k<3>(c, reps, t, b);
+  if (e == cudaSuccess)
+    e = k == 1 ? profile_pcg_k<1>(c, reps, t, b)
+        : k == 2 ? profile_pcg_k<2>(c, reps, t, b) : profile_pcg_k<3>(c, reps, t, b);
   if (e != cudaSuccess) {
     c->err = std::string("amg_profile_pcg: ") + cudaGetErrorString(e);
     return AMG_ERR_CUDA;

@@ -42,6 +42,7 @@ static void qmat(int d, const double *t, double *q) {
   const int k = kdim(d);
   for (int i = 0; i < k * k; ++i) q[i] = 0.0;
   for (int i = 0; i < k; ++i) q[i * k + i] = 1.0;
+  if (d == 1) return;  // the scalar problem: Q = 1
   if (d == 2) {
     q[0 * k + 2] = -t[1];
     q[1 * k + 2] = t[0];
@@ -78,6 +79,7 @@ static void mtm(const double *A, const double *B, double *C, int m, int n, int p
 
 // S = Skew(t) as a d x (k-d) block
 static void skew_block(int d, const double *t, double *S) {
+  if (d == 1) return;  // no rotations
   if (d == 2) {
     S[0] = -t[1];
     S[1] = t[0];
@@ -374,6 +376,40 @@ Topo finest_topology(int d, int n, const double *coords, const uint8_t *dirichle
       }
   T.build_adj();
   T.rot_free = true;  // finest elasticity edges: displacement blocks only, M = 0
+  return T;
+}
+
+// The scalar problem (Sec. 4 after Def. deng): E^{ij} = |A_ij|, M^i =
+// max{0, A_ii - sum_{j != i} |A_ij|} over the full matrix.  Its kernel
+// transfers are the identity (k = 1), which the topology expresses with one
+// coordinate per vertex (kdim(1) = 1), the first of the mesh.
+Topo finest_topology_scalar(int dim, int n, const double *coords, const uint8_t *dirichlet,
+                            const int32_t *rp, const int32_t *ci, const double *vals) {
+  Topo T;
+  T.n = n;
+  T.d = 1;
+  T.k = 1;
+  T.pos.resize(n);
+  for (int i = 0; i < n; ++i) T.pos[i] = coords[(size_t)i * dim];
+  T.dir.assign(n, 0);
+  for (int i = 0; i < n; ++i) T.dir[i] = dirichlet ? (dirichlet[i] != 0) : 0;
+  T.M.assign(n, 0.0);
+  for (int i = 0; i < n; ++i) {
+    double diag = 0.0, off = 0.0;
+    for (int p = rp[i]; p < rp[i + 1]; ++p) {
+      if (ci[p] == i)
+        diag += vals[p];
+      else
+        off += fabs(vals[p]);
+      if (ci[p] > i) {
+        T.ei.push_back(i);
+        T.ej.push_back(ci[p]);
+        T.E.push_back(fabs(vals[p]));
+      }
+    }
+    T.M[i] = std::max(0.0, diag - off);
+  }
+  T.build_adj();
   return T;
 }
 
@@ -850,7 +886,7 @@ static Coarsening successive_matching(const Topo &T0, const SetupParams &prm, in
     for (size_t c0 = 0; c0 < order.size(); c0 += chunk) {
       const size_t c1 = std::min(order.size(), c0 + chunk);
       done.clear();
-      for (size_t q = c0; q < c1; ++q) {
+      for (size_t q = c0; q < c1 && !prm.scalar_only; ++q) {
         const int ci = order[q];
         if (!inT[ci]) continue;
         candidates(ci, cands);
@@ -863,6 +899,17 @@ static Coarsening successive_matching(const Topo &T0, const SetupParams &prm, in
         inT[ci] = 0;
         candidates(ci, cands);
         bool matched = false;
+        if (prm.scalar_only) {
+          // mu_s alone: the candidate of minimal mu_s is taken (Sec. 5's
+          // comparison and the paper's scalar runs)
+          if (!cands.empty()) {
+            groups.push_back({ci, cands[0].cj});
+            inT[cands[0].cj] = 0;
+          } else {
+            singles.push_back(ci);
+          }
+          continue;
+        }
         for (size_t u = 0; u < cands.size(); ++u) {
           const int cj = cands[u].cj;
           auto it = done.find((long long)ci * m + cj);
@@ -1114,12 +1161,17 @@ int build_levels(const Problem &prob, const SetupParams &prm, LevelSink &sink, s
     ~ThreadScope() { omp_set_num_threads(saved); }
   } scope(prm.host_threads);
 #endif
-  const int d = prob.dim, n_all = prob.n_vertices;
-  if (d != 2 && d != 3) {
+  const int dim = prob.dim, n_all = prob.n_vertices;
+  if (dim != 2 && dim != 3) {
     err = "dim must be 2 or 3";
     return -1;
   }
-  Topo T = finest_topology(d, n_all, prob.coords, prob.dirichlet, prob.rowptr, prob.colidx, prob.vals);
+  const bool scalar = prob.block == 1;
+  const int d = scalar ? 1 : dim;  // block size of A_0
+  Topo T = scalar ? finest_topology_scalar(dim, n_all, prob.coords, prob.dirichlet, prob.rowptr,
+                                           prob.colidx, prob.vals)
+                  : finest_topology(d, n_all, prob.coords, prob.dirichlet, prob.rowptr, prob.colidx,
+                                    prob.vals);
   // A_0: rows / columns of the free vertices
   std::vector<int> rowmap, newid(n_all, -1);
   for (int v = 0; v < n_all; ++v)

@@ -31,6 +31,7 @@ struct Topo {
 
 struct Problem {
   int dim = 0, n_vertices = 0;
+  int block = 0;  // dofs per vertex: dim (elasticity; also 0) or 1 (the scalar problem)
   const double *coords = nullptr;
   const uint8_t *dirichlet = nullptr;
   const int32_t *rowptr = nullptr, *colidx = nullptr;
@@ -47,6 +48,7 @@ struct SetupParams {
   double min_ratio = 1.5;
   int max_levels = 16;
   int host_threads = 0;  // OpenMP threads of this call (0: the process default)
+  bool scalar_only = false;  // Algorithm 1 with mu_s alone (the paper's scalar runs)
 };
 
 // Receives the levels as they are built: first(A_0), then for every level
@@ -79,6 +81,9 @@ struct LevelSink {
 
 Topo finest_topology(int d, int n, const double *coords, const uint8_t *dirichlet,
                      const int32_t *rp, const int32_t *ci, const double *vals);
+// the scalar problem (1 x 1 blocks; coords hold dim values per vertex)
+Topo finest_topology_scalar(int dim, int n, const double *coords, const uint8_t *dirichlet,
+                            const int32_t *rp, const int32_t *ci, const double *vals);
 
 int build_levels(const Problem &prob, const SetupParams &prm, LevelSink &sink, std::string &err);
 

@@ -93,18 +93,19 @@ int main(int argc, char **argv) {
   const std::string dir = argv[1];
   FILE *f = fopen((dir + "/problem.bin").c_str(), "rb");
   if (!f) return 3;
-  int32_t hdr[3];
-  if (fread(hdr, 4, 3, f) != 3) return 3;
-  const int dim = hdr[0], n = hdr[1], nnzb = hdr[2];
+  int32_t hdr[4];
+  if (fread(hdr, 4, 4, f) != 4) return 3;
+  const int dim = hdr[0], n = hdr[1], nnzb = hdr[2], block = hdr[3];
   std::vector<double> coords, vals;
   std::vector<uint8_t> dirichlet;
   std::vector<int32_t> rowptr, colidx;
   if (!get(f, coords, (size_t)n * dim) || !get(f, dirichlet, n) || !get(f, rowptr, n + 1) ||
-      !get(f, colidx, nnzb) || !get(f, vals, (size_t)nnzb * dim * dim))
+      !get(f, colidx, nnzb) || !get(f, vals, (size_t)nnzb * block * block))
     return 3;
   fclose(f);
   Problem pb;
   pb.dim = dim;
+  pb.block = block;
   pb.n_vertices = n;
   pb.coords = coords.data();
   pb.dirichlet = dirichlet.data();
@@ -116,6 +117,11 @@ int main(int argc, char **argv) {
   if (argc > 4) {  // matching passes on the first / later levels
     prm.passes_first = atoi(argv[3]);
     prm.passes_later = atoi(argv[4]);
+  }
+  if (argc > 7) {  // mu_s alone; row caps of real-matrix rows on the first / later levels
+    prm.scalar_only = atoi(argv[5]) != 0;
+    prm.cap_S_first = atoi(argv[6]);
+    prm.cap_S_later = atoi(argv[7]);
   }
   HostGalerkinSink sink;
   std::string err;

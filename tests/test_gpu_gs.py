@@ -21,6 +21,8 @@ CASES = {
                          hierarchy.SetupParams(coarse_max=6)),
     "jump11": lambda: (configs.jump11(12), hierarchy.SetupParams(coarse_max=8, passes_first=4,
                                                                   passes_later=3)),
+    "poisson": lambda: (configs.poisson(14), hierarchy.SetupParams(coarse_max=12,
+                                                                    **configs.SETUP["poisson"])),
 }
 _H = {}
 

@@ -36,6 +36,10 @@ CASES = {
     # (one cell per box side), 4 passes on the first level and 3 later
     "jump11": lambda: (configs.jump11(12), hierarchy.SetupParams(coarse_max=8, passes_first=4,
                                                                   passes_later=3)),
+    # Sec. 7's scalar model problem (1 x 1 blocks), with the paper's scalar
+    # setup (mu_s alone, 4 / 3 passes, caps 4)
+    "poisson": lambda: (configs.poisson(14), hierarchy.SetupParams(coarse_max=12,
+                                                                    **configs.SETUP["poisson"])),
 }
 
 

@@ -37,6 +37,12 @@ CASES = {
     "checker2d": (lambda: make_problem((17, 17), seed=1, nu=0.25, E_fn=_checker), {"coarse_max": 4}),
     "beam": (lambda: configs.beam(4), {"coarse_max": 8}),
     "jump11": (lambda: configs.jump11(12), {"coarse_max": 8, "passes_first": 4, "passes_later": 3}),
+    # the scalar model problem with the paper's scalar parameters (mu_s alone,
+    # 4 / 3 passes, real-row cap 4) and with the full criteria
+    "poisson3d": (lambda: configs.poisson(14), dict(configs.SETUP["poisson"], coarse_max=12)),
+    "poisson3d_full": (lambda: configs.poisson(12), {"coarse_max": 10}),
+    "poisson2d": (lambda: __import__("workloads.poisson", fromlist=["x"]).make_poisson((23, 19), seed=5),
+                  {"coarse_max": 6}),
 }
 
 
@@ -56,7 +62,8 @@ def harness(tmp_path_factory):
 def _write_problem(p, d):
     Af = p.A_full
     with open(os.path.join(d, "problem.bin"), "wb") as f:
-        np.array([p.dim, p.coords.shape[0], Af.colidx.shape[0]], dtype=np.int32).tofile(f)
+        np.array([p.dim, p.coords.shape[0], Af.colidx.shape[0], getattr(p, "k", p.dim)],
+                 dtype=np.int32).tofile(f)
         np.ascontiguousarray(p.coords, dtype=np.float64).tofile(f)
         np.ascontiguousarray(p.dirichlet, dtype=np.uint8).tofile(f)
         np.ascontiguousarray(Af.rowptr, dtype=np.int32).tofile(f)
@@ -103,7 +110,9 @@ def test_host_setup_matches_oracle_setup(harness, tmp_path, name, threads):
     _write_problem(p, str(tmp_path))
     env = dict(os.environ, OMP_NUM_THREADS=str(threads))
     r = subprocess.run([harness, str(tmp_path), str(kw.get("coarse_max", 0)),
-                        str(kw.get("passes_first", 5)), str(kw.get("passes_later", 4))],
+                        str(kw.get("passes_first", 5)), str(kw.get("passes_later", 4)),
+                        str(int(kw.get("scalar_only", False))), str(kw.get("cap_S_first", 8)),
+                        str(kw.get("cap_S_later", 6))],
                        capture_output=True,
                        text=True, env=env, timeout=300)
     assert r.returncode == 0, r.stderr

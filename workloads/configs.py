@@ -27,6 +27,9 @@ The paper's own three workloads (Sec. 7), on structured perturbed meshes:
   mu = lambda = 1 elsewhere (nu = 1/3, E = 4/3 mu); default 67^3 vertices
   (six cells per box side), 296,274 free, 888,822 dofs; seed 7.
 Body forces are not given in the paper; both use (0, 0, -1).
+* ``poisson``   the scalar model problem: -Laplace u = 1 on the unit cube,
+  u = 0 on the boundary; default 128^3 vertices (126^3 = 2,000,376
+  unknowns); seed 8.
 """
 from __future__ import annotations
 
@@ -105,6 +108,26 @@ def jump11(n: int = 67, seed: int = 7):
                         E_fn=jump11_modulus, name=f"jump11_{n}")
 
 
+def poisson(n: int = 128, seed: int = 8):
+    """The scalar model problem: -Laplace u = 1 on the unit cube with n^3
+    vertices, u = 0 on the whole boundary ((n - 2)^3 unknowns)."""
+    from .poisson import make_poisson
+    return make_poisson((n, n, n), seed=seed, name=f"poisson{n}")
+
+
 # Setup parameters the paper states per workload (Sec. 7); the rest are the
-# defaults (5 passes on the first level and 4 later, caps 8 / 6 / 4).
-SETUP = {"jump11": {"passes_first": 4, "passes_later": 3}}
+# defaults (5 passes on the first level and 4 later, caps 8 / 6 / 4).  The
+# scalar problem: mu_s alone, 4 passes first and 3 later, every real-matrix
+# row of P capped at 4 entries (the paper: 4 on the first three levels); its
+# coarse size min(1600, n / 1250) is set where the problem size is known.
+SETUP = {"jump11": {"passes_first": 4, "passes_later": 3},
+         "poisson": {"scalar_only": True, "passes_first": 4, "passes_later": 3, "cap_S_first": 4,
+                     "cap_S_later": 4}}
+
+
+def coarse_size(name, n0):
+    """The coarse size a workload's setup stops at (0: the library default)."""
+    if name == "poisson":
+        import math
+        return min(1600, math.ceil(n0 / 1250))
+    return 0
