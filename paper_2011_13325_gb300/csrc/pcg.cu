@@ -15,7 +15,9 @@ constexpr int kRedThreads = 256;
 constexpr double kReplaceDrop = 1e-6;
 
 static int red_grid(const Ctx *c) { return c->num_sms * 8; }  // SpMV + dot kernels
-static int vec_grid(const Ctx *c) { return c->num_sms * 2; }  // pure vector reductions
+// pure vector reductions: 8 blocks of 256 threads per SM keep enough loads
+// in flight for HBM (2 per SM left r.z and the x / r update latency-bound)
+static int vec_grid(const Ctx *c) { return c->num_sms * 8; }
 
 // Block-wide sum of NV values; returns the sums in thread 0.
 template <int NV>
