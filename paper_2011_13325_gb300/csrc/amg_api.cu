@@ -472,6 +472,7 @@ static double wall_s() {
 }
 
 namespace amg {
+amgsetup::PairMeasure *make_device_pair_measure(Ctx *c);
 cudaError_t device_coarse_topology(Ctx *c, const amgsetup::Topo &T, const std::vector<int> &agg, int nc,
                                    const std::vector<double> &xc, amgsetup::Topo &C);
 cudaError_t device_prolongation(Ctx *c, int level, const amgsetup::Topo &T, const std::vector<int> &agg,
@@ -486,8 +487,14 @@ struct DeviceSink : amgsetup::LevelSink {
   double device_s = 0.0, device_setup_s = 0.0;
   bool device = true, keep = false;
   std::vector<char> p_on_device;  // per level: P_l already built on the device
+  amgsetup::PairMeasure *pm = nullptr;
   explicit DeviceSink(Ctx *cc) : c(cc) {}
+  ~DeviceSink() override { delete pm; }
   bool device_stages() const override { return device; }
+  amgsetup::PairMeasure *pair_measure() override {
+    if (!pm) pm = make_device_pair_measure(c);
+    return pm;
+  }
   int coarse_topology(int level, const amgsetup::Topo &T, const std::vector<int> &agg, int nc,
                       const std::vector<double> &xc, amgsetup::Topo &out) override {
     const double t0 = wall_s();

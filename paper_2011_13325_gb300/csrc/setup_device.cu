@@ -24,6 +24,7 @@
 // displacement blocks of the edge matrices), D = its diagonal block.  Two
 // passes: row lengths, then columns (ascending) and values.
 #include <algorithm>
+#include <array>
 
 #include "amg_internal.h"
 #include "dense_dev.cuh"
@@ -676,5 +677,240 @@ cudaError_t device_prolongation(Ctx *c, int level, const amgsetup::Topo &T, cons
   *handled = 1;
   return cudaSuccess;
 }
+
+// ---------------------------------------------------------------- pair measure
+
+// Eigen-decomposition of the symmetric part of A (w eigenvalues, V columns).
+template <int K>
+__device__ void sym_eig_dev(const double *A, double *w, double *V) {
+  double a[K * K];
+  for (int i = 0; i < K; ++i)
+    for (int j = 0; j < K; ++j) a[i * K + j] = 0.5 * (A[i * K + j] + A[j * K + i]);
+  jacobi_eig<K>(a, V);
+  for (int i = 0; i < K; ++i) w[i] = a[i * K + i];
+}
+
+// H(A, B) = A (A + B)^+ B, symmetrised (the harmonic mean of Lemma mu2)
+template <int K>
+__device__ void harmonic_dev(const double *A, const double *B, double *H) {
+  double S[K * K], P[K * K], T[K * K];
+  for (int i = 0; i < K * K; ++i) S[i] = A[i] + B[i];
+  pinv_dev<K>(S, P);
+  for (int i = 0; i < K; ++i)
+    for (int j = 0; j < K; ++j) {
+      double s = 0.0;
+      for (int l = 0; l < K; ++l) s += P[i * K + l] * B[l * K + j];
+      T[i * K + j] = s;
+    }
+  for (int i = 0; i < K; ++i)
+    for (int j = 0; j < K; ++j) {
+      double s = 0.0;
+      for (int l = 0; l < K; ++l) s += A[i * K + l] * T[l * K + j];
+      S[i * K + j] = s;
+    }
+  for (int i = 0; i < K; ++i)
+    for (int j = 0; j < K; ++j) H[i * K + j] = 0.5 * (S[i * K + j] + S[j * K + i]);
+}
+
+// The smallest mu with L <= mu R on the range of R (eigenvalues of R above
+// 1e-10 of its largest); +inf when L has energy (above 1e-8 of its largest
+// eigenvalue) on the kernel of R.
+template <int K>
+__device__ double gen_lambda_max_dev(const double *L, const double *R) {
+  double wl[K], Vl[K * K], wr[K], Vr[K * K];
+  sym_eig_dev<K>(L, wl, Vl);
+  double lmax = 0.0;
+  for (int i = 0; i < K; ++i) lmax = fmax(lmax, wl[i]);
+  if (lmax <= 0.0) return 0.0;
+  sym_eig_dev<K>(R, wr, Vr);
+  double rmax = 0.0;
+  for (int i = 0; i < K; ++i) rmax = fmax(rmax, wr[i]);
+  if (rmax <= 0.0) return INFINITY;
+  double Sr[K * K], Kr[K * K];
+  int nr = 0, nk = 0;
+  for (int m = 0; m < K; ++m) {
+    if (wr[m] > 1e-10 * rmax) {
+      const double sc = 1.0 / sqrt(wr[m]);
+      for (int i = 0; i < K; ++i) Sr[i * K + nr] = Vr[i * K + m] * sc;
+      ++nr;
+    } else {
+      for (int i = 0; i < K; ++i) Kr[i * K + nk] = Vr[i * K + m];
+      ++nk;
+    }
+  }
+  // C = B^T L B for the columns B (n x m, stride K), returned m x m (stride K)
+  auto project = [&](const double *Bc, int m, double *C) {
+    for (int a = 0; a < m; ++a)
+      for (int b = 0; b < m; ++b) {
+        double s = 0.0;
+        for (int i = 0; i < K; ++i) {
+          double li = 0.0;
+          for (int j = 0; j < K; ++j) li += L[i * K + j] * Bc[j * K + b];
+          s += Bc[i * K + a] * li;
+        }
+        C[a * K + b] = s;
+      }
+  };
+  double C[K * K], Cm[K * K], w[K], V[K * K];
+  if (nk > 0) {
+    project(Kr, nk, C);
+    // eigenvalues of the nk x nk leading block
+    for (int i = 0; i < K * K; ++i) Cm[i] = 0.0;
+    for (int a = 0; a < nk; ++a)
+      for (int b = 0; b < nk; ++b) Cm[a * K + b] = C[a * K + b];
+    sym_eig_dev<K>(Cm, w, V);
+    double leak = -INFINITY;
+    // the padding rows / columns add zero eigenvalues; the leak is the
+    // largest eigenvalue of the nk x nk block, which is >= 0 here as L >= 0
+    for (int i = 0; i < K; ++i) leak = fmax(leak, w[i]);
+    if (leak > 1e-8 * lmax) return INFINITY;
+  }
+  project(Sr, nr, C);
+  for (int i = 0; i < K * K; ++i) Cm[i] = 0.0;
+  for (int a = 0; a < nr; ++a)
+    for (int b = 0; b < nr; ++b) Cm[a * K + b] = C[a * K + b];
+  sym_eig_dev<K>(Cm, w, V);
+  double mu = 0.0;
+  for (int i = 0; i < K; ++i) mu = fmax(mu, w[i]);
+  return mu;
+}
+
+struct PairArgs {
+  int n, delta;
+  const double *pos, *E, *Dh;  // pass topology: positions, edge matrices, D-hat blocks
+  const int *adj_ptr, *adj_nbr, *adj_edge;
+};
+
+// Lemma mu2: mu_p^delta(v_i, v_j) of one candidate pair (one thread).
+template <int D>
+__global__ void __launch_bounds__(64) mu_p_kernel(PairArgs g, int n_pairs, const int *__restrict__ pairs,
+                                                  double *__restrict__ mu_out) {
+  constexpr int K = D == 2 ? 3 : 6, KK = K * K;
+  const int q = blockIdx.x * blockDim.x + threadIdx.x;
+  if (q >= n_pairs) return;
+  const int i = pairs[2 * q], j = pairs[2 * q + 1];
+  double t[D], A[KK], B[KK], Lm[KK], R[KK], X[KK], Y[KK], H[KK];
+  for (int a = 0; a < D; ++a) t[a] = 0.5 * (g.pos[(size_t)i * D + a] - g.pos[(size_t)j * D + a]);
+  transfer_dev<D>(t, t, g.Dh + (size_t)i * KK, A);  // Q^{ji, T} D_ii Q^{ji}
+  for (int a = 0; a < D; ++a) t[a] = -t[a];
+  transfer_dev<D>(t, t, g.Dh + (size_t)j * KK, B);  // Q^{ij, T} D_jj Q^{ij}
+  harmonic_dev<K>(A, B, Lm);
+  // the edge (i, j): its slot in i's sorted neighbour list
+  int e = -1;
+  {
+    int lo = g.adj_ptr[i], hi = g.adj_ptr[i + 1];
+    while (lo < hi) {
+      const int mid = (lo + hi) >> 1;
+      if (g.adj_nbr[mid] < j) lo = mid + 1; else hi = mid;
+    }
+    if (lo < g.adj_ptr[i + 1] && g.adj_nbr[lo] == j) e = g.adj_edge[lo];
+  }
+  if (e < 0) {
+    mu_out[q] = INFINITY;
+    return;
+  }
+  for (int s = 0; s < KK; ++s) R[s] = g.E[(size_t)e * KK + s];
+  if (g.delta) {
+    int p = g.adj_ptr[i], r = g.adj_ptr[j];
+    const int pe = g.adj_ptr[i + 1], re = g.adj_ptr[j + 1];
+    while (p < pe && r < re) {
+      const int a = g.adj_nbr[p], b = g.adj_nbr[r];
+      if (a < b) {
+        ++p;
+      } else if (b < a) {
+        ++r;
+      } else {
+        const int l = a;
+        for (int s = 0; s < D; ++s) t[s] = 0.5 * (g.pos[(size_t)i * D + s] - g.pos[(size_t)l * D + s]);
+        transfer_dev<D>(t, t, g.E + (size_t)g.adj_edge[p] * KK, X);   // Q^{li}
+        for (int s = 0; s < D; ++s) t[s] = 0.5 * (g.pos[(size_t)j * D + s] - g.pos[(size_t)l * D + s]);
+        transfer_dev<D>(t, t, g.E + (size_t)g.adj_edge[r] * KK, Y);   // Q^{lj}
+        harmonic_dev<K>(X, Y, H);
+        // pulled back with Q^{v_i -> v_l} Q^{ji}: one shift x_l - (x_i + x_j)/2
+        for (int s = 0; s < D; ++s)
+          t[s] = g.pos[(size_t)l * D + s] - 0.5 * (g.pos[(size_t)i * D + s] + g.pos[(size_t)j * D + s]);
+        transfer_dev<D>(t, t, H, X);
+        for (int s = 0; s < KK; ++s) R[s] += 0.5 * g.delta * X[s];
+        ++p;
+        ++r;
+      }
+    }
+  }
+  mu_out[q] = gen_lambda_max_dev<K>(Lm, R);
+}
+
+// Device evaluation of mu_p for the batches of one matching pass: the
+// pass's topology is uploaded once (begin_pass), every batch of pairs is one
+// launch.
+struct DevicePairMeasure : amgsetup::PairMeasure {
+  Ctx *c;
+  DevScratch buf;
+  PairArgs g{};
+  int d = 0;
+  int *d_pairs = nullptr;
+  double *d_mu = nullptr;
+  size_t cap = 0;
+  explicit DevicePairMeasure(Ctx *cc) : c(cc) {}
+  int begin_pass(const amgsetup::Topo &T, const std::vector<double> &Dh, int delta) override {
+    for (void *p : buf.ptrs) dfree(p);
+    buf.ptrs.clear();
+    d_pairs = nullptr;
+    d_mu = nullptr;
+    cap = 0;
+    d = T.d;
+    g.n = T.n;
+    g.delta = delta;
+    double *pos, *E, *dh;
+    int *ap, *an, *ae;
+    if (buf.put(c, &pos, T.pos.data(), T.pos.size()) != cudaSuccess ||
+        buf.put(c, &E, T.E.data(), T.E.size()) != cudaSuccess ||
+        buf.put(c, &dh, Dh.data(), Dh.size()) != cudaSuccess ||
+        buf.put(c, &ap, T.adj_ptr.data(), T.adj_ptr.size()) != cudaSuccess ||
+        buf.put(c, &an, T.adj_nbr.data(), T.adj_nbr.size()) != cudaSuccess ||
+        buf.put(c, &ae, T.adj_edge.data(), T.adj_edge.size()) != cudaSuccess)
+      return -1;
+    g.pos = pos;
+    g.E = E;
+    g.Dh = dh;
+    g.adj_ptr = ap;
+    g.adj_nbr = an;
+    g.adj_edge = ae;
+    return cudaStreamSynchronize(c->stream) == cudaSuccess ? 0 : -1;
+  }
+  int evaluate(const std::vector<std::array<int, 2>> &pairs, std::vector<double> &mu) override {
+    const size_t n = pairs.size();
+    mu.resize(n);
+    if (n == 0) return 0;
+    if (n > cap) {
+      if (d_pairs) dfree(d_pairs);
+      if (d_mu) dfree(d_mu);
+      d_pairs = nullptr;
+      d_mu = nullptr;
+      cap = std::max(n, (size_t)4096);
+      if (dalloc((void **)&d_pairs, cap * 2 * sizeof(int)) != cudaSuccess ||
+          dalloc((void **)&d_mu, cap * sizeof(double)) != cudaSuccess)
+        return -1;
+    }
+    if (cudaMemcpyAsync(d_pairs, pairs.data(), n * 2 * sizeof(int), cudaMemcpyHostToDevice, c->stream) !=
+        cudaSuccess)
+      return -1;
+    const int nb = (int)((n + 63) / 64);
+    if (d == 2)
+      mu_p_kernel<2><<<nb, 64, 0, c->stream>>>(g, (int)n, d_pairs, d_mu);
+    else
+      mu_p_kernel<3><<<nb, 64, 0, c->stream>>>(g, (int)n, d_pairs, d_mu);
+    if (cudaGetLastError() != cudaSuccess) return -1;
+    if (cudaMemcpyAsync(mu.data(), d_mu, n * sizeof(double), cudaMemcpyDeviceToHost, c->stream) !=
+        cudaSuccess)
+      return -1;
+    return cudaStreamSynchronize(c->stream) == cudaSuccess ? 0 : -1;
+  }
+  ~DevicePairMeasure() override {
+    if (d_pairs) dfree(d_pairs);
+    if (d_mu) dfree(d_mu);
+  }
+};
+
+amgsetup::PairMeasure *make_device_pair_measure(Ctx *c) { return new DevicePairMeasure(c); }
 
 }  // namespace amg

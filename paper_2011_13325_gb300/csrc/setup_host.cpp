@@ -792,7 +792,7 @@ struct Coarsening {
 // final_topology = false leaves the coarse edge / vertex matrices of the
 // last pass to the caller (positions only).
 static Coarsening successive_matching(const Topo &T0, const SetupParams &prm, int passes,
-                                      bool final_topology = true) {
+                                      bool final_topology, PairMeasure *pm, std::string &err) {
   const int n = T0.n, k = T0.k, d = T0.d;
   const double sigma = prm.sigma;
   std::vector<double> Dh0 = aux_diagonal(T0);
@@ -814,6 +814,13 @@ static Coarsening successive_matching(const Topo &T0, const SetupParams &prm, in
   const Topo *Tc = &T0;
   for (int pass = 1; pass <= passes; ++pass) {
     std::vector<double> Dh = (pass == 1) ? Dh0 : aux_diagonal(*Tc);
+    // a device evaluator of mu_p for this pass (elasticity levels; the
+    // scalar problem's 1 x 1 measures stay on the host)
+    PairMeasure *dev_pm = (pm && !prm.scalar_only && Tc->d >= 2) ? pm : nullptr;
+    if (dev_pm && dev_pm->begin_pass(*Tc, Dh, prm.delta) != 0) {
+      err = "device pair measure: upload failed";
+      dev_pm = nullptr;
+    }
     const int m = Tc->n;
     std::vector<double> tmax(m, 0.0);
     for (int v = 0; v < m; ++v) {
@@ -875,11 +882,29 @@ static Coarsening successive_matching(const Topo &T0, const SetupParams &prm, in
     std::unordered_map<long long, Eval> done;
     std::vector<std::array<int, 2>> tasks;
     std::vector<Eval> res;
+    // batches of at least kDeviceBatch pairs go to the device evaluator of
+    // mu_p (if any); the mu_g tests stay on the host
+    const size_t kDeviceBatch = 512;
+    std::vector<double> dmu;
     auto run_tasks = [&]() {
       res.resize(tasks.size());
+      if (dev_pm && tasks.size() >= kDeviceBatch && dev_pm->evaluate(tasks, dmu) == 0) {
 #pragma omp parallel for schedule(dynamic, 1)
-      for (long long q = 0; q < (long long)tasks.size(); ++q)
-        evaluate(tasks[q][0], tasks[q][1], res[q].mu, res[q].gok);
+        for (long long q = 0; q < (long long)tasks.size(); ++q) {
+          const int ci = tasks[q][0], cj = tasks[q][1];
+          res[q].mu = dmu[q];
+          res[q].gok = 1;
+          if (dmu[q] < sigma && members[ci].size() + members[cj].size() > 2) {
+            std::vector<int> uni(members[ci]);
+            uni.insert(uni.end(), members[cj].begin(), members[cj].end());
+            res[q].gok = mu_g_below(T0, Dh0, uni, prm.delta, sigma) ? 1 : 0;
+          }
+        }
+      } else {
+#pragma omp parallel for schedule(dynamic, 1)
+        for (long long q = 0; q < (long long)tasks.size(); ++q)
+          evaluate(tasks[q][0], tasks[q][1], res[q].mu, res[q].gok);
+      }
       for (size_t q = 0; q < tasks.size(); ++q) done[(long long)tasks[q][0] * m + tasks[q][1]] = res[q];
       tasks.clear();
     };
@@ -1208,7 +1233,9 @@ int build_levels(const Problem &prob, const SetupParams &prm, LevelSink &sink, s
     const bool first = level == 0;
     double t0 = now_s();
     const bool dev = sink.device_stages();
-    Coarsening cs = successive_matching(T, prm, first ? prm.passes_first : prm.passes_later, !dev);
+    Coarsening cs = successive_matching(T, prm, first ? prm.passes_first : prm.passes_later, !dev,
+                                        dev ? sink.pair_measure() : nullptr, err);
+    if (!err.empty()) return -1;
     if (verbose)
       fprintf(stderr, "[amg setup] level %d: %d vertices -> %d agglomerates, matching %.2f s\n",
               level, T.n, cs.nc, now_s() - t0);

@@ -3,6 +3,7 @@
 
 #include <stdint.h>
 
+#include <array>
 #include <string>
 #include <vector>
 
@@ -51,6 +52,16 @@ struct SetupParams {
   bool scalar_only = false;  // Algorithm 1 with mu_s alone (the paper's scalar runs)
 };
 
+// Batched evaluation of the pair measure mu_p (Lemma mu2) of one matching
+// pass of Algorithm 1: begin_pass receives the pass's topology and its D-hat
+// blocks, evaluate the measures of a batch of pairs.  Each returns 0 or an
+// error.
+struct PairMeasure {
+  virtual ~PairMeasure() {}
+  virtual int begin_pass(const Topo &T, const std::vector<double> &Dh, int delta) = 0;
+  virtual int evaluate(const std::vector<std::array<int, 2>> &pairs, std::vector<double> &mu) = 0;
+};
+
 // Receives the levels as they are built: first(A_0), then for every level
 // the prolongation P_l; it must return A_{l+1} = P_l^T A_l P_l on the host.
 // A sink with device_stages() true also builds, for the agglomerates of
@@ -62,6 +73,8 @@ struct LevelSink {
   virtual int first(const HostBSR &A0) = 0;
   virtual int next(int level, const HostBSR &P, HostBSR &A_next) = 0;
   virtual bool device_stages() const { return false; }
+  // an evaluator of mu_p for Algorithm 1 (owned by the sink), or NULL: host
+  virtual PairMeasure *pair_measure() { return nullptr; }
   virtual int coarse_topology(int level, const Topo &T, const std::vector<int> &agg, int nc,
                               const std::vector<double> &xc, Topo &out) {
     (void)level; (void)T; (void)agg; (void)nc; (void)xc; (void)out;
