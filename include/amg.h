@@ -438,7 +438,10 @@ typedef struct {
  *  device_setup 1 (default): the coarse edge / vertex matrices (Thm.
  *               cemats) and the auxiliary smoothed prolongation (Def.
  *               aux_sp) are built on the device for the agglomerates that
- *               Algorithm 1 finds on the host; 0: on the host
+ *               Algorithm 1 finds on the host, and Algorithm 1's pair
+ *               measure mu_p (Lemma mu2) is evaluated on the device for its
+ *               batches of candidate pairs (>= 512 pairs; the greedy loop
+ *               and the mu_g tests stay on the host); 0: all on the host
  *  keep_topology 1: keep the coarse topologies the device stages build, for
  *               amg_download_topology (host memory: a level's edge and
  *               vertex matrices); 0 (default): drop them
@@ -480,10 +483,14 @@ void amg_default_setup_params(amg_setup_params *p);
 int amg_setup(amg_ctx *ctx, const amg_problem *prob, const amg_setup_params *params, int precision,
               int smoother);
 
-/* Wall-clock seconds of the last amg_setup's device stages, split into the
- * Galerkin products with their transfers and the coarse edge / vertex
- * matrices with the smoothed prolongation (either pointer may be NULL). */
-int amg_setup_device_split(const amg_ctx *ctx, double *galerkin_s, double *topology_prolongation_s);
+/* Wall-clock seconds of the last amg_setup's device stages: the Galerkin
+ * products with their transfers, the coarse edge / vertex matrices with the
+ * smoothed prolongation, and the device evaluation of Algorithm 1's pair
+ * measure mu_p (the batches of candidate pairs it takes; counted inside the
+ * host part of amg_setup_times, whose greedy loop waits on it).  Any pointer
+ * may be NULL. */
+int amg_setup_device_split(const amg_ctx *ctx, double *galerkin_s, double *topology_prolongation_s,
+                           double *pair_measure_s);
 
 /* The coarse topology of level `level` (>= 1) built by amg_setup's device
  * stages (Thm. cemats: edge matrices E^{IJ} of the coarse edges (ei < ej),

@@ -106,7 +106,8 @@ _SIGS = {
     "amg_set_layout_policy": (_I, [_P, _I]),
     "amg_probe_fma_rate": (_I, [_P, C.POINTER(C.c_double), C.POINTER(C.c_double)]),
     "amg_setup_times": (_I, [_P, C.POINTER(C.c_double)]),
-    "amg_setup_device_split": (_I, [_P, C.POINTER(C.c_double), C.POINTER(C.c_double)]),
+    "amg_setup_device_split": (_I, [_P, C.POINTER(C.c_double), C.POINTER(C.c_double),
+                                    C.POINTER(C.c_double)]),
     "amg_download_topology": (_I, [_P, _I, C.POINTER(C.c_int32), C.POINTER(C.c_int64),
                                    C.POINTER(C.c_int32), _P, _P, _P, _P, _P]),
     "amg_default_setup_params": (None, [C.POINTER(amg_setup_params)]),
@@ -399,10 +400,11 @@ class Context:
     def setup_times(self):
         t = (C.c_double * 4)()
         self._check(lib().amg_setup_times(self.h, t))
-        g, tp = C.c_double(), C.c_double()
-        self._check(lib().amg_setup_device_split(self.h, C.byref(g), C.byref(tp)))
+        g, tp, pm = C.c_double(), C.c_double(), C.c_double()
+        self._check(lib().amg_setup_device_split(self.h, C.byref(g), C.byref(tp), C.byref(pm)))
         return dict(host_s=t[0], device_s=t[1], finalize_s=t[2], total_s=t[3],
-                    device_galerkin_s=g.value, device_topology_prolongation_s=tp.value)
+                    device_galerkin_s=g.value, device_topology_prolongation_s=tp.value,
+                    device_pair_measure_s=pm.value)
 
     def download_topology(self, level):
         """(pos, edges (m x 2), E (m x k x k), M (n x k x k)) of the coarse

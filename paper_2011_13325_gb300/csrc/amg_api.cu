@@ -1072,10 +1072,12 @@ int amg_setup_times(const amg_ctx *h, double *times4) {
   return AMG_OK;
 }
 
-int amg_setup_device_split(const amg_ctx *h, double *galerkin_s, double *topology_prolongation_s) {
+int amg_setup_device_split(const amg_ctx *h, double *galerkin_s, double *topology_prolongation_s,
+                           double *pair_measure_s) {
   if (!h) return AMG_ERR_ARG;
   if (galerkin_s) *galerkin_s = h->c.setup_times[1] - h->c.setup_times[4];
   if (topology_prolongation_s) *topology_prolongation_s = h->c.setup_times[4];
+  if (pair_measure_s) *pair_measure_s = h->c.setup_times[5];
   return AMG_OK;
 }
 
@@ -1233,6 +1235,7 @@ int amg_setup(amg_ctx *h, const amg_problem *prob, const amg_setup_params *param
   sink.device = (!params || params->device_setup != 0) && blk != 1;
   sink.keep = params && params->keep_topology != 0;
   c->topo.clear();
+  c->setup_times[5] = 0.0;
   std::string err;
   const double t0 = wall_s();
   if (amgsetup::build_levels(pb, prm, sink, err) != 0) {

@@ -108,7 +108,8 @@ struct Ctx {
   // host setup, device stages (Galerkin, transfers, coarse topology,
   // prolongation), finalize, total, and the coarse topology + prolongation
   // part of the device stages (s)
-  double setup_times[5] = {0, 0, 0, 0, 0};
+  // [5]: device evaluation of the pair measure mu_p (inside the host part)
+  double setup_times[6] = {0, 0, 0, 0, 0, 0};
   // coarse topologies built by the device stages of amg_setup (kept when
   // asked for, level l >= 1 at index l)
   std::vector<amgsetup::Topo> topo;

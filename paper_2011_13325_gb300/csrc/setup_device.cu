@@ -25,6 +25,7 @@
 // passes: row lengths, then columns (ascending) and values.
 #include <algorithm>
 #include <array>
+#include <chrono>
 
 #include "amg_internal.h"
 #include "dense_dev.cuh"
@@ -878,6 +879,12 @@ struct DevicePairMeasure : amgsetup::PairMeasure {
     return cudaStreamSynchronize(c->stream) == cudaSuccess ? 0 : -1;
   }
   int evaluate(const std::vector<std::array<int, 2>> &pairs, std::vector<double> &mu) override {
+    const auto t0 = std::chrono::steady_clock::now();
+    const int rc = evaluate_impl(pairs, mu);
+    c->setup_times[5] += std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+    return rc;
+  }
+  int evaluate_impl(const std::vector<std::array<int, 2>> &pairs, std::vector<double> &mu) {
     const size_t n = pairs.size();
     mu.resize(n);
     if (n == 0) return 0;
