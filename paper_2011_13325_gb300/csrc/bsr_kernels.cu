@@ -505,17 +505,29 @@ __global__ void __launch_bounds__(256) sell_perm_kernel(int n_rows, int n_slices
   A acc[BR];
 #pragma unroll
   for (int r = 0; r < BR; ++r) acc[r] = 0;
-#pragma unroll 2
-  for (int j = j0; j < j1; ++j) {
-    const int c = __ldg(sell_col + (size_t)j * 32 + t);
-    const V *v = vals + (size_t)j * E * 32 + t;
-    A xv[BC];
+  // the rows of transfer operators are short (about five blocks): take the
+  // slots four at a time, column indices first, then all their x gathers,
+  // so that the dependent loads of four blocks are in flight together
+  constexpr int U = 4;
+  for (int j = j0; j < j1; j += U) {
+    int cc[U];
 #pragma unroll
-    for (int q = 0; q < BC; ++q) xv[q] = (A)ld(x + (size_t)c * BC + q);
+    for (int u = 0; u < U; ++u) cc[u] = (j + u < j1) ? __ldg(sell_col + (size_t)(j + u) * 32 + t) : 0;
+    A xv[U][BC];
 #pragma unroll
-    for (int r = 0; r < BR; ++r)
+    for (int u = 0; u < U; ++u)
 #pragma unroll
-      for (int q = 0; q < BC; ++q) acc[r] += (A)lds(v + (r * BC + q) * 32) * xv[q];
+      for (int q = 0; q < BC; ++q) xv[u][q] = (j + u < j1) ? (A)ld(x + (size_t)cc[u] * BC + q) : (A)0;
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+      if (j + u < j1) {
+        const V *v = vals + (size_t)(j + u) * E * 32 + t;
+#pragma unroll
+        for (int r = 0; r < BR; ++r)
+#pragma unroll
+          for (int q = 0; q < BC; ++q) acc[r] += (A)lds(v + (r * BC + q) * 32) * xv[u][q];
+      }
+    }
   }
   if (row >= n_rows) return;
   const size_t o = (size_t)row * BR;
