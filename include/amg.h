@@ -282,7 +282,8 @@ int amg_pcg_launches(const amg_ctx *ctx, int32_t *per_iteration, int32_t *fixed)
  * amg_upload_hierarchy / amg_setup:
  *   AMG_LAYOUT_AUTO             SELL-32 copy (one thread per block row) for
  *                               operators with >= 16 * 32 rows per SM and at
- *                               most 32 blocks per row; warp-per-row BSR
+ *                               most 32 blocks per row (rectangular ones: 64,
+ *                               with length-sorted slices); warp-per-row BSR
  *                               kernels (one warp streams a block row,
  *                               shuffle reduction) for the rest (default)
  *   AMG_LAYOUT_SELL_SHORT_ROWS  SELL-32 for every operator with short rows,

@@ -870,13 +870,16 @@ __global__ void sell_fill_kernel(int n_rows, int n_slices, const int *__restrict
 
 bool want_sell(const Ctx *c, const DevBSR &m) {
   // thread-per-row pays off when there are enough rows to fill the GPU with
-  // warps (>= 16 warps per SM) and the rows are short
+  // warps (>= 16 warps per SM) and the rows are short; rectangular operators
+  // (length-sorted slices, little padding) up to 64 blocks per row, so that
+  // the tuner also times the sorted SELL-32 form of the first restriction
   const double avg = m.n_rows ? (double)m.nnzb / m.n_rows : 0.0;
+  const bool rect = m.br != m.bc || m.n_rows != m.n_cols;
   if (c->layout_policy == AMG_LAYOUT_WARP_ROWS || c->layout_policy == AMG_LAYOUT_ROW_LANES ||
       c->layout_policy == AMG_LAYOUT_BLOCK_LANES)
     return false;
   if (c->layout_policy == AMG_LAYOUT_SELL_SHORT_ROWS) return avg <= 32.0;
-  return m.n_rows >= 32 * 16 * c->num_sms && avg <= 32.0;
+  return m.n_rows >= 32 * 16 * c->num_sms && avg <= (rect ? 64.0 : 32.0);
 }
 
 cudaError_t build_sell(Ctx *c, DevBSR &m) {
