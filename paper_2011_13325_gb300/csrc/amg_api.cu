@@ -368,9 +368,9 @@ static cudaError_t tune_operators(Ctx *c) {
     const char names[3] = {'A', 'P', 'R'};
     for (int i = 0; i < 3; ++i) {
       DevBSR *m = cand[i].first;
-      // a square operator with a SELL-32 copy keeps it (A_0 is also the CG
-      // operator, whose FP64 kernels use that copy)
-      if (!m->nnzb || (m == &L.A && m->sell_ptr)) continue;
+      // A_0 with a SELL-32 copy keeps it (it is also the CG operator, whose
+      // kernels use that copy)
+      if (!m->nnzb || (l == 0 && m == &L.A && m->sell_ptr)) continue;
       const std::string key = tune_key(l, names[i], *m, c->precision);
       bool hit = false;
       for (const auto &kv : cache)
@@ -449,7 +449,8 @@ static int finalize_hierarchy(Ctx *c) {
     CUDA_OR_FAIL(c, alloc_level_vectors(c, L), "level vectors");
     DevBSR *ops[] = {&L.A, &L.P, &L.R};
     for (DevBSR *m : ops)
-      if (m->nnzb && want_sell(c, *m)) CUDA_OR_FAIL(c, build_sell(c, *m), "sell layout");
+      if (m->nnzb && want_sell(c, *m, m == &L.A && l > 0))
+        CUDA_OR_FAIL(c, build_sell(c, *m, m == &L.A && l > 0), "sell layout");
     // the CG operator's double-float copy of A_0 (rows in order, 2x2 / 3x3)
     if (l == 0 && L.A.s64 && !L.A.sell_perm && (L.k == 1 || L.k == 2 || L.k == 3))
       CUDA_OR_FAIL(c, build_double_float(c, L.A), "double-float A_0");
@@ -805,7 +806,7 @@ int amg_galerkin(amg_ctx *h, int level, amg_bsr_out *out) {
   }
   CUDA_OR_FAIL(c, galerkin_device(c, level), "galerkin");
   Level &Cl = c->levels[level + 1];
-  if (want_sell(c, Cl.A)) CUDA_OR_FAIL(c, build_sell(c, Cl.A), "sell layout");
+  if (want_sell(c, Cl.A, true)) CUDA_OR_FAIL(c, build_sell(c, Cl.A, true), "sell layout");
   if (c->precision != AMG_PREC_FP64)
     CUDA_OR_FAIL(c, make_low_precision(c, Cl.A, c->precision), "low precision A");
   if (out) {

@@ -188,9 +188,11 @@ cudaError_t launch_gs_sweep(const Ctx *c, const Level &L, int prec, const void *
                             bool forward);
 cudaError_t coarse_setup(Ctx *c);
 cudaError_t make_low_precision(Ctx *c, DevBSR &m, int prec);
-cudaError_t build_sell(Ctx *c, DevBSR &m);
+// sort_square: length-sorted slices for a square operator too (coarse
+// levels; A_0 keeps its rows in order, which the CG kernels assume)
+cudaError_t build_sell(Ctx *c, DevBSR &m, bool sort_square = false);
 cudaError_t build_double_float(Ctx *c, DevBSR &m);
-bool want_sell(const Ctx *c, const DevBSR &m);
+bool want_sell(const Ctx *c, const DevBSR &m, bool coarse_square = false);
 cudaError_t scan_exclusive(Ctx *c, int n, int *a, int *total_dev);
 
 // V-cycle on device buffers (FP64 in / out), stream-ordered.

@@ -481,9 +481,10 @@ __global__ void __launch_bounds__(256) sell_kernel(int n_rows, int n_slices,
   }
 }
 
-// The same for a sorted SELL-32 copy (rectangular operators: no smoothing
-// mode): lane t of a slice computes row perm[32 * slice + t] (n_rows on a
-// padding lane), so rows of similar length share a slice.
+// The same for a sorted SELL-32 copy (the transfer operators and the square
+// operators of the coarse levels): lane t of a slice computes row
+// perm[32 * slice + t] (n_rows on a padding lane), so rows of similar length
+// share a slice.
 template <int BR, int BC, typename V, typename T, int MODE>
 __global__ void __launch_bounds__(256) sell_perm_kernel(int n_rows, int n_slices,
                                                         const int *__restrict__ sell_ptr,
@@ -492,8 +493,9 @@ __global__ void __launch_bounds__(256) sell_perm_kernel(int n_rows, int n_slices
                                                         const V *__restrict__ vals,
                                                         const T *__restrict__ x,
                                                         const T *__restrict__ b,
+                                                        const T *__restrict__ minv,
                                                         T *__restrict__ y) {
-  static_assert(MODE != SPMV_SMOOTH, "sorted slices serve rectangular operators only");
+  static_assert(MODE != SPMV_SMOOTH || BR == BC, "smoothing needs a square operator");
   pdl_enter();
   using A = typename AccT<T>::type;
   constexpr int E = BR * BC;
@@ -531,6 +533,19 @@ __global__ void __launch_bounds__(256) sell_perm_kernel(int n_rows, int n_slices
   }
   if (row >= n_rows) return;
   const size_t o = (size_t)row * BR;
+  if (MODE == SPMV_SMOOTH) {
+    A res[BR];
+#pragma unroll
+    for (int r = 0; r < BR; ++r) res[r] = (A)b[o + r] - acc[r];
+#pragma unroll
+    for (int r = 0; r < BR; ++r) {
+      A u = 0;
+#pragma unroll
+      for (int q = 0; q < BR; ++q) u += (A)minv[(o + r) * BR + q] * res[q];
+      y[o + r] = (T)((A)x[o + r] + u);
+    }
+    return;
+  }
 #pragma unroll
   for (int r = 0; r < BR; ++r) {
     if (MODE == SPMV_SET) y[o + r] = (T)acc[r];
@@ -551,11 +566,18 @@ static cudaError_t sell_mode(const Ctx *c, const DevBSR &A, const V *vals, int m
   if (A.sell_perm) {
 #define AMG_SELL_PERM_LAUNCH(M_)                                                                 \
   AMG_KLAUNCH(c, sell_perm_kernel<BR, BC, V, T, M_>, g, 64, A.n_rows, A.n_slices, A.sell_ptr, \
-              A.sell_col, A.sell_perm, vals, xx, bb, yy)
+              A.sell_col, A.sell_perm, vals, xx, bb, mm, yy)
     switch (mode) {
       case SPMV_SET: AMG_SELL_PERM_LAUNCH(SPMV_SET); break;
       case SPMV_RESID: AMG_SELL_PERM_LAUNCH(SPMV_RESID); break;
       case SPMV_ADD: AMG_SELL_PERM_LAUNCH(SPMV_ADD); break;
+      case SPMV_SMOOTH:
+        if constexpr (BR == BC) {
+          AMG_SELL_PERM_LAUNCH(SPMV_SMOOTH);
+          break;
+        } else {
+          return cudaErrorInvalidValue;
+        }
       default: return cudaErrorInvalidValue;
     }
 #undef AMG_SELL_PERM_LAUNCH
@@ -868,7 +890,7 @@ __global__ void sell_fill_kernel(int n_rows, int n_slices, const int *__restrict
   }
 }
 
-bool want_sell(const Ctx *c, const DevBSR &m) {
+bool want_sell(const Ctx *c, const DevBSR &m, bool coarse_square) {
   // thread-per-row pays off when there are enough rows to fill the GPU with
   // warps (>= 16 warps per SM) and the rows are short; rectangular operators
   // (length-sorted slices, little padding) up to 64 blocks per row, so that
@@ -879,10 +901,11 @@ bool want_sell(const Ctx *c, const DevBSR &m) {
       c->layout_policy == AMG_LAYOUT_BLOCK_LANES)
     return false;
   if (c->layout_policy == AMG_LAYOUT_SELL_SHORT_ROWS) return avg <= 32.0;
-  return m.n_rows >= 32 * 16 * c->num_sms && avg <= (rect ? 64.0 : 32.0);
+  // coarse square operators (sorted slices too) up to 96 blocks per row
+  return m.n_rows >= 32 * 16 * c->num_sms && avg <= (rect ? 64.0 : coarse_square ? 96.0 : 32.0);
 }
 
-cudaError_t build_sell(Ctx *c, DevBSR &m) {
+cudaError_t build_sell(Ctx *c, DevBSR &m, bool sort_square) {
   const int E = m.br * m.bc;
   dfree(m.sell_ptr);
   dfree(m.sell_col);
@@ -893,8 +916,9 @@ cudaError_t build_sell(Ctx *c, DevBSR &m) {
   m.sell_perm = nullptr;
   m.s64 = nullptr;
   m.n_slices = (m.n_rows + 31) / 32;
-  // rectangular operators (P_l, R_l) get length-sorted slices
-  if ((m.br != m.bc || m.n_rows != m.n_cols) && m.n_slices > 0) {
+  // rectangular operators (P_l, R_l) and, when asked, square ones get
+  // length-sorted slices
+  if ((m.br != m.bc || m.n_rows != m.n_cols || sort_square) && m.n_slices > 0) {
     const int n_slots = m.n_slices * 32;
     AMG_CUDA_TRY(dalloc((void **)&m.sell_perm, (size_t)n_slots * sizeof(int)));
     sell_sort_kernel<<<(n_slots + 255) / 256, 256, 0, c->stream>>>(m.n_rows, n_slots, m.rowptr,

@@ -317,10 +317,12 @@ def test_launch_overlap_gives_identical_results(case):
 
 
 def test_sell_layout_sorts_rectangular_operators():
-    """Under the SELL-32 layout the transfer operators P_l, R_l (rows of
-    varying length) get length-sorted slices and the square A_l keep rows in
+    """Under the SELL-32 layout the transfer operators P_l, R_l and the
+    coarse square operators A_l (l >= 1; rows of varying length) get
+    length-sorted slices, and A_0 (also the CG operator) keeps its rows in
     order; the sorted copies fill more of their slots than rows in order
-    would, and a V-cycle through them matches the oracle."""
+    would, and a V-cycle through them (smoothing included) matches the
+    oracle."""
     amg = _amg()
     p, H = _hier("box_jump")
     ctx = amg.Context(0)
@@ -329,7 +331,9 @@ def test_sell_layout_sorts_rectangular_operators():
     lines = [ln for ln in ctx.describe().splitlines() if "SELL-32" in ln]
     trans = [ln for ln in lines if " P:" in ln or " R:" in ln]
     assert trans and all("rows sorted by length" in ln for ln in trans)
-    assert all("rows sorted" not in ln for ln in lines if " A:" in ln)
+    assert all("rows sorted" not in ln for ln in lines if ln.startswith("level 0 A:"))
+    assert all("rows sorted by length" in ln for ln in lines
+               if " A:" in ln and not ln.startswith("level 0 A:"))
     # fill of the sorted P_0 against the rows-in-order slice widths
     P = H.P[0]
     lens = np.diff(P.rowptr)
