@@ -773,8 +773,17 @@ __global__ void coarse_gemv_kernel(int n, const double *__restrict__ cinv, const
   const int row = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   if (row >= n) return;
   const double *a = cinv + (size_t)row * n;
-  double acc = 0.0;
-  for (int j = lane; j < n; j += 32) acc += a[j] * (double)b[j];
+  // four independent partial sums keep four loads in flight per lane
+  double acc0 = 0.0, acc1 = 0.0, acc2 = 0.0, acc3 = 0.0;
+  int j = lane;
+  for (; j + 96 < n; j += 128) {
+    acc0 += a[j] * (double)b[j];
+    acc1 += a[j + 32] * (double)b[j + 32];
+    acc2 += a[j + 64] * (double)b[j + 64];
+    acc3 += a[j + 96] * (double)b[j + 96];
+  }
+  for (; j < n; j += 32) acc0 += a[j] * (double)b[j];
+  double acc = (acc0 + acc1) + (acc2 + acc3);
 #pragma unroll
   for (int s = 16; s > 0; s >>= 1) acc += __shfl_down_sync(0xffffffffu, acc, s);
   if (lane == 0) y[row] = (T)acc;
