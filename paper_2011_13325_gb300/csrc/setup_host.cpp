@@ -873,7 +873,10 @@ static Coarsening successive_matching(const Topo &T0, const SetupParams &prm, in
     // succeeds), and where the loop needs a pair not evaluated yet, that
     // pair together with the vertex's next live candidates.  The decisions
     // are those of evaluating each pair when the loop reaches it.
-    const int chunk = 2048, ahead = 2, refill = 8;
+    // a device evaluator wants large batches (one thread per pair: a batch
+    // of a 2,048-vertex chunk occupies a fraction of the device); the chunk
+    // only decides how far the look-ahead reaches, not the decisions
+    const int chunk = dev_pm ? 32768 : 2048, ahead = 2, refill = 8;
     std::vector<Cand> cands;
     struct Eval {
       double mu;
