@@ -56,7 +56,7 @@ WORKLOADS = {
                 "E U[0.1,10], nu U[0.2,0.4] per system (seed 4), clamped x=0, 6 load cases "
                 "(unit body forces +-x, +-y, +-z) each"),
 }
-PREC_NAMES = {0: "fp64", 1: "fp32_vcycle", 2: "bf16_storage"}
+PREC_NAMES = {0: "fp64", 1: "fp32_vcycle", 2: "bf16_storage", 3: "bf16_coarse"}
 
 
 def make_workload(name):
@@ -149,7 +149,8 @@ def algorithmic_bytes_per_iteration(levels, prec, nr=1):
     """Bytes one PCG iteration must move at least once (matrices, smoother
     blocks, vectors), from the actual level sizes; with nr load cases solved
     together the operators are read once and the vectors nr times."""
-    w = {0: 8, 1: 4, 2: 2}[prec]          # matrix value bytes
+    # matrix value bytes per level (BF16 coarse: FP32 on level 0, BF16 below)
+    wl = lambda l: {0: 8, 1: 4, 2: 2, 3: 4 if l == 0 else 2}[prec]
     wv = 8 if prec == 0 else 4            # V-cycle vector / smoother bytes
     n0, k0 = levels[0]["n_rows"], levels[0]["block"]
     N0 = n0 * k0
@@ -164,6 +165,7 @@ def algorithmic_bytes_per_iteration(levels, prec, nr=1):
             mat += (N * N) * 8
             vec += 2 * N * wv
             continue
+        w = wl(l)
         Ab = L["nnzb"] * (k * k * w + 4) + 4 * (n + 1)
         kc = levels[l + 1]["block"]
         Pb = L["nnzb_P"] * (k * kc * w + 4) + 4 * (n + 1)
@@ -291,9 +293,9 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
     ap.add_argument("--workload", default="cube128jump", choices=sorted(WORKLOADS))
-    ap.add_argument("--precision", type=int, default=1, choices=[0, 1, 2],
+    ap.add_argument("--precision", type=int, default=1, choices=[0, 1, 2, 3],
                     help="V-cycle precision of the timed path: 0 fp64, 1 fp32 (default), 2 bf16 "
-                         "storage; the CG is FP64 in all three")
+                         "storage, 3 bf16 storage on the levels below 0; the CG is FP64 in all")
     ap.add_argument("--cg-operator", default="auto", choices=["auto", "double_float", "fp64"],
                     help="arithmetic of the CG operator q = A_0 p: auto (default: double-float "
                          "pairs on the FP32 pipe with the FP32 / BF16 V-cycles, FP64 with the "
@@ -454,7 +456,7 @@ def run_single(args, ws, rank, local, train_problems):
     plain = variant(c2, "plain_fp64", 0)
     c2.close()
     if args.variants == "auto":
-        vlist = [] if args.smoother == "learned" else [p for p in (1, 2) if p != args.precision]
+        vlist = [] if args.smoother == "learned" else [p for p in (1, 2, 3) if p != args.precision]
     else:
         vlist = [int(v) for v in args.variants.split(",") if v.strip()]
     for prec in vlist:
@@ -550,7 +552,8 @@ def run_single(args, ws, rank, local, train_problems):
         "value": round(ms, 3), "unit": "ms", "n_gpus": ws, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": round(ms, 3), "higher_is_better": False,
         "scaling": "weak", "vs_baseline": None,
-        "dtype": {0: "f64", 1: "f64 CG + f32 V-cycle", 2: "f64 CG + f32 V-cycle (bf16 storage)"}[args.precision],
+        "dtype": {0: "f64", 1: "f64 CG + f32 V-cycle", 2: "f64 CG + f32 V-cycle (bf16 storage)",
+                  3: "f64 CG + f32 V-cycle (bf16 storage below level 0)"}[args.precision],
         "data": "synthetic",
         "config": {"workload": args.workload, "description": WORKLOADS[args.workload],
                    "precision": PREC_NAMES[args.precision] + " V-cycle, fp64 CG (FP64 residual 1e-8)",
@@ -992,7 +995,8 @@ def run_batch(args, ws, rank, local, problems):
         "value": round(ms, 3), "unit": "ms", "n_gpus": ws, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": round(ms, 3), "higher_is_better": False,
         "scaling": "weak", "vs_baseline": None,
-        "dtype": {0: "f64", 1: "f64 CG + f32 V-cycle", 2: "f64 CG + f32 V-cycle (bf16 storage)"}[prec],
+        "dtype": {0: "f64", 1: "f64 CG + f32 V-cycle", 2: "f64 CG + f32 V-cycle (bf16 storage)",
+                  3: "f64 CG + f32 V-cycle (bf16 storage below level 0)"}[prec],
         "data": "synthetic",
         "config": {"workload": "batch64", "description": WORKLOADS["batch64"],
                    "systems": len(problems), "load_cases": 6, "dofs_total": int(sum(n_dofs)),

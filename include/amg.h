@@ -85,7 +85,13 @@ enum {
   AMG_PREC_FP64 = 0,          /* FP64 values, vectors and accumulation        */
   AMG_PREC_FP32_VCYCLE = 1,   /* V-cycle matrices, smoother blocks, vectors
                                  and accumulation in FP32; coarsest solve FP64 */
-  AMG_PREC_BF16_STORAGE = 2   /* as FP32 but A_l, P_l, R_l stored in BF16     */
+  AMG_PREC_BF16_STORAGE = 2,  /* as FP32 but A_l, P_l, R_l stored in BF16     */
+  AMG_PREC_BF16_COARSE = 3    /* as FP32, with A_l, P_l, R_l of the levels
+                                 l >= 1 stored in BF16 (level 0 in FP32): the
+                                 coarse operators move half the bytes, while
+                                 A_0, whose rounding to BF16 spoils the
+                                 smoother on coefficient jumps, stays FP32.
+                                 Not accepted by amg_batch_create.            */
 };
 
 /* Smoother of the V-cycle.
@@ -141,7 +147,8 @@ const char *amg_last_error(const amg_ctx *ctx);
  *     (Sec. 3 after Lemma eet_is_diag) in FP64 on the device and stores
  *     its inverse,
  *   - for AMG_PREC_FP32_VCYCLE / AMG_PREC_BF16_STORAGE, keeps FP32 / BF16
- *     copies of the level operators.
+ *     copies of the level operators (AMG_PREC_BF16_COARSE: FP32 copies of
+ *     level 0's, BF16 copies of the coarser levels').
  * Replaces any previous hierarchy of ctx. */
 int amg_upload_hierarchy(amg_ctx *ctx, const amg_hierarchy *h, int precision, int smoother);
 
@@ -443,6 +450,9 @@ typedef struct {
  *               measure mu_p (Lemma mu2) is evaluated on the device for its
  *               batches of candidate pairs (>= 512 pairs; the greedy loop
  *               and the mu_g tests stay on the host); 0: all on the host
+ *  device_pair_measure 1 (default): with device_setup, mu_p as above on
+ *               the device; 0: mu_p on the host (same hierarchy; the choice
+ *               is a matter of speed only)
  *  keep_topology 1: keep the coarse topologies the device stages build, for
  *               amg_download_topology (host memory: a level's edge and
  *               vertex matrices); 0 (default): drop them
@@ -468,6 +478,7 @@ typedef struct {
   int32_t device_setup;
   int32_t keep_topology;
   int32_t scalar_only;
+  int32_t device_pair_measure;
 } amg_setup_params;
 
 /* Fill *p with the defaults listed above (the readings of Sec. 5, 6, 7). */
@@ -487,9 +498,10 @@ int amg_setup(amg_ctx *ctx, const amg_problem *prob, const amg_setup_params *par
 /* Wall-clock seconds of the last amg_setup's device stages: the Galerkin
  * products with their transfers, the coarse edge / vertex matrices with the
  * smoothed prolongation, and the device evaluation of Algorithm 1's pair
- * measure mu_p (the batches of candidate pairs it takes; counted inside the
- * host part of amg_setup_times, whose greedy loop waits on it).  Any pointer
- * may be NULL. */
+ * measure mu_p (the upload of each matching pass's topology and the batches
+ * of candidate pairs it takes; counted inside the host part of
+ * amg_setup_times, whose greedy loop waits on it).  Any pointer may be
+ * NULL. */
 int amg_setup_device_split(const amg_ctx *ctx, double *galerkin_s, double *topology_prolongation_s,
                            double *pair_measure_s);
 
@@ -535,8 +547,9 @@ typedef struct amg_batch amg_batch;
  * length-sorted slices as in the single-system layout; block lanes, 8 or 16
  * lanes per block row with one whole block per lane, for 6x6 and 6x3
  * blocks) and the fastest is kept (amg_batch_describe lists the choices).
- * Errors: AMG_ERR_ARG (also: a context with AMG_SMOOTHER_HYBRID_GS),
- * AMG_ERR_STATE (a context without hierarchy), AMG_ERR_CUDA. */
+ * Errors: AMG_ERR_ARG (also: a context with AMG_SMOOTHER_HYBRID_GS or
+ * AMG_PREC_BF16_COARSE), AMG_ERR_STATE (a context without hierarchy),
+ * AMG_ERR_CUDA. */
 int amg_batch_create(amg_batch **batch, amg_ctx *const *systems, int n_systems, int nrhs);
 void amg_batch_destroy(amg_batch *batch);
 const char *amg_batch_last_error(const amg_batch *batch);

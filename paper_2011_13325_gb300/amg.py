@@ -28,6 +28,7 @@ ERRORS = {AMG_ERR_ARG: "AMG_ERR_ARG", AMG_ERR_CUDA: "AMG_ERR_CUDA", AMG_ERR_NOT_
 AMG_PREC_FP64 = 0
 AMG_PREC_FP32_VCYCLE = 1
 AMG_PREC_BF16_STORAGE = 2
+AMG_PREC_BF16_COARSE = 3
 AMG_LAYOUT_AUTO = 0
 AMG_LAYOUT_SELL_SHORT_ROWS = 1
 AMG_LAYOUT_WARP_ROWS = 2
@@ -66,7 +67,8 @@ class amg_setup_params(C.Structure):
                 ("cap_S_later", C.c_int32), ("cap_A", C.c_int32), ("coarse_max", C.c_int32),
                 ("min_ratio", C.c_double), ("max_levels", C.c_int32),
                 ("host_threads", C.c_int32), ("device_setup", C.c_int32),
-                ("keep_topology", C.c_int32), ("scalar_only", C.c_int32)]
+                ("keep_topology", C.c_int32), ("scalar_only", C.c_int32),
+                ("device_pair_measure", C.c_int32)]
 
 
 class AmgError(RuntimeError):

@@ -95,7 +95,7 @@ static const void *minv_of(const Level &L, int prec) {
 // the FP64 result z64 directly (casts fused into its first / last kernel).
 static cudaError_t vcycle_level(Ctx *c, int l, const void *b, void *y, const double *r64 = nullptr,
                                 double *z64 = nullptr) {
-  const int prec = c->precision;
+  const int prec = mat_prec(c, l);
   Level &L = c->levels[l];
   if (l == (int)c->levels.size() - 1) return launch_coarse_gemv(c, c->coarse_n, c->cinv, b, y, prec);
   Level &Cn = c->levels[l + 1];
@@ -360,6 +360,7 @@ static cudaError_t tune_operators(Ctx *c) {
   // (operator, its mode in the V-cycle): A residual, P prolongation-add,
   // R restriction
   std::vector<std::pair<DevBSR *, int>> ops;
+  std::vector<int> op_prec;
   std::vector<std::string> keys;
   size_t nx = 0, ny = 0;
   for (int l = 0; l + 1 < (int)c->levels.size(); ++l) {
@@ -371,7 +372,7 @@ static cudaError_t tune_operators(Ctx *c) {
       // A_0 with a SELL-32 copy keeps it (it is also the CG operator, whose
       // kernels use that copy)
       if (!m->nnzb || (l == 0 && m == &L.A && m->sell_ptr)) continue;
-      const std::string key = tune_key(l, names[i], *m, c->precision);
+      const std::string key = tune_key(l, names[i], *m, mat_prec(c, l));
       bool hit = false;
       for (const auto &kv : cache)
         if (kv.first == key && (kv.second != KERN_SELL || m->sell_ptr)) {
@@ -380,6 +381,7 @@ static cudaError_t tune_operators(Ctx *c) {
         }
       if (hit) continue;
       ops.push_back(cand[i]);
+      op_prec.push_back(mat_prec(c, l));
       keys.push_back(key);
       nx = std::max(nx, (size_t)m->n_cols * m->bc);
       ny = std::max(ny, (size_t)m->n_rows * m->br);
@@ -399,17 +401,17 @@ static cudaError_t tune_operators(Ctx *c) {
   const int kerns[4] = {KERN_SELL, KERN_WARP_ROWS, KERN_ROW_LANES, KERN_BLOCK_LANES};
   for (size_t i = 0; i < ops.size() && e == cudaSuccess; ++i) {
     DevBSR &m = *ops[i].first;
-    const int mode = ops[i].second;
+    const int mode = ops[i].second, prec = op_prec[i];
     float best = 1e30f;
     int pick = m.sell_ptr ? KERN_SELL : KERN_WARP_ROWS;
     for (int k : kerns) {
       if (k == KERN_SELL && !m.sell_ptr) continue;
       m.kern = k;
       // the operator's own V-cycle mode; best of two timed triples
-      e = launch_bsr(c, m, c->precision, mode, x, b, nullptr, y);
+      e = launch_bsr(c, m, prec, mode, x, b, nullptr, y);
       for (int trial = 0; trial < 2 && e == cudaSuccess; ++trial) {
         e = cudaEventRecord(e0, c->stream);
-        for (int r = 0; r < 3 && e == cudaSuccess; ++r) e = launch_bsr(c, m, c->precision, mode, x, b, nullptr, y);
+        for (int r = 0; r < 3 && e == cudaSuccess; ++r) e = launch_bsr(c, m, prec, mode, x, b, nullptr, y);
         if (e == cudaSuccess) e = cudaEventRecord(e1, c->stream);
         if (e == cudaSuccess) e = cudaEventSynchronize(e1);
         float ms = 0.f;
@@ -440,9 +442,9 @@ static cudaError_t tune_operators(Ctx *c) {
 
 // Smoothers, level vectors, low-precision copies, coarsest inverse, CG buffers.
 static int finalize_hierarchy(Ctx *c) {
-  const int precision = c->precision;
   for (int l = 0; l < (int)c->levels.size(); ++l) {
     Level &L = c->levels[l];
+    const int precision = mat_prec(c, l);
     if (l + 1 < (int)c->levels.size() && c->smoother == AMG_SMOOTHER_HYBRID_GS)
       CUDA_OR_FAIL(c, gs_prepare(c, l), "colouring");
     if (l + 1 < (int)c->levels.size()) CUDA_OR_FAIL(c, smoother_setup(c, l), "smoother setup");
@@ -486,13 +488,14 @@ cudaError_t device_prolongation(Ctx *c, int level, const amgsetup::Topo &T, cons
 struct DeviceSink : amgsetup::LevelSink {
   Ctx *c;
   double device_s = 0.0, device_setup_s = 0.0;
-  bool device = true, keep = false;
+  bool device = true, keep = false, device_pm = true;
   std::vector<char> p_on_device;  // per level: P_l already built on the device
   amgsetup::PairMeasure *pm = nullptr;
   explicit DeviceSink(Ctx *cc) : c(cc) {}
   ~DeviceSink() override { delete pm; }
   bool device_stages() const override { return device; }
   amgsetup::PairMeasure *pair_measure() override {
+    if (!device_pm) return nullptr;
     if (!pm) pm = make_device_pair_measure(c);
     return pm;
   }
@@ -623,8 +626,7 @@ int amg_profile_vcycle(amg_ctx *h, int reps, int32_t *level, int32_t *kind, doub
   Ctx *c = &h->c;
   if (c->levels.empty()) return fail(c, AMG_ERR_STATE, "amg_profile_vcycle: no hierarchy uploaded");
   CUDA_OR_FAIL(c, cudaSetDevice(c->device), "cudaSetDevice");
-  const int prec = c->precision;
-  const double wv = prec == AMG_PREC_FP64 ? 8.0 : 4.0;
+  const double wv = c->precision == AMG_PREC_FP64 ? 8.0 : 4.0;
   const int nl = (int)c->levels.size();
   int n = 0;
   auto put = [&](int l, int k, double t, double b) {
@@ -638,6 +640,7 @@ int amg_profile_vcycle(amg_ctx *h, int reps, int32_t *level, int32_t *kind, doub
   };
   for (int l = 0; l < nl; ++l) {
     Level &L = c->levels[l];
+    const int prec = mat_prec(c, l);
     const double N = (double)L.A.n_rows * L.k;
     double t = 0.0;
     void *b = vb(L, prec, 'b'), *x = vb(L, prec, 'x'), *tt = vb(L, prec, 't'), *y = vb(L, prec, 'y');
@@ -738,7 +741,7 @@ int amg_upload_hierarchy(amg_ctx *h, const amg_hierarchy *hier, int precision, i
   Ctx *c = &h->c;
   if (!hier || hier->n_levels < 1 || (hier->n_levels > 1 && !hier->P))
     return fail(c, AMG_ERR_ARG, "hierarchy: need n_levels >= 1 and P for n_levels > 1");
-  if (precision < AMG_PREC_FP64 || precision > AMG_PREC_BF16_STORAGE)
+  if (precision < AMG_PREC_FP64 || precision > AMG_PREC_BF16_COARSE)
     return fail(c, AMG_ERR_ARG, "unknown precision");
   if (smoother != AMG_SMOOTHER_L1_JACOBI && smoother != AMG_SMOOTHER_HYBRID_GS)
     return fail(c, AMG_ERR_ARG, "unknown smoother");
@@ -808,7 +811,7 @@ int amg_galerkin(amg_ctx *h, int level, amg_bsr_out *out) {
   Level &Cl = c->levels[level + 1];
   if (want_sell(c, Cl.A, true)) CUDA_OR_FAIL(c, build_sell(c, Cl.A, true), "sell layout");
   if (c->precision != AMG_PREC_FP64)
-    CUDA_OR_FAIL(c, make_low_precision(c, Cl.A, c->precision), "low precision A");
+    CUDA_OR_FAIL(c, make_low_precision(c, Cl.A, mat_prec(c, level + 1)), "low precision A");
   if (out) {
     if (!out->rowptr || (Cl.A.nnzb > 0 && (!out->colidx || !out->vals)))
       return fail(c, AMG_ERR_ARG, "amg_galerkin: NULL output array");
@@ -1179,6 +1182,7 @@ void amg_default_setup_params(amg_setup_params *p) {
   p->device_setup = 1;
   p->keep_topology = 0;
   p->scalar_only = 0;
+  p->device_pair_measure = 1;
 }
 
 int amg_setup(amg_ctx *h, const amg_problem *prob, const amg_setup_params *params, int precision,
@@ -1187,7 +1191,7 @@ int amg_setup(amg_ctx *h, const amg_problem *prob, const amg_setup_params *param
   Ctx *c = &h->c;
   if (!prob || (prob->dim != 2 && prob->dim != 3) || prob->n_vertices < 1 || !prob->coords)
     return fail(c, AMG_ERR_ARG, "amg_setup: bad problem");
-  if (precision < AMG_PREC_FP64 || precision > AMG_PREC_BF16_STORAGE)
+  if (precision < AMG_PREC_FP64 || precision > AMG_PREC_BF16_COARSE)
     return fail(c, AMG_ERR_ARG, "unknown precision");
   if (smoother != AMG_SMOOTHER_L1_JACOBI && smoother != AMG_SMOOTHER_HYBRID_GS)
     return fail(c, AMG_ERR_ARG, "unknown smoother");
@@ -1235,6 +1239,7 @@ int amg_setup(amg_ctx *h, const amg_problem *prob, const amg_setup_params *param
   DeviceSink sink(c);
   sink.device = (!params || params->device_setup != 0) && blk != 1;
   sink.keep = params && params->keep_topology != 0;
+  sink.device_pm = !params || params->device_pair_measure != 0;
   c->topo.clear();
   c->setup_times[5] = 0.0;
   std::string err;

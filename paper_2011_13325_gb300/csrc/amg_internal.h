@@ -187,6 +187,13 @@ cudaError_t gs_prepare(Ctx *c, int level);
 cudaError_t launch_gs_sweep(const Ctx *c, const Level &L, int prec, const void *b, void *x,
                             bool forward);
 cudaError_t coarse_setup(Ctx *c);
+// Storage precision of level l's matrices (and the precision its kernels run
+// in): the V-cycle precision, except AMG_PREC_BF16_COARSE, which keeps level
+// 0 in FP32 and stores the coarser levels in BF16.
+inline int mat_prec(const Ctx *c, int l) {
+  if (c->precision != AMG_PREC_BF16_COARSE) return c->precision;
+  return l == 0 ? AMG_PREC_FP32_VCYCLE : AMG_PREC_BF16_STORAGE;
+}
 cudaError_t make_low_precision(Ctx *c, DevBSR &m, int prec);
 // sort_square: length-sorted slices for a square operator too (coarse
 // levels; A_0 keeps its rows in order, which the CG kernels assume)

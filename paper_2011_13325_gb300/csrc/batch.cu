@@ -696,6 +696,8 @@ int amg_batch_create(amg_batch **out, amg_ctx *const *systems, int n_systems, in
       return AMG_ERR_ARG;
     // the grouped V-cycle runs the block-l1 Jacobi (or learned) smoother only
     if (systems[s]->c.smoother == AMG_SMOOTHER_HYBRID_GS) return AMG_ERR_ARG;
+    // and one storage precision on every level
+    if (systems[s]->c.precision == AMG_PREC_BF16_COARSE) return AMG_ERR_ARG;
   }
   amg_batch *hb = new amg_batch();
   Batch *B = &hb->b;

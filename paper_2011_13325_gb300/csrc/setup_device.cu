@@ -853,6 +853,12 @@ struct DevicePairMeasure : amgsetup::PairMeasure {
   size_t cap = 0;
   explicit DevicePairMeasure(Ctx *cc) : c(cc) {}
   int begin_pass(const amgsetup::Topo &T, const std::vector<double> &Dh, int delta) override {
+    const auto t0 = std::chrono::steady_clock::now();
+    const int rc = begin_pass_impl(T, Dh, delta);
+    c->setup_times[5] += std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+    return rc;
+  }
+  int begin_pass_impl(const amgsetup::Topo &T, const std::vector<double> &Dh, int delta) {
     for (void *p : buf.ptrs) dfree(p);
     buf.ptrs.clear();
     d_pairs = nullptr;

@@ -62,7 +62,7 @@ static size_t scratch_bytes(const Ctx *c) {
 static cudaError_t vcycle_static_level(Ctx *c, int l, void *const *bx, void *const *xx,
                                        void *const *tx, void *const *yx, const void *b, void *y,
                                        const double *r64, double *z64) {
-  const int prec = c->precision;
+  const int prec = mat_prec(c, l);
   Level &L = c->levels[l];
   if (l == (int)c->levels.size() - 1) return launch_coarse_gemv(c, c->coarse_n, c->cinv, b, y, prec);
   const void *mi = prec == AMG_PREC_FP64 ? (const void *)L.minv64 : (const void *)L.minv32;
@@ -137,7 +137,7 @@ extern "C" int amg_vcycle_static(amg_ctx *h, const double *r_dev, double *z_dev)
   else if (nl == 1) {
     const size_t n = (size_t)c->levels[0].A.n_rows * c->levels[0].k;
     e = launch_convert(c, n, r_dev, AMG_PREC_FP64, bx[0], AMG_PREC_FP32_VCYCLE);
-    if (e == cudaSuccess) e = launch_coarse_gemv(c, c->coarse_n, c->cinv, bx[0], yx[0], c->precision);
+    if (e == cudaSuccess) e = launch_coarse_gemv(c, c->coarse_n, c->cinv, bx[0], yx[0], mat_prec(c, 0));
     if (e == cudaSuccess) e = launch_convert(c, n, yx[0], AMG_PREC_FP32_VCYCLE, z_dev, AMG_PREC_FP64);
   } else {
     e = vcycle_static_level(c, 0, bx, xx, tx, yx, bx[0], yx[0], r_dev, z_dev);

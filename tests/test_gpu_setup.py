@@ -102,22 +102,25 @@ def test_setup_rejects_bad_problem():
 def test_device_pair_measure_gives_the_host_hierarchy():
     """Algorithm 1 with mu_p evaluated on the device (batches of candidate
     pairs) takes the decisions of the host evaluation: on a 3D jump problem
-    large enough for many device batches, both setups give prolongations
-    with identical patterns and values to 1e-12, and the device evaluated
-    pairs (its time is reported)."""
+    large enough for many device batches, the setups with mu_p on the device,
+    with mu_p on the host (other device stages on), and all on the host give
+    prolongations with identical patterns and values to 1e-12; only the
+    first reports device time for mu_p."""
     from paper_2011_13325_gb300 import amg
     p = make_problem((20, 19, 18), seed=9, jump_boxes=30, nu_range=(0.25, 0.45))
     out = []
-    for dev in (1, 0):
+    for dev, dpm in ((1, 1), (1, 0), (0, 1)):
         ctx = amg.Context(0)
-        ctx.setup(p, amg.AMG_PREC_FP64, device_setup=dev)
+        ctx.setup(p, amg.AMG_PREC_FP64, device_setup=dev, device_pair_measure=dpm)
         out.append(([ctx.download_prolongation(l) for l in range(ctx.n_levels - 1)], ctx.setup_times()))
         ctx.close()
-    (Pd, td), (Ph, th) = out
-    assert td["device_pair_measure_s"] > 0.0 and th["device_pair_measure_s"] == 0.0
-    assert len(Pd) == len(Ph)
-    for (n, m, rp, ci, v), (n2, m2, rp2, ci2, v2) in zip(Pd, Ph):
-        assert (n, m) == (n2, m2)
-        np.testing.assert_array_equal(rp, rp2)
-        np.testing.assert_array_equal(ci, ci2)
-        assert np.abs(v - v2).max() <= 1e-12 * np.abs(v2).max()
+    (Pd, td), (Pm, tm), (Ph, th) = out
+    assert td["device_pair_measure_s"] > 0.0
+    assert tm["device_pair_measure_s"] == 0.0 and th["device_pair_measure_s"] == 0.0
+    for Px in (Pd, Pm):
+        assert len(Px) == len(Ph)
+        for (n, m, rp, ci, v), (n2, m2, rp2, ci2, v2) in zip(Px, Ph):
+            assert (n, m) == (n2, m2)
+            np.testing.assert_array_equal(rp, rp2)
+            np.testing.assert_array_equal(ci, ci2)
+            assert np.abs(v - v2).max() <= 1e-12 * np.abs(v2).max()
