@@ -446,13 +446,15 @@ typedef struct {
  *  device_setup 1 (default): the coarse edge / vertex matrices (Thm.
  *               cemats) and the auxiliary smoothed prolongation (Def.
  *               aux_sp) are built on the device for the agglomerates that
- *               Algorithm 1 finds on the host, and Algorithm 1's pair
- *               measure mu_p (Lemma mu2) is evaluated on the device for its
- *               batches of candidate pairs (>= 512 pairs; the greedy loop
- *               and the mu_g tests stay on the host); 0: all on the host
- *  device_pair_measure 1 (default): with device_setup, mu_p as above on
- *               the device; 0: mu_p on the host (same hierarchy; the choice
- *               is a matter of speed only)
+ *               Algorithm 1 finds on the host, and (with
+ *               device_pair_measure) Algorithm 1's pair measure mu_p (Lemma
+ *               mu2) is evaluated on the device for its batches of candidate
+ *               pairs (>= 512 pairs; the greedy loop and the mu_g tests stay
+ *               on the host); 0: all on the host
+ *  device_pair_measure 1: with device_setup, mu_p as above on the device;
+ *               0 (default): mu_p on the host, in the same parallel pass as
+ *               the mu_g tests, which a 16-core host finishes sooner than
+ *               the device path (same hierarchy: a matter of speed only)
  *  keep_topology 1: keep the coarse topologies the device stages build, for
  *               amg_download_topology (host memory: a level's edge and
  *               vertex matrices); 0 (default): drop them

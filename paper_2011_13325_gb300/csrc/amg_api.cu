@@ -488,7 +488,7 @@ cudaError_t device_prolongation(Ctx *c, int level, const amgsetup::Topo &T, cons
 struct DeviceSink : amgsetup::LevelSink {
   Ctx *c;
   double device_s = 0.0, device_setup_s = 0.0;
-  bool device = true, keep = false, device_pm = true;
+  bool device = true, keep = false, device_pm = false;
   std::vector<char> p_on_device;  // per level: P_l already built on the device
   amgsetup::PairMeasure *pm = nullptr;
   explicit DeviceSink(Ctx *cc) : c(cc) {}
@@ -1182,7 +1182,7 @@ void amg_default_setup_params(amg_setup_params *p) {
   p->device_setup = 1;
   p->keep_topology = 0;
   p->scalar_only = 0;
-  p->device_pair_measure = 1;
+  p->device_pair_measure = 0;
 }
 
 int amg_setup(amg_ctx *h, const amg_problem *prob, const amg_setup_params *params, int precision,
@@ -1239,7 +1239,7 @@ int amg_setup(amg_ctx *h, const amg_problem *prob, const amg_setup_params *param
   DeviceSink sink(c);
   sink.device = (!params || params->device_setup != 0) && blk != 1;
   sink.keep = params && params->keep_topology != 0;
-  sink.device_pm = !params || params->device_pair_measure != 0;
+  sink.device_pm = params && params->device_pair_measure != 0;
   c->topo.clear();
   c->setup_times[5] = 0.0;
   std::string err;

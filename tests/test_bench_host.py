@@ -69,6 +69,18 @@ def test_algorithmic_bytes_count():
             assert bench.algorithmic_bytes_per_iteration(lv, prec, nr) == mat + nr * vec
 
 
+def test_algorithmic_bytes_bf16_below_level_0():
+    """BF16 storage below level 0: level 0's A, P, R count 4 bytes per value,
+    level 1's A, P, R 2 bytes; vectors as in the FP32 V-cycle."""
+    lv = [dict(n_rows=10, block=3, nnzb=40, nnzb_P=12), dict(n_rows=4, block=6, nnzb=10, nnzb_P=3),
+          dict(n_rows=1, block=6, nnzb=1, nnzb_P=0)]
+    b1 = bench.algorithmic_bytes_per_iteration(lv, 1)
+    b3 = bench.algorithmic_bytes_per_iteration(lv, 3)
+    # only level 1's operators change: A_1 twice (residual, smoothing), P_1 and R_1 once
+    saved = 2 * 10 * 36 * 2 + 3 * 36 * 2 + 3 * 36 * 2
+    assert b1 - b3 == saved
+
+
 def test_kernel_source_key_finds_every_named_kernel():
     src = os.path.join(os.path.dirname(bench.__file__), "paper_2011_13325_gb300", "csrc", "pcg.cu")
     a = bench.kernel_source_sha1(src, "pcg_spmv_dot_sell_df_kernel")

@@ -40,7 +40,8 @@ def test_library_setup_matches_oracle_setup(name, device_setup):
     from paper_2011_13325_gb300 import amg
     p, kw, H = _oracle(name)
     ctx = amg.Context(0)
-    ctx.setup(p, amg.AMG_PREC_FP64, device_setup=device_setup, **kw)
+    # device_setup = 1 with every device stage, mu_p included
+    ctx.setup(p, amg.AMG_PREC_FP64, device_setup=device_setup, device_pair_measure=device_setup, **kw)
     assert ctx.n_levels == H.n_levels
     for l, P in enumerate(H.P):
         n, m, rp, ci, v = ctx.download_prolongation(l)
