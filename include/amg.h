@@ -289,35 +289,43 @@ int amg_pcg_launches(const amg_ctx *ctx, int32_t *per_iteration, int32_t *fixed)
  * amg_upload_hierarchy / amg_setup:
  *   AMG_LAYOUT_AUTO             SELL-32 copy (one thread per block row) for
  *                               operators with >= 16 * 32 rows per SM and at
- *                               most 32 blocks per row (rectangular ones: 64,
- *                               with length-sorted slices); warp-per-row BSR
- *                               kernels (one warp streams a block row,
- *                               shuffle reduction) for the rest (default)
- *   AMG_LAYOUT_SELL_SHORT_ROWS  SELL-32 for every operator with short rows,
- *                               warp-per-row kernels for the rest
+ *                               most 32 blocks per row (A_0), 64
+ *                               (rectangular P_l, R_l) or 96 (A_l, l >= 1);
+ *                               warp-per-row BSR kernels (one warp streams a
+ *                               block row, shuffle reduction) for the rest
+ *                               (default)
+ *   AMG_LAYOUT_SELL_SHORT_ROWS  SELL-32 for every operator with at most 32
+ *                               blocks per row, warp-per-row kernels for the
+ *                               rest
  *   AMG_LAYOUT_WARP_ROWS        warp-per-row BSR kernels only
  *   AMG_LAYOUT_ROW_LANES        row-lane BSR kernels only (one lane per
  *                               scalar row of a block row, no reduction)
  *   AMG_LAYOUT_BLOCK_LANES      block-lane BSR kernels only (one warp per
  *                               block row, one whole block per lane)
+ *   AMG_LAYOUT_SELL_SPLIT       as AMG_LAYOUT_SELL_SHORT_ROWS, with the
+ *                               sorted copies of P_l and R_l run by one warp
+ *                               per output row of a slice (the block rows'
+ *                               br output rows on br warps)
  * Under AMG_LAYOUT_AUTO the upload also times, for every V-cycle operator
- * but a square one with a SELL-32 copy, the warp-row, row-lane and
- * block-lane kernels (and the SELL-32 copy where there is one) on the
- * operator itself and keeps the fastest.  With the environment variable
+ * but A_0 (whose SELL-32 copy the CG kernels read), the warp-row, row-lane
+ * and block-lane kernels and the SELL-32 copy where there is one (for P_l
+ * and R_l in both the thread-per-row and the split form) on the operator
+ * itself and keeps the fastest.  With the environment variable
  * AMG_TUNE_CACHE naming a file, choices recorded there are reused without
  * timing and new ones appended (a profiled process then applies the kernels
  * an earlier plain process chose).
- * The SELL-32 copies of the transfer operators P_l, R_l (rows of varying
- * length) hold, inside each window of 256 rows, the rows sorted by length,
- * so that each slice of 32 rows carries little padding; square operators
- * keep their rows in order.
+ * The SELL-32 copies of the transfer operators P_l, R_l and of the coarse
+ * A_l (rows of varying length) hold, inside each window of 256 rows, the
+ * rows sorted by length, so that each slice of 32 rows carries little
+ * padding; A_0 keeps its rows in order.
  * The result of every operator is the same up to the order of the sums. */
 enum {
   AMG_LAYOUT_AUTO = 0,
   AMG_LAYOUT_SELL_SHORT_ROWS = 1,
   AMG_LAYOUT_WARP_ROWS = 2,
   AMG_LAYOUT_ROW_LANES = 3,
-  AMG_LAYOUT_BLOCK_LANES = 4
+  AMG_LAYOUT_BLOCK_LANES = 4,
+  AMG_LAYOUT_SELL_SPLIT = 5
 };
 int amg_set_layout_policy(amg_ctx *ctx, int policy);
 

@@ -34,6 +34,7 @@ AMG_LAYOUT_SELL_SHORT_ROWS = 1
 AMG_LAYOUT_WARP_ROWS = 2
 AMG_LAYOUT_ROW_LANES = 3
 AMG_LAYOUT_BLOCK_LANES = 4
+AMG_LAYOUT_SELL_SPLIT = 5
 AMG_SMOOTHER_L1_JACOBI = 0
 AMG_SMOOTHER_LEARNED = 1
 AMG_SMOOTHER_HYBRID_GS = 2

@@ -347,7 +347,7 @@ static std::vector<std::pair<std::string, int>> load_tune_cache(const char *path
   char key[128];
   int k = 0;
   while (fscanf(f, "%127s %d", key, &k) == 2)
-    if (k >= KERN_WARP_ROWS && k <= KERN_SELL) out.emplace_back(key, k);
+    if (k >= KERN_WARP_ROWS && k <= KERN_SELL_SPLIT) out.emplace_back(key, k);
   fclose(f);
   return out;
 }
@@ -375,7 +375,8 @@ static cudaError_t tune_operators(Ctx *c) {
       const std::string key = tune_key(l, names[i], *m, mat_prec(c, l));
       bool hit = false;
       for (const auto &kv : cache)
-        if (kv.first == key && (kv.second != KERN_SELL || m->sell_ptr)) {
+        if (kv.first == key && ((kv.second != KERN_SELL && kv.second != KERN_SELL_SPLIT) || m->sell_ptr) &&
+            (kv.second != KERN_SELL_SPLIT || m->sell_perm)) {
           m->kern = kv.second;
           hit = true;
         }
@@ -398,7 +399,7 @@ static cudaError_t tune_operators(Ctx *c) {
   if (e == cudaSuccess) e = cudaMemsetAsync(b, 0, ny * sizeof(double), c->stream);
   if (e == cudaSuccess) e = cudaEventCreate(&e0);
   if (e == cudaSuccess) e = cudaEventCreate(&e1);
-  const int kerns[4] = {KERN_SELL, KERN_WARP_ROWS, KERN_ROW_LANES, KERN_BLOCK_LANES};
+  const int kerns[5] = {KERN_SELL, KERN_SELL_SPLIT, KERN_WARP_ROWS, KERN_ROW_LANES, KERN_BLOCK_LANES};
   for (size_t i = 0; i < ops.size() && e == cudaSuccess; ++i) {
     DevBSR &m = *ops[i].first;
     const int mode = ops[i].second, prec = op_prec[i];
@@ -406,6 +407,10 @@ static cudaError_t tune_operators(Ctx *c) {
     int pick = m.sell_ptr ? KERN_SELL : KERN_WARP_ROWS;
     for (int k : kerns) {
       if (k == KERN_SELL && !m.sell_ptr) continue;
+      // the split form: sorted copies of rectangular operators (which never
+      // run the smoothing mode)
+      if (k == KERN_SELL_SPLIT && !(m.sell_ptr && m.sell_perm && (m.br != m.bc || m.n_rows != m.n_cols)))
+        continue;
       m.kern = k;
       // the operator's own V-cycle mode; best of two timed triples
       e = launch_bsr(c, m, prec, mode, x, b, nullptr, y);
@@ -451,8 +456,10 @@ static int finalize_hierarchy(Ctx *c) {
     CUDA_OR_FAIL(c, alloc_level_vectors(c, L), "level vectors");
     DevBSR *ops[] = {&L.A, &L.P, &L.R};
     for (DevBSR *m : ops)
-      if (m->nnzb && want_sell(c, *m, m == &L.A && l > 0))
+      if (m->nnzb && want_sell(c, *m, m == &L.A && l > 0)) {
         CUDA_OR_FAIL(c, build_sell(c, *m, m == &L.A && l > 0), "sell layout");
+        if (c->layout_policy == AMG_LAYOUT_SELL_SPLIT && m->sell_perm && m != &L.A) m->kern = KERN_SELL_SPLIT;
+      }
     // the CG operator's double-float copy of A_0 (rows in order, 2x2 / 3x3)
     if (l == 0 && L.A.s64 && !L.A.sell_perm && (L.k == 1 || L.k == 2 || L.k == 3))
       CUDA_OR_FAIL(c, build_double_float(c, L.A), "double-float A_0");
@@ -710,8 +717,9 @@ const char *amg_describe(amg_ctx *h) {
       const DevBSR &m = *ops[i];
       if (!m.nnzb) continue;
       char k[96];
-      if (m.sell_ptr && m.kern == KERN_SELL)
-        snprintf(k, sizeof k, "SELL-32 (thread per block row,%s %.0f%% of the slots filled)",
+      if (m.sell_ptr && (m.kern == KERN_SELL || m.kern == KERN_SELL_SPLIT))
+        snprintf(k, sizeof k, "SELL-32 (%s,%s %.0f%% of the slots filled)",
+                 m.kern == KERN_SELL_SPLIT ? "warp per output row of a slice" : "thread per block row",
                  m.sell_perm ? " rows sorted by length," : "",
                  100.0 * (double)m.nnzb / (32.0 * (double)m.sell_slots));
       else
@@ -1115,7 +1123,7 @@ int amg_probe_fma_rate(amg_ctx *h, double *fp64_gflops, double *fp32_gflops) {
 
 int amg_set_layout_policy(amg_ctx *h, int policy) {
   if (!h) return AMG_ERR_ARG;
-  if (policy < AMG_LAYOUT_AUTO || policy > AMG_LAYOUT_BLOCK_LANES)
+  if (policy < AMG_LAYOUT_AUTO || policy > AMG_LAYOUT_SELL_SPLIT)
     return fail(&h->c, AMG_ERR_ARG, "unknown layout policy");
   h->c.layout_policy = policy;
   return AMG_OK;

@@ -15,7 +15,13 @@ namespace amg {
 
 // Device block-sparse-row matrix.  Values exist in FP64 always; FP32 / BF16
 // copies only for the mixed-precision V-cycles.
-enum BsrKernel { KERN_WARP_ROWS = 0, KERN_ROW_LANES = 1, KERN_BLOCK_LANES = 2, KERN_SELL = 3 };
+enum BsrKernel {
+  KERN_WARP_ROWS = 0,
+  KERN_ROW_LANES = 1,
+  KERN_BLOCK_LANES = 2,
+  KERN_SELL = 3,
+  KERN_SELL_SPLIT = 4  // sorted SELL-32, one warp per output row of a slice (rectangular operators)
+};
 
 struct DevBSR {
   int n_rows = 0, n_cols = 0, br = 0, bc = 0;
@@ -37,7 +43,7 @@ struct DevBSR {
   // holds row 32s + t (square operators, whose CG kernels assume that).
   // kernel choice (set by the upload's tuner under AMG_LAYOUT_AUTO); the
   // SELL-32 copy is used when present unless the tuner picked a BSR kernel
-  int kern = KERN_SELL;  // KERN_WARP_ROWS / KERN_ROW_LANES / KERN_BLOCK_LANES / KERN_SELL
+  int kern = KERN_SELL;  // KERN_WARP_ROWS / KERN_ROW_LANES / KERN_BLOCK_LANES / KERN_SELL(_SPLIT)
   int n_slices = 0;
   int64_t sell_slots = 0;
   int *sell_ptr = nullptr;

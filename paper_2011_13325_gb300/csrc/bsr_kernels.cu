@@ -554,6 +554,60 @@ __global__ void __launch_bounds__(256) sell_perm_kernel(int n_rows, int n_slices
   }
 }
 
+// The sorted SELL-32 product with the BR output rows of a slice split over
+// BR warps: warp r of a slice computes output row r of its 32 block rows
+// from row r of every block (BC contiguous 32-wide rows of a slot).  The BR
+// warps of a slice read the same column indices and x entries (the second
+// and later from L1) and each a BR-th of the values, so a transfer operator
+// with short rows has BR times the warps in flight, each with a BR-th of the
+// arithmetic.  Per output entry the sums run in sell_perm_kernel's order, so
+// both give the same bits.
+template <int BR, int BC, typename V, typename T, int MODE>
+__global__ void __launch_bounds__(256) sell_split_kernel(int n_rows, int n_slices,
+                                                         const int *__restrict__ sell_ptr,
+                                                         const int *__restrict__ sell_col,
+                                                         const int *__restrict__ perm,
+                                                         const V *__restrict__ vals,
+                                                         const T *__restrict__ x,
+                                                         const T *__restrict__ b,
+                                                         T *__restrict__ y) {
+  static_assert(MODE != SPMV_SMOOTH, "the smoothing mode needs every output row of a block row");
+  pdl_enter();
+  using A = typename AccT<T>::type;
+  constexpr int E = BR * BC;
+  const int gw = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int slice = gw / BR, r = gw - slice * BR;
+  if (slice >= n_slices) return;
+  const int t = threadIdx.x & 31;
+  const int row = __ldg(perm + slice * 32 + t);
+  const int j0 = sell_ptr[slice], j1 = sell_ptr[slice + 1];
+  A acc = 0;
+  constexpr int U = 4;
+  for (int j = j0; j < j1; j += U) {
+    int cc[U];
+#pragma unroll
+    for (int u = 0; u < U; ++u) cc[u] = (j + u < j1) ? __ldg(sell_col + (size_t)(j + u) * 32 + t) : 0;
+    A xv[U][BC];
+#pragma unroll
+    for (int u = 0; u < U; ++u)
+#pragma unroll
+      for (int q = 0; q < BC; ++q) xv[u][q] = (j + u < j1) ? (A)ld(x + (size_t)cc[u] * BC + q) : (A)0;
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+      if (j + u < j1) {
+        const V *v = vals + (size_t)(j + u) * E * 32 + (size_t)r * BC * 32 + t;
+#pragma unroll
+        for (int q = 0; q < BC; ++q) acc += (A)lds(v + q * 32) * xv[u][q];
+      }
+    }
+  }
+  if (row >= n_rows) return;
+  const size_t o = (size_t)row * BR + r;
+  if (MODE == SPMV_SET) y[o] = (T)acc;
+  if (MODE == SPMV_RESID) y[o] = (T)((A)b[o] - acc);
+  if (MODE == SPMV_ADD) y[o] = (T)((A)y[o] + acc);
+}
+
 template <int BR, int BC, typename V, typename T>
 static cudaError_t sell_mode(const Ctx *c, const DevBSR &A, const V *vals, int mode, const void *x,
                              const void *b, const void *minv, void *y) {
@@ -563,6 +617,21 @@ static cudaError_t sell_mode(const Ctx *c, const DevBSR &A, const V *vals, int m
   const T *bb = (const T *)b;
   const T *mm = (const T *)minv;
   T *yy = (T *)y;
+  if (A.sell_perm && A.kern == KERN_SELL_SPLIT && mode != SPMV_SMOOTH) {
+    // BR warps per slice, 8 warps per block
+    const int gs = (int)(((long long)A.n_slices * BR + 7) / 8);
+#define AMG_SELL_SPLIT_LAUNCH(M_)                                                                  \
+  AMG_KLAUNCH(c, sell_split_kernel<BR, BC, V, T, M_>, gs, 256, A.n_rows, A.n_slices, A.sell_ptr, \
+              A.sell_col, A.sell_perm, vals, xx, bb, yy)
+    switch (mode) {
+      case SPMV_SET: AMG_SELL_SPLIT_LAUNCH(SPMV_SET); break;
+      case SPMV_RESID: AMG_SELL_SPLIT_LAUNCH(SPMV_RESID); break;
+      case SPMV_ADD: AMG_SELL_SPLIT_LAUNCH(SPMV_ADD); break;
+      default: return cudaErrorInvalidValue;
+    }
+#undef AMG_SELL_SPLIT_LAUNCH
+    return cudaGetLastError();
+  }
   if (A.sell_perm) {
 #define AMG_SELL_PERM_LAUNCH(M_)                                                                 \
   AMG_KLAUNCH(c, sell_perm_kernel<BR, BC, V, T, M_>, g, 64, A.n_rows, A.n_slices, A.sell_ptr, \
@@ -607,14 +676,14 @@ template <int BR, int BC>
 static cudaError_t bsr_prec(const Ctx *c, const DevBSR &A, int prec, int mode, const void *x,
                             const void *b, const void *minv, void *y) {
   if (A.n_rows == 0) return cudaSuccess;
-  if (A.sell_ptr && A.kern == KERN_SELL) {
+  if (A.sell_ptr && (A.kern == KERN_SELL || A.kern == KERN_SELL_SPLIT)) {
     if (prec == AMG_PREC_FP64)
       return sell_mode<BR, BC, double, double>(c, A, A.s64, mode, x, b, minv, y);
     if (prec == AMG_PREC_FP32_VCYCLE)
       return sell_mode<BR, BC, float, float>(c, A, A.s32, mode, x, b, minv, y);
     return sell_mode<BR, BC, __nv_bfloat16, float>(c, A, A.s16, mode, x, b, minv, y);
   }
-  int kern = A.kern == KERN_SELL ? KERN_WARP_ROWS : A.kern;
+  int kern = (A.kern == KERN_SELL || A.kern == KERN_SELL_SPLIT) ? KERN_WARP_ROWS : A.kern;
   if (c->layout_policy == AMG_LAYOUT_ROW_LANES) kern = KERN_ROW_LANES;
   if (c->layout_policy == AMG_LAYOUT_BLOCK_LANES) kern = KERN_BLOCK_LANES;
   if (kern == KERN_BLOCK_LANES) {
@@ -909,7 +978,8 @@ bool want_sell(const Ctx *c, const DevBSR &m, bool coarse_square) {
   if (c->layout_policy == AMG_LAYOUT_WARP_ROWS || c->layout_policy == AMG_LAYOUT_ROW_LANES ||
       c->layout_policy == AMG_LAYOUT_BLOCK_LANES)
     return false;
-  if (c->layout_policy == AMG_LAYOUT_SELL_SHORT_ROWS) return avg <= 32.0;
+  if (c->layout_policy == AMG_LAYOUT_SELL_SHORT_ROWS || c->layout_policy == AMG_LAYOUT_SELL_SPLIT)
+    return avg <= 32.0;
   // coarse square operators (sorted slices too) up to 96 blocks per row
   return m.n_rows >= 32 * 16 * c->num_sms && avg <= (rect ? 64.0 : coarse_square ? 96.0 : 32.0);
 }

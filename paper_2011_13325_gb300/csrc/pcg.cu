@@ -273,9 +273,12 @@ struct SellDfView {
 
 // q = A_0 p in double-float arithmetic (p given as hi/lo pairs in pdf) and
 // the per-block partial of p.q in FP64 (64-thread blocks, two slices each,
-// thread per block row, as the FP64 kernel above).
+// thread per block row, as the FP64 kernel above).  At most 32 registers
+// per thread (one slot per loop trip), so that 64 warps fit on an SM: the
+// kernel waits on memory, and a 64^3 operator's 8,064 slices then fit in
+// one wave.
 template <int BR>
-__global__ void __launch_bounds__(kSellThreads) pcg_spmv_dot_sell_df_kernel(
+__global__ void __launch_bounds__(kSellThreads, 32) pcg_spmv_dot_sell_df_kernel(
     SellDfView A, const float2 *__restrict__ pdf, const double *__restrict__ p,
     double *__restrict__ q, double *__restrict__ partials) {
   pdl_enter();
@@ -289,7 +292,7 @@ __global__ void __launch_bounds__(kSellThreads) pcg_spmv_dot_sell_df_kernel(
 #pragma unroll
     for (int r = 0; r < BR; ++r) hi[r] = lo[r] = 0.f;
     const int j1 = A.ptr[s + 1];
-#pragma unroll 2
+#pragma unroll 1
     for (int j = A.ptr[s]; j < j1; ++j) {
       const int c = __ldg(A.col + (size_t)j * 32 + t);
       const float2 *a = A.v + (size_t)j * E * 32 + t;

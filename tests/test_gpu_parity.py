@@ -55,11 +55,11 @@ def _hier(name):
     return _HIER[name]
 
 
-LAYOUTS = {"auto": 0, "warp": 2, "sell": 1, "rowlane": 3, "blocklane": 4}
+LAYOUTS = {"auto": 0, "warp": 2, "sell": 1, "rowlane": 3, "blocklane": 4, "sellsplit": 5}
 
 
 # every case runs with each operator layout (tuned, warp per row, SELL-32,
-# row lanes, block lanes)
+# row lanes, block lanes, SELL-32 with the transfers split by output row)
 @pytest.fixture(scope="module", params=[(n, lay) for n in sorted(CASES) for lay in LAYOUTS],
                 ids=lambda v: f"{v[0]}-{v[1]}")
 def case(request):
@@ -397,6 +397,50 @@ def test_sell_layout_sorts_rectangular_operators():
     ctx.vcycle(dev(r), z)
     assert maxrel(host(z), solve.vcycle(H, r)) <= 1e-10
     ctx.close()
+
+
+@pytest.mark.parametrize("prec", [0, 1])
+@pytest.mark.parametrize("name", sorted(CASES))
+def test_split_transfers_give_the_same_bits(name, prec):
+    """The split SELL-32 form of P_l and R_l (one warp per output row of a
+    slice) sums every output entry in the order of the thread-per-row form:
+    restriction, prolongation and whole V-cycles agree bit for bit, and the
+    split form is the one that ran (the context's description says so)."""
+    amg = _amg()
+    p, H = _hier(name)
+    ctxs = []
+    for pol in (amg.AMG_LAYOUT_SELL_SHORT_ROWS, amg.AMG_LAYOUT_SELL_SPLIT):
+        c = amg.Context(0)
+        c.set_layout_policy(pol)
+        c.upload_hierarchy(H.A[0], H.P, prec)
+        ctxs.append(c)
+    lines = [ln for ln in ctxs[1].describe().splitlines() if " P:" in ln or " R:" in ln]
+    split = [ln for ln in lines if "warp per output row" in ln]
+    if not split:
+        pytest.skip("no transfer operator of this mesh has a SELL-32 copy")
+    assert all("rows sorted by length" in ln for ln in split)
+    n = H.A[0].n_rows * H.A[0].br
+    r = np.random.default_rng(11).normal(size=n)
+    z = [dev(np.zeros(n)) for _ in ctxs]
+    for c, zz in zip(ctxs, z):
+        c.vcycle(dev(r), zz)
+    assert np.array_equal(host(z[0]), host(z[1]))
+    if prec == 0:
+        for l in range(H.n_levels - 1):
+            nc = H.P[l].n_cols * H.P[l].bc
+            y = np.random.default_rng(12 + l).normal(size=nc)
+            t = np.random.default_rng(20 + l).normal(size=H.P[l].n_rows * H.P[l].br)
+            outs = []
+            for c in ctxs:
+                b = dev(np.zeros(nc))
+                c.restrict(l, dev(t), b)
+                x = dev(np.ones(H.P[l].n_rows * H.P[l].br))
+                c.prolong_add(l, dev(y), x)
+                outs.append((host(b), host(x)))
+            assert np.array_equal(outs[0][0], outs[1][0]) and np.array_equal(outs[0][1], outs[1][1]), l
+            assert maxrel(outs[1][0], solve.spmv(H.R[l], t)) <= 1e-13
+    for c in ctxs:
+        c.close()
 
 
 def test_cg_operator_both_arithmetics(case):
