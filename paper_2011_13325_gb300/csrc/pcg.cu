@@ -273,12 +273,11 @@ struct SellDfView {
 
 // q = A_0 p in double-float arithmetic (p given as hi/lo pairs in pdf) and
 // the per-block partial of p.q in FP64 (64-thread blocks, two slices each,
-// thread per block row, as the FP64 kernel above).  At most 32 registers
-// per thread (one slot per loop trip), so that 64 warps fit on an SM: the
-// kernel waits on memory, and a 64^3 operator's 8,064 slices then fit in
-// one wave.
+// thread per block row, as the FP64 kernel above).  Two slots per loop trip
+// at 40 registers (48 warps per SM) hold more loads in flight than one slot
+// at 32 registers (64 warps per SM): 393 against 487 us at 128^3.
 template <int BR>
-__global__ void __launch_bounds__(kSellThreads, 32) pcg_spmv_dot_sell_df_kernel(
+__global__ void __launch_bounds__(kSellThreads) pcg_spmv_dot_sell_df_kernel(
     SellDfView A, const float2 *__restrict__ pdf, const double *__restrict__ p,
     double *__restrict__ q, double *__restrict__ partials) {
   pdl_enter();
@@ -292,7 +291,7 @@ __global__ void __launch_bounds__(kSellThreads, 32) pcg_spmv_dot_sell_df_kernel(
 #pragma unroll
     for (int r = 0; r < BR; ++r) hi[r] = lo[r] = 0.f;
     const int j1 = A.ptr[s + 1];
-#pragma unroll 1
+#pragma unroll 2
     for (int j = A.ptr[s]; j < j1; ++j) {
       const int c = __ldg(A.col + (size_t)j * 32 + t);
       const float2 *a = A.v + (size_t)j * E * 32 + t;
@@ -372,7 +371,23 @@ __global__ void __launch_bounds__(kRedThreads) pcg_dot_rz_kernel(size_t n, const
   double v[2] = {0.0, 0.0};
   const size_t stride = (size_t)gridDim.x * blockDim.x;
   const bool flex = st->flexible != 0;
-  for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) {
+  size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+  // four entries per trip, their loads issued together, then the rest
+  for (; i + 3 * stride < n; i += 4 * stride) {
+    double ri[4], zi[4], oi[4];
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+      ri[u] = r[i + u * stride];
+      zi[u] = z[i + u * stride];
+      oi[u] = flex ? zold[i + u * stride] : 0.0;
+    }
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+      v[0] += ri[u] * zi[u];
+      v[1] += ri[u] * oi[u];
+    }
+  }
+  for (; i < n; i += stride) {
     const double ri = r[i];
     v[0] += ri * z[i];
     if (flex) v[1] += ri * zold[i];
@@ -433,8 +448,16 @@ __global__ void __launch_bounds__(kFinThreads) pcg_alpha_kernel(PcgState *st,
   pdl_enter();
   __shared__ double sh[kFinThreads / 32];
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-  double a = 0.0;
-  for (int b = threadIdx.x; b < n_pq; b += blockDim.x) a += pq_partials[b];
+  // eight partials per trip in flight together (up to ~33K of them), then
+  // the rest
+  double a8[8] = {0.0, 0.0, 0.0, 0.0, 0.0, 0.0, 0.0, 0.0};
+  int b = threadIdx.x;
+  for (; b + 7 * (int)blockDim.x < n_pq; b += 8 * (int)blockDim.x) {
+#pragma unroll
+    for (int u = 0; u < 8; ++u) a8[u] += pq_partials[b + u * (int)blockDim.x];
+  }
+  for (; b < n_pq; b += blockDim.x) a8[0] += pq_partials[b];
+  double a = ((a8[0] + a8[1]) + (a8[2] + a8[3])) + ((a8[4] + a8[5]) + (a8[6] + a8[7]));
   for (int o = 16; o > 0; o >>= 1) a += __shfl_down_sync(0xffffffffu, a, o);
   if (lane == 0) sh[w] = a;
   __syncthreads();
@@ -458,7 +481,26 @@ __global__ void __launch_bounds__(kRedThreads) pcg_update_xr_kernel(
   const double alpha = st->alpha;
   double v = 0.0;
   const size_t stride = (size_t)gridDim.x * blockDim.x;
-  for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) {
+  size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+  // four entries per trip, their loads issued together, then the rest
+  for (; i + 3 * stride < n; i += 4 * stride) {
+    double xi[4], pi[4], ri[4], qi[4];
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+      xi[u] = x[i + u * stride];
+      pi[u] = p[i + u * stride];
+      ri[u] = r[i + u * stride];
+      qi[u] = q[i + u * stride];
+    }
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+      x[i + u * stride] = xi[u] + alpha * pi[u];
+      const double rn = ri[u] - alpha * qi[u];
+      r[i + u * stride] = rn;
+      v += rn * rn;
+    }
+  }
+  for (; i < n; i += stride) {
     x[i] += alpha * p[i];
     const double ri = r[i] - alpha * q[i];
     r[i] = ri;
@@ -489,8 +531,14 @@ __global__ void pcg_guard_kernel(PcgState *st, const double *rr_partials, int n_
                                  unsigned *counter, cudaGraphConditionalHandle h, int in_graph,
                                  int verify) {
   pdl_enter();
-  double v = 0.0;
-  for (int b = threadIdx.x; b < n_rr; b += 32) v += rr_partials[b];
+  double v8[8] = {0.0, 0.0, 0.0, 0.0, 0.0, 0.0, 0.0, 0.0};
+  int b = threadIdx.x;
+  for (; b + 7 * 32 < n_rr; b += 8 * 32) {
+#pragma unroll
+    for (int u = 0; u < 8; ++u) v8[u] += rr_partials[b + u * 32];
+  }
+  for (; b < n_rr; b += 32) v8[0] += rr_partials[b];
+  double v = ((v8[0] + v8[1]) + (v8[2] + v8[3])) + ((v8[4] + v8[5]) + (v8[6] + v8[7]));
   for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
   if (threadIdx.x != 0) return;
   st->rr = v;
