@@ -371,23 +371,7 @@ __global__ void __launch_bounds__(kRedThreads) pcg_dot_rz_kernel(size_t n, const
   double v[2] = {0.0, 0.0};
   const size_t stride = (size_t)gridDim.x * blockDim.x;
   const bool flex = st->flexible != 0;
-  size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
-  // four entries per trip, their loads issued together, then the rest
-  for (; i + 3 * stride < n; i += 4 * stride) {
-    double ri[4], zi[4], oi[4];
-#pragma unroll
-    for (int u = 0; u < 4; ++u) {
-      ri[u] = r[i + u * stride];
-      zi[u] = z[i + u * stride];
-      oi[u] = flex ? zold[i + u * stride] : 0.0;
-    }
-#pragma unroll
-    for (int u = 0; u < 4; ++u) {
-      v[0] += ri[u] * zi[u];
-      v[1] += ri[u] * oi[u];
-    }
-  }
-  for (; i < n; i += stride) {
+  for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) {
     const double ri = r[i];
     v[0] += ri * z[i];
     if (flex) v[1] += ri * zold[i];
@@ -448,16 +432,8 @@ __global__ void __launch_bounds__(kFinThreads) pcg_alpha_kernel(PcgState *st,
   pdl_enter();
   __shared__ double sh[kFinThreads / 32];
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-  // eight partials per trip in flight together (up to ~33K of them), then
-  // the rest
-  double a8[8] = {0.0, 0.0, 0.0, 0.0, 0.0, 0.0, 0.0, 0.0};
-  int b = threadIdx.x;
-  for (; b + 7 * (int)blockDim.x < n_pq; b += 8 * (int)blockDim.x) {
-#pragma unroll
-    for (int u = 0; u < 8; ++u) a8[u] += pq_partials[b + u * (int)blockDim.x];
-  }
-  for (; b < n_pq; b += blockDim.x) a8[0] += pq_partials[b];
-  double a = ((a8[0] + a8[1]) + (a8[2] + a8[3])) + ((a8[4] + a8[5]) + (a8[6] + a8[7]));
+  double a = 0.0;
+  for (int b = threadIdx.x; b < n_pq; b += blockDim.x) a += pq_partials[b];
   for (int o = 16; o > 0; o >>= 1) a += __shfl_down_sync(0xffffffffu, a, o);
   if (lane == 0) sh[w] = a;
   __syncthreads();
@@ -481,26 +457,7 @@ __global__ void __launch_bounds__(kRedThreads) pcg_update_xr_kernel(
   const double alpha = st->alpha;
   double v = 0.0;
   const size_t stride = (size_t)gridDim.x * blockDim.x;
-  size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
-  // four entries per trip, their loads issued together, then the rest
-  for (; i + 3 * stride < n; i += 4 * stride) {
-    double xi[4], pi[4], ri[4], qi[4];
-#pragma unroll
-    for (int u = 0; u < 4; ++u) {
-      xi[u] = x[i + u * stride];
-      pi[u] = p[i + u * stride];
-      ri[u] = r[i + u * stride];
-      qi[u] = q[i + u * stride];
-    }
-#pragma unroll
-    for (int u = 0; u < 4; ++u) {
-      x[i + u * stride] = xi[u] + alpha * pi[u];
-      const double rn = ri[u] - alpha * qi[u];
-      r[i + u * stride] = rn;
-      v += rn * rn;
-    }
-  }
-  for (; i < n; i += stride) {
+  for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) {
     x[i] += alpha * p[i];
     const double ri = r[i] - alpha * q[i];
     r[i] = ri;
@@ -531,14 +488,8 @@ __global__ void pcg_guard_kernel(PcgState *st, const double *rr_partials, int n_
                                  unsigned *counter, cudaGraphConditionalHandle h, int in_graph,
                                  int verify) {
   pdl_enter();
-  double v8[8] = {0.0, 0.0, 0.0, 0.0, 0.0, 0.0, 0.0, 0.0};
-  int b = threadIdx.x;
-  for (; b + 7 * 32 < n_rr; b += 8 * 32) {
-#pragma unroll
-    for (int u = 0; u < 8; ++u) v8[u] += rr_partials[b + u * 32];
-  }
-  for (; b < n_rr; b += 32) v8[0] += rr_partials[b];
-  double v = ((v8[0] + v8[1]) + (v8[2] + v8[3])) + ((v8[4] + v8[5]) + (v8[6] + v8[7]));
+  double v = 0.0;
+  for (int b = threadIdx.x; b < n_rr; b += 32) v += rr_partials[b];
   for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
   if (threadIdx.x != 0) return;
   st->rr = v;
