@@ -125,16 +125,6 @@ __global__ void __launch_bounds__(256) bsr_warp_kernel(int n_rows, const int *__
   const int nwarps = (gridDim.x * blockDim.x) >> 5;
   for (int row = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; row < n_rows; row += nwarps) {
     const int s = rowptr[row], e = rowptr[row + 1];
-    const size_t o = (size_t)row * BR;
-    // the epilogue's operands (b, the old x or y), loaded before the block
-    // loop so that their latency overlaps it (not the row of M^+: holding
-    // it through the loop costs 8 registers and with them occupancy)
-    A pre_b = 0, pre_x = 0;
-    if (lane < BR) {
-      if (MODE == SPMV_RESID || MODE == SPMV_SMOOTH) pre_b = (A)b[o + lane];
-      if (MODE == SPMV_SMOOTH) pre_x = (A)x[o + lane];
-      if (MODE == SPMV_ADD) pre_x = (A)y[o + lane];
-    }
     A acc = 0;
     if (active) {
       int p = s + bl;
@@ -163,23 +153,24 @@ __global__ void __launch_bounds__(256) bsr_warp_kernel(int n_rows, const int *__
     }
 #pragma unroll
     for (int sft = 1; sft < NB; sft <<= 1) {
-      A ov = __shfl_down_sync(0xffffffffu, acc, sft * BR);
-      if (bl + sft < NB) acc += ov;
+      A o = __shfl_down_sync(0xffffffffu, acc, sft * BR);
+      if (bl + sft < NB) acc += o;
     }
+    const size_t o = (size_t)row * BR;
     if (MODE == SPMV_SMOOTH) {
       // x_out = x_in + M^+ (b - A x_in) for this vertex (block-l1 Jacobi)
-      A res = (lane < BR) ? pre_b - acc : (A)0;
+      A res = (lane < BR) ? (A)b[o + lane] - acc : (A)0;
       A upd = 0;
 #pragma unroll
       for (int q = 0; q < BR; ++q) {
         A rq = __shfl_sync(0xffffffffu, res, q);
         if (lane < BR) upd += (A)minv[(o + lane) * BR + q] * rq;
       }
-      if (lane < BR) y[o + lane] = (TO)(pre_x + upd);
+      if (lane < BR) y[o + lane] = (TO)((A)x[o + lane] + upd);
     } else if (lane < BR) {
       if (MODE == SPMV_SET) y[o + lane] = (TO)acc;
-      if (MODE == SPMV_RESID) y[o + lane] = (TO)(pre_b - acc);
-      if (MODE == SPMV_ADD) y[o + lane] = (TO)(pre_x + acc);
+      if (MODE == SPMV_RESID) y[o + lane] = (TO)((A)b[o + lane] - acc);
+      if (MODE == SPMV_ADD) y[o + lane] = (TO)((A)y[o + lane] + acc);
     }
   }
 }
