@@ -339,8 +339,10 @@ int amg_set_layout_policy(amg_ctx *ctx, int policy);
  *                        bytes), products are formed exactly with FP32 fused
  *                        multiply-adds (Dekker's two-product) and summed with
  *                        Knuth's two-sum (the double-float arithmetic of
- *                        Dekker 1971 / Bailey's double-float method); q is
- *                        returned in FP64.  Each term carries a relative error
+ *                        Dekker 1971 / Bailey's double-float method), the
+ *                        low parts of each block summed on their own and
+ *                        two-summed into the row's low word; q is returned
+ *                        in FP64.  Each term carries a relative error
  *                        of about 2^-47 (FP64: 2^-53); p.q, the CG scalars and
  *                        all vector updates stay FP64.  Entries of p below
  *                        about 2^-102 in magnitude lose low-word bits (FP32

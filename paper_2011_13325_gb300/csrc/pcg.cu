@@ -254,6 +254,9 @@ __device__ __forceinline__ double float_to_double_scaled(float f, int s) {
 }
 
 // (sh, sl) += (ah + al) * (xh + xl)
+// sh takes the rounded products through Knuth's two-sum (its rounding
+// errors kept exactly), sl the errors and the cross terms, summed plainly
+// (the kernel below gives each block its own sl)
 __device__ __forceinline__ void df_mac(float &sh, float &sl, float2 a, float2 x) {
   const float p = __fmul_rn(a.x, x.x);
   const float pe = __fmaf_rn(a.x, x.x, -p);                     // a.x * x.x = p + pe exactly
@@ -265,6 +268,14 @@ __device__ __forceinline__ void df_mac(float &sh, float &sl, float2 a, float2 x)
   sl = __fadd_rn(sl, __fadd_rn(err, cross));
 }
 
+// (s, e) += t by Knuth's two-sum: s the rounded sum, its error added to e
+__device__ __forceinline__ void two_sum_into(float &s, float &e, float t) {
+  const float u = __fadd_rn(s, t);
+  const float bb = __fsub_rn(u, s);
+  e = __fadd_rn(e, __fadd_rn(__fsub_rn(s, __fsub_rn(u, bb)), __fsub_rn(t, bb)));
+  s = u;
+}
+
 struct SellDfView {
   int n_rows, n_slices, df_exp;
   const int *ptr, *col;
@@ -274,10 +285,11 @@ struct SellDfView {
 // q = A_0 p in double-float arithmetic (p given as hi/lo pairs in pdf) and
 // the per-block partial of p.q in FP64 (64-thread blocks, two slices each,
 // thread per block row, as the FP64 kernel above).  Two slots per loop trip
-// at 40 registers (48 warps per SM) hold more loads in flight than one slot
-// at 32 registers (64 warps per SM): 393 against 487 us at 128^3.
+// at 40 registers (48 warps per SM; the bound keeps the compensated low
+// word within them) hold more loads in flight than one slot at 32 registers
+// (64 warps per SM): 393 against 487 us at 128^3.
 template <int BR>
-__global__ void __launch_bounds__(kSellThreads) pcg_spmv_dot_sell_df_kernel(
+__global__ void __launch_bounds__(kSellThreads, 24) pcg_spmv_dot_sell_df_kernel(
     SellDfView A, const float2 *__restrict__ pdf, const double *__restrict__ p,
     double *__restrict__ q, double *__restrict__ partials) {
   pdl_enter();
@@ -287,9 +299,15 @@ __global__ void __launch_bounds__(kSellThreads) pcg_spmv_dot_sell_df_kernel(
   const int s = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   double v = 0.0;
   if (s < A.n_slices) {
-    float hi[BR], lo[BR];
+    // per output row: hi the two-summed products, lo the low parts of the
+    // blocks so far (each block's low parts summed on their own, then
+    // two-summed into lo), lo2 lo's rounding errors.  Summing the low parts
+    // of a whole row plainly would round at 2^-24 of their running total, an
+    // error that rows with strong cancellation (coefficient jumps) amplify
+    // beyond the 48-bit storage of the values.
+    float hi[BR], lo[BR], lo2[BR];
 #pragma unroll
-    for (int r = 0; r < BR; ++r) hi[r] = lo[r] = 0.f;
+    for (int r = 0; r < BR; ++r) hi[r] = lo[r] = lo2[r] = 0.f;
     const int j1 = A.ptr[s + 1];
 #pragma unroll 2
     for (int j = A.ptr[s]; j < j1; ++j) {
@@ -299,9 +317,12 @@ __global__ void __launch_bounds__(kSellThreads) pcg_spmv_dot_sell_df_kernel(
 #pragma unroll
       for (int k = 0; k < BR; ++k) xv[k] = __ldg(pdf + (size_t)c * BR + k);
 #pragma unroll
-      for (int r = 0; r < BR; ++r)
+      for (int r = 0; r < BR; ++r) {
+        float lt = 0.f;
 #pragma unroll
-        for (int k = 0; k < BR; ++k) df_mac(hi[r], lo[r], __ldcs(a + (r * BR + k) * 32), xv[k]);
+        for (int k = 0; k < BR; ++k) df_mac(hi[r], lt, __ldcs(a + (r * BR + k) * 32), xv[k]);
+        two_sum_into(lo[r], lo2[r], lt);
+      }
     }
     const int row = s * 32 + t;
     if (row < A.n_rows) {
@@ -309,7 +330,8 @@ __global__ void __launch_bounds__(kSellThreads) pcg_spmv_dot_sell_df_kernel(
       for (int r = 0; r < BR; ++r) {
         const size_t i = (size_t)row * BR + r;
         const double qi = float_to_double_scaled(hi[r], A.df_exp) +
-                          float_to_double_scaled(lo[r], A.df_exp);
+                          (float_to_double_scaled(lo[r], A.df_exp) +
+                           float_to_double_scaled(lo2[r], A.df_exp));
         q[i] = qi;
         v += p[i] * qi;
       }
