@@ -7,6 +7,10 @@
 // blocks: a warp step reads NB*BR*BC contiguous values (fully coalesced), the
 // x gather reads BC contiguous entries per lane.  Partial sums of lanes with
 // the same r are combined with warp shuffles; lanes 0..BR-1 finish the row.
+#include <mutex>
+#include <type_traits>
+#include <unordered_map>
+
 #include "amg_internal.h"
 
 namespace amg {
@@ -175,9 +179,32 @@ __global__ void __launch_bounds__(256) bsr_warp_kernel(int n_rows, const int *__
   }
 }
 
-static int grid_for_rows(const Ctx *c, int n_rows) {
+// Blocks of `threads` threads of kernel k that are resident on one SM at
+// once (from its registers and shared memory; cached per kernel).
+template <typename... P>
+static int resident_blocks(void (*k)(P...), int threads) {
+  static std::mutex mu;
+  static std::unordered_map<const void *, int> cache;
+  std::lock_guard<std::mutex> lock(mu);
+  const auto it = cache.find((const void *)k);
+  if (it != cache.end()) return it->second;
+  int n = 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k, threads, 0) != cudaSuccess || n < 1) {
+    (void)cudaGetLastError();
+    n = 1;
+  }
+  cache[(const void *)k] = n;
+  return n;
+}
+
+// Grid of a grid-stride kernel with one warp per block row: one block per 8
+// rows, at most as many blocks as are resident at once (every block then
+// starts at once and the rows are spread evenly; a grid above that would
+// run its last blocks on a mostly idle GPU).
+template <typename... P>
+static int grid_for_rows(const Ctx *c, int n_rows, void (*k)(P...)) {
   long want = ((long)n_rows + 7) / 8;  // 8 warps per 256-thread block
-  long cap = (long)c->num_sms * 8;     // 8 resident blocks of 256 threads per SM
+  const long cap = (long)c->num_sms * resident_blocks(k, 256);
   if (want > cap) want = cap;
   return (int)(want < 1 ? 1 : want);
 }
@@ -185,24 +212,27 @@ static int grid_for_rows(const Ctx *c, int n_rows) {
 template <int BR, int BC, typename V, typename T>
 static cudaError_t bsr_mode(const Ctx *c, const DevBSR &A, const V *vals, int mode, const void *x,
                             const void *b, const void *minv, void *y) {
-  const int g = grid_for_rows(c, A.n_rows);
   const T *xx = (const T *)x;
   const T *bb = (const T *)b;
   const T *mm = (const T *)minv;
   T *yy = (T *)y;
+#define AMG_WARP_LAUNCH(M_)                                                                    \
+  AMG_KLAUNCH(c, bsr_warp_kernel<BR, BC, V, T, M_>,                                            \
+              grid_for_rows(c, A.n_rows, bsr_warp_kernel<BR, BC, V, T, M_>), 256, A.n_rows,    \
+              A.rowptr, A.colidx, vals, xx, bb, mm, yy)
   switch (mode) {
     case SPMV_SET:
-      AMG_KLAUNCH(c, bsr_warp_kernel<BR, BC, V, T, SPMV_SET>, g, 256, A.n_rows, A.rowptr, A.colidx, vals, xx, bb, mm, yy);
+      AMG_WARP_LAUNCH(SPMV_SET);
       break;
     case SPMV_RESID:
-      AMG_KLAUNCH(c, bsr_warp_kernel<BR, BC, V, T, SPMV_RESID>, g, 256, A.n_rows, A.rowptr, A.colidx, vals, xx, bb, mm, yy);
+      AMG_WARP_LAUNCH(SPMV_RESID);
       break;
     case SPMV_ADD:
-      AMG_KLAUNCH(c, bsr_warp_kernel<BR, BC, V, T, SPMV_ADD>, g, 256, A.n_rows, A.rowptr, A.colidx, vals, xx, bb, mm, yy);
+      AMG_WARP_LAUNCH(SPMV_ADD);
       break;
     case SPMV_SMOOTH:
       if constexpr (BR == BC) {
-        AMG_KLAUNCH(c, bsr_warp_kernel<BR, BC, V, T, SPMV_SMOOTH>, g, 256, A.n_rows, A.rowptr, A.colidx, vals, xx, bb, mm, yy);
+        AMG_WARP_LAUNCH(SPMV_SMOOTH);
         break;
       } else {
         return cudaErrorInvalidValue;
@@ -210,6 +240,7 @@ static cudaError_t bsr_mode(const Ctx *c, const DevBSR &A, const V *vals, int mo
     default:
       return cudaErrorInvalidValue;
   }
+#undef AMG_WARP_LAUNCH
   return cudaGetLastError();
 }
 
@@ -339,6 +370,46 @@ __device__ __forceinline__ void ldblock(const __nv_bfloat16 *p, float *out) {
   ldn_stream<E>(p, out);
 }
 
+// Staging of a warp's 32 blocks in shared memory (block-lane kernel): the
+// blocks of one pass are contiguous in memory, so the warp copies them with
+// coalesced word loads and each lane then reads its own block from shared
+// memory.  Read straight from global memory, a lane's block (not 16-byte
+// aligned) takes several 8-byte loads 32 blocks apart, each touching 32
+// sectors for 256 useful bytes.
+template <int E, typename V>
+struct LbStage {
+  static constexpr int BYTES = E * (int)sizeof(V);
+  static constexpr bool ON = (BYTES % 16 != 0) && (32 * BYTES <= 4608);
+  using W = typename std::conditional<
+      BYTES % 8 == 0, uint2,
+      typename std::conditional<BYTES % 4 == 0, unsigned, unsigned short>::type>::type;
+};
+
+template <int E>
+__device__ __forceinline__ void stage_read(const float *p, float *out) {
+  if constexpr (E % 2 == 0) {
+#pragma unroll
+    for (int i = 0; i < E; i += 2) {
+      const float2 v = *reinterpret_cast<const float2 *>(p + i);
+      out[i] = v.x;
+      out[i + 1] = v.y;
+    }
+  } else {
+#pragma unroll
+    for (int i = 0; i < E; ++i) out[i] = p[i];
+  }
+}
+template <int E>
+__device__ __forceinline__ void stage_read(const double *p, double *out) {
+#pragma unroll
+  for (int i = 0; i < E; ++i) out[i] = p[i];
+}
+template <int E>
+__device__ __forceinline__ void stage_read(const __nv_bfloat16 *p, float *out) {
+#pragma unroll
+  for (int i = 0; i < E; ++i) out[i] = __bfloat162float(p[i]);
+}
+
 template <int BR, int BC, typename V, typename T, int MODE>
 __global__ void __launch_bounds__(256) bsr_lblock_kernel(int n_rows, const int *__restrict__ rowptr,
                                                          const int *__restrict__ colidx,
@@ -352,6 +423,7 @@ __global__ void __launch_bounds__(256) bsr_lblock_kernel(int n_rows, const int *
   constexpr int E = BR * BC;
   // a block starts 16-byte aligned when E * sizeof(V) is a multiple of 16
   constexpr bool W16 = (E * sizeof(V)) % 16 == 0;
+  using St = LbStage<E, V>;
   const int lane = threadIdx.x & 31;
   const int nwarps = (gridDim.x * blockDim.x) >> 5;
   for (int row = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; row < n_rows; row += nwarps) {
@@ -359,15 +431,42 @@ __global__ void __launch_bounds__(256) bsr_lblock_kernel(int n_rows, const int *
     A acc[BR];
 #pragma unroll
     for (int r = 0; r < BR; ++r) acc[r] = 0;
-    for (int p = s + lane; p < e; p += 32) {
-      const int c = __ldg(colidx + p);
-      A xv[BC], v[E];
-      ldn_cached<BC>(x + (size_t)c * BC, xv);
-      ldblock<E, W16>(vals + (size_t)p * E, v);
+    if constexpr (St::ON) {
+      using W = typename St::W;
+      constexpr int WPB = St::BYTES / (int)sizeof(W);  // words per block
+      // one 32-block buffer per warp of the 256-thread block
+      __shared__ __align__(16) W stage_w[8 * 32 * WPB];
+      W *dst = stage_w + (threadIdx.x >> 5) * 32 * WPB;
+      const V *stage = reinterpret_cast<const V *>(dst);
+      // passes of 32 blocks (uniform over the warp)
+      for (int p0 = s; p0 < e; p0 += 32) {
+        const int nb = min(32, e - p0);
+        const W *src = reinterpret_cast<const W *>(vals + (size_t)p0 * E);
+        for (int k = lane; k < nb * WPB; k += 32) dst[k] = __ldcs(src + k);
+        __syncwarp();
+        if (lane < nb) {
+          const int c = __ldg(colidx + p0 + lane);
+          A xv[BC], v[E];
+          ldn_cached<BC>(x + (size_t)c * BC, xv);
+          stage_read<E>(stage + lane * E, v);
 #pragma unroll
-      for (int r = 0; r < BR; ++r)
+          for (int r = 0; r < BR; ++r)
 #pragma unroll
-        for (int q = 0; q < BC; ++q) acc[r] += v[r * BC + q] * xv[q];
+            for (int q = 0; q < BC; ++q) acc[r] += v[r * BC + q] * xv[q];
+        }
+        __syncwarp();
+      }
+    } else {
+      for (int p = s + lane; p < e; p += 32) {
+        const int c = __ldg(colidx + p);
+        A xv[BC], v[E];
+        ldn_cached<BC>(x + (size_t)c * BC, xv);
+        ldblock<E, W16>(vals + (size_t)p * E, v);
+#pragma unroll
+        for (int r = 0; r < BR; ++r)
+#pragma unroll
+          for (int q = 0; q < BC; ++q) acc[r] += v[r * BC + q] * xv[q];
+      }
     }
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1)
@@ -395,15 +494,14 @@ __global__ void __launch_bounds__(256) bsr_lblock_kernel(int n_rows, const int *
 template <int BR, int BC, typename V, typename T>
 static cudaError_t lblock_mode(const Ctx *c, const DevBSR &A, const V *vals, int mode, const void *x,
                                const void *b, const void *minv, void *y) {
-  long want = ((long)A.n_rows + 7) / 8;
-  const long cap = (long)c->num_sms * 8;
-  if (want > cap) want = cap;
-  const int g = (int)(want < 1 ? 1 : want);
   const T *xx = (const T *)x;
   const T *bb = (const T *)b;
   const T *mm = (const T *)minv;
   T *yy = (T *)y;
-#define AMG_LB_LAUNCH(M_)                                                                        AMG_KLAUNCH(c, bsr_lblock_kernel<BR, BC, V, T, M_>, g, 256, A.n_rows, A.rowptr, A.colidx,                                                                  vals, xx, bb, mm, yy)
+#define AMG_LB_LAUNCH(M_)                                                                    \
+  AMG_KLAUNCH(c, bsr_lblock_kernel<BR, BC, V, T, M_>,                                        \
+              grid_for_rows(c, A.n_rows, bsr_lblock_kernel<BR, BC, V, T, M_>), 256, A.n_rows, \
+              A.rowptr, A.colidx, vals, xx, bb, mm, yy)
   switch (mode) {
     case SPMV_SET: AMG_LB_LAUNCH(SPMV_SET); break;
     case SPMV_RESID: AMG_LB_LAUNCH(SPMV_RESID); break;
@@ -517,9 +615,14 @@ __global__ void __launch_bounds__(256) sell_perm_kernel(int n_rows, int n_slices
     for (int u = 0; u < U; ++u) cc[u] = (j + u < j1) ? __ldg(sell_col + (size_t)(j + u) * 32 + t) : 0;
     A xv[U][BC];
 #pragma unroll
-    for (int u = 0; u < U; ++u)
+    for (int u = 0; u < U; ++u) {
+      if (j + u < j1) {
+        ldn_cached<BC>(x + (size_t)cc[u] * BC, xv[u]);
+      } else {
 #pragma unroll
-      for (int q = 0; q < BC; ++q) xv[u][q] = (j + u < j1) ? (A)ld(x + (size_t)cc[u] * BC + q) : (A)0;
+        for (int q = 0; q < BC; ++q) xv[u][q] = (A)0;
+      }
+    }
 #pragma unroll
     for (int u = 0; u < U; ++u) {
       if (j + u < j1) {
@@ -589,9 +692,14 @@ __global__ void __launch_bounds__(256) sell_split_kernel(int n_rows, int n_slice
     for (int u = 0; u < U; ++u) cc[u] = (j + u < j1) ? __ldg(sell_col + (size_t)(j + u) * 32 + t) : 0;
     A xv[U][BC];
 #pragma unroll
-    for (int u = 0; u < U; ++u)
+    for (int u = 0; u < U; ++u) {
+      if (j + u < j1) {
+        ldn_cached<BC>(x + (size_t)cc[u] * BC, xv[u]);
+      } else {
 #pragma unroll
-      for (int q = 0; q < BC; ++q) xv[u][q] = (j + u < j1) ? (A)ld(x + (size_t)cc[u] * BC + q) : (A)0;
+        for (int q = 0; q < BC; ++q) xv[u][q] = (A)0;
+      }
+    }
 #pragma unroll
     for (int u = 0; u < U; ++u) {
       if (j + u < j1) {
@@ -716,7 +824,8 @@ static cudaError_t smooth_out64_k(const Ctx *c, const DevBSR &A, const V *bsr_va
     AMG_KLAUNCH(c, sell_kernel<K, K, V, float, SPMV_SMOOTH, double>, (A.n_slices + 1) / 2, 64, 
         A.n_rows, A.n_slices, A.sell_ptr, A.sell_col, sell_vals, x, b, minv, y);
   } else {
-    AMG_KLAUNCH(c, bsr_warp_kernel<K, K, V, float, SPMV_SMOOTH, double>, grid_for_rows(c, A.n_rows), 256, 
+    AMG_KLAUNCH(c, bsr_warp_kernel<K, K, V, float, SPMV_SMOOTH, double>,
+                grid_for_rows(c, A.n_rows, bsr_warp_kernel<K, K, V, float, SPMV_SMOOTH, double>), 256, 
         A.n_rows, A.rowptr, A.colidx, bsr_vals, x, b, minv, y);
   }
   return cudaGetLastError();
