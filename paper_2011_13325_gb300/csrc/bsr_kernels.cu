@@ -373,13 +373,14 @@ __device__ __forceinline__ void ldblock(const __nv_bfloat16 *p, float *out) {
 // Staging of a warp's 32 blocks in shared memory (block-lane kernel): the
 // blocks of one pass are contiguous in memory, so the warp copies them with
 // coalesced word loads and each lane then reads its own block from shared
-// memory.  Read straight from global memory, a lane's block (not 16-byte
-// aligned) takes several 8-byte loads 32 blocks apart, each touching 32
-// sectors for 256 useful bytes.
+// memory.  Read straight from global memory, a lane's block takes several
+// loads 32 blocks apart, each touching 32 sectors for 256 or 512 useful
+// bytes.  Every shape whose 32 blocks fit in 4.5 KB is staged (8 warps per
+// block: at most 36 KB of shared memory); FP64 6x6 blocks are not.
 template <int E, typename V>
 struct LbStage {
   static constexpr int BYTES = E * (int)sizeof(V);
-  static constexpr bool ON = (BYTES % 16 != 0) && (32 * BYTES <= 4608);
+  static constexpr bool ON = 32 * BYTES <= 4608;
   using W = typename std::conditional<
       BYTES % 8 == 0, uint2,
       typename std::conditional<BYTES % 4 == 0, unsigned, unsigned short>::type>::type;

@@ -285,11 +285,12 @@ struct SellDfView {
 // q = A_0 p in double-float arithmetic (p given as hi/lo pairs in pdf) and
 // the per-block partial of p.q in FP64 (64-thread blocks, two slices each,
 // thread per block row, as the FP64 kernel above).  Two slots per loop trip
-// at 40 registers (48 warps per SM; the bound keeps the compensated low
-// word within them) hold more loads in flight than one slot at 32 registers
-// (64 warps per SM): 393 against 487 us at 128^3.
+// (48 registers with the compensated low word, 42 warps per SM) hold more
+// loads in flight than one slot at 32 registers (64 warps per SM: 487
+// against 393 us at 128^3 before the compensation), and forcing the
+// compensated kernel into 40 registers cost more (445 against 405 us).
 template <int BR>
-__global__ void __launch_bounds__(kSellThreads, 24) pcg_spmv_dot_sell_df_kernel(
+__global__ void __launch_bounds__(kSellThreads) pcg_spmv_dot_sell_df_kernel(
     SellDfView A, const float2 *__restrict__ pdf, const double *__restrict__ p,
     double *__restrict__ q, double *__restrict__ partials) {
   pdl_enter();
