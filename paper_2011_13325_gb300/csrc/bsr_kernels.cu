@@ -111,6 +111,49 @@ __device__ __forceinline__ void ldn_cached(const float *p, A *out) {
   }
 }
 
+// Staging of the blocks a warp reads in one pass in shared memory (warp-row
+// and block-lane kernels): the blocks of a pass are contiguous in memory, so
+// the warp copies them with coalesced word loads and each lane then reads its
+// part from shared memory.  Read straight from global memory, a lane's part
+// takes several loads whose addresses are 24 to 288 bytes apart across the
+// lanes, so each warp load touches up to 32 sectors for 256 useful bytes.
+// LbStage: the block-lane kernel's 32 blocks per pass, staged for every
+// shape whose 32 blocks fit in 4.5 KB (8 warps per block: at most 36 KB of
+// shared memory; FP64 6x6 blocks are not staged).
+template <int E, typename V>
+struct LbStage {
+  static constexpr int BYTES = E * (int)sizeof(V);
+  static constexpr bool ON = 32 * BYTES <= 4608;
+  using W = typename std::conditional<
+      BYTES % 8 == 0, uint2,
+      typename std::conditional<BYTES % 4 == 0, unsigned, unsigned short>::type>::type;
+};
+
+template <int E>
+__device__ __forceinline__ void stage_read(const float *p, float *out) {
+  if constexpr (E % 2 == 0) {
+#pragma unroll
+    for (int i = 0; i < E; i += 2) {
+      const float2 v = *reinterpret_cast<const float2 *>(p + i);
+      out[i] = v.x;
+      out[i + 1] = v.y;
+    }
+  } else {
+#pragma unroll
+    for (int i = 0; i < E; ++i) out[i] = p[i];
+  }
+}
+template <int E>
+__device__ __forceinline__ void stage_read(const double *p, double *out) {
+#pragma unroll
+  for (int i = 0; i < E; ++i) out[i] = p[i];
+}
+template <int E>
+__device__ __forceinline__ void stage_read(const __nv_bfloat16 *p, float *out) {
+#pragma unroll
+  for (int i = 0; i < E; ++i) out[i] = __bfloat162float(p[i]);
+}
+
 template <int BR, int BC, typename V, typename T, int MODE, typename TO = T>
 __global__ void __launch_bounds__(256) bsr_warp_kernel(int n_rows, const int *__restrict__ rowptr,
                                                        const int *__restrict__ colidx,
@@ -122,6 +165,13 @@ __global__ void __launch_bounds__(256) bsr_warp_kernel(int n_rows, const int *__
   pdl_enter();
   using A = typename AccT<T>::type;
   constexpr int NB = 32 / BR;
+  constexpr int E = BR * BC;
+  // the 2 * NB blocks of a loop trip, staged in shared memory (see LbStage)
+  using St = LbStage<E, V>;
+  using W = typename St::W;
+  constexpr int WPB = St::BYTES / (int)sizeof(W);
+  constexpr bool STAGE = 2 * NB * St::BYTES <= 4608;
+  __shared__ __align__(16) W stage_w[STAGE ? 8 * 2 * NB * WPB : 1];
   const int lane = threadIdx.x & 31;
   const int bl = lane / BR;
   const int r = lane - bl * BR;
@@ -130,7 +180,40 @@ __global__ void __launch_bounds__(256) bsr_warp_kernel(int n_rows, const int *__
   for (int row = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; row < n_rows; row += nwarps) {
     const int s = rowptr[row], e = rowptr[row + 1];
     A acc = 0;
-    if (active) {
+    if constexpr (STAGE) {
+      W *dst = stage_w + (threadIdx.x >> 5) * 2 * NB * WPB;
+      const V *stg = reinterpret_cast<const V *>(dst);
+      // trips of 2 * NB blocks (uniform over the warp); lane (bl, r) takes
+      // blocks bl and bl + NB of a trip as the unstaged loop below does, so
+      // the sums run in the same order
+      for (int p0 = s; p0 < e; p0 += 2 * NB) {
+        const int nblk = min(2 * NB, e - p0);
+        const W *src = reinterpret_cast<const W *>(vals + (size_t)p0 * E);
+        for (int k = lane; k < nblk * WPB; k += 32) dst[k] = __ldcs(src + k);
+        __syncwarp();
+        if (active && bl + NB < nblk) {
+          const int c0 = __ldg(colidx + p0 + bl), c1 = __ldg(colidx + p0 + bl + NB);
+          A a0[BC], a1[BC], x0[BC], x1[BC];
+          stage_read<BC>(stg + (bl * BR + r) * BC, a0);
+          stage_read<BC>(stg + ((bl + NB) * BR + r) * BC, a1);
+          ldn_cached<BC>(x + (size_t)c0 * BC, x0);
+          ldn_cached<BC>(x + (size_t)c1 * BC, x1);
+#pragma unroll
+          for (int q = 0; q < BC; ++q) {
+            acc += a0[q] * x0[q];
+            acc += a1[q] * x1[q];
+          }
+        } else if (active && bl < nblk) {
+          const int c0 = __ldg(colidx + p0 + bl);
+          A a0[BC], x0[BC];
+          stage_read<BC>(stg + (bl * BR + r) * BC, a0);
+          ldn_cached<BC>(x + (size_t)c0 * BC, x0);
+#pragma unroll
+          for (int q = 0; q < BC; ++q) acc += a0[q] * x0[q];
+        }
+        __syncwarp();
+      }
+    } else if (active) {
       int p = s + bl;
       // two block steps per iteration keep more loads in flight
       for (; p + NB < e; p += 2 * NB) {
@@ -368,47 +451,6 @@ __device__ __forceinline__ void ldblock(const double *p, double *out) {
 template <int E, bool W16>
 __device__ __forceinline__ void ldblock(const __nv_bfloat16 *p, float *out) {
   ldn_stream<E>(p, out);
-}
-
-// Staging of a warp's 32 blocks in shared memory (block-lane kernel): the
-// blocks of one pass are contiguous in memory, so the warp copies them with
-// coalesced word loads and each lane then reads its own block from shared
-// memory.  Read straight from global memory, a lane's block takes several
-// loads 32 blocks apart, each touching 32 sectors for 256 or 512 useful
-// bytes.  Every shape whose 32 blocks fit in 4.5 KB is staged (8 warps per
-// block: at most 36 KB of shared memory); FP64 6x6 blocks are not.
-template <int E, typename V>
-struct LbStage {
-  static constexpr int BYTES = E * (int)sizeof(V);
-  static constexpr bool ON = 32 * BYTES <= 4608;
-  using W = typename std::conditional<
-      BYTES % 8 == 0, uint2,
-      typename std::conditional<BYTES % 4 == 0, unsigned, unsigned short>::type>::type;
-};
-
-template <int E>
-__device__ __forceinline__ void stage_read(const float *p, float *out) {
-  if constexpr (E % 2 == 0) {
-#pragma unroll
-    for (int i = 0; i < E; i += 2) {
-      const float2 v = *reinterpret_cast<const float2 *>(p + i);
-      out[i] = v.x;
-      out[i + 1] = v.y;
-    }
-  } else {
-#pragma unroll
-    for (int i = 0; i < E; ++i) out[i] = p[i];
-  }
-}
-template <int E>
-__device__ __forceinline__ void stage_read(const double *p, double *out) {
-#pragma unroll
-  for (int i = 0; i < E; ++i) out[i] = p[i];
-}
-template <int E>
-__device__ __forceinline__ void stage_read(const __nv_bfloat16 *p, float *out) {
-#pragma unroll
-  for (int i = 0; i < E; ++i) out[i] = __bfloat162float(p[i]);
 }
 
 template <int BR, int BC, typename V, typename T, int MODE>
