@@ -111,15 +111,16 @@ __device__ __forceinline__ void ldn_cached(const float *p, A *out) {
   }
 }
 
-// Staging of the blocks a warp reads in one pass in shared memory (warp-row
-// and block-lane kernels): the blocks of a pass are contiguous in memory, so
-// the warp copies them with coalesced word loads and each lane then reads its
-// part from shared memory.  Read straight from global memory, a lane's part
-// takes several loads whose addresses are 24 to 288 bytes apart across the
-// lanes, so each warp load touches up to 32 sectors for 256 useful bytes.
-// LbStage: the block-lane kernel's 32 blocks per pass, staged for every
-// shape whose 32 blocks fit in 4.5 KB (8 warps per block: at most 36 KB of
-// shared memory; FP64 6x6 blocks are not staged).
+// Staging of a warp's 32 blocks in shared memory (block-lane kernel): the
+// blocks of one pass are contiguous in memory, so the warp copies them with
+// coalesced word loads and each lane then reads its own block from shared
+// memory.  Read straight from global memory, a lane's block takes several
+// loads 32 blocks apart, each touching 32 sectors for 256 or 512 useful
+// bytes.  Every shape whose 32 blocks fit in 4.5 KB is staged (8 warps per
+// block: at most 36 KB of shared memory; FP64 6x6 blocks are not).  The
+// warp-row kernel reads its blocks directly: staged, it was slower (its
+// lanes already read contiguous 24-byte rows, and the copy serialises each
+// trip's loads behind the previous trip's arithmetic).
 template <int E, typename V>
 struct LbStage {
   static constexpr int BYTES = E * (int)sizeof(V);
@@ -165,13 +166,6 @@ __global__ void __launch_bounds__(256) bsr_warp_kernel(int n_rows, const int *__
   pdl_enter();
   using A = typename AccT<T>::type;
   constexpr int NB = 32 / BR;
-  constexpr int E = BR * BC;
-  // the 2 * NB blocks of a loop trip, staged in shared memory (see LbStage)
-  using St = LbStage<E, V>;
-  using W = typename St::W;
-  constexpr int WPB = St::BYTES / (int)sizeof(W);
-  constexpr bool STAGE = 2 * NB * St::BYTES <= 4608;
-  __shared__ __align__(16) W stage_w[STAGE ? 8 * 2 * NB * WPB : 1];
   const int lane = threadIdx.x & 31;
   const int bl = lane / BR;
   const int r = lane - bl * BR;
@@ -180,40 +174,7 @@ __global__ void __launch_bounds__(256) bsr_warp_kernel(int n_rows, const int *__
   for (int row = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; row < n_rows; row += nwarps) {
     const int s = rowptr[row], e = rowptr[row + 1];
     A acc = 0;
-    if constexpr (STAGE) {
-      W *dst = stage_w + (threadIdx.x >> 5) * 2 * NB * WPB;
-      const V *stg = reinterpret_cast<const V *>(dst);
-      // trips of 2 * NB blocks (uniform over the warp); lane (bl, r) takes
-      // blocks bl and bl + NB of a trip as the unstaged loop below does, so
-      // the sums run in the same order
-      for (int p0 = s; p0 < e; p0 += 2 * NB) {
-        const int nblk = min(2 * NB, e - p0);
-        const W *src = reinterpret_cast<const W *>(vals + (size_t)p0 * E);
-        for (int k = lane; k < nblk * WPB; k += 32) dst[k] = __ldcs(src + k);
-        __syncwarp();
-        if (active && bl + NB < nblk) {
-          const int c0 = __ldg(colidx + p0 + bl), c1 = __ldg(colidx + p0 + bl + NB);
-          A a0[BC], a1[BC], x0[BC], x1[BC];
-          stage_read<BC>(stg + (bl * BR + r) * BC, a0);
-          stage_read<BC>(stg + ((bl + NB) * BR + r) * BC, a1);
-          ldn_cached<BC>(x + (size_t)c0 * BC, x0);
-          ldn_cached<BC>(x + (size_t)c1 * BC, x1);
-#pragma unroll
-          for (int q = 0; q < BC; ++q) {
-            acc += a0[q] * x0[q];
-            acc += a1[q] * x1[q];
-          }
-        } else if (active && bl < nblk) {
-          const int c0 = __ldg(colidx + p0 + bl);
-          A a0[BC], x0[BC];
-          stage_read<BC>(stg + (bl * BR + r) * BC, a0);
-          ldn_cached<BC>(x + (size_t)c0 * BC, x0);
-#pragma unroll
-          for (int q = 0; q < BC; ++q) acc += a0[q] * x0[q];
-        }
-        __syncwarp();
-      }
-    } else if (active) {
+    if (active) {
       int p = s + bl;
       // two block steps per iteration keep more loads in flight
       for (; p + NB < e; p += 2 * NB) {
@@ -984,36 +945,49 @@ cudaError_t launch_blockdiag(const Ctx *c, int n, int k, int prec, const void *m
   return cudaErrorInvalidValue;
 }
 
-// y = Cinv b (FP64 dense inverse of the regularised coarsest matrix), one
-// warp per row; input/output in the V-cycle precision.
+// y = Cinv b (FP64 dense inverse of the regularised coarsest matrix); input
+// and output in the V-cycle precision.  Four warps per row, each summing a
+// quarter of it with four partial sums per lane, combined in shared memory:
+// a row of the inverse (up to ~10 KB) read by one warp alone is a chain of
+// dependent trips that leaves the GPU idle (13 us for 1,242 rows).
 template <typename T>
-__global__ void coarse_gemv_kernel(int n, const double *__restrict__ cinv, const T *__restrict__ b,
-                                   T *__restrict__ y) {
+__global__ void __launch_bounds__(256) coarse_gemv_kernel(int n, const double *__restrict__ cinv,
+                                                          const T *__restrict__ b,
+                                                          T *__restrict__ y) {
   pdl_enter();
-  const int lane = threadIdx.x & 31;
-  const int row = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-  if (row >= n) return;
-  const double *a = cinv + (size_t)row * n;
-  // four independent partial sums keep four loads in flight per lane
-  double acc0 = 0.0, acc1 = 0.0, acc2 = 0.0, acc3 = 0.0;
-  int j = lane;
-  for (; j + 96 < n; j += 128) {
-    acc0 += a[j] * (double)b[j];
-    acc1 += a[j + 32] * (double)b[j + 32];
-    acc2 += a[j + 64] * (double)b[j + 64];
-    acc3 += a[j + 96] * (double)b[j + 96];
-  }
-  for (; j < n; j += 32) acc0 += a[j] * (double)b[j];
-  double acc = (acc0 + acc1) + (acc2 + acc3);
+  __shared__ double part[8];
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;  // 2 rows x 4 quarters
+  const int row = blockIdx.x * 2 + (w >> 2), qtr = w & 3;
+  double acc = 0.0;
+  if (row < n) {
+    const int j0 = (int)((long)n * qtr / 4), j1 = (int)((long)n * (qtr + 1) / 4);
+    const double *a = cinv + (size_t)row * n;
+    double acc0 = 0.0, acc1 = 0.0, acc2 = 0.0, acc3 = 0.0;
+    int j = j0 + lane;
+    for (; j + 96 < j1; j += 128) {
+      acc0 += a[j] * (double)b[j];
+      acc1 += a[j + 32] * (double)b[j + 32];
+      acc2 += a[j + 64] * (double)b[j + 64];
+      acc3 += a[j + 96] * (double)b[j + 96];
+    }
+    for (; j < j1; j += 32) acc0 += a[j] * (double)b[j];
+    acc = (acc0 + acc1) + (acc2 + acc3);
 #pragma unroll
-  for (int s = 16; s > 0; s >>= 1) acc += __shfl_down_sync(0xffffffffu, acc, s);
-  if (lane == 0) y[row] = (T)acc;
+    for (int s = 16; s > 0; s >>= 1) acc += __shfl_down_sync(0xffffffffu, acc, s);
+  }
+  if (lane == 0) part[w] = acc;
+  __syncthreads();
+  if (threadIdx.x < 2) {
+    const int r = blockIdx.x * 2 + threadIdx.x;
+    const double *pp = part + 4 * threadIdx.x;
+    if (r < n) y[r] = (T)((pp[0] + pp[1]) + (pp[2] + pp[3]));
+  }
 }
 
 cudaError_t launch_coarse_gemv(const Ctx *c, int n, const double *cinv, const void *b, void *y,
                                int prec) {
   if (n == 0) return cudaSuccess;
-  const int g = (n + 7) / 8;
+  const int g = (n + 1) / 2;
   if (prec == AMG_PREC_FP64)
     AMG_KLAUNCH(c, coarse_gemv_kernel<double>, g, 256, n, cinv, (const double *)b, (double *)y);
   else
