@@ -114,17 +114,18 @@ __device__ __forceinline__ void ldn_cached(const float *p, A *out) {
 // Staging of a warp's 32 blocks in shared memory (block-lane kernel): the
 // blocks of one pass are contiguous in memory, so the warp copies them with
 // coalesced word loads and each lane then reads its own block from shared
-// memory.  Read straight from global memory, a lane's block takes several
-// loads 32 blocks apart, each touching 32 sectors for 256 or 512 useful
-// bytes.  Every shape whose 32 blocks fit in 4.5 KB is staged (8 warps per
-// block: at most 36 KB of shared memory; FP64 6x6 blocks are not).  The
-// warp-row kernel reads its blocks directly: staged, it was slower (its
-// lanes already read contiguous 24-byte rows, and the copy serialises each
-// trip's loads behind the previous trip's arithmetic).
+// memory.  Read straight from global memory, a block that is not 16-byte
+// aligned takes several 8-byte loads 32 blocks apart, each touching 32
+// sectors for 256 useful bytes; those shapes are staged when their 32 blocks
+// fit in 4.5 KB (8 warps per block: at most 36 KB of shared memory).  Blocks
+// that are 16-byte aligned (6x6 FP32, read as 16-byte vectors) ran slower
+// staged, and so did the warp-row kernel (its lanes already read contiguous
+// 24-byte rows; the copy serialises each trip's loads behind the previous
+// trip's arithmetic).
 template <int E, typename V>
 struct LbStage {
   static constexpr int BYTES = E * (int)sizeof(V);
-  static constexpr bool ON = 32 * BYTES <= 4608;
+  static constexpr bool ON = (BYTES % 16 != 0) && (32 * BYTES <= 4608);
   using W = typename std::conditional<
       BYTES % 8 == 0, uint2,
       typename std::conditional<BYTES % 4 == 0, unsigned, unsigned short>::type>::type;
