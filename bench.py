@@ -931,6 +931,20 @@ def run_batch(args, ws, rank, local, problems):
         variants["batch_fp64"] = {"ms": round(float(np.mean(t64)), 3), "iters_max": max(it64),
                                   "iters_mean": round(float(np.mean(it64)), 2)}
         B64.close()
+    # the same batch with the other arithmetic of the CG product
+    main_df = "(double-float)" in B.describe()
+    ctx_op = batch_upload(amg, problems, P_lists, prec, local)
+    for c in ctx_op:
+        c.set_cg_operator(amg.AMG_CG_FP64 if main_df else amg.AMG_CG_DOUBLE_FLOAT)
+    Bop = amg.Batch(ctx_op, 6)
+    run(Bop, 3, False)
+    top, itop = run(Bop, args.steps, True)
+    variants["cg_product_" + ("fp64" if main_df else "double_float")] = {
+        "ms": round(float(np.mean(top)), 3), "iters_max": max(itop),
+        "iters_mean": round(float(np.mean(itop)), 2)}
+    Bop.close()
+    for c in ctx_op:
+        c.close()
     # plain FP64 GPU PCG, one system and one load case at a time (384 graph
     # launches per step), device time summed
     seq_steps = 2
@@ -973,15 +987,29 @@ def run_batch(args, ws, rank, local, problems):
     per_it, fixed = B.launches()
     launches = fixed + max(its) * per_it
     tuned = [ln for ln in B.describe().splitlines() if "lanes/row" in ln or "SELL-32" in ln]
-    # dominant kernel: the grouped FP64 CG product q = A_0 p (6 load cases),
-    # bound by the FP64 pipe; its per-launch time from the tuner's CUDA events
+    # dominant kernel: the grouped CG product q = A_0 p (6 load cases); in
+    # FP64 bound by the FP64 pipe, in double-float arithmetic by HBM; its
+    # per-launch time from the tuner's CUDA events
     import re
     cg_us = [float(re.search(r"([0-9.]+) us$", ln).group(1)) for ln in tuned if "q = A_0 p" in ln]
     nnzb0 = sum(levels[0]["nnzb"] * levels[0]["block"] ** 2 for levels in levels_per_system)
     cg_flops = 2.0 * 6 * nnzb0
     fp64_gflops, _ = ctx_main[0].probe_fma_rate()
     roof = None
-    if cg_us:
+    if cg_us and main_df:
+        # values as pairs (8 bytes each) and column indices once, p pairs
+        # read and q written for the 6 load cases of every dof
+        cg_bytes = sum(L[0]["nnzb"] * (L[0]["block"] ** 2 * 8 + 4) + 4 * (L[0]["n_rows"] + 1) +
+                       2 * 8 * 6 * L[0]["n_rows"] * L[0]["block"] for L in levels_per_system)
+        ach = cg_bytes / (cg_us[0] * 1e-6) / 1e9
+        roof = {"bound": "hbm", "achieved": round(ach, 1), "peak": pk["hbm_gbs"], "unit": "GB/s",
+                "frac": round(ach / pk["hbm_gbs"], 3), "traffic": None,
+                "kernel": "grouped CG product q = A_0 p in double-float arithmetic (gsell_df_kernel), "
+                          "all systems, 6 load cases",
+                "bytes_per_launch": int(cg_bytes), "us_per_launch": cg_us[0],
+                "flops_per_launch": int(cg_flops), "tflops": round(cg_flops / (cg_us[0] * 1e-6) / 1e12, 3),
+                "peak_kind": pk_kind}
+    elif cg_us:
         ach = cg_flops / (cg_us[0] * 1e-6) / 1e12
         roof = {"bound": "alu", "achieved": round(ach, 3), "peak": round(fp64_gflops / 1e3, 3),
                 "unit": "TFLOP/s", "frac": round(ach / (fp64_gflops / 1e3), 3), "traffic": None,

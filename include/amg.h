@@ -559,6 +559,12 @@ typedef struct amg_batch amg_batch;
  * length-sorted slices as in the single-system layout; block lanes, 8 or 16
  * lanes per block row with one whole block per lane, for 6x6 and 6x3
  * blocks) and the fastest is kept (amg_batch_describe lists the choices).
+ * The CG product q = A_0 p runs in double-float arithmetic (as described
+ * at amg_set_cg_operator) when the contexts' CG operator setting, read at
+ * creation, asks for it (AMG_CG_DOUBLE_FLOAT, or AMG_CG_AUTO with the FP32
+ * or BF16-storage V-cycle; the same setting on every context) and every A_0
+ * has 2x2 or 3x3 blocks; otherwise in FP64.  The batched loop stops on every
+ * load case's recurrence residual in either arithmetic.
  * Errors: AMG_ERR_ARG (also: a context with AMG_SMOOTHER_HYBRID_GS or
  * AMG_PREC_BF16_COARSE), AMG_ERR_STATE (a context without hierarchy),
  * AMG_ERR_CUDA. */

@@ -60,6 +60,7 @@ struct SysVec {
 
 struct Batch {
   int device = 0, nr = 1, precision = 0, num_sms = 0;
+  bool df = false;  // CG product q = A_0 p in double-float arithmetic
   cudaStream_t stream = nullptr;
   std::vector<Ctx *> ctx;
   std::vector<GSys> gsh;  // host copy of the per-system descriptors
@@ -105,6 +106,7 @@ static void build_spmm_items(Stage &S) {
     it.sell_perm = o.A->sell_perm;
     it.svals = o.svals;
     it.n_slices = o.A->n_slices;
+    it.df_exp = o.A->df_exp;
     first += S.lpr ? cdiv(o.A->n_rows, rpb) : cdiv(o.A->n_slices, S.wpb);
     S.sp.push_back(it);
   }
@@ -319,9 +321,15 @@ static void build_stages(Batch *B) {
     std::vector<SpmmOp> ops;
     for (int s = 0; s < ns; ++s) {
       const DevBSR &A = B->ctx[s]->levels[0].A;
-      ops.push_back(SpmmOp{&A, A.v64, B->gsh[s].p, nullptr, nullptr, B->gsh[s].q, s, svals_of(A, 0)});
+      if (B->df)
+        ops.push_back(SpmmOp{&A, A.v64, B->gsh[s].pdf, nullptr, nullptr, B->gsh[s].q, s, A.sdf});
+      else
+        ops.push_back(SpmmOp{&A, A.v64, B->gsh[s].p, nullptr, nullptr, B->gsh[s].q, s, svals_of(A, 0)});
     }
-    add_spmm(B->body, "q = A_0 p", ops, SPMV_SET, 0, 0);
+    if (B->df)
+      add_spmm(B->body, "q = A_0 p (double-float)", ops, SPMV_SET, 3, 0);
+    else
+      add_spmm(B->body, "q = A_0 p", ops, SPMV_SET, 0, 0);
   }
   {
     Stage S = sys_stage(B, ST_DOTS, "p.q -> alpha", true);
@@ -420,6 +428,7 @@ static cudaError_t autotune(Batch *B) {
         const int lpr = cw[0], wpb = cw[1];
         if (lpr > 0 && lpr < S.key.br) continue;
         if (lpr == 0 && !sell) continue;
+        if (S.key.vt == 3 && lpr != 0) continue;  // the double-float product: SELL-32 only
         if (lpr < 0 && !gblock_supported(S.key.br, S.key.bc)) continue;
         {
           S.lpr = lpr;
@@ -500,6 +509,7 @@ static void free_batch(Batch *B) {
   for (GSys &G : B->gsh) {
     double *d[] = {G.f, G.x, G.r, G.z, G.zold, G.p, G.q, G.partials};
     for (double *p : d) dfree(p);
+    dfree(G.pdf);
     dfree(G.counter);
   }
   for (SysVec &V : B->vec)
@@ -543,7 +553,12 @@ static std::string describe(const Batch *B) {
 }
 
 // SELL-32 copies of every system's A_0 and P_0 (candidates of the tuner;
-// they also serve the system's own single-system kernels)
+// they also serve the system's own single-system kernels), and, for the
+// double-float CG product, A_0's double-float copy.  The CG product runs in
+// double-float arithmetic when the contexts ask for it (amg_set_cg_operator
+// before the batch is created: AMG_CG_DOUBLE_FLOAT, or AMG_CG_AUTO with a
+// mixed-precision V-cycle) and every A_0 has a SELL-32 copy with its rows in
+// order.
 static cudaError_t ensure_sell(Batch *B) {
   for (Ctx *c : B->ctx) {
     DevBSR *ops[2] = {&c->levels[0].A, c->levels.size() > 1 ? &c->levels[0].P : nullptr};
@@ -554,6 +569,19 @@ static cudaError_t ensure_sell(Batch *B) {
       AMG_CUDA_TRY(cudaStreamSynchronize(c->stream));
     }
   }
+  const Ctx *c0 = B->ctx[0];
+  bool df = c0->cg_op == AMG_CG_DOUBLE_FLOAT || (c0->cg_op == AMG_CG_AUTO && c0->precision != AMG_PREC_FP64);
+  for (Ctx *c : B->ctx) {
+    const DevBSR &A = c->levels[0].A;
+    df = df && c->cg_op == c0->cg_op && A.sell_ptr && !A.sell_perm && A.br == A.bc && (A.br == 2 || A.br == 3);
+  }
+  B->df = df;
+  if (df)
+    for (Ctx *c : B->ctx)
+      if (!c->levels[0].A.sdf) {
+        AMG_CUDA_TRY(build_double_float(c, c->levels[0].A));
+        AMG_CUDA_TRY(cudaStreamSynchronize(c->stream));
+      }
   return cudaSuccess;
 }
 
@@ -580,6 +608,10 @@ static cudaError_t create_buffers(Batch *B) {
     for (double **p : d) {
       AMG_CUDA_TRY(dalloc((void **)p, bytes));
       AMG_CUDA_TRY(cudaMemset(*p, 0, bytes));
+    }
+    if (B->df) {
+      AMG_CUDA_TRY(dalloc((void **)&G.pdf, G.n * nr * sizeof(float2)));
+      AMG_CUDA_TRY(cudaMemset(G.pdf, 0, G.n * nr * sizeof(float2)));
     }
     for (const Level &L : c->levels) {
       const size_t lb = (size_t)L.A.n_rows * L.k * nr * w;

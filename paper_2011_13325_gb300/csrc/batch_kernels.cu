@@ -6,6 +6,7 @@
 #include <cuda_bf16.h>
 
 #include "batch_kernels.h"
+#include "df_arith.cuh"
 
 namespace amg {
 
@@ -215,6 +216,69 @@ __global__ void __launch_bounds__(128) gsell_kernel(const SpmmItem *__restrict__
   }
 }
 
+// The CG product q = A_0 p in double-float arithmetic on the SELL-32 copy
+// (thread per block row, rows in order): the values as hi/lo FP32 pairs
+// scaled by 2^-df_exp, p as pairs (written by the p update), every product
+// exact by two-product, summed by two-sum, the low parts of each block on
+// their own and two-summed into the row's low word (as the single-system
+// kernel); q in FP64.
+template <int BR, int NR>
+__global__ void __launch_bounds__(128) gsell_df_kernel(const SpmmItem *__restrict__ items, int n_items,
+                                                       const McgState *__restrict__ st) {
+  constexpr int E = BR * BR;
+  const int ii = find_item(items, n_items, blockIdx.x);
+  const SpmmItem &I = items[ii];
+  if (!st[I.sys].active) return;
+  const int slice = (blockIdx.x - I.first_block) * (blockDim.x >> 5) + (threadIdx.x >> 5);
+  if (slice >= I.n_slices) return;  // whole warp
+  const int t = threadIdx.x & 31;
+  const int row = slice * 32 + t;
+  const int j0 = __ldg(I.sell_ptr + slice), j1 = __ldg(I.sell_ptr + slice + 1);
+  const float2 *__restrict__ x = (const float2 *)I.x;
+  const float2 *__restrict__ sv = (const float2 *)I.svals;
+  float hi[BR][NR], lo[BR][NR], lo2[BR][NR];
+#pragma unroll
+  for (int r = 0; r < BR; ++r)
+#pragma unroll
+    for (int j = 0; j < NR; ++j) hi[r][j] = lo[r][j] = lo2[r][j] = 0.f;
+  for (int j = j0; j < j1; ++j) {
+    const int c = __ldg(I.sell_col + (size_t)j * 32 + t);
+    const float2 *v = sv + (size_t)j * E * 32 + t;
+    const float2 *xp = x + (size_t)c * BR * NR;
+    float lt[BR][NR];
+#pragma unroll
+    for (int r = 0; r < BR; ++r)
+#pragma unroll
+      for (int jj = 0; jj < NR; ++jj) lt[r][jj] = 0.f;
+#pragma unroll
+    for (int q = 0; q < BR; ++q) {
+      float2 xv[NR];
+#pragma unroll
+      for (int jj = 0; jj < NR; ++jj) xv[jj] = __ldg(xp + q * NR + jj);
+#pragma unroll
+      for (int r = 0; r < BR; ++r) {
+        const float2 a = __ldcs(v + (r * BR + q) * 32);
+#pragma unroll
+        for (int jj = 0; jj < NR; ++jj) df_mac(hi[r][jj], lt[r][jj], a, xv[jj]);
+      }
+    }
+#pragma unroll
+    for (int r = 0; r < BR; ++r)
+#pragma unroll
+      for (int jj = 0; jj < NR; ++jj) two_sum_into(lo[r][jj], lo2[r][jj], lt[r][jj]);
+  }
+  if (row >= I.n_rows) return;
+  double *__restrict__ y = (double *)I.y;
+  const size_t o = (size_t)row * BR;
+#pragma unroll
+  for (int r = 0; r < BR; ++r)
+#pragma unroll
+    for (int jj = 0; jj < NR; ++jj)
+      y[(o + r) * NR + jj] = float_to_double_scaled(hi[r][jj], I.df_exp) +
+                             (float_to_double_scaled(lo[r][jj], I.df_exp) +
+                              float_to_double_scaled(lo2[r][jj], I.df_exp));
+}
+
 // Block-lane form for long rows of large blocks: G lanes per block row
 // (32 / G rows per warp); lane j of a row's group takes the blocks j, j + G,
 // ... whole (BR x BC values) for all NR load cases, and an xor butterfly
@@ -408,6 +472,21 @@ cudaError_t launch_gspmm(const SpmmKey &k, int nr, int lpr, int wpb, const SpmmI
   if (grid <= 0 || n_items <= 0) return cudaSuccess;
   if (wpb < 1 || wpb > 8 || (lpr > 0 && lpr < k.br)) return cudaErrorInvalidValue;
   if (lpr == 0 && wpb > 4) return cudaErrorInvalidValue;
+  if (k.vt == 3) {
+    // the double-float CG product: SELL-32 copy, square 2x2 / 3x3 blocks
+    if (lpr != 0 || k.mode != SPMV_SET || k.br != k.bc) return cudaErrorInvalidValue;
+#define G_DF(R_, N_)                                                                    \
+  if (k.br == R_ && nr == N_) {                                                         \
+    gsell_df_kernel<R_, N_><<<grid, wpb * 32, 0, s>>>(items, n_items, st);              \
+    return cudaGetLastError();                                                          \
+  }
+    G_DF(2, 1)
+    G_DF(2, 6)
+    G_DF(3, 1)
+    G_DF(3, 6)
+#undef G_DF
+    return cudaErrorInvalidValue;
+  }
   if (nr == 6) return gspmm_nr<6>(k, lpr, wpb, items, n_items, grid, st, s);
   if (nr == 1) return gspmm_nr<1>(k, lpr, wpb, items, n_items, grid, st, s);
   return cudaErrorInvalidValue;
@@ -665,7 +744,9 @@ __global__ void __launch_bounds__(256) gupdate_p_kernel(const SysItem *__restric
   for (int j = 0; j < NR; ++j) {
     if (S->done[j]) continue;
     const double zi = G.z[i * NR + j];
-    G.p[i * NR + j] = S->it[j] == 0 ? zi : zi + S->beta[j] * G.p[i * NR + j];
+    const double pi = S->it[j] == 0 ? zi : zi + S->beta[j] * G.p[i * NR + j];
+    G.p[i * NR + j] = pi;
+    if (G.pdf) G.pdf[i * NR + j] = split_double_float(pi);  // for the double-float CG product
     if (S->flexible) G.zold[i * NR + j] = zi;
   }
 }

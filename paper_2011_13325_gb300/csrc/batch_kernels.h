@@ -32,6 +32,7 @@ struct GSys {
   size_t n;       // dofs of A_0
   size_t offset;  // offset of the system's load cases in the stacked f / u
   double *f, *x, *r, *z, *zold, *p, *q;
+  float2 *pdf;  // p as double-float pairs (the double-float CG operator), else null
   double *partials;
   unsigned *counter;
   int red_blocks;
@@ -47,6 +48,7 @@ struct SpmmItem {
   const int *sell_ptr, *sell_col, *sell_perm;
   const void *svals;
   int n_slices;
+  int df_exp;  // double-float copy: values scaled by 2^-df_exp
 };
 struct DiagItem {
   const void *minv, *bin;
@@ -63,7 +65,9 @@ struct SysItem {
   int sys, first_block;
 };
 
-// value type of the operator: 0 FP64, 1 FP32, 2 BF16 (vectors FP32 for 1, 2)
+// value type of the operator: 0 FP64, 1 FP32, 2 BF16 (vectors FP32 for 1, 2),
+// 3 double-float pairs (the CG product q = A_0 p: SELL-32 copy only, x the
+// pairs of p, FP64 output)
 struct SpmmKey {
   int br, bc, vt, mode, to64;  // to64: FP64 output from an FP32 / BF16 operator
 };

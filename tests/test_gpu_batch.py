@@ -5,7 +5,9 @@ the same hierarchies, load case by load case.
 FP64: iteration counts +-1 and iterates 1e-10 relative at equal iteration
 counts (the multi-load-case kernels sum in another order than the oracle).
 FP32 / BF16-storage V-cycle: FP64 true residual <= 1.5e-8 and energy-norm
-error <= 1e-6 against the FP64 oracle solution.
+error <= 1e-6 against the FP64 oracle solution.  The CG product in
+double-float arithmetic (48 significant bits per value): iteration counts
++-1 and iterates 1e-8.
 """
 import numpy as np
 import pytest
@@ -48,7 +50,7 @@ def systems():
     return _SYS
 
 
-def _batch(prec, nrhs=6, layout=0):
+def _batch(prec, nrhs=6, layout=0, cg_op=None):
     amg = _amg()
     ctxs = []
     for p, H in systems():
@@ -56,6 +58,8 @@ def _batch(prec, nrhs=6, layout=0):
         if layout:
             c.set_layout_policy(layout)
         c.upload_hierarchy(H.A[0], H.P, prec)
+        if cg_op is not None:
+            c.set_cg_operator(cg_op)
         ctxs.append(c)
     return ctxs, amg.Batch(ctxs, nrhs)
 
@@ -122,6 +126,36 @@ def test_batch_fp64_matches_oracle(layout):
             assert maxrel(us[si][j], u_k) <= 1e-10, (si, j)
             true = np.linalg.norm(p.b[j] - solve.spmv(H.A[0], us[si][j])) / np.linalg.norm(p.b[j])
             assert true <= 1.5e-8
+
+
+def test_batch_double_float_cg_product_matches_oracle():
+    """The batched CG product q = A_0 p in double-float arithmetic (contexts
+    set to AMG_CG_DOUBLE_FLOAT before the batch is created; FP64 V-cycle, so
+    the rest is as in the FP64 test): every load case within +-1 iteration
+    of the oracle's PCG, its iterate within 1e-8 of the oracle's at the same
+    count, true residual <= 1.5e-8; with the FP64 V-cycle and AMG_CG_AUTO the
+    product stays FP64, with the FP32 V-cycle AUTO takes the double-float
+    one."""
+    amg = _amg()
+    ctxs, B = _batch(0, cg_op=amg.AMG_CG_DOUBLE_FLOAT)
+    assert "q = A_0 p (double-float)" in B.describe()
+    f = _stack(B, [p.b for p, _ in systems()])
+    u = torch.zeros_like(f)
+    s, its, rr, ms = B.pcg_solve(f, u, rtol=1e-8, maxit=500)
+    us = _unstack(B, u, 6)
+    for si, (p, H) in enumerate(systems()):
+        for j in range(6):
+            it = its[si * 6 + j]
+            _, it_or, _ = solve.pcg(H, p.b[j], rtol=1e-8, maxit=500)
+            assert abs(it - it_or) <= 1, (si, j, it, it_or)
+            u_k, _, _ = solve.pcg(H, p.b[j], rtol=0.0, maxit=it)
+            assert maxrel(us[si][j], u_k) <= 1e-8, (si, j)
+            true = np.linalg.norm(p.b[j] - solve.spmv(H.A[0], us[si][j])) / np.linalg.norm(p.b[j])
+            assert true <= 1.5e-8
+    _, B64 = _batch(0)
+    assert "double-float" not in B64.describe()
+    _, B32 = _batch(1)
+    assert "q = A_0 p (double-float)" in B32.describe()
 
 
 def test_batch_single_load_case_matches_context_solve():
