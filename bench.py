@@ -425,13 +425,13 @@ def run_single(args, ws, rank, local, train_problems):
     true_rel = float(torch.linalg.norm(res) / torch.linalg.norm(f))
     P_list = [ctx.download_prolongation(l) for l in range(ctx.n_levels - 1)]
 
-    def upload(prec, cg):
+    def upload(prec, cg, smoother=amg.AMG_SMOOTHER_L1_JACOBI):
         c2 = amg.Context(local, stream.cuda_stream)
         c2.set_pcg_graph(args.pcg_mode == "graph")
         c2.set_cg_operator(cg)
         Ps = [type("P", (), dict(n_rows=n, n_cols=m, rowptr=rp, colidx=ci, vals=v))
               for (n, m, rp, ci, v) in P_list]
-        c2.upload_hierarchy(problem.A, Ps, prec)
+        c2.upload_hierarchy(problem.A, Ps, prec, smoother)
         return c2
 
     solutions = {}
@@ -467,6 +467,12 @@ def run_single(args, ws, rank, local, train_problems):
     for prec in vlist:
         c2 = upload(prec, cg_mode)
         variants[PREC_NAMES[prec]] = variant(c2, PREC_NAMES[prec], prec)
+        c2.close()
+    # the other smoother of Sec. 7's block-l1 family: hybrid Gauss-Seidel
+    # (colour classes), same hierarchy, precision and CG operator
+    if args.smoother == "l1" and args.variants == "auto":
+        c2 = upload(args.precision, cg_mode, amg.AMG_SMOOTHER_HYBRID_GS)
+        variants["hybrid_gs"] = variant(c2, "hybrid_gs", args.precision)
         c2.close()
     # the timed configuration with the other CG operator arithmetic
     main_df = "pcg_spmv_dot_sell_df_kernel" in ctx.describe()
