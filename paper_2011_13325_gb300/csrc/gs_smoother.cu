@@ -13,6 +13,7 @@
 #include <algorithm>
 
 #include "amg_internal.h"
+#include "bsr_loads.cuh"
 
 namespace amg {
 
@@ -61,14 +62,12 @@ cudaError_t gs_prepare(Ctx *c, int level) {
   return cudaStreamSynchronize(c->stream);
 }
 
-__device__ __forceinline__ double gs_val(const double *p) { return __ldg(p); }
-__device__ __forceinline__ float gs_val(const float *p) { return __ldg(p); }
-__device__ __forceinline__ float gs_val(const __nv_bfloat16 *p) { return __bfloat162float(*p); }
-
 // One colour class: warp w updates block row rows[w] (lanes = block slot x
-// row of the block, as the warp-row SpMV kernels), x in place.  Rows of one
-// class do not couple, so no warp reads a value another warp of this launch
-// writes.
+// row of the block, two block steps per trip with vector loads, as the
+// warp-row SpMV kernel), x in place.  Rows of one class do not couple, so no
+// warp reads an x entry another warp of this launch writes (a warp reads its
+// own row's entries before it writes them): x is read through the
+// read-only path.
 template <int K, typename V, typename T>
 __global__ void __launch_bounds__(256) gs_colour_kernel(int n, const int *__restrict__ rows,
                                                         const int *__restrict__ rowptr,
@@ -82,15 +81,31 @@ __global__ void __launch_bounds__(256) gs_colour_kernel(int n, const int *__rest
   const int bl = lane / K, r = lane - bl * K;
   const int w = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   if (w >= n) return;  // whole warps leave together
-  const int row = rows[w];
+  const int row = __ldg(rows + w);
   T acc = 0;
   if (bl < NB) {
-    const int e = rowptr[row + 1];
-    for (int p = rowptr[row] + bl; p < e; p += NB) {
-      const int cc = __ldg(colidx + p);
-      const V *a = vals + ((size_t)p * K + r) * K;
+    const int e = __ldg(rowptr + row + 1);
+    int p = __ldg(rowptr + row) + bl;
+    for (; p + NB < e; p += 2 * NB) {
+      const int c0 = __ldg(colidx + p), c1 = __ldg(colidx + p + NB);
+      T a0[K], a1[K], x0[K], x1[K];
+      ldn_stream<K>(vals + ((size_t)p * K + r) * K, a0);
+      ldn_stream<K>(vals + ((size_t)(p + NB) * K + r) * K, a1);
+      ldn_cached<K>(x + (size_t)c0 * K, x0);
+      ldn_cached<K>(x + (size_t)c1 * K, x1);
 #pragma unroll
-      for (int q = 0; q < K; ++q) acc += (T)gs_val(a + q) * x[(size_t)cc * K + q];
+      for (int q = 0; q < K; ++q) {
+        acc += a0[q] * x0[q];
+        acc += a1[q] * x1[q];
+      }
+    }
+    if (p < e) {
+      const int c0 = __ldg(colidx + p);
+      T a0[K], x0[K];
+      ldn_stream<K>(vals + ((size_t)p * K + r) * K, a0);
+      ldn_cached<K>(x + (size_t)c0 * K, x0);
+#pragma unroll
+      for (int q = 0; q < K; ++q) acc += a0[q] * x0[q];
     }
   }
 #pragma unroll
