@@ -124,6 +124,51 @@ __global__ void __launch_bounds__(256) gs_colour_kernel(int n, const int *__rest
   if (lane < K) x[o + lane] += upd;
 }
 
+// The same update with block lanes, for the long rows of the coarse levels
+// (6x6 blocks, 50 to 90 per row): lane j takes the blocks j, j + 32, ... of
+// the row whole, all K of its sums at once, and an xor butterfly leaves the
+// row's K sums on every lane.  One warp then covers 32 blocks per trip
+// instead of 5, which shortens the chain of dependent loads that bounds a
+// colour class of few rows.
+template <int K, typename V, typename T>
+__global__ void __launch_bounds__(256) gs_block_kernel(int n, const int *__restrict__ rows,
+                                                       const int *__restrict__ rowptr,
+                                                       const int *__restrict__ colidx,
+                                                       const V *__restrict__ vals,
+                                                       const T *__restrict__ minv,
+                                                       const T *__restrict__ b, T *x) {
+  pdl_enter();
+  const int lane = threadIdx.x & 31;
+  const int w = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  if (w >= n) return;  // whole warps leave together
+  const int row = __ldg(rows + w);
+  const int e = __ldg(rowptr + row + 1);
+  T acc[K];
+#pragma unroll
+  for (int r = 0; r < K; ++r) acc[r] = 0;
+  for (int p = __ldg(rowptr + row) + lane; p < e; p += 32) {
+    const int cc = __ldg(colidx + p);
+    T xv[K], v[K * K];
+    ldn_cached<K>(x + (size_t)cc * K, xv);
+    ldn_stream<K * K>(vals + (size_t)p * K * K, v);
+#pragma unroll
+    for (int r = 0; r < K; ++r)
+#pragma unroll
+      for (int q = 0; q < K; ++q) acc[r] += v[r * K + q] * xv[q];
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1)
+#pragma unroll
+    for (int r = 0; r < K; ++r) acc[r] += __shfl_xor_sync(0xffffffffu, acc[r], o);
+  if (lane < K) {
+    const size_t o = (size_t)row * K;
+    T upd = 0;
+#pragma unroll
+    for (int q = 0; q < K; ++q) upd += minv[(o + lane) * K + q] * (b[o + q] - acc[q]);
+    x[o + lane] += upd;
+  }
+}
+
 template <int K, typename V, typename T>
 static cudaError_t gs_sweep_k(const Ctx *c, const Level &L, const V *vals, const T *minv, const T *b,
                               T *x, bool forward) {
@@ -132,9 +177,14 @@ static cudaError_t gs_sweep_k(const Ctx *c, const Level &L, const V *vals, const
     const int k = forward ? s : nc - 1 - s;
     const int n = L.gs_ptr[k + 1] - L.gs_ptr[k];
     if (n == 0) continue;
-    AMG_KLAUNCH(c, gs_colour_kernel<K, V, T>, (n + 7) / 8, 256, n,
-                (const int *)(L.gs_rows + L.gs_ptr[k]), (const int *)L.A.rowptr,
-                (const int *)L.A.colidx, vals, minv, b, x);
+    if constexpr (K == 6)
+      AMG_KLAUNCH(c, gs_block_kernel<K, V, T>, (n + 7) / 8, 256, n,
+                  (const int *)(L.gs_rows + L.gs_ptr[k]), (const int *)L.A.rowptr,
+                  (const int *)L.A.colidx, vals, minv, b, x);
+    else
+      AMG_KLAUNCH(c, gs_colour_kernel<K, V, T>, (n + 7) / 8, 256, n,
+                  (const int *)(L.gs_rows + L.gs_ptr[k]), (const int *)L.A.rowptr,
+                  (const int *)L.A.colidx, vals, minv, b, x);
   }
   return cudaGetLastError();
 }
