@@ -145,10 +145,12 @@ class ClockSampler:
                 "reasons": sorted(reasons), "samples": len(sm)}
 
 
-def algorithmic_bytes_per_iteration(levels, prec, nr=1):
+def algorithmic_bytes_per_iteration(levels, prec, nr=1, gs=False):
     """Bytes one PCG iteration must move at least once (matrices, smoother
     blocks, vectors), from the actual level sizes; with nr load cases solved
-    together the operators are read once and the vectors nr times."""
+    together the operators are read once and the vectors nr times.  gs: the
+    hybrid Gauss-Seidel V-cycle, whose pre-smoothing is a full sweep (A_l read
+    three times per level instead of twice)."""
     # matrix value bytes per level (BF16 coarse: FP32 on level 0, BF16 below)
     wl = lambda l: {0: 8, 1: 4, 2: 2, 3: 4 if l == 0 else 2}[prec]
     wv = 8 if prec == 0 else 4            # V-cycle vector / smoother bytes
@@ -172,8 +174,8 @@ def algorithmic_bytes_per_iteration(levels, prec, nr=1):
         Rb = L["nnzb_P"] * (k * kc * w + 4) + 4 * (levels[l + 1]["n_rows"] + 1)
         Mb = n * k * k * wv
         Nc = levels[l + 1]["n_rows"] * kc
-        mat += 2 * Mb + 2 * Ab + Rb + Pb
-        vec += 2 * N * wv + 3 * N * wv              # x = M b ; t = b - A x
+        mat += 2 * Mb + (3 if gs else 2) * Ab + Rb + Pb
+        vec += (3 if gs else 2) * N * wv + 3 * N * wv   # pre-smoothing ; t = b - A x
         vec += N * wv + Nc * wv + Nc * wv + 2 * N * wv   # restriction, prolongation
         vec += 3 * N * wv                           # y = x + M(b - A x)
     if prec:
@@ -310,8 +312,10 @@ def main():
     ap.add_argument("--pcg-mode", default="graph", choices=["graph", "host"],
                     help="graph: whole PCG in one CUDA graph (default); host: the same kernels "
                          "launched one by one (per-kernel view for profilers)")
-    ap.add_argument("--smoother", default="auto", choices=["auto", "l1", "learned"],
-                    help="level-0 smoother (auto: learned for cube96nu, block-l1 Jacobi otherwise)")
+    ap.add_argument("--smoother", default="auto", choices=["auto", "l1", "gs", "learned"],
+                    help="smoother of the timed solve: l1 block-l1 Jacobi, gs block-l1 hybrid "
+                         "Gauss-Seidel (colour classes), learned (level 0; cube96nu); auto: "
+                         "learned for cube96nu, block-l1 Jacobi otherwise")
     ap.add_argument("--train-epochs", type=int, default=40)
     ap.add_argument("--systems", type=int, default=64,
                     help="batch64: number of systems (the workload has 64)")
@@ -372,7 +376,8 @@ def run_single(args, ws, rank, local, train_problems):
     ctx.set_pcg_graph(args.pcg_mode == "graph")
     ctx.set_cg_operator(cg_mode)
     t0 = time.perf_counter()
-    ctx.setup(problem, args.precision, **setup_params(args.workload, problem))
+    main_sm = amg.AMG_SMOOTHER_HYBRID_GS if args.smoother == "gs" else amg.AMG_SMOOTHER_L1_JACOBI
+    ctx.setup(problem, args.precision, main_sm, **setup_params(args.workload, problem))
     torch.cuda.synchronize()
     setup_s = time.perf_counter() - t0
     setup_parts = {k: round(v, 2) for k, v in ctx.setup_times().items()}
@@ -425,7 +430,8 @@ def run_single(args, ws, rank, local, train_problems):
     true_rel = float(torch.linalg.norm(res) / torch.linalg.norm(f))
     P_list = [ctx.download_prolongation(l) for l in range(ctx.n_levels - 1)]
 
-    def upload(prec, cg, smoother=amg.AMG_SMOOTHER_L1_JACOBI):
+    def upload(prec, cg, smoother=None):
+        smoother = main_sm if smoother is None else smoother
         c2 = amg.Context(local, stream.cuda_stream)
         c2.set_pcg_graph(args.pcg_mode == "graph")
         c2.set_cg_operator(cg)
@@ -450,7 +456,7 @@ def run_single(args, ws, rank, local, train_problems):
                "true_relres": float(torch.linalg.norm(res) / torch.linalg.norm(f)),
                "ms_ratio_to_main": round(float(np.mean(tv)) / ms, 3)}
         if base is not None:
-            out["solve_gbs"] = round(algorithmic_bytes_per_iteration(levels, base) * float(np.mean(iv)) /
+            out["solve_gbs"] = round(algorithmic_bytes_per_iteration(levels, base, gs=(name == "hybrid_gs" or (name != "l1_jacobi" and args.smoother == "gs"))) * float(np.mean(iv)) /
                                      (float(np.mean(tv)) * 1e-3) / 1e9, 1)
         return out
 
@@ -468,11 +474,14 @@ def run_single(args, ws, rank, local, train_problems):
         c2 = upload(prec, cg_mode)
         variants[PREC_NAMES[prec]] = variant(c2, PREC_NAMES[prec], prec)
         c2.close()
-    # the other smoother of Sec. 7's block-l1 family: hybrid Gauss-Seidel
-    # (colour classes), same hierarchy, precision and CG operator
-    if args.smoother == "l1" and args.variants == "auto":
-        c2 = upload(args.precision, cg_mode, amg.AMG_SMOOTHER_HYBRID_GS)
-        variants["hybrid_gs"] = variant(c2, "hybrid_gs", args.precision)
+    # the other smoother of Sec. 7's block-l1 family (hybrid Gauss-Seidel with
+    # colour classes, or block-l1 Jacobi), same hierarchy, precision and CG
+    # operator
+    if args.smoother in ("l1", "gs") and args.variants == "auto":
+        other_sm = amg.AMG_SMOOTHER_L1_JACOBI if args.smoother == "gs" else amg.AMG_SMOOTHER_HYBRID_GS
+        name = "l1_jacobi" if args.smoother == "gs" else "hybrid_gs"
+        c2 = upload(args.precision, cg_mode, other_sm)
+        variants[name] = variant(c2, name, args.precision)
         c2.close()
     # the timed configuration with the other CG operator arithmetic
     main_df = "pcg_spmv_dot_sell_df_kernel" in ctx.describe()
@@ -543,7 +552,7 @@ def run_single(args, ws, rank, local, train_problems):
                 "fp32_fma_peak_tflops": round(fp32_gflops / 1e3, 1)}
 
     it_mean = float(np.mean(its))
-    per_it_bytes = algorithmic_bytes_per_iteration(levels, args.precision)
+    per_it_bytes = algorithmic_bytes_per_iteration(levels, args.precision, gs=args.smoother == "gs")
     solve_gbs = per_it_bytes * it_mean / (ms * 1e-3) / 1e9
     per_it, fixed = ctx.pcg_launches()
     launches = fixed + int(round(it_mean)) * per_it
@@ -598,6 +607,8 @@ def run_single(args, ws, rank, local, train_problems):
         kr.append({"level": lev, "step": step, "us": round(us_k, 2), "mbytes": round(by / 1e6, 2),
                    "gbs": round(gbs_k, 1), "frac_hbm": round(gbs_k / pk["hbm_gbs"], 3)})
     line["vcycle_kernels"] = kr
+    line["config"]["smoother"] = {"l1": "block-l1 Jacobi",
+                                  "gs": "block-l1 hybrid Gauss-Seidel (colour classes)"}.get(args.smoother)
     if learned_info is not None:
         line["config"]["smoother"] = "learned MLP (level 0), block-l1 Jacobi below"
         line["learned"] = learned_info
