@@ -45,7 +45,8 @@ void free_levels(Ctx *c) {
     free_bsr(L.P);
     free_bsr(L.R);
     void *ptrs[] = {L.minv64, L.minv32, L.b64, L.x64, L.t64, L.y64, L.b32, L.x32, L.t32, L.y32,
-                    L.gs_colour, L.gs_rows};
+                    L.gs_colour, L.gs_rows, L.gs_sell_ptr, L.gs_sell_col, L.gs_sell_perm,
+                    L.gs_sell_vals};
     for (void *p : ptrs) dfree(p);
   }
   c->levels.clear();
@@ -468,6 +469,11 @@ static int finalize_hierarchy(Ctx *c) {
       if (L.P.nnzb) CUDA_OR_FAIL(c, make_low_precision(c, L.P, precision), "low precision P");
       if (L.R.nnzb) CUDA_OR_FAIL(c, make_low_precision(c, L.R, precision), "low precision R");
     }
+    // hybrid Gauss-Seidel on a level 0 with a SELL-32 copy: A_0 again as
+    // SELL-32 slices in colour order, so a class's sweep is one thread per row
+    if (l == 0 && l + 1 < (int)c->levels.size() && c->smoother == AMG_SMOOTHER_HYBRID_GS &&
+        L.A.sell_ptr && L.k <= 3)
+      CUDA_OR_FAIL(c, gs_build_sell(c, l, precision), "colour-ordered sell layout");
   }
   CUDA_OR_FAIL(c, tune_operators(c), "kernel tuner");
   CUDA_OR_FAIL(c, coarse_setup(c), "coarse setup");

@@ -73,6 +73,14 @@ struct Level {
   int *gs_colour = nullptr;
   int *gs_rows = nullptr;
   std::vector<int> gs_ptr;
+  // level 0 with a SELL-32 copy: A's rows in colour order as SELL-32 slices
+  // (every class padded to whole slices; class k owns the slices
+  // gs_slice_ptr[k] .. gs_slice_ptr[k+1]), values in the level's storage
+  // precision, gs_sell_perm the row of every slice lane (n_rows on padding)
+  int *gs_sell_ptr = nullptr, *gs_sell_col = nullptr, *gs_sell_perm = nullptr;
+  void *gs_sell_vals = nullptr;
+  int gs_sell_prec = -1;
+  std::vector<int> gs_slice_ptr;
 };
 
 // Scalars of the device-resident PCG iteration.
@@ -190,6 +198,9 @@ cudaError_t smoother_setup(Ctx *c, int level);
 // hybrid Gauss-Seidel: colouring of level l (host greedy, uploaded), and one
 // sweep over the colour classes (forward or backward) updating x in place
 cudaError_t gs_prepare(Ctx *c, int level);
+// Colour-ordered SELL-32 copy of level `level`'s A for the Gauss-Seidel
+// sweeps (after the level's low-precision copies exist).
+cudaError_t gs_build_sell(Ctx *c, int level, int prec);
 cudaError_t launch_gs_sweep(const Ctx *c, const Level &L, int prec, const void *b, void *x,
                             bool forward);
 cudaError_t coarse_setup(Ctx *c);

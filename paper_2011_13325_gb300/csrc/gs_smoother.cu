@@ -11,6 +11,7 @@
 // runs the classes forward, the post-smoothing sweep backward, which keeps
 // the V-cycle symmetric.
 #include <algorithm>
+#include <type_traits>
 
 #include "amg_internal.h"
 #include "bsr_loads.cuh"
@@ -60,6 +61,172 @@ cudaError_t gs_prepare(Ctx *c, int level) {
   AMG_CUDA_TRY(cudaMemcpyAsync(L.gs_rows, rows.data(), (size_t)n * sizeof(int),
                                cudaMemcpyHostToDevice, c->stream));
   return cudaStreamSynchronize(c->stream);
+}
+
+// Gather of the colour-ordered SELL-32 values: entry (slot, element e, lane)
+// takes element e of block map[slot * 32 + lane] (0 where the map is -1).
+template <typename V>
+__global__ void gs_sell_gather_kernel(size_t n, int E, const int *__restrict__ map,
+                                      const V *__restrict__ src, V *__restrict__ dst) {
+  const size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  const size_t lane = i & 31, rest = i >> 5;
+  const size_t e = rest % (size_t)E, slot = rest / (size_t)E;
+  const int blk = map[slot * 32 + lane];
+  dst[i] = blk >= 0 ? src[(size_t)blk * E + e] : (V)0.0f;
+}
+
+cudaError_t gs_build_sell(Ctx *c, int level, int prec) {
+  Level &L = c->levels[level];
+  const DevBSR &A = L.A;
+  const int n = A.n_rows, E = A.br * A.bc, nc = (int)L.gs_ptr.size() - 1;
+  if (n == 0 || nc < 1) return cudaSuccess;
+  std::vector<int> rp(n + 1), rows(n);
+  AMG_CUDA_TRY(cudaMemcpyAsync(rp.data(), A.rowptr, (n + 1) * sizeof(int), cudaMemcpyDeviceToHost,
+                               c->stream));
+  AMG_CUDA_TRY(cudaMemcpyAsync(rows.data(), L.gs_rows, n * sizeof(int), cudaMemcpyDeviceToHost,
+                               c->stream));
+  std::vector<int> ci(A.nnzb > 0 ? A.nnzb : 1);
+  if (A.nnzb)
+    AMG_CUDA_TRY(cudaMemcpyAsync(ci.data(), A.colidx, A.nnzb * sizeof(int), cudaMemcpyDeviceToHost,
+                                 c->stream));
+  AMG_CUDA_TRY(cudaStreamSynchronize(c->stream));
+  // slices of 32 rows of one class, rows in the class's (ascending) order
+  std::vector<int> slice_ptr(nc + 1, 0), perm, sptr(1, 0);
+  for (int k = 0; k < nc; ++k) {
+    const int r0 = L.gs_ptr[k], r1 = L.gs_ptr[k + 1];
+    for (int q = r0; q < r1; q += 32) {
+      int w = 0;
+      for (int t = 0; t < 32; ++t) {
+        const int row = q + t < r1 ? rows[q + t] : n;
+        perm.push_back(row);
+        if (row < n) w = std::max(w, rp[row + 1] - rp[row]);
+      }
+      sptr.push_back(sptr.back() + w);
+    }
+    slice_ptr[k + 1] = (int)sptr.size() - 1;
+  }
+  const int ns = (int)sptr.size() - 1;
+  const size_t slots = (size_t)sptr.back();
+  std::vector<int> col(slots * 32 > 0 ? slots * 32 : 1, 0), map(slots * 32 > 0 ? slots * 32 : 1, -1);
+  for (int s = 0; s < ns; ++s)
+    for (int t = 0; t < 32; ++t) {
+      const int row = perm[(size_t)s * 32 + t];
+      if (row >= n) continue;
+      const int len = rp[row + 1] - rp[row];
+      for (int j = 0; j < len; ++j) {
+        const size_t at = ((size_t)sptr[s] + j) * 32 + t;
+        col[at] = ci[rp[row] + j];
+        map[at] = rp[row] + j;
+      }
+    }
+  // padding slots of a row point at its own first column (value 0)
+  for (int s = 0; s < ns; ++s)
+    for (int t = 0; t < 32; ++t) {
+      const int row = perm[(size_t)s * 32 + t];
+      const int len = row < n ? rp[row + 1] - rp[row] : 0;
+      const int c0 = row < n && len > 0 ? ci[rp[row]] : 0;
+      for (int j = len; j < sptr[s + 1] - sptr[s]; ++j) col[((size_t)sptr[s] + j) * 32 + t] = c0;
+    }
+  for (void *q : {(void *)L.gs_sell_ptr, (void *)L.gs_sell_col, (void *)L.gs_sell_perm, L.gs_sell_vals})
+    dfree(q);
+  L.gs_sell_ptr = L.gs_sell_col = L.gs_sell_perm = nullptr;
+  L.gs_sell_vals = nullptr;
+  L.gs_slice_ptr.clear();
+  int *d_map = nullptr;
+  const size_t wv = prec == AMG_PREC_FP64 ? 8 : prec == AMG_PREC_FP32_VCYCLE ? 4 : 2;
+  AMG_CUDA_TRY(dalloc((void **)&L.gs_sell_ptr, sptr.size() * sizeof(int)));
+  AMG_CUDA_TRY(dalloc((void **)&L.gs_sell_col, col.size() * sizeof(int)));
+  AMG_CUDA_TRY(dalloc((void **)&L.gs_sell_perm, perm.size() * sizeof(int)));
+  AMG_CUDA_TRY(dalloc((void **)&d_map, map.size() * sizeof(int)));
+  AMG_CUDA_TRY(dalloc(&L.gs_sell_vals, (slots > 0 ? slots : 1) * 32 * E * wv));
+  AMG_CUDA_TRY(cudaMemcpyAsync(L.gs_sell_ptr, sptr.data(), sptr.size() * sizeof(int),
+                               cudaMemcpyHostToDevice, c->stream));
+  AMG_CUDA_TRY(cudaMemcpyAsync(L.gs_sell_col, col.data(), col.size() * sizeof(int),
+                               cudaMemcpyHostToDevice, c->stream));
+  AMG_CUDA_TRY(cudaMemcpyAsync(L.gs_sell_perm, perm.data(), perm.size() * sizeof(int),
+                               cudaMemcpyHostToDevice, c->stream));
+  AMG_CUDA_TRY(cudaMemcpyAsync(d_map, map.data(), map.size() * sizeof(int), cudaMemcpyHostToDevice,
+                               c->stream));
+  const size_t total = slots * 32 * (size_t)E;
+  if (total) {
+    const unsigned g = (unsigned)((total + 255) / 256);
+    if (prec == AMG_PREC_FP64)
+      gs_sell_gather_kernel<double><<<g, 256, 0, c->stream>>>(total, E, d_map, A.v64, (double *)L.gs_sell_vals);
+    else if (prec == AMG_PREC_FP32_VCYCLE)
+      gs_sell_gather_kernel<float><<<g, 256, 0, c->stream>>>(total, E, d_map, A.v32, (float *)L.gs_sell_vals);
+    else
+      gs_sell_gather_kernel<__nv_bfloat16><<<g, 256, 0, c->stream>>>(total, E, d_map, A.v16,
+                                                                      (__nv_bfloat16 *)L.gs_sell_vals);
+    AMG_CUDA_TRY(cudaGetLastError());
+  }
+  AMG_CUDA_TRY(cudaStreamSynchronize(c->stream));
+  dfree(d_map);
+  L.gs_slice_ptr = slice_ptr;
+  L.gs_sell_prec = prec;
+  return cudaSuccess;
+}
+
+// One colour class from the colour-ordered SELL-32 copy: thread per row
+// (slice lane), the row's blocks four slots at a time (column indices, then
+// their x gathers, then the values), x in place as in the warp kernels.
+template <int K, typename V, typename T>
+__global__ void __launch_bounds__(64) gs_sell_kernel(int n_rows, int s0, int s1,
+                                                     const int *__restrict__ sell_ptr,
+                                                     const int *__restrict__ sell_col,
+                                                     const int *__restrict__ perm,
+                                                     const V *__restrict__ vals,
+                                                     const T *__restrict__ minv,
+                                                     const T *__restrict__ b, T *x) {
+  pdl_enter();
+  constexpr int E = K * K;
+  const int slice = s0 + ((blockIdx.x * blockDim.x + threadIdx.x) >> 5);
+  if (slice >= s1) return;  // whole warp
+  const int t = threadIdx.x & 31;
+  const int row = __ldg(perm + slice * 32 + t);
+  const int j0 = __ldg(sell_ptr + slice), j1 = __ldg(sell_ptr + slice + 1);
+  T acc[K];
+#pragma unroll
+  for (int r = 0; r < K; ++r) acc[r] = 0;
+  constexpr int U = 4;
+  for (int j = j0; j < j1; j += U) {
+    int cc[U];
+#pragma unroll
+    for (int u = 0; u < U; ++u) cc[u] = (j + u < j1) ? __ldg(sell_col + (size_t)(j + u) * 32 + t) : 0;
+    T xv[U][K];
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+      if (j + u < j1) {
+        ldn_cached<K>(x + (size_t)cc[u] * K, xv[u]);
+      } else {
+#pragma unroll
+        for (int q = 0; q < K; ++q) xv[u][q] = 0;
+      }
+    }
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+      if (j + u < j1) {
+        const V *v = vals + (size_t)(j + u) * E * 32 + t;
+#pragma unroll
+        for (int r = 0; r < K; ++r)
+#pragma unroll
+          for (int q = 0; q < K; ++q) acc[r] += (T)lds(v + (r * K + q) * 32) * xv[u][q];
+      }
+    }
+  }
+  if (row >= n_rows) return;
+  const size_t o = (size_t)row * K;
+  T res[K], upd[K];
+#pragma unroll
+  for (int r = 0; r < K; ++r) res[r] = b[o + r] - acc[r];
+#pragma unroll
+  for (int r = 0; r < K; ++r) {
+    upd[r] = 0;
+#pragma unroll
+    for (int q = 0; q < K; ++q) upd[r] += minv[(o + r) * K + q] * res[q];
+  }
+#pragma unroll
+  for (int r = 0; r < K; ++r) x[o + r] += upd[r];
 }
 
 // One colour class: warp w updates block row rows[w] (lanes = block slot x
@@ -173,6 +340,22 @@ template <int K, typename V, typename T>
 static cudaError_t gs_sweep_k(const Ctx *c, const Level &L, const V *vals, const T *minv, const T *b,
                               T *x, bool forward) {
   const int nc = (int)L.gs_ptr.size() - 1;
+  if constexpr (K <= 3) {
+    // the colour-ordered SELL-32 copy, where the level has one in this precision
+    const int want = std::is_same<V, double>::value ? AMG_PREC_FP64
+                     : std::is_same<V, float>::value ? AMG_PREC_FP32_VCYCLE : AMG_PREC_BF16_STORAGE;
+    if (L.gs_sell_vals && L.gs_sell_prec == want) {
+      for (int s = 0; s < nc; ++s) {
+        const int k = forward ? s : nc - 1 - s;
+        const int s0 = L.gs_slice_ptr[k], s1 = L.gs_slice_ptr[k + 1];
+        if (s1 == s0) continue;
+        AMG_KLAUNCH(c, gs_sell_kernel<K, V, T>, (s1 - s0 + 1) / 2, 64, L.A.n_rows, s0, s1,
+                    (const int *)L.gs_sell_ptr, (const int *)L.gs_sell_col,
+                    (const int *)L.gs_sell_perm, (const V *)L.gs_sell_vals, minv, b, x);
+      }
+      return cudaGetLastError();
+    }
+  }
   for (int s = 0; s < nc; ++s) {
     const int k = forward ? s : nc - 1 - s;
     const int n = L.gs_ptr[k + 1] - L.gs_ptr[k];
