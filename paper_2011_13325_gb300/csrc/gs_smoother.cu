@@ -340,26 +340,28 @@ template <int K, typename V, typename T>
 static cudaError_t gs_sweep_k(const Ctx *c, const Level &L, const V *vals, const T *minv, const T *b,
                               T *x, bool forward) {
   const int nc = (int)L.gs_ptr.size() - 1;
+  // the colour-ordered SELL-32 copy (thread per row), where the level has one
+  // in this precision, for the classes with rows enough to fill the GPU
+  // with thread-per-row warps (16 per SM; every class under
+  // AMG_LAYOUT_SELL_SHORT_ROWS); smaller classes run a warp per row
+  bool sell = false;
   if constexpr (K <= 3) {
-    // the colour-ordered SELL-32 copy, where the level has one in this precision
     const int want = std::is_same<V, double>::value ? AMG_PREC_FP64
                      : std::is_same<V, float>::value ? AMG_PREC_FP32_VCYCLE : AMG_PREC_BF16_STORAGE;
-    if (L.gs_sell_vals && L.gs_sell_prec == want) {
-      for (int s = 0; s < nc; ++s) {
-        const int k = forward ? s : nc - 1 - s;
-        const int s0 = L.gs_slice_ptr[k], s1 = L.gs_slice_ptr[k + 1];
-        if (s1 == s0) continue;
-        AMG_KLAUNCH(c, gs_sell_kernel<K, V, T>, (s1 - s0 + 1) / 2, 64, L.A.n_rows, s0, s1,
-                    (const int *)L.gs_sell_ptr, (const int *)L.gs_sell_col,
-                    (const int *)L.gs_sell_perm, (const V *)L.gs_sell_vals, minv, b, x);
-      }
-      return cudaGetLastError();
-    }
+    sell = L.gs_sell_vals && L.gs_sell_prec == want;
   }
+  const int sell_min_rows = c->layout_policy == AMG_LAYOUT_SELL_SHORT_ROWS ? 0 : 32 * 16 * c->num_sms;
   for (int s = 0; s < nc; ++s) {
     const int k = forward ? s : nc - 1 - s;
     const int n = L.gs_ptr[k + 1] - L.gs_ptr[k];
     if (n == 0) continue;
+    if (sell && n >= sell_min_rows) {
+      const int s0 = L.gs_slice_ptr[k], s1 = L.gs_slice_ptr[k + 1];
+      AMG_KLAUNCH(c, gs_sell_kernel<K, V, T>, (s1 - s0 + 1) / 2, 64, L.A.n_rows, s0, s1,
+                  (const int *)L.gs_sell_ptr, (const int *)L.gs_sell_col, (const int *)L.gs_sell_perm,
+                  (const V *)L.gs_sell_vals, minv, b, x);
+      continue;
+    }
     if constexpr (K == 6)
       AMG_KLAUNCH(c, gs_block_kernel<K, V, T>, (n + 7) / 8, 256, n,
                   (const int *)(L.gs_rows + L.gs_ptr[k]), (const int *)L.A.rowptr,
