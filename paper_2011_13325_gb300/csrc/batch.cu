@@ -36,7 +36,6 @@ struct Stage {
   // products
   SpmmKey key{};
   int lpr = 32, wpb = 8;
-  int wps = 1;  // SELL-32 form: warps per slice (the double-float product with six load cases: 2)
   std::vector<SpmmOp> ops;
   // block diagonal
   int k = 0, dkind = 0;
@@ -108,7 +107,7 @@ static void build_spmm_items(Stage &S) {
     it.svals = o.svals;
     it.n_slices = o.A->n_slices;
     it.df_exp = o.A->df_exp;
-    first += S.lpr ? cdiv(o.A->n_rows, rpb) : cdiv((long)o.A->n_slices * S.wps, S.wpb);
+    first += S.lpr ? cdiv(o.A->n_rows, rpb) : cdiv(o.A->n_slices, S.wpb);
     S.sp.push_back(it);
   }
   S.n_items = (int)S.sp.size();
@@ -327,14 +326,8 @@ static void build_stages(Batch *B) {
       else
         ops.push_back(SpmmOp{&A, A.v64, B->gsh[s].p, nullptr, nullptr, B->gsh[s].q, s, svals_of(A, 0)});
     }
-    if (B->df) {
-      const size_t first = B->body.size();
+    if (B->df)
       add_spmm(B->body, "q = A_0 p (double-float)", ops, SPMV_SET, 3, 0);
-      for (size_t i = first; i < B->body.size(); ++i) {
-        B->body[i].wps = B->nr == 6 ? 2 : 1;
-        build_spmm_items(B->body[i]);
-      }
-    }
     else
       add_spmm(B->body, "q = A_0 p", ops, SPMV_SET, 0, 0);
   }

@@ -221,20 +221,15 @@ __global__ void __launch_bounds__(128) gsell_kernel(const SpmmItem *__restrict__
 // scaled by 2^-df_exp, p as pairs (written by the p update), every product
 // exact by two-product, summed by two-sum, the low parts of each block on
 // their own and two-summed into the row's low word (as the single-system
-// kernel); q in FP64.  With six load cases two warps share a slice, three
-// load cases each (the second reads the slice's values and indices from L1):
-// all six in one thread take 128 registers and leave 16 warps per SM.
-template <int BR, int NRT>
+// kernel); q in FP64.
+template <int BR, int NR>
 __global__ void __launch_bounds__(128) gsell_df_kernel(const SpmmItem *__restrict__ items, int n_items,
                                                        const McgState *__restrict__ st) {
   constexpr int E = BR * BR;
-  constexpr int G = NRT == 6 ? 2 : 1;  // warps per slice
-  constexpr int NR = NRT / G;          // load cases of one thread
   const int ii = find_item(items, n_items, blockIdx.x);
   const SpmmItem &I = items[ii];
   if (!st[I.sys].active) return;
-  const int gw = (blockIdx.x - I.first_block) * (blockDim.x >> 5) + (threadIdx.x >> 5);
-  const int slice = gw / G, j_off = (gw - slice * G) * NR;
+  const int slice = (blockIdx.x - I.first_block) * (blockDim.x >> 5) + (threadIdx.x >> 5);
   if (slice >= I.n_slices) return;  // whole warp
   const int t = threadIdx.x & 31;
   const int row = slice * 32 + t;
@@ -249,7 +244,7 @@ __global__ void __launch_bounds__(128) gsell_df_kernel(const SpmmItem *__restric
   for (int j = j0; j < j1; ++j) {
     const int c = __ldg(I.sell_col + (size_t)j * 32 + t);
     const float2 *v = sv + (size_t)j * E * 32 + t;
-    const float2 *xp = x + (size_t)c * BR * NRT + j_off;
+    const float2 *xp = x + (size_t)c * BR * NR;
     float lt[BR][NR];
 #pragma unroll
     for (int r = 0; r < BR; ++r)
@@ -259,7 +254,7 @@ __global__ void __launch_bounds__(128) gsell_df_kernel(const SpmmItem *__restric
     for (int q = 0; q < BR; ++q) {
       float2 xv[NR];
 #pragma unroll
-      for (int jj = 0; jj < NR; ++jj) xv[jj] = __ldg(xp + q * NRT + jj);
+      for (int jj = 0; jj < NR; ++jj) xv[jj] = __ldg(xp + q * NR + jj);
 #pragma unroll
       for (int r = 0; r < BR; ++r) {
         const float2 a = __ldcs(v + (r * BR + q) * 32);
@@ -279,7 +274,7 @@ __global__ void __launch_bounds__(128) gsell_df_kernel(const SpmmItem *__restric
   for (int r = 0; r < BR; ++r)
 #pragma unroll
     for (int jj = 0; jj < NR; ++jj)
-      y[(o + r) * NRT + j_off + jj] = float_to_double_scaled(hi[r][jj], I.df_exp) +
+      y[(o + r) * NR + jj] = float_to_double_scaled(hi[r][jj], I.df_exp) +
                              (float_to_double_scaled(lo[r][jj], I.df_exp) +
                               float_to_double_scaled(lo2[r][jj], I.df_exp));
 }
