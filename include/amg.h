@@ -254,8 +254,8 @@ int amg_pcg_solve_host(amg_ctx *ctx, const double *f_host, double *u_host, int n
  *  - The first call on a device is its set-up: it looks up the array's
  *    device address with that device current.  Under lazy module loading
  *    (the CUDA default) this also loads the array's module, and the driver
- *    reserves its 16 MiB at that moment.  Make that first call before any
- *    stream capture and while 16 MiB are free; later calls allocate nothing.
+ *    reserves its 16 MiB at that moment.  Make that first call while
+ *    16 MiB are free; later calls allocate nothing.
  *  - The call returns after synchronising the context's stream.
  *  - Every GPU that loads the library holds the array until the process
  *    exits.  All calls on a device share it and it keeps the last call's
