@@ -12,8 +12,7 @@
 // address (cudaGetSymbolAddress, with that device current).  With lazy module
 // loading (the CUDA default) that lookup also loads this file's device module,
 // and the driver reserves the array's 16 MiB then.  Make that first call
-// before any stream capture and while 16 MiB are free; every later call on
-// the device allocates nothing.
+// while 16 MiB are free; every later call on the device allocates nothing.
 #include <mutex>
 
 #include "amg_internal.h"
