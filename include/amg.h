@@ -101,7 +101,9 @@ enum {
  *  AMG_SMOOTHER_HYBRID_GS  block-l1 hybrid Gauss-Seidel, the other form of the
  *                          l1 smoothers Sec. 7 cites, read for one device:
  *                          the block rows of every level are coloured at
- *                          upload (greedy, rows in index order, each the
+ *                          upload (greedy in smallest-last order: rows
+ *                          removed by least remaining degree, ties by the
+ *                          smallest index, coloured in reverse, each the
  *                          smallest colour no already coloured neighbour
  *                          holds: a distance-1 colouring) and a sweep visits
  *                          the colour classes in order, every row of a class

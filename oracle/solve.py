@@ -130,13 +130,38 @@ def block_l1_inverse(A: Mat):
     return batched_pinv(Mv, KERNEL_RTOL)
 
 
+def smallest_last_order(A: Mat):
+    """Smallest-last order of the block graph of A (Matula and Beck):
+    repeatedly remove a remaining block row of least degree among the
+    remaining rows (ties: the smallest index); the order is the reverse of
+    the removals."""
+    import heapq
+    n = A.n_rows
+    deg = [int(np.sum(A.colidx[A.rowptr[i]:A.rowptr[i + 1]] != i)) for i in range(n)]
+    heap = [(deg[i], i) for i in range(n)]
+    heapq.heapify(heap)
+    removed = [False] * n
+    out = []
+    while heap:
+        d, i = heapq.heappop(heap)
+        if removed[i] or d != deg[i]:
+            continue
+        removed[i] = True
+        out.append(i)
+        for j in A.colidx[A.rowptr[i]:A.rowptr[i + 1]].tolist():
+            if j != i and not removed[j]:
+                deg[j] -= 1
+                heapq.heappush(heap, (deg[j], j))
+    return out[::-1]
+
+
 def greedy_colouring(A: Mat):
-    """Distance-1 colouring of the block graph of A: block rows in index
-    order, each takes the smallest colour that none of its already coloured
-    neighbours holds.  Rows of one colour never couple."""
+    """Distance-1 colouring of the block graph of A: block rows in
+    smallest-last order, each takes the smallest colour that none of its
+    already coloured neighbours holds.  Rows of one colour never couple."""
     n = A.n_rows
     col = -np.ones(n, dtype=np.int64)
-    for i in range(n):
+    for i in smallest_last_order(A):
         nb = A.colidx[A.rowptr[i]:A.rowptr[i + 1]]
         used = set(col[nb].tolist())
         c = 0

@@ -27,6 +27,30 @@ def test_colouring_is_distance_one_and_greedy_bounded():
         assert set(np.unique(col).tolist()) == set(range(int(col.max()) + 1))
 
 
+def _path_in_bad_order():
+    """The path a - b - c - d stored as rows a = 0, d = 1, b = 2, c = 3 (1x1
+    blocks): in index order the greedy colouring takes a = 0, d = 0, b = 1
+    and c, next to b = 1 and d = 0, needs a third colour."""
+    edges = {0: [2], 1: [3], 2: [0, 3], 3: [1, 2]}
+    rowptr, colidx = [0], []
+    for i in range(4):
+        colidx.extend(sorted(edges[i] + [i]))
+        rowptr.append(len(colidx))
+    return solve.Mat(n_rows=4, n_cols=4, rowptr=np.array(rowptr), colidx=np.array(colidx),
+                     vals=np.ones((len(colidx), 1, 1)))
+
+
+def test_colouring_follows_smallest_last_order_by_hand():
+    """Smallest-last on the path above, derived by hand: degrees a 1, d 1,
+    b 2, c 2; remove a (least degree, smallest index), then d (b and d have
+    degree 1, d has the smaller index), then b, then c.  The order is the
+    reverse, c, b, d, a; greedy: c = 0, b = 1, d = 1, a = 0 -- two colours
+    where the index order needs three."""
+    A = _path_in_bad_order()
+    assert solve.smallest_last_order(A) == [3, 2, 1, 0]
+    assert solve.greedy_colouring(A).tolist() == [0, 1, 1, 0]
+
+
 def test_sweep_equals_block_triangular_splitting():
     """A forward sweep is x + (L + D)^{-1}(b - A x) with the matrix ordered by
     colour (classes in order, rows by index inside a class), L its strictly

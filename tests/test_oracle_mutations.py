@@ -193,6 +193,41 @@ def test_gauss_seidel_with_stale_values(monkeypatch):
     _fails(tg.test_sweep_equals_block_triangular_splitting)
 
 
+def test_colouring_in_index_order(monkeypatch):
+    """Rows coloured in index order instead of smallest-last order fail the
+    hand-derived colouring pin."""
+    from tests import test_oracle_gs as tg
+    monkeypatch.setattr(S, "smallest_last_order", lambda A: list(range(A.n_rows)))
+    _fails(tg.test_colouring_follows_smallest_last_order_by_hand)
+
+
+def test_smallest_last_without_tie_break_by_index(monkeypatch):
+    """Ties of least degree broken by the largest index fail the pin too."""
+    from tests import test_oracle_gs as tg
+    import heapq
+
+    def largest_index_first(A):
+        n = A.n_rows
+        deg = [int(np.sum(A.colidx[A.rowptr[i]:A.rowptr[i + 1]] != i)) for i in range(n)]
+        heap = [(deg[i], -i) for i in range(n)]
+        heapq.heapify(heap)
+        removed, out = [False] * n, []
+        while heap:
+            d, mi = heapq.heappop(heap)
+            i = -mi
+            if removed[i] or d != deg[i]:
+                continue
+            removed[i] = True
+            out.append(i)
+            for j in A.colidx[A.rowptr[i]:A.rowptr[i + 1]].tolist():
+                if j != i and not removed[j]:
+                    deg[j] -= 1
+                    heapq.heappush(heap, (deg[j], -j))
+        return out[::-1]
+    monkeypatch.setattr(S, "smallest_last_order", largest_index_first)
+    _fails(tg.test_colouring_follows_smallest_last_order_by_hand)
+
+
 def test_scalar_edge_weights_with_sign(monkeypatch):
     """E^{ij} = A_ij instead of |A_ij| (negative weights) fails the exact
     M-matrix splitting pin."""
