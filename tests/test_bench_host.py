@@ -69,6 +69,20 @@ def test_algorithmic_bytes_count():
             assert bench.algorithmic_bytes_per_iteration(lv, prec, nr) == mat + nr * vec
 
 
+def test_algorithmic_bytes_gauss_seidel_reads_each_operator_once_more():
+    """The hybrid Gauss-Seidel V-cycle's pre-smoothing is a full sweep: A_l
+    of every level but the coarsest is read once more than in the Jacobi
+    V-cycle (whose pre-smoothing only applies M^+), plus the sweep's x."""
+    lv = [dict(n_rows=10, block=3, nnzb=40, nnzb_P=12), dict(n_rows=4, block=6, nnzb=10, nnzb_P=3),
+          dict(n_rows=1, block=6, nnzb=1, nnzb_P=0)]
+    for prec, w, wv in ((0, 8, 8), (1, 4, 4)):
+        jac = bench.algorithmic_bytes_per_iteration(lv, prec)
+        gs = bench.algorithmic_bytes_per_iteration(lv, prec, gs=True)
+        A0 = 40 * (9 * w + 4) + 4 * 11
+        A1 = 10 * (36 * w + 4) + 4 * 5
+        assert gs - jac == A0 + A1 + 30 * wv + 24 * wv
+
+
 def test_algorithmic_bytes_bf16_below_level_0():
     """BF16 storage below level 0: level 0's A, P, R count 4 bytes per value,
     level 1's A, P, R 2 bytes; vectors as in the FP32 V-cycle."""
