@@ -108,9 +108,12 @@ enum {
  *                          holds: a distance-1 colouring) and a sweep visits
  *                          the colour classes in order, every row of a class
  *                          x_v <- x_v + M_v^+ (b - A x)_v with the values of
- *                          the classes before (one kernel per class); M_v =
- *                          A_vv + diag of the |entries| coupling v to rows of
- *                          its own class (none for a distance-1 colouring).
+ *                          the classes before (one launch per class; a level
+ *                          0 with a SELL-32 copy also keeps one in colour
+ *                          order and sweeps its large classes from it, one
+ *                          thread per row); M_v = A_vv + diag of the
+ *                          |entries| coupling v to rows of its own class
+ *                          (none for a distance-1 colouring).
  *                          Forward sweep before the coarse correction,
  *                          backward sweep after it (the V-cycle stays
  *                          symmetric).  Not available to amg_batch_create,
