@@ -11,7 +11,6 @@
 // runs the classes forward, the post-smoothing sweep backward, which keeps
 // the V-cycle symmetric.
 #include <algorithm>
-#include <queue>
 #include <type_traits>
 
 #include "amg_internal.h"
@@ -36,46 +35,8 @@ cudaError_t gs_prepare(Ctx *c, int level) {
     AMG_CUDA_TRY(cudaMemcpyAsync(ci.data(), L.A.colidx, L.A.nnzb * sizeof(int),
                                  cudaMemcpyDeviceToHost, c->stream));
   AMG_CUDA_TRY(cudaStreamSynchronize(c->stream));
-  // smallest-last order: a heap of (degree, row) with stale entries skipped
-  std::vector<int> deg(n, 0), order;
-  order.reserve(n);
-  for (int i = 0; i < n; ++i)
-    for (int p = rp[i]; p < rp[i + 1]; ++p) deg[i] += ci[p] != i;
-  {
-    std::priority_queue<std::pair<int, int>, std::vector<std::pair<int, int>>,
-                        std::greater<std::pair<int, int>>> heap;
-    for (int i = 0; i < n; ++i) heap.push({deg[i], i});
-    std::vector<char> removed(n, 0);
-    while (!heap.empty()) {
-      const auto top = heap.top();
-      heap.pop();
-      const int i = top.second;
-      if (removed[i] || top.first != deg[i]) continue;
-      removed[i] = 1;
-      order.push_back(i);
-      for (int p = rp[i]; p < rp[i + 1]; ++p) {
-        const int j = ci[p];
-        if (j != i && !removed[j]) heap.push({--deg[j], j});
-      }
-    }
-    std::reverse(order.begin(), order.end());
-  }
-  std::vector<int> colour(n, -1), mark;
   int n_col = 0;
-  for (int i : order) {
-    // colours held by the already coloured neighbours of row i
-    for (int p = rp[i]; p < rp[i + 1]; ++p) {
-      const int cc = colour[ci[p]];
-      if (cc >= 0) {
-        if (cc >= (int)mark.size()) mark.resize(cc + 1, -1);
-        mark[cc] = i;
-      }
-    }
-    int cc = 0;
-    while (cc < (int)mark.size() && mark[cc] == i) ++cc;
-    colour[i] = cc;
-    n_col = std::max(n_col, cc + 1);
-  }
+  const std::vector<int> colour = amgsetup::smallest_last_colouring(n, rp.data(), ci.data(), &n_col);
   L.gs_ptr.assign(n_col + 1, 0);
   for (int i = 0; i < n; ++i) ++L.gs_ptr[colour[i] + 1];
   for (int k = 0; k < n_col; ++k) L.gs_ptr[k + 1] += L.gs_ptr[k];

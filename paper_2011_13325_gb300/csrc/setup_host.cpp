@@ -18,6 +18,7 @@
 #include <stdlib.h>
 
 #include <algorithm>
+#include <queue>
 #include <array>
 #include <chrono>
 #include <unordered_map>
@@ -1284,6 +1285,52 @@ int build_levels(const Problem &prob, const SetupParams &prm, LevelSink &sink, s
     ++level;
   }
   return 0;
+}
+
+std::vector<int> smallest_last_colouring(int n, const int *rp, const int *ci, int *n_colours) {
+  // smallest-last order: a heap of (degree, row) with stale entries skipped
+  std::vector<int> deg(n, 0), order;
+  order.reserve(n);
+  for (int i = 0; i < n; ++i)
+    for (int p = rp[i]; p < rp[i + 1]; ++p) deg[i] += ci[p] != i;
+  {
+    std::priority_queue<std::pair<int, int>, std::vector<std::pair<int, int>>,
+                        std::greater<std::pair<int, int>>>
+        heap;
+    for (int i = 0; i < n; ++i) heap.push({deg[i], i});
+    std::vector<char> removed(n, 0);
+    while (!heap.empty()) {
+      const auto top = heap.top();
+      heap.pop();
+      const int i = top.second;
+      if (removed[i] || top.first != deg[i]) continue;
+      removed[i] = 1;
+      order.push_back(i);
+      for (int p = rp[i]; p < rp[i + 1]; ++p) {
+        const int j = ci[p];
+        if (j != i && !removed[j]) heap.push({--deg[j], j});
+      }
+    }
+    std::reverse(order.begin(), order.end());
+  }
+  std::vector<int> colour(n, -1), mark;
+  int nc = 0;
+  for (int i : order) {
+    // colours held by the already coloured neighbours of row i
+    for (int p = rp[i]; p < rp[i + 1]; ++p) {
+      const int cc = colour[ci[p]];
+      if (cc >= 0) {
+        if (cc >= (int)mark.size()) mark.resize(cc + 1, -1);
+        mark[cc] = i;
+      }
+    }
+    int cc = 0;
+    while (cc < (int)mark.size() && mark[cc] == i) ++cc;
+    colour[i] = cc;
+    nc = std::max(nc, cc + 1);
+  }
+  if (n_colours) *n_colours = nc;
+  return colour;
 }
 
 }  // namespace amgsetup

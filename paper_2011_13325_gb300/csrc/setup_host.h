@@ -100,4 +100,12 @@ Topo finest_topology_scalar(int dim, int n, const double *coords, const uint8_t 
 
 int build_levels(const Problem &prob, const SetupParams &prm, LevelSink &sink, std::string &err);
 
+// Distance-1 colouring of the block graph of a matrix pattern (CSR, n rows)
+// for the hybrid Gauss-Seidel smoother: greedy in smallest-last order
+// (repeatedly remove a remaining row of least degree, ties by the smallest
+// index; colour in the reverse of the removals, each row the smallest
+// colour no already coloured neighbour holds).  Returns the colour of every
+// row; *n_colours the number of colours.
+std::vector<int> smallest_last_colouring(int n, const int *rowptr, const int *colidx, int *n_colours);
+
 }  // namespace amgsetup

@@ -10,6 +10,11 @@
 //   float64 vals (nnzb x dim x dim)
 //   writes <dir>/P.bin: int32 n_levels-1; per level int32 n_rows, n_cols,
 //   br, bc, nnzb, rowptr, colidx; float64 vals
+//
+// usage: host_setup_harness --colour <dir>
+//   runs amgsetup::smallest_last_colouring (the hybrid Gauss-Seidel
+//   smoother's colouring) on <dir>/pattern.bin: int32 n, nnz, rowptr
+//   (n+1), colidx (nnz); writes <dir>/colour.bin: int32 n_colours, colour (n)
 #include <stdint.h>
 #include <stdio.h>
 #include <stdlib.h>
@@ -85,7 +90,27 @@ struct HostGalerkinSink : LevelSink {
   }
 };
 
+static int colour_main(const std::string &dir) {
+  FILE *f = fopen((dir + "/pattern.bin").c_str(), "rb");
+  if (!f) return 3;
+  int32_t hdr[2];
+  if (fread(hdr, 4, 2, f) != 2) return 3;
+  std::vector<int32_t> rowptr, colidx;
+  if (!get(f, rowptr, (size_t)hdr[0] + 1) || !get(f, colidx, hdr[1])) return 3;
+  fclose(f);
+  int nc = 0;
+  const std::vector<int> colour = smallest_last_colouring(hdr[0], rowptr.data(), colidx.data(), &nc);
+  FILE *o = fopen((dir + "/colour.bin").c_str(), "wb");
+  if (!o) return 3;
+  const int32_t n_col = nc;
+  fwrite(&n_col, 4, 1, o);
+  fwrite(colour.data(), 4, colour.size(), o);
+  fclose(o);
+  return 0;
+}
+
 int main(int argc, char **argv) {
+  if (argc == 3 && std::string(argv[1]) == "--colour") return colour_main(argv[2]);
   if (argc < 3) {
     fprintf(stderr, "usage: %s <dir> <coarse_max> [passes_first passes_later]\n", argv[0]);
     return 2;

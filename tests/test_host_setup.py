@@ -129,3 +129,31 @@ def test_host_setup_matches_oracle_setup(harness, tmp_path, name, threads):
     _, it_lib, _ = solve.pcg(Hl, f, rtol=1e-8)
     _, it_or, _ = solve.pcg(H, f, rtol=1e-8)
     assert abs(it_lib - it_or) <= 1
+
+
+def _colour_with_library(harness, d, A):
+    with open(os.path.join(d, "pattern.bin"), "wb") as f:
+        np.array([A.n_rows, A.colidx.shape[0]], dtype=np.int32).tofile(f)
+        np.ascontiguousarray(A.rowptr, dtype=np.int32).tofile(f)
+        np.ascontiguousarray(A.colidx, dtype=np.int32).tofile(f)
+    r = subprocess.run([harness, "--colour", d], capture_output=True, text=True, timeout=120)
+    assert r.returncode == 0, r.stderr
+    raw = np.fromfile(os.path.join(d, "colour.bin"), dtype=np.int32)
+    assert raw.shape[0] == A.n_rows + 1
+    return int(raw[0]), raw[1:].astype(np.int64)
+
+
+@pytest.mark.parametrize("name", ["cube10", "box_jump", "checker2d", "jump11", "poisson3d"])
+def test_gs_colouring_matches_oracle_colouring(harness, tmp_path, name):
+    """The hybrid Gauss-Seidel smoother's colouring in the library
+    (smallest-last greedy order, ties by the smallest index) equals the
+    oracle's on every level of the oracle's hierarchy, colour by colour, and
+    is a distance-1 colouring: no two rows of one colour couple."""
+    _, _, H = _oracle(name)
+    for l, A in enumerate(H.A):
+        n_col, col = _colour_with_library(harness, str(tmp_path), A)
+        np.testing.assert_array_equal(col, solve.greedy_colouring(A), err_msg=f"level {l}")
+        assert n_col == int(col.max()) + 1
+        rows = np.repeat(np.arange(A.n_rows), np.diff(A.rowptr))
+        off = A.colidx != rows
+        assert not np.any(col[rows[off]] == col[A.colidx[off]]), l
