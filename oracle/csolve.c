@@ -14,11 +14,18 @@
  *  - block products y = M x, the residual b - A x, the block-l1 Jacobi sweep
  *    x + M^+ (b - A x) with the blocks M^+ supplied (Sec. 7), restriction
  *    R r and prolongation x + P e (Algorithm tg);
+ *  - the block-l1 hybrid Gauss-Seidel sweep (the hybrid member of Sec. 7's
+ *    block-l1 smoother family, one processor block per colour class): the
+ *    colour classes in increasing (forward) or decreasing (backward) order,
+ *    the rows of a class take x_v + M_v^+ (b - A x)_v with x as the classes
+ *    before left it, Jacobi-wise inside the class; classes and M_v^+
+ *    supplied;
  *  - the coarsest solve with a supplied lower Cholesky factor L of
  *    A_L + (I - E_L E_L^T) (Sec. 3 after Lemma eet_is_diag): L L^T x = b;
  *  - the V-cycle (Algorithm tg applied recursively, one pre- and one post-
- *    sweep from x = 0) and CG preconditioned by it (Sec. 7), stopping when
- *    ||r|| <= rtol ||f|| (recurrence residual).
+ *    sweep from x = 0; with Gauss-Seidel a forward sweep before the coarse
+ *    correction and a backward one after it) and CG preconditioned by it
+ *    (Sec. 7), stopping when ||r|| <= rtol ||f|| (recurrence residual).
  *
  * Matrices are BSR: rowptr (int64, n_rows+1), colidx (int32), values
  * row-major br x bc per block.  Vectors are interleaved per block row.
@@ -230,6 +237,42 @@ static void smooth(const oc_bsr *A, const double *Minv, const double *b, const d
   }
 }
 
+/* One block-l1 hybrid Gauss-Seidel sweep on x (in place): class c holds
+ * the rows rows[ptr[c] .. ptr[c+1]); forward visits the classes 0, 1, ...,
+ * backward the reverse.  The residuals of a class are all taken before any
+ * of its rows changes (Jacobi-wise inside a class), into tmp (n_rows x k,
+ * indexed by the position in rows). */
+static void gs_sweep(const oc_bsr *A, const double *Minv, int n_cls, const int32_t *ptr,
+                     const int32_t *rows, const double *b, double *x, double *tmp, int forward) {
+  const int k = A->br;
+  for (int s = 0; s < n_cls; ++s) {
+    const int c = forward ? s : n_cls - 1 - s;
+#pragma omp parallel for schedule(static)
+    for (int q = ptr[c]; q < ptr[c + 1]; ++q) {
+      const int i = rows[q];
+      double *res = tmp + (size_t)q * k;
+      for (int r = 0; r < k; ++r) res[r] = b[(size_t)i * k + r];
+      for (int64_t p = A->rp[i]; p < A->rp[i + 1]; ++p) {
+        const double *B = A->v + (size_t)p * k * k;
+        const double *xj = x + (size_t)A->ci[p] * k;
+        for (int r = 0; r < k; ++r)
+          for (int cc = 0; cc < k; ++cc) res[r] -= B[r * k + cc] * xj[cc];
+      }
+    }
+#pragma omp parallel for schedule(static)
+    for (int q = ptr[c]; q < ptr[c + 1]; ++q) {
+      const int i = rows[q];
+      const double *Mi = Minv + (size_t)i * k * k;
+      const double *res = tmp + (size_t)q * k;
+      for (int r = 0; r < k; ++r) {
+        double u = 0.0;
+        for (int cc = 0; cc < k; ++cc) u += Mi[r * k + cc] * res[cc];
+        x[(size_t)i * k + r] += u;
+      }
+    }
+  }
+}
+
 /* r = b - A x */
 static void residual(const oc_bsr *A, const double *b, const double *x, double *r) {
   const int k = A->br;
@@ -265,6 +308,9 @@ typedef struct {
   int n_levels;
   oc_bsr *A, *P, *R;       /* A[0..L-1], P/R[0..L-2] */
   const double **Minv;     /* per level but the coarsest */
+  const int *n_cls;        /* colour classes per level (NULL: block-l1 Jacobi) */
+  const int32_t *const *cls_ptr, *const *cls_rows; /* class c of level l: rows
+                              cls_rows[l][cls_ptr[l][c] .. cls_ptr[l][c+1]) */
   int nc;                  /* coarsest size (scalar) */
   const double *Lc;        /* coarsest Cholesky factor */
   double **b, **x, **t, **e; /* work vectors per level */
@@ -278,6 +324,18 @@ static void vcycle(const oc_hier *H, int l, const double *b, double *y) {
   const oc_bsr *A = &H->A[l];
   const size_t n = (size_t)A->n_rows * A->br;
   double *x = H->x[l], *t = H->t[l];
+  if (H->n_cls) {                                     /* hybrid Gauss-Seidel */
+    const int nc = H->n_cls[l];
+    memset(x, 0, n * sizeof(double));
+    gs_sweep(A, H->Minv[l], nc, H->cls_ptr[l], H->cls_rows[l], b, x, t, 1);
+    residual(A, b, x, t);
+    bsr_apply(&H->R[l], t, H->b[l + 1], 0);
+    vcycle(H, l + 1, H->b[l + 1], H->e[l + 1]);
+    bsr_apply(&H->P[l], H->e[l + 1], x, 1);
+    gs_sweep(A, H->Minv[l], nc, H->cls_ptr[l], H->cls_rows[l], b, x, t, 0);
+    memcpy(y, x, n * sizeof(double));
+    return;
+  }
   smooth(A, H->Minv[l], b, NULL, x);                  /* pre-smoothing from 0 */
   residual(A, b, x, t);                               /* t = b - A x */
   bsr_apply(&H->R[l], t, H->b[l + 1], 0);             /* restriction */
@@ -294,13 +352,16 @@ static double dot(size_t n, const double *a, const double *b) {
   return s;
 }
 
-/* Arrays of level l are passed flattened: Arp[l], Aci[l], Av[l] etc.  Returns
- * the iteration count (or -1 on allocation failure); hist receives the
- * relative residual after every iteration (maxit + 1 entries). */
+/* Arrays of level l are passed flattened: Arp[l], Aci[l], Av[l] etc.;
+ * n_cls NULL selects block-l1 Jacobi, else n_cls[l] colour classes with
+ * cls_ptr[l] / cls_rows[l] select hybrid Gauss-Seidel (Minv then holds its
+ * blocks).  Returns the iteration count (or -1 on allocation failure); hist
+ * receives the relative residual after every iteration (maxit + 1 entries). */
 int oc_pcg(int n_levels, const int *nrows, const int *k, const int64_t *const *Arp,
            const int32_t *const *Aci, const double *const *Av, const int64_t *const *Prp,
            const int32_t *const *Pci, const double *const *Pv, const int64_t *const *Rrp,
            const int32_t *const *Rci, const double *const *Rv, const double *const *Minv,
+           const int *n_cls, const int32_t *const *cls_ptr, const int32_t *const *cls_rows,
            const double *Lc, const double *f, double *x, double rtol, int maxit, double *hist) {
   oc_hier H;
   H.n_levels = n_levels;
@@ -329,6 +390,9 @@ int oc_pcg(int n_levels, const int *nrows, const int *k, const int64_t *const *A
   }
   H.nc = nrows[n_levels - 1] * k[n_levels - 1];
   H.Lc = Lc;
+  H.n_cls = n_cls;
+  H.cls_ptr = cls_ptr;
+  H.cls_rows = cls_rows;
   const size_t n = (size_t)nrows[0] * k[0];
   double *r = (double *)malloc((n + 1) * sizeof(double));
   double *z = (double *)malloc((n + 1) * sizeof(double));
@@ -388,6 +452,7 @@ int oc_vcycle(int n_levels, const int *nrows, const int *k, const int64_t *const
               const int32_t *const *Aci, const double *const *Av, const int64_t *const *Prp,
               const int32_t *const *Pci, const double *const *Pv, const int64_t *const *Rrp,
               const int32_t *const *Rci, const double *const *Rv, const double *const *Minv,
+              const int *n_cls, const int32_t *const *cls_ptr, const int32_t *const *cls_rows,
               const double *Lc, const double *r, double *z) {
   oc_hier H;
   H.n_levels = n_levels;
@@ -420,6 +485,9 @@ int oc_vcycle(int n_levels, const int *nrows, const int *k, const int64_t *const
   }
   H.nc = nrows[n_levels - 1] * k[n_levels - 1];
   H.Lc = Lc;
+  H.n_cls = n_cls;
+  H.cls_ptr = cls_ptr;
+  H.cls_rows = cls_rows;
   if (ok) vcycle(&H, 0, r, z);
   for (int l = 0; l < n_levels; ++l) {
     free(bb[l]);

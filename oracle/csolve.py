@@ -5,11 +5,12 @@ TEST INFRASTRUCTURE ONLY (see ``oracle/__init__``).
 
 It computes what ``oracle/solve.py`` computes -- Galerkin products A_{l+1} =
 P_l^T A_l P_l with the structural block pattern (Sec. 3, Sec. 6), the V-cycle
-of Algorithm tg with the block-l1 Jacobi smoother of Sec. 7 and the
-regularised coarsest solve of Sec. 3 after Lemma eet_is_diag, and the PCG of
-Sec. 7 -- with the products written out as C loops, so that the CPU baseline
-can use every host core.  The smoother blocks, the explicit transposes and
-the coarsest Cholesky factor come from ``oracle/solve.py`` itself.  Pinned
+of Algorithm tg with the block-l1 Jacobi or the block-l1 hybrid Gauss-Seidel
+smoother of Sec. 7 and the regularised coarsest solve of Sec. 3 after Lemma
+eet_is_diag, and the PCG of Sec. 7 -- with the products written out as C
+loops, so that the CPU baseline can use every host core.  The smoother
+blocks, the colour classes, the explicit transposes and the coarsest
+Cholesky factor come from ``oracle/solve.py`` itself.  Pinned
 against ``oracle/solve.py`` (which is pinned against the paper) and by its
 own closed-form checks in ``tests/test_oracle_csolve.py``.
 """
@@ -100,16 +101,27 @@ def galerkin(P: solve.Mat, A: solve.Mat, R: solve.Mat = None) -> solve.Mat:
 
 class Hierarchy:
     """The solve-phase data of one hierarchy {A_0, P_l}: coarse matrices by
-    the C Galerkin product, R_l = P_l^T, block-l1 smoother blocks and the
-    coarsest factor by oracle/solve.py."""
+    the C Galerkin product, R_l = P_l^T, the smoother's blocks (and for
+    smoother="hybrid_gs" its colour classes, solve.greedy_colouring) and the
+    coarsest factor by oracle/solve.py.  smoother: "l1_jacobi" or
+    "hybrid_gs", as solve.prepare."""
 
-    def __init__(self, A0: solve.Mat, P):
+    def __init__(self, A0: solve.Mat, P, smoother: str = "l1_jacobi"):
+        if smoother not in ("l1_jacobi", "hybrid_gs"):
+            raise ValueError(f"unknown smoother {smoother!r}")
+        self.smoother = smoother
         self.P = list(P)
         self.R = [solve.transpose(Pl) for Pl in self.P]
         self.A = [A0]
         for Pl, Rl in zip(self.P, self.R):
             self.A.append(galerkin(Pl, self.A[-1], Rl))
-        self.Minv = [np.ascontiguousarray(solve.block_l1_inverse(Al)) for Al in self.A[:-1]]
+        if smoother == "hybrid_gs":
+            self.colour = [solve.greedy_colouring(Al) for Al in self.A[:-1]]
+            self.Minv = [np.ascontiguousarray(solve.hybrid_gs_inverse(Al, c))
+                         for Al, c in zip(self.A[:-1], self.colour)]
+        else:
+            self.colour = []
+            self.Minv = [np.ascontiguousarray(solve.block_l1_inverse(Al)) for Al in self.A[:-1]]
         self.Lc = np.ascontiguousarray(np.linalg.cholesky(solve.coarsest_matrix(self.A[-1])))
         self._pack()
 
@@ -132,12 +144,27 @@ class Hierarchy:
         Mb = self.Minv + [np.zeros(1)]
         self._keep += [Ab, Pb, Rb, Mb]
         VP = C.c_void_p
+        if self.colour:
+            # class c of a level: its rows in ascending order (the order
+            # inside a class does not matter: Jacobi-wise there)
+            cls = []
+            for col in self.colour:
+                nc = int(col.max()) + 1 if col.size else 0
+                ptr = np.zeros(nc + 1, dtype=np.int32)
+                np.cumsum(np.bincount(col, minlength=nc), out=ptr[1:])
+                cls.append((nc, ptr, np.ascontiguousarray(np.argsort(col, kind="stable"), dtype=np.int32)))
+            cls.append((0, np.zeros(1, np.int32), np.zeros(1, np.int32)))
+            self._keep.append(cls)
+            gs = (arr(C.c_int, [c[0] for c in cls]), arr(VP, [_p(c[1]) for c in cls]),
+                  arr(VP, [_p(c[2]) for c in cls]))
+        else:
+            gs = (None, None, None)
         self._args = (
             L, arr(C.c_int, [A.n_rows for A in self.A]), arr(C.c_int, [A.br for A in self.A]),
             arr(VP, [_p(a[0]) for a in Ab]), arr(VP, [_p(a[1]) for a in Ab]), arr(VP, [_p(a[2]) for a in Ab]),
             arr(VP, [_p(a[0]) for a in Pb]), arr(VP, [_p(a[1]) for a in Pb]), arr(VP, [_p(a[2]) for a in Pb]),
             arr(VP, [_p(a[0]) for a in Rb]), arr(VP, [_p(a[1]) for a in Rb]), arr(VP, [_p(a[2]) for a in Rb]),
-            arr(VP, [_p(m) for m in Mb]), _p(self.Lc))
+            arr(VP, [_p(m) for m in Mb]), *gs, _p(self.Lc))
 
     def vcycle(self, r):
         r = np.ascontiguousarray(r, dtype=np.float64)

@@ -189,23 +189,28 @@ def test_clock_sampler_parses_nvidia_smi_lines():
     assert s.stop() is None
 
 
-def test_reference_arm_oracle_timing_on_cpu():
-    """The reference arm's CPU pieces: the oracle hierarchy rebuilt from
-    downloaded prolongations (here the oracle's own) and the bounded
-    oracle PCG timing, scaled to the full iteration count."""
+def test_batch_oracle_uses_its_own_iteration_counts():
+    """The batched CPU legs (cpu_baseline and the reference arm): the C
+    oracle rebuilt from downloaded prolongations (here the oracle's own)
+    solves every load case to rtol with the numpy oracle's iteration counts
+    (never the GPU's), and the bounded sample scales per dof-iteration to
+    every load case at those counts."""
     from oracle import hierarchy, solve
-    from workloads import configs
-    p = configs.square32()
-    H = hierarchy.setup(p)
-    P_list = [(P.n_rows, P.n_cols, P.rowptr.astype(np.int32), P.colidx.astype(np.int32), P.vals)
-              for P in H.P]
-    H2 = bench.oracle_hierarchy(p, P_list)
-    assert H2.n_levels == H.n_levels
-    _, its, _ = solve.pcg(H2, p.b[0], rtol=1e-8)
-    _, its_o, _ = solve.pcg(H, p.b[0], rtol=1e-8)
-    assert its == its_o
-    ms, m, dt = bench.time_oracle(H2, p.b[0], its, budget_s=0.2)
-    assert ms > 0 and 1 <= m <= its and dt > 0
+    from workloads import configs, make_problem
+    probs = [make_problem(shape, seed=seed, h=1.0 / 32, forces=configs.SIX_LOADS)
+             for shape, seed in (((6, 5, 5), 2), ((5, 6, 7), 3))]
+    P_lists, want = [], []
+    for p in probs:
+        H = hierarchy.setup(p, hierarchy.SetupParams(coarse_max=4))
+        P_lists.append([(P.n_rows, P.n_cols, P.rowptr.astype(np.int32), P.colidx.astype(np.int32),
+                         P.vals) for P in H.P])
+        want += [solve.pcg(H, p.b[j], rtol=1e-8)[1] for j in range(p.b.shape[0])]
+    ob = bench.OracleBatch(probs, P_lists, 1e-8)
+    ms, its = ob.solve_all()
+    assert ms > 0 and len(its) == 6 * len(probs)
+    assert all(abs(a - b) <= 1 for a, b in zip(its, want)), (its, want)
+    v, sample = ob.sample(budget_s=0.05)
+    assert v > 0 and "own iteration counts" in sample
 
 
 def test_oracle_leg_on_cpu():
@@ -227,3 +232,25 @@ def test_oracle_leg_on_cpu():
     assert cpu["value"] > 0 and cpu["single_thread"]["cores"] == 1
     assert acc["energy_error"] <= 1e-6 and acc["variants"]["same"] == acc["energy_error"]
     assert acc["oracle_1e8"] <= 1e-6
+
+
+def test_oracle_leg_follows_the_gauss_seidel_smoother():
+    """With --smoother gs the CPU legs run the oracle with the hybrid
+    Gauss-Seidel smoother: the numpy oracle's GS iteration count, not the
+    block-l1 Jacobi one."""
+    import types
+    from oracle import hierarchy, solve
+    from workloads import make_problem
+    p = make_problem((9, 7, 8), seed=3, jump_boxes=6, nu_range=(0.25, 0.45))
+    H = hierarchy.setup(p, hierarchy.SetupParams(coarse_max=6))
+    P_list = [(P.n_rows, P.n_cols, P.rowptr.astype(np.int32), P.colidx.astype(np.int32), P.vals)
+              for P in H.P]
+    Hg = solve.prepare(H.A[0], H.P, smoother="hybrid_gs")
+    u, it_gs, _ = solve.pcg(Hg, p.b[0], rtol=1e-8)
+    it_j = solve.pcg(H, p.b[0], rtol=1e-8)[1]
+    assert it_gs != it_j
+    args = types.SimpleNamespace(rtol=1e-8, smoother="gs")
+    cpu, _ = bench.oracle_leg(p, P_list, None, args, u, {}, it_gs, skip_accuracy=True,
+                              single_budget_s=0.05)
+    assert abs(cpu["iters"] - it_gs) <= 1 and "hybrid_gs" in cpu["sample"]
+    assert bench.oracle_smoother(types.SimpleNamespace(smoother="l1")) == "l1_jacobi"

@@ -1,8 +1,9 @@
 """The C solve phase of the oracle (oracle/csolve.c) against oracle/solve.py
-(itself pinned against the paper by tests/test_oracle_solve.py) and against
-facts of its own: the Galerkin product equals the dense P^T A P, the V-cycle
-is symmetric positive definite, PCG recovers a manufactured solution, and
-the results do not depend on the number of threads."""
+(itself pinned against the paper by tests/test_oracle_solve.py and
+tests/test_oracle_gs.py) and against facts of its own: the Galerkin product
+equals the dense P^T A P, the V-cycle (block-l1 Jacobi and hybrid
+Gauss-Seidel) is symmetric positive definite, PCG recovers a manufactured
+solution, and the results do not depend on the number of threads."""
 import numpy as np
 import pytest
 
@@ -123,3 +124,71 @@ def test_pcg_zero_rhs_stops_at_once():
     p, H, Hc = _case("square32")
     u, it, hist = Hc.pcg(np.zeros_like(p.b[0]), rtol=1e-8)
     assert it == 0 and not u.any() and hist == [0.0]
+
+
+_GS = {}
+
+
+def _gs_case(name):
+    """The same hierarchy with the block-l1 hybrid Gauss-Seidel smoother, in
+    oracle/solve.py and in the C solve phase."""
+    if name not in _GS:
+        p, H, _ = _case(name)
+        _GS[name] = (p, solve.prepare(H.A[0], H.P, smoother="hybrid_gs"),
+                     csolve.Hierarchy(H.A[0], H.P, smoother="hybrid_gs"))
+    return _GS[name]
+
+
+@pytest.mark.parametrize("name", sorted(CASES))
+def test_gs_vcycle_matches_numpy_oracle(name):
+    p, Hg, Hc = _gs_case(name)
+    for l, c in enumerate(Hg.colour):
+        np.testing.assert_array_equal(Hc.colour[l], c)
+    n = Hg.A[0].n_rows * Hg.A[0].br
+    for r in (p.b[0], np.random.default_rng(8).normal(size=n)):
+        assert maxrel(Hc.vcycle(r), solve.vcycle(Hg, r)) <= 1e-11
+
+
+def test_gs_vcycle_differs_from_jacobi_and_is_symmetric_positive():
+    """The forward / backward sweeps make a symmetric V-cycle (the backward
+    sweep is the adjoint of the forward one); it is not the Jacobi V-cycle."""
+    p, Hg, Hc = _gs_case("cube10")
+    _, _, Hj = _case("cube10")
+    rng = np.random.default_rng(9)
+    n = Hg.A[0].n_rows * Hg.A[0].br
+    x, y = rng.normal(size=(2, n))
+    bx, by = Hc.vcycle(x), Hc.vcycle(y)
+    assert abs(y @ bx - x @ by) <= 1e-12 * abs(x @ bx)
+    assert x @ bx > 0 and y @ by > 0
+    assert maxrel(bx, Hj.vcycle(x)) > 1e-3
+
+
+@pytest.mark.parametrize("name", sorted(CASES))
+def test_gs_pcg_matches_numpy_oracle(name):
+    p, Hg, Hc = _gs_case(name)
+    f = p.b[0]
+    u, it, hist = Hc.pcg(f, rtol=1e-8)
+    u_np, it_np, _ = solve.pcg(Hg, f, rtol=1e-8)
+    assert abs(it - it_np) <= 1 and hist[-1] <= 1e-8
+    u_k = u_np if it == it_np else solve.pcg(Hg, f, rtol=0.0, maxit=it)[0]
+    assert maxrel(u, u_k) <= 1e-10
+
+
+def test_gs_results_do_not_depend_on_threads():
+    p, Hg, Hc = _gs_case("box_jump")
+    f = p.b[0]
+    outs = []
+    try:
+        for t in (1, 4):
+            csolve.set_threads(t)
+            outs.append(Hc.pcg(f, rtol=1e-8)[:2])
+    finally:
+        csolve.set_threads(csolve.max_threads())
+    (u1, i1), (u4, i4) = outs
+    assert i1 == i4 and maxrel(u4, u1) <= 1e-12
+
+
+def test_unknown_smoother_rejected():
+    p, H, _ = _case("square32")
+    with pytest.raises(ValueError):
+        csolve.Hierarchy(H.A[0], H.P, smoother="gs")
