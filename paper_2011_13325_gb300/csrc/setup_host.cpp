@@ -841,13 +841,14 @@ static Coarsening successive_matching(const Topo &T0, const SetupParams &prm, in
       double mu;
       int rank, cj;
     };
-    // candidates of ci among the unmatched neighbours with mu_s < sigma,
-    // ordered by mu_s, ties by the iteration order (Def. muc, Algorithm 1)
-    auto candidates = [&](int ci, std::vector<Cand> &cands) {
+    // candidates of ci among the unmatched neighbours (live[] != 0) with
+    // mu_s < sigma, ordered by mu_s, ties by the iteration order (Def. muc,
+    // Algorithm 1)
+    auto candidates = [&](int ci, const std::vector<char> &live, std::vector<Cand> &cands) {
       cands.clear();
       for (int p = Tc->adj_ptr[ci]; p < Tc->adj_ptr[ci + 1]; ++p) {
         const int cj = Tc->adj_nbr[p];
-        if (!inT[cj]) continue;
+        if (!live[cj]) continue;
         const double tr = trace(k, Tc->E.data() + (size_t)Tc->adj_edge[p] * k * k);
         if (!(tr > 0.0)) continue;
         const double ms = sqrt(tmax[ci] * tmax[cj]) / tr;
@@ -869,15 +870,18 @@ static Coarsening successive_matching(const Topo &T0, const SetupParams &prm, in
       }
     };
     // The greedy loop below decides pairs in iteration order; the measures
-    // it consults are evaluated ahead of it, in parallel: for every vertex of
-    // a chunk its first two live candidates (the first one usually
-    // succeeds), and where the loop needs a pair not evaluated yet, that
-    // pair together with the vertex's next live candidates.  The decisions
-    // are those of evaluating each pair when the loop reaches it.
+    // it consults are evaluated ahead of it, in parallel batches.  A dry run
+    // of the loop over the rest of a chunk predicts its walk: a pair already
+    // evaluated decides as in the loop, a pair not evaluated yet is taken to
+    // succeed (the first live candidate usually does) and goes into the
+    // batch.  One dry run starts each chunk; wherever the loop meets a pair
+    // not evaluated yet (its walk left the prediction there), a new dry run
+    // starts at that point.  The decisions are those of evaluating each
+    // pair when the loop reaches it.
     // a device evaluator wants large batches (one thread per pair: a batch
     // of a 2,048-vertex chunk occupies a fraction of the device); the chunk
     // only decides how far the look-ahead reaches, not the decisions
-    const int chunk = dev_pm ? 32768 : 2048, ahead = 2, refill = 8;
+    const int chunk = dev_pm ? 32768 : 2048, ahead = 1;
     std::vector<Cand> cands;
     struct Eval {
       double mu;
@@ -912,28 +916,58 @@ static Coarsening successive_matching(const Topo &T0, const SetupParams &prm, in
       for (size_t q = 0; q < tasks.size(); ++q) done[(long long)tasks[q][0] * m + tasks[q][1]] = res[q];
       tasks.clear();
     };
+    // live: inT as the dry run sees it (equal to inT between chunks)
+    std::vector<char> live(inT);
+    std::vector<int> touched;
+    // dry run of the loop from position q0 of a chunk to its end c1 (with
+    // first_taken, order[q0] has been taken out by the loop already): every
+    // pair it meets that is not evaluated yet goes into tasks
+    std::vector<Cand> dcands;
+    auto dry_run = [&](size_t q0, size_t c1, bool first_taken) {
+      for (size_t q = q0; q < c1; ++q) {
+        const int ci = order[q];
+        if (!(first_taken && q == q0)) {
+          if (!live[ci]) continue;
+          live[ci] = 0;
+          touched.push_back(ci);
+        }
+        candidates(ci, live, dcands);
+        for (size_t u = 0; u < dcands.size(); ++u) {
+          const int cj = dcands[u].cj;
+          auto it = done.find((long long)ci * m + cj);
+          if (it == done.end()) {  // not evaluated yet: evaluate, take it to succeed
+            for (size_t w = u; w < dcands.size() && w < u + (size_t)ahead; ++w)
+              if (!done.count((long long)ci * m + dcands[w].cj)) tasks.push_back({ci, dcands[w].cj});
+          } else if (!(it->second.mu < sigma && it->second.gok)) {
+            continue;
+          }
+          live[cj] = 0;
+          touched.push_back(cj);
+          break;
+        }
+      }
+      for (int v : touched) live[v] = 1;
+      touched.clear();
+    };
     for (size_t c0 = 0; c0 < order.size(); c0 += chunk) {
       const size_t c1 = std::min(order.size(), c0 + chunk);
       done.clear();
-      for (size_t q = c0; q < c1 && !prm.scalar_only; ++q) {
-        const int ci = order[q];
-        if (!inT[ci]) continue;
-        candidates(ci, cands);
-        for (size_t u = 0; u < cands.size() && u < (size_t)ahead; ++u) tasks.push_back({ci, cands[u].cj});
+      if (!prm.scalar_only) {
+        dry_run(c0, c1, false);
+        run_tasks();
       }
-      run_tasks();
       for (size_t q = c0; q < c1; ++q) {
         const int ci = order[q];
         if (!inT[ci]) continue;
-        inT[ci] = 0;
-        candidates(ci, cands);
+        inT[ci] = live[ci] = 0;
+        candidates(ci, inT, cands);
         bool matched = false;
         if (prm.scalar_only) {
           // mu_s alone: the candidate of minimal mu_s is taken (Sec. 5's
           // comparison and the paper's scalar runs)
           if (!cands.empty()) {
             groups.push_back({ci, cands[0].cj});
-            inT[cands[0].cj] = 0;
+            inT[cands[0].cj] = live[cands[0].cj] = 0;
           } else {
             singles.push_back(ci);
           }
@@ -943,16 +977,23 @@ static Coarsening successive_matching(const Topo &T0, const SetupParams &prm, in
           const int cj = cands[u].cj;
           auto it = done.find((long long)ci * m + cj);
           if (it == done.end()) {
-            for (size_t w = u; w < cands.size() && tasks.size() < (size_t)refill; ++w)
-              if (!done.count((long long)ci * m + cands[w].cj)) tasks.push_back({ci, cands[w].cj});
+            // the walk left the last prediction here: predict the rest of
+            // the chunk from this point (it starts with this pair)
+            dry_run(q, c1, true);
+            if (tasks.empty()) tasks.push_back({ci, cj});
             run_tasks();
             it = done.find((long long)ci * m + cj);
+            if (it == done.end()) {
+              tasks.push_back({ci, cj});
+              run_tasks();
+              it = done.find((long long)ci * m + cj);
+            }
           }
           const double mu = it->second.mu;
           const int gok = it->second.gok;
           if (mu < sigma && gok) {
             groups.push_back({ci, cj});
-            inT[cj] = 0;
+            inT[cj] = live[cj] = 0;
             matched = true;
             break;
           }
