@@ -254,3 +254,46 @@ def test_oracle_leg_follows_the_gauss_seidel_smoother():
                               single_budget_s=0.05)
     assert abs(cpu["iters"] - it_gs) <= 1 and "hybrid_gs" in cpu["sample"]
     assert bench.oracle_smoother(types.SimpleNamespace(smoother="l1")) == "l1_jacobi"
+
+
+@pytest.mark.parametrize("smoother", ["l1", "gs"])
+def test_reference_arm_line_on_cpu(monkeypatch, capsys, smoother):
+    """bench.py --impl reference on the 2D workload, with the library's
+    setup replaced by a stand-in that hands over the oracle's prolongations
+    (the setup needs a GPU): one JSON line with the contract's keys, the
+    oracle's smoother named, the value equal to cpu_baseline and e2e."""
+    import json
+    import types
+    from oracle import hierarchy
+    from paper_2011_13325_gb300 import amg
+
+    class FakeContext:
+        def __init__(self, device):
+            self.P = None
+
+        def setup(self, problem, prec, **kw):
+            H = hierarchy.setup(problem, hierarchy.SetupParams(
+                coarse_max=kw.get("coarse_max", 0) or hierarchy.SetupParams().coarse_max))
+            self.P = H.P
+            self.n_levels = H.n_levels
+
+        def download_prolongation(self, l):
+            P = self.P[l]
+            return (P.n_rows, P.n_cols, P.rowptr.astype(np.int32), P.colidx.astype(np.int32), P.vals)
+
+        def close(self):
+            pass
+
+    monkeypatch.setattr(amg, "Context", FakeContext)
+    args = types.SimpleNamespace(workload="square32", steps=2, warmup=3, rtol=1e-8, smoother=smoother)
+    bench.run_reference(args, 1, 0, 0)
+    line = json.loads(capsys.readouterr().out.strip().splitlines()[-1])
+    for key in ("impl", "metric", "value", "unit", "n_gpus", "steps", "warmup", "ms_per_step",
+                "higher_is_better", "config", "cpu_baseline", "e2e"):
+        assert key in line, key
+    assert line["impl"] == "reference" and line["value"] > 0 and line["higher_is_better"] is False
+    assert line["cpu_baseline"]["kind"] == "oracle" and line["cpu_baseline"]["value"] == line["value"]
+    assert line["e2e"]["value"] == line["value"] and line["e2e"]["h2d_bytes_per_step"] == 0
+    want = {"l1": "block-l1 Jacobi", "gs": "block-l1 hybrid Gauss-Seidel (colour classes)"}[smoother]
+    assert line["config"]["workload"] == "square32" and line["config"]["smoother"] == want
+    assert ("hybrid_gs" in line["cpu_baseline"]["sample"]) == (smoother == "gs")
